@@ -1,0 +1,1040 @@
+/*
+ * lbrmhd_oracle.c -- TEST INFRASTRUCTURE, not part of the product.
+ *
+ * A plain, slow, obviously-correct FP64 CPU restatement of the lattice
+ * Boltzmann model for resistive relativistic MHD of Mohseni, Mendoza, Succi and
+ * Herrmann (arXiv:1508.03452). It exists so that the CUDA library can be
+ * checked against something written straight from the paper. Only the tests,
+ * __graft_entry__.smoke() and bench.py's CPU-baseline / reference legs may load
+ * it. The product library never links, loads or calls it, and it shares no
+ * code, header or table with the CUDA path.
+ *
+ * Every function names the section / equation of the paper it follows. The
+ * per-step order is the one of the "Coupling between fluid and electromagnetic
+ * fields" subsection of Sec. III:
+ *   fluid f (Eq. eq:rlb), number density g (Eq. Hupp), Maxwell h (Eq.
+ *   LB_Maxwell), moments, Landau eigenproblem (power method), n from N^mu,
+ *   B (Eq. Cal_B), E from Eq. Ex_force with Ohm's law (Eq. Ohm), J, EOS
+ *   (Eq. EOS), rho_c (Eq. Cal_rhoc); then boundaries and driving.
+ *
+ * Readings taken where the paper is silent, garbled or ambiguous (each repeated
+ * at its point of use):
+ *   R1  delta_{i0} EOS term of Eq. Dis_fun_EM: (361/33)(3p - eps)/(eps + p).
+ *   R2  sign of the (nu^2/5)[c^2(B.c_a)^2 + (E.c_a)^2] term: minus.
+ *   R3  "c_a^y c_a^y E^z E^z" read as c_a^y c_a^z E^y E^z (and the same for B).
+ *   R4  Poynting term carries c: -(nu c / sqrt 3)(B x E).c_a.
+ *   R5  moments T^{mu nu} = sum p^mu p^nu f, N^mu = sum p^mu g with
+ *       p_i^mu = (c_t/c_0, c_a chat_i), in components with x^0 = c t.
+ *   R6  Anderson-Witting factor of Eq. eq:rlb = (dt/tau) gamma (1 - v_i.u/c^2),
+ *       v_i = c sqrt(19/27) chat_i; nu cancels. tau is in units of dt.
+ *   R7  the collision term of Eq. eq:rlb is evaluated at time t:
+ *       -K_i [f_i(x,t) - f_i^eq(x,t)]. As printed (f(t+dt) against f^eq(t)) the
+ *       update conserves T^{mu nu} only up to a factor 1/(1+K): every wave then
+ *       runs 1/(1+K) too slow (half speed at tau = 1), which contradicts the
+ *       paper's own Alfven and current-sheet results. The printed form stays
+ *       available as the ORC_IMPLICIT_AS_PRINTED test switch.
+ *   R8  g collision (Eq. eq:rlb with the AW factor replaced by unity):
+ *       plain BGK with rate dt/tau.
+ *   R9  Eq. Hupp velocities are u/c.
+ *   R10 streaming flux h_i^a (defined only in a cited 2013 paper): MUSCL /
+ *       Sweby flux-limited upwind face values with the minmod limiter,
+ *       dimensionally unsplit. Parity with the 2013 flux: UNPINNED.
+ *   R11 bulk-viscosity term: alpha (c dt/dx) sum_a [f(x+e_a) - 2 f + f(x-e_a)],
+ *       i != 0. Coefficient: parity UNPINNED.
+ *   R12 one rest EM population h_0 (25 EM populations per cell).
+ *   R13 both the subtraction before the eigen-solve and the eigenvalue shift use
+ *       E, B of the previous step; "F^{mu rho} F^nu_rho" is the first term of
+ *       T_EM with the index placement that gives T^00_EM = eps0 (E^2+c^2B^2)/2.
+ *   R14 power method to ||dU||/||U|| <= 1e-14, seeded with the previous U.
+ *   R15 n = N^0 / U^0.
+ *   R16 the 3x3 Ohm system is solved in closed form (Sherman-Morrison).
+ *   R17 initial populations are the equilibria of the initial fields.
+ *   R18 initial rho_c = eps0 div E by second-order central differences.
+ *   R19 open boundaries copy every population and the primitive state from the
+ *       first interior cell (faces in order -x,+x,-y,+y,-z,+z).
+ *   R20 normal-B fix on open faces: B_n of the boundary cell is set so that the
+ *       central-difference div B of the first interior cell is zero; the change
+ *       is carried by the h populations whose b is parallel to the normal.
+ *       Parity: UNPINNED against the paper (which does not give the mechanism).
+ *   R21 driving: the lowest drive_layers z-layers are reset every step to the
+ *       equilibrium of their own n, eps, B, rho_c with u given by the paper's
+ *       two-vortex pattern scaled to max |u| = drive_u0, E = -u x B.
+ *       Parity: UNPINNED (the paper's forcing scheme is not stated).
+ *   R22 nu (the temperature parameter, not given in the paper) only changes the
+ *       number-density lattice weights w'_i; nu = sqrt(27), i.e. c_t = c_0.
+ *
+ * Units: mu_0 = 1, eps_0 = 1/(mu_0 c^2); dt = dx / (sqrt(2) c) (Sec. III,
+ * time-step synchronisation).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#include "lbrmhd_oracle.h"
+
+/* ------------------------------------------------------------------------- */
+/* Lattices                                                                   */
+/* ------------------------------------------------------------------------- */
+
+/* D3Q19 unit directions chat_i (Eq. cellconfigs1): rest, 6 axis, 12 face
+ * diagonals. The order is the interface order of the library as well. */
+static const int CHAT[19][3] = {
+    {0, 0, 0},
+    {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0}, {0, 0, 1},  {0, 0, -1},
+    {1, 1, 0},  {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0},
+    {1, 0, 1},  {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+    {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1},
+};
+
+/* The two in-plane axes of D3Q13 plane p (Sec. III, Maxwell equations):
+ * p = 0 -> (x, y), p = 1 -> (x, z), p = 2 -> (y, z). */
+static const int PLANE_AXES[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+
+void orc_lattice_init(const orc_params* P, orc_lattice* L)
+{
+    const double nu = P->nu;
+    const double c = P->c;
+    memset(L, 0, sizeof(*L));
+    L->nu = nu;
+    /* constants below the weights: c_a = sqrt(19)/nu, c_t/c_0 = sqrt(27)/nu,
+     * c_0 = 3/8 (9 - 2 sqrt 3) */
+    L->ca = sqrt(19.0) / nu;
+    L->ct_c0 = sqrt(27.0) / nu;
+    L->c0 = 3.0 / 8.0 * (9.0 - 2.0 * sqrt(3.0));
+    L->ct = L->ct_c0 * L->c0;
+    const double ct2_c02 = L->ct_c0 * L->ct_c0;
+    const double ca2 = L->ca * L->ca;
+
+    for (int i = 0; i < 19; ++i) {
+        int nnz = abs(CHAT[i][0]) + abs(CHAT[i][1]) + abs(CHAT[i][2]);
+        /* weights w_i of the D3Q19 quadrature */
+        if (nnz == 0)
+            L->w[i] = 1.0 + 4.0 * ct2_c02 * nu * nu / 361.0 - ct2_c02 / ca2;
+        else if (nnz == 1)
+            L->w[i] = ct2_c02 / (2166.0 * ca2) * (361.0 - 8.0 * ca2 * nu * nu);
+        else
+            L->w[i] = ct2_c02 * nu * nu / 1083.0;
+        /* weights w'_i of Eq. Hupp */
+        if (nnz == 0)
+            L->wg[i] = 1.0 / 10.0;
+        else if (nnz == 1)
+            L->wg[i] = 3.0 / 10.0 - 1.0 / (6.0 * ca2);
+        else
+            L->wg[i] = 1.0 / (12.0 * ca2) - 3.0 / 40.0;
+        /* R5: p_i^mu = xi_i^mu = (c_t/c_0, c_a chat_i) */
+        L->p[i][0] = L->ct_c0;
+        for (int a = 0; a < 3; ++a) L->p[i][a + 1] = L->ca * CHAT[i][a];
+        for (int a = 0; a < 3; ++a) L->chat[i][a] = CHAT[i][a];
+    }
+
+    /* D3Q13: v_i^p = 2c (cos((2i+1)pi/4), sin((2i+1)pi/4)) in plane p,
+     * e_{i0}^p = v_{(i+3) mod 4}^p / 2, e_{i1}^p = v_{(i+1) mod 4}^p / 2,
+     * b_{ij}^p = v_i^p x e_{ij}^p / (2 c^2). Index k = 8 p + 2 i + j. */
+    const double dt = orc_dt(P);
+    for (int p = 0; p < 3; ++p) {
+        double vp[4][3];
+        for (int i = 0; i < 4; ++i) {
+            double th = (2 * i + 1) * M_PI / 4.0;
+            vp[i][0] = vp[i][1] = vp[i][2] = 0.0;
+            vp[i][PLANE_AXES[p][0]] = 2.0 * c * cos(th);
+            vp[i][PLANE_AXES[p][1]] = 2.0 * c * sin(th);
+        }
+        for (int i = 0; i < 4; ++i) {
+            for (int j = 0; j < 2; ++j) {
+                int k = 8 * p + 2 * i + j;
+                int src = (j == 0) ? (i + 3) % 4 : (i + 1) % 4;
+                for (int a = 0; a < 3; ++a) {
+                    L->v[k][a] = vp[i][a];
+                    L->e[k][a] = 0.5 * vp[src][a];
+                }
+                const double* v = L->v[k];
+                const double* e = L->e[k];
+                L->b[k][0] = (v[1] * e[2] - v[2] * e[1]) / (2.0 * c * c);
+                L->b[k][1] = (v[2] * e[0] - v[0] * e[2]) / (2.0 * c * c);
+                L->b[k][2] = (v[0] * e[1] - v[1] * e[0]) / (2.0 * c * c);
+                /* with dx/dt = sqrt(2) c every v_i^p dt is one face-diagonal hop */
+                for (int a = 0; a < 3; ++a)
+                    L->hop[k][a] = (int)lround(L->v[k][a] * dt / P->dx);
+            }
+        }
+    }
+}
+
+double orc_dt(const orc_params* P)
+{
+    /* Sec. III: dx/dt = sqrt(2) c */
+    return P->dx / (sqrt(2.0) * P->c);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Small helpers                                                              */
+/* ------------------------------------------------------------------------- */
+
+static double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+static void cross3(const double* a, const double* b, double* out)
+{
+    out[0] = a[1] * b[2] - a[2] * b[1];
+    out[1] = a[2] * b[0] - a[0] * b[2];
+    out[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static double eps0_of(const orc_params* P) { return 1.0 / (P->c * P->c); /* c^2 eps0 mu0 = 1, mu0 = 1 */ }
+
+/* Eq. EOS: p = (Gamma - 1)(eps - n c^2) */
+double orc_eos_pressure(const orc_params* P, double n, double eps)
+{
+    return (P->gamma_ad - 1.0) * (eps - n * P->c * P->c);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Equilibria                                                                 */
+/* ------------------------------------------------------------------------- */
+
+/* Eq. Dis_fun_EM with readings R1-R4. */
+void orc_feq(const orc_params* P, const orc_lattice* L, double n, double eps, const double* u,
+             const double* E, const double* B, double* feq)
+{
+    const double c = P->c, nu = L->nu, c0 = L->c0, ct = L->ct;
+    const double eps0 = eps0_of(P);
+    const double p = orc_eos_pressure(P, n, eps);
+    const double gam = 1.0 / sqrt(1.0 - dot3(u, u) / (c * c));
+    /* chi^mu = U^mu / c_s with U^mu = gamma (c, u) and c_s = c / nu */
+    const double chi0 = gam * nu;
+    const double chi[3] = {gam * u[0] * nu / c, gam * u[1] * nu / c, gam * u[2] * nu / c};
+    const double pref = (c0 * c0) / (ct * ct);
+    /* second and third terms of the first bracket: ideal-gas EOS contribution */
+    const double A = (3.0 * p - eps) / (p + eps);
+    const int printed = (P->flags & ORC_PRINTED_FEQ) != 0; /* test switch: Eq. Dis_fun_EM as printed */
+    /* R1; as printed the term is 361[eps - p] / (33 [p - eps]) */
+    const double D = printed ? 361.0 * (eps - p) / (33.0 * (p - eps)) : (361.0 / 33.0) * (3.0 * p - eps) / (eps + p);
+    double BxE[3];
+    cross3(B, E, BxE);
+    const double B2 = dot3(B, B), E2 = dot3(E, E);
+    for (int i = 0; i < 19; ++i) {
+        const double cav[3] = {L->ca * L->chat[i][0], L->ca * L->chat[i][1], L->ca * L->chat[i][2]};
+        double bra = 1.0 + A + (i == 0 ? D : 0.0);
+        bra += cav[0] * cav[1] * chi[0] * chi[1] + cav[0] * cav[2] * chi[0] * chi[2] +
+               cav[1] * cav[2] * chi[1] * chi[2];
+        bra += (ct * chi0 / (2.0 * c0 * c0) - chi0 / (nu * c0)) * dot3(cav, chi);
+        bra += 4.0 / 15.0 *
+               (cav[0] * cav[0] * chi[0] * chi[0] + cav[1] * cav[1] * chi[1] * chi[1] +
+                cav[2] * cav[2] * chi[2] * chi[2] - 4.0 / (nu * nu) * dot3(chi, chi));
+        const double fluid = 0.75 * (eps + p) * pref * L->w[i] * bra;
+
+        const double Bc = dot3(B, cav), Ec = dot3(E, cav);
+        double em = 1.5 * (c * c * B2 + E2) + 0.8 * (c * c * B2 + E2);
+        em -= nu * c / sqrt(3.0) * dot3(BxE, cav);                      /* R4 */
+        em += (printed ? 1.0 : -1.0) * nu * nu / 5.0 * (c * c * Bc * Bc + Ec * Ec); /* R2 */
+        em -= 7.0 * nu * nu / 20.0 *                                     /* R3 */
+              (cav[0] * cav[1] * E[0] * E[1] + cav[0] * cav[2] * E[0] * E[2] + cav[1] * cav[2] * E[1] * E[2] +
+               c * c * (cav[0] * cav[1] * B[0] * B[1] + cav[0] * cav[2] * B[0] * B[2] +
+                        cav[1] * cav[2] * B[1] * B[2]));
+        feq[i] = fluid + pref * eps0 * L->w[i] * em;
+    }
+}
+
+/* Eq. Hupp with reading R9 (velocities in units of c). */
+void orc_geq(const orc_params* P, const orc_lattice* L, double n, const double* u, double* geq)
+{
+    const double c = P->c;
+    const double beta[3] = {u[0] / c, u[1] / c, u[2] / c};
+    const double gam = 1.0 / sqrt(1.0 - dot3(beta, beta));
+    for (int i = 0; i < 19; ++i) {
+        const double cav[3] = {L->ca * L->chat[i][0], L->ca * L->chat[i][1], L->ca * L->chat[i][2]};
+        const double cu = dot3(cav, beta);
+        geq[i] = L->wg[i] * n * gam * (1.0 / L->ct_c0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * dot3(beta, beta));
+    }
+}
+
+/* Eq. Maxwell-eq for one moving population k = 8 p + 2 i + j. */
+static double heq_moving(const orc_params* P, const orc_lattice* L, int k, const double* E, const double* B,
+                         const double* J)
+{
+    const double c = P->c;
+    return dot3(L->v[k], J) / 16.0 + dot3(E, L->e[k]) / (8.0 * c * c) + dot3(B, L->b[k]) / 8.0;
+}
+
+/* Eq. Maxwell-eq; index 24 is the rest population h_0 (R12), h_0^eq = rho_c. */
+void orc_heq(const orc_params* P, const orc_lattice* L, const double* E, const double* B, const double* J,
+             double rho_c, double* heq)
+{
+    for (int k = 0; k < 24; ++k) heq[k] = heq_moving(P, L, k, E, B, J);
+    heq[24] = rho_c;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Ohm's law and the E solve                                                  */
+/* ------------------------------------------------------------------------- */
+
+/* Eq. Ohm: J = sigma gamma [E + u x B - (E.u) u / c^2] + rho_c u */
+void orc_ohm_current(const orc_params* P, const double* E, const double* u, const double* B, double rho_c,
+                     double* J)
+{
+    const double c = P->c;
+    const double gam = 1.0 / sqrt(1.0 - dot3(u, u) / (c * c));
+    double uxB[3];
+    cross3(u, B, uxB);
+    const double Eu = dot3(E, u);
+    for (int a = 0; a < 3; ++a)
+        J[a] = P->sigma * gam * (E[a] + uxB[a] - Eu * u[a] / (c * c)) + rho_c * u[a];
+}
+
+/* Eq. Ex_force, E = E' - (dt/2) mu0 c^2 J(E), with Eq. Ohm substituted:
+ *   [(1+k) I - (k/c^2) u u^T] E = E' - k u x B - (dt/2) mu0 c^2 rho_c u,
+ *   k = (dt/2) mu0 c^2 sigma gamma,
+ * solved in closed form (R16, Sherman-Morrison):
+ *   E = [rhs + (k/c^2) u (u.rhs) / (1 + k/gamma^2)] / (1 + k). */
+void orc_ohm_solve(const orc_params* P, const double* Ep, const double* u, const double* B, double rho_c,
+                   double* E)
+{
+    const double c = P->c, dt = orc_dt(P), mu0 = 1.0;
+    const double gam2 = 1.0 / (1.0 - dot3(u, u) / (c * c));
+    const double gam = sqrt(gam2);
+    const double k = 0.5 * dt * mu0 * c * c * P->sigma * gam;
+    double uxB[3], rhs[3];
+    cross3(u, B, uxB);
+    for (int a = 0; a < 3; ++a) rhs[a] = Ep[a] - k * uxB[a] - 0.5 * dt * mu0 * c * c * rho_c * u[a];
+    const double urhs = dot3(u, rhs);
+    const double s = (k / (c * c)) * urhs / (1.0 + k / gam2);
+    for (int a = 0; a < 3; ++a) E[a] = (rhs[a] + s * u[a]) / (1.0 + k);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Moments and the Landau eigenproblem                                        */
+/* ------------------------------------------------------------------------- */
+
+/* T^{mu nu} = sum_i p_i^mu p_i^nu f_i; N^mu = sum_i p_i^mu g_i (R5);
+ * Eqs. Cal_E, Cal_B, Cal_rhoc for E', B, rho_c. */
+void orc_moments(const orc_lattice* L, const double* f, const double* g, const double* h, double* T16,
+                 double* N4, double* Ep, double* B, double* rho_c)
+{
+    for (int m = 0; m < 16; ++m) T16[m] = 0.0;
+    for (int m = 0; m < 4; ++m) N4[m] = 0.0;
+    for (int i = 0; i < 19; ++i) {
+        for (int mu = 0; mu < 4; ++mu) {
+            N4[mu] += L->p[i][mu] * g[i];
+            for (int nv = 0; nv < 4; ++nv) T16[4 * mu + nv] += L->p[i][mu] * L->p[i][nv] * f[i];
+        }
+    }
+    for (int a = 0; a < 3; ++a) Ep[a] = B[a] = 0.0;
+    double rc = h[24];
+    for (int k = 0; k < 24; ++k) {
+        for (int a = 0; a < 3; ++a) {
+            Ep[a] += h[k] * L->e[k][a];
+            B[a] += h[k] * L->b[k][a];
+        }
+        rc += h[k];
+    }
+    *rho_c = rc;
+}
+
+/* Eq. Maxwell_tensor: F^{0i} = -E^i, F^{ij} = -eps_{ijk} c B^k. */
+void orc_maxwell_tensor(double c, const double* E, const double* B, double* F16)
+{
+    double F[4][4] = {{0.0, -E[0], -E[1], -E[2]},
+                      {E[0], 0.0, -c * B[2], c * B[1]},
+                      {E[1], c * B[2], 0.0, -c * B[0]},
+                      {E[2], -c * B[1], c * B[0], 0.0}};
+    memcpy(F16, F, sizeof(F));
+}
+
+/* The tensor eps0 F^{mu rho} F^nu_rho subtracted before the eigen-solve (R13):
+ * the first term of Eq. EM_EM, with the index placement F^{mu rho} F_rho^nu,
+ * which is the one that reproduces the printed T^00_EM, T^0i_EM and T^ij_EM. */
+void orc_em_ff(const orc_params* P, const double* E, const double* B, double* S16)
+{
+    const double eta[4] = {1.0, -1.0, -1.0, -1.0};
+    const double eps0 = eps0_of(P);
+    double F[16];
+    orc_maxwell_tensor(P->c, E, B, F);
+    for (int mu = 0; mu < 4; ++mu)
+        for (int nv = 0; nv < 4; ++nv) {
+            double s = 0.0;
+            /* F_rho^nu = eta_{rho sigma} F^{sigma nu} */
+            for (int rho = 0; rho < 4; ++rho) s += F[4 * mu + rho] * eta[rho] * F[4 * rho + nv];
+            S16[4 * mu + nv] = eps0 * s;
+        }
+}
+
+/* Landau-Lifshitz eigenproblem of the coupling subsection:
+ *   U_mu [T^{mu nu} - eps0 F^{mu rho} F^nu_rho] = lambda U^nu,
+ * largest eigenvalue by the power method (R14). With A = M eta the problem is
+ * A U = lambda U. Returns the number of iterations, or -1 if it did not
+ * converge or the eigenvector is not timelike. U_out = gamma (1, u/c). */
+int orc_landau(const orc_params* P, const double* T16, const double* E_prev, const double* B_prev,
+               const double* U_seed, double* U_out, double* lambda_out)
+{
+    const double eta[4] = {1.0, -1.0, -1.0, -1.0};
+    double S[16], A[16];
+    orc_em_ff(P, E_prev, B_prev, S);
+    for (int mu = 0; mu < 4; ++mu)
+        for (int nv = 0; nv < 4; ++nv) A[4 * mu + nv] = (T16[4 * mu + nv] - S[4 * mu + nv]) * eta[nv];
+    double U[4];
+    for (int m = 0; m < 4; ++m) U[m] = U_seed[m] / U_seed[0];
+    int it;
+    double lambda = 0.0;
+    for (it = 1; it <= P->max_power_iters; ++it) {
+        double V[4];
+        for (int m = 0; m < 4; ++m) {
+            V[m] = 0.0;
+            for (int nv = 0; nv < 4; ++nv) V[m] += A[4 * m + nv] * U[nv];
+        }
+        lambda = V[0] / U[0];
+        const double v0 = V[0];
+        double diff = 0.0, nrm = 0.0;
+        for (int m = 0; m < 4; ++m) {
+            V[m] /= v0;
+            diff += (V[m] - U[m]) * (V[m] - U[m]);
+            nrm += V[m] * V[m];
+            U[m] = V[m];
+        }
+        if (sqrt(diff) <= P->power_tol * sqrt(nrm)) break;
+    }
+    const double norm2 = U[0] * U[0] - (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]);
+    if (it > P->max_power_iters || !(norm2 > 0.0)) return -1;
+    const double s = 1.0 / sqrt(norm2);
+    for (int m = 0; m < 4; ++m) U_out[m] = U[m] * s;
+    *lambda_out = lambda;
+    return it;
+}
+
+/* The recovery chain of the coupling subsection, for one cell. prim layout:
+ * ORC_N, ORC_EPS, ORC_U (3), ORC_E (3), ORC_B (3), ORC_RHOC, ORC_J (3). prim_prev
+ * holds the previous step's values (E, B subtracted before the eigen-solve,
+ * and U as the seed). Returns the power-method iteration count or -1. */
+int orc_recover_cell(const orc_params* P, const orc_lattice* L, const double* f, const double* g,
+                     const double* h, const double* prim_prev, double* prim_out)
+{
+    const double c = P->c;
+    double T[16], N[4], Ep[3], B[3], rho_c;
+    orc_moments(L, f, g, h, T, N, Ep, B, &rho_c);
+    const double* up = prim_prev + ORC_U;
+    const double gp = 1.0 / sqrt(1.0 - dot3(up, up) / (c * c));
+    const double seed[4] = {gp, gp * up[0] / c, gp * up[1] / c, gp * up[2] / c};
+    double U[4], lambda;
+    int it = orc_landau(P, T, prim_prev + ORC_E, prim_prev + ORC_B, seed, U, &lambda);
+    if (it < 0) return -1;
+    const double* Eo = prim_prev + ORC_E;
+    const double* Bo = prim_prev + ORC_B;
+    /* eigenvalue = eps + (eps0/2)(c^2 B^2 - E^2), E and B of the previous step */
+    const double eps = lambda - 0.5 * eps0_of(P) * (c * c * dot3(Bo, Bo) - dot3(Eo, Eo));
+    const double n = N[0] / U[0]; /* R15; both in units with U^0 = gamma */
+    double u[3] = {c * U[1] / U[0], c * U[2] / U[0], c * U[3] / U[0]};
+    double E[3], J[3];
+    orc_ohm_solve(P, Ep, u, B, rho_c, E);
+    orc_ohm_current(P, E, u, B, rho_c, J);
+    prim_out[ORC_N] = n;
+    prim_out[ORC_EPS] = eps;
+    for (int a = 0; a < 3; ++a) {
+        prim_out[ORC_U + a] = u[a];
+        prim_out[ORC_E + a] = E[a];
+        prim_out[ORC_B + a] = B[a];
+        prim_out[ORC_J + a] = J[a];
+    }
+    prim_out[ORC_RHOC] = rho_c;
+    return it;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Streaming of the fluid populations                                         */
+/* ------------------------------------------------------------------------- */
+
+/* Neighbour index along axis a at offset d: periodic wrap, or clamp to the
+ * grid on open / driven faces. */
+static int64_t nb_index(const orc_params* P, int x, int y, int z, int a, int d)
+{
+    int q[3] = {x, y, z};
+    const int n[3] = {P->nx, P->ny, P->nz};
+    int s = q[a] + d;
+    const int bc_lo = P->bc[2 * a], bc_hi = P->bc[2 * a + 1];
+    if (s < 0) s = (bc_lo == ORC_PERIODIC) ? ((s % n[a]) + n[a]) % n[a] : 0;
+    if (s >= n[a]) s = (bc_hi == ORC_PERIODIC) ? s % n[a] : n[a] - 1;
+    q[a] = s;
+    return (int64_t)q[0] + (int64_t)P->nx * ((int64_t)q[1] + (int64_t)P->ny * q[2]);
+}
+
+/* Lattice index of x - hop (EM pull), same boundary rule per axis. */
+static int64_t shift_index(const orc_params* P, int x, int y, int z, const int* hop)
+{
+    int q[3] = {x - hop[0], y - hop[1], z - hop[2]};
+    const int n[3] = {P->nx, P->ny, P->nz};
+    for (int a = 0; a < 3; ++a) {
+        if (q[a] < 0) q[a] = (P->bc[2 * a] == ORC_PERIODIC) ? ((q[a] % n[a]) + n[a]) % n[a] : 0;
+        if (q[a] >= n[a]) q[a] = (P->bc[2 * a + 1] == ORC_PERIODIC) ? q[a] % n[a] : n[a] - 1;
+    }
+    return (int64_t)q[0] + (int64_t)P->nx * ((int64_t)q[1] + (int64_t)P->ny * q[2]);
+}
+
+/* R10: limited face value between the upwind cell (f_up) and the downwind
+ * cell (f_down); f_up2 is the cell upwind of f_up. r is the ratio of
+ * consecutive gradients, phi(r) = max(0, min(1, r)) is minmod. */
+static double limited_face(double f_up2, double f_up, double f_down, double C, int first_order)
+{
+    const double d = f_down - f_up;
+    const double r = (d != 0.0) ? (f_up - f_up2) / d : 0.0;
+    const double phi = first_order ? 0.0 : fmax(0.0, fmin(1.0, r));
+    return f_up + 0.5 * (1.0 - C) * phi * d;
+}
+
+/* Flux-difference part of Eq. eq:rlb for population i at one cell:
+ * returns sum_a C [F_out - F_in] over the axes along which chat_i moves. */
+static double flux_divergence(const orc_params* P, const orc_lattice* L, const double* fi, int x, int y,
+                              int z, int i)
+{
+    const double C = orc_courant(P, L);
+    const int first_order = (P->flags & ORC_FIRST_ORDER) != 0;
+    double div = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const int s = L->chat[i][a];
+        if (s == 0) continue;
+        /* values along the flow: upwind2, upwind, self, downwind */
+        const double f_m2 = fi[nb_index(P, x, y, z, a, -2 * s)];
+        const double f_m1 = fi[nb_index(P, x, y, z, a, -s)];
+        const double f_0 = fi[nb_index(P, x, y, z, a, 0)];
+        const double f_p1 = fi[nb_index(P, x, y, z, a, s)];
+        const double F_out = limited_face(f_m1, f_0, f_p1, C, first_order);
+        const double F_in = limited_face(f_m2, f_m1, f_0, C, first_order);
+        div += C * (F_out - F_in);
+    }
+    return div;
+}
+
+/* Courant number of one axis component: (c_0/c_t) c_a c dt / dx = sqrt(19/27) c dt/dx. */
+double orc_courant(const orc_params* P, const orc_lattice* L)
+{
+    return L->ca / L->ct_c0 * P->c * orc_dt(P) / P->dx;
+}
+
+/* R11: second central difference summed over the three axes. */
+static double laplacian(const orc_params* P, const double* fi, int x, int y, int z)
+{
+    double s = 0.0;
+    const double f0 = fi[nb_index(P, x, y, z, 0, 0)];
+    for (int a = 0; a < 3; ++a) s += fi[nb_index(P, x, y, z, a, 1)] - 2.0 * f0 + fi[nb_index(P, x, y, z, a, -1)];
+    return s;
+}
+
+/* One population streamed (flux + bulk viscosity), no collision: exported so
+ * the tests can pin the streaming operator on its own. */
+void orc_stream_population(const orc_params* P, int i, const double* fi, double* out)
+{
+    orc_lattice L;
+    orc_get_lattice(P, &L);
+    const double kvisc = P->alpha * P->c * orc_dt(P) / P->dx;
+    for (int z = 0; z < P->nz; ++z)
+        for (int y = 0; y < P->ny; ++y)
+            for (int x = 0; x < P->nx; ++x) {
+                int64_t id = (int64_t)x + (int64_t)P->nx * ((int64_t)y + (int64_t)P->ny * z);
+                double v = fi[id] - flux_divergence(P, &L, fi, x, y, z, i);
+                if (i != 0) v += kvisc * laplacian(P, fi, x, y, z);
+                out[id] = v;
+            }
+}
+
+/* ------------------------------------------------------------------------- */
+/* The simulation                                                              */
+/* ------------------------------------------------------------------------- */
+
+struct orc_sim {
+    orc_params P;
+    orc_lattice L;
+    int64_t N;
+    double *f, *g, *h, *prim;       /* state at t: f[19][N], g[19][N], h[25][N], prim[ORC_NPRIM][N] */
+    double *f2, *g2, *h2, *prim2;   /* state at t + dt */
+    double *fc, *gc, *hc;           /* post-collision populations at t */
+    int64_t iter_total, iter_max, recover_fail;
+    int64_t steps;
+};
+
+static int64_t cell_id(const orc_params* P, int x, int y, int z)
+{
+    return (int64_t)x + (int64_t)P->nx * ((int64_t)y + (int64_t)P->ny * z);
+}
+
+orc_sim* orc_create(const orc_params* P)
+{
+    if (P->nx < 1 || P->ny < 1 || P->nz < 1 || !(P->c > 0) || !(P->tau > 0) || !(P->dx > 0) || P->sigma < 0)
+        return NULL;
+    orc_sim* s = (orc_sim*)calloc(1, sizeof(orc_sim));
+    if (!s) return NULL;
+    s->P = *P;
+    if (s->P.max_power_iters <= 0) s->P.max_power_iters = 1000;
+    if (!(s->P.power_tol > 0)) s->P.power_tol = 1e-14;
+    if (!(s->P.nu > 0)) s->P.nu = sqrt(27.0); /* R22 */
+    orc_lattice_init(&s->P, &s->L);
+    s->N = (int64_t)P->nx * P->ny * P->nz;
+    const int64_t N = s->N;
+    s->f = (double*)calloc(19 * N, sizeof(double));
+    s->g = (double*)calloc(19 * N, sizeof(double));
+    s->h = (double*)calloc(25 * N, sizeof(double));
+    s->prim = (double*)calloc(ORC_NPRIM * N, sizeof(double));
+    s->f2 = (double*)calloc(19 * N, sizeof(double));
+    s->g2 = (double*)calloc(19 * N, sizeof(double));
+    s->h2 = (double*)calloc(25 * N, sizeof(double));
+    s->prim2 = (double*)calloc(ORC_NPRIM * N, sizeof(double));
+    s->fc = (double*)calloc(19 * N, sizeof(double));
+    s->gc = (double*)calloc(19 * N, sizeof(double));
+    s->hc = (double*)calloc(25 * N, sizeof(double));
+    if (!s->f || !s->g || !s->h || !s->prim || !s->f2 || !s->g2 || !s->h2 || !s->prim2 || !s->fc || !s->gc ||
+        !s->hc) {
+        orc_destroy(s);
+        return NULL;
+    }
+    return s;
+}
+
+void orc_destroy(orc_sim* s)
+{
+    if (!s) return;
+    free(s->f); free(s->g); free(s->h); free(s->prim);
+    free(s->f2); free(s->g2); free(s->h2); free(s->prim2);
+    free(s->fc); free(s->gc); free(s->hc);
+    free(s);
+}
+
+static void gather_cell(const double* arr, int npop, int64_t N, int64_t id, double* out)
+{
+    for (int k = 0; k < npop; ++k) out[k] = arr[(int64_t)k * N + id];
+}
+
+static void scatter_cell(double* arr, int npop, int64_t N, int64_t id, const double* in)
+{
+    for (int k = 0; k < npop; ++k) arr[(int64_t)k * N + id] = in[k];
+}
+
+/* Equilibrium populations of one cell from its primitive state. */
+static void set_cell_equilibrium(orc_sim* s, int64_t id)
+{
+    double pr[ORC_NPRIM], fe[19], ge[19], he[25];
+    gather_cell(s->prim, ORC_NPRIM, s->N, id, pr);
+    orc_feq(&s->P, &s->L, pr[ORC_N], pr[ORC_EPS], pr + ORC_U, pr + ORC_E, pr + ORC_B, fe);
+    orc_geq(&s->P, &s->L, pr[ORC_N], pr + ORC_U, ge);
+    orc_heq(&s->P, &s->L, pr + ORC_E, pr + ORC_B, pr + ORC_J, pr[ORC_RHOC], he);
+    scatter_cell(s->f, 19, s->N, id, fe);
+    scatter_cell(s->g, 19, s->N, id, ge);
+    scatter_cell(s->h, 25, s->N, id, he);
+}
+
+/* Initial state (Sec. IV set-ups): eps from Eq. EOS, E from ideal Ohm (Eq.
+ * Ohm_ideal) when E is NULL, rho_c = eps0 div E (Eq. Gauss_E, R18), J from
+ * Eq. Ohm, populations at equilibrium (R17). Arrays are x-fastest; u, B, E hold
+ * three planes (x components, then y, then z). */
+int orc_init(orc_sim* s, const double* n, const double* p, const double* u, const double* B, const double* E)
+{
+    const orc_params* P = &s->P;
+    const int64_t N = s->N;
+    const double c = P->c;
+    double* pr = s->prim;
+    for (int64_t id = 0; id < N; ++id) {
+        pr[ORC_N * N + id] = n[id];
+        pr[ORC_EPS * N + id] = n[id] * c * c + p[id] / (P->gamma_ad - 1.0);
+        double uu[3] = {u[id], u[N + id], u[2 * N + id]};
+        double bb[3] = {B[id], B[N + id], B[2 * N + id]};
+        double ee[3];
+        if (E) {
+            ee[0] = E[id]; ee[1] = E[N + id]; ee[2] = E[2 * N + id];
+        } else {
+            cross3(uu, bb, ee);
+            for (int a = 0; a < 3; ++a) ee[a] = -ee[a];
+        }
+        if (!(dot3(uu, uu) < c * c)) return -1;
+        for (int a = 0; a < 3; ++a) {
+            pr[(ORC_U + a) * N + id] = uu[a];
+            pr[(ORC_B + a) * N + id] = bb[a];
+            pr[(ORC_E + a) * N + id] = ee[a];
+        }
+    }
+    const double eps0 = eps0_of(P);
+    for (int z = 0; z < P->nz; ++z)
+        for (int y = 0; y < P->ny; ++y)
+            for (int x = 0; x < P->nx; ++x) {
+                const int64_t id = cell_id(P, x, y, z);
+                double div = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    const int na = (a == 0) ? P->nx : (a == 1) ? P->ny : P->nz;
+                    if (na == 1) continue;
+                    div += (pr[(ORC_E + a) * N + nb_index(P, x, y, z, a, 1)] -
+                            pr[(ORC_E + a) * N + nb_index(P, x, y, z, a, -1)]) / (2.0 * P->dx);
+                }
+                pr[ORC_RHOC * N + id] = eps0 * div;
+            }
+    for (int64_t id = 0; id < N; ++id) {
+        double pc[ORC_NPRIM];
+        gather_cell(pr, ORC_NPRIM, N, id, pc);
+        orc_ohm_current(P, pc + ORC_E, pc + ORC_U, pc + ORC_B, pc[ORC_RHOC], pc + ORC_J);
+        scatter_cell(pr, ORC_NPRIM, N, id, pc);
+        set_cell_equilibrium(s, id);
+    }
+    s->steps = 0;
+    return 0;
+}
+
+/* Collision of one cell at time t (R6-R8 and Eq. LB_Maxwell with tau_h = 1/2):
+ *   f_c = f - K_i (f - f^eq(t)),  g_c = g - (dt/tau)(g - g^eq(t)),
+ *   h_c = h - 2 (h - h^eq(t)) = 2 h^eq - h  (h_0 included, h_0^eq = rho_c).
+ * The post-collision populations are then streamed (collide-then-stream). */
+static void collide_cell(const orc_sim* s, int64_t id, double* fc, double* gc, double* hc)
+{
+    const orc_params* P = &s->P;
+    const orc_lattice* L = &s->L;
+    const int64_t N = s->N;
+    const double c = P->c;
+    const double dt_tau = 1.0 / P->tau; /* R6: tau in units of dt */
+    double pr[ORC_NPRIM], feq[19], geq[19], heq[25];
+    gather_cell(s->prim, ORC_NPRIM, N, id, pr);
+    orc_feq(P, L, pr[ORC_N], pr[ORC_EPS], pr + ORC_U, pr + ORC_E, pr + ORC_B, feq);
+    orc_geq(P, L, pr[ORC_N], pr + ORC_U, geq);
+    orc_heq(P, L, pr + ORC_E, pr + ORC_B, pr + ORC_J, pr[ORC_RHOC], heq);
+    const double* u = pr + ORC_U;
+    const double gam = 1.0 / sqrt(1.0 - dot3(u, u) / (c * c));
+    for (int i = 0; i < 19; ++i) {
+        double vu = 0.0;
+        for (int a = 0; a < 3; ++a) vu += (L->ca / L->ct_c0) * c * L->chat[i][a] * u[a];
+        const double K = dt_tau * gam * (1.0 - vu / (c * c));
+        const double fi = s->f[(int64_t)i * N + id], gi = s->g[(int64_t)i * N + id];
+        fc[(int64_t)i * N + id] = fi - K * (fi - feq[i]);
+        gc[(int64_t)i * N + id] = gi - dt_tau * (gi - geq[i]); /* R8 */
+    }
+    const int em_coll = (P->flags & ORC_NO_EM_COLLISION) == 0;
+    for (int k = 0; k < 25; ++k) {
+        const double hk = s->h[(int64_t)k * N + id];
+        hc[(int64_t)k * N + id] = em_coll ? 2.0 * heq[k] - hk : hk;
+    }
+}
+
+/* Streaming of the post-collision populations into cell (x, y, z) at t + dt,
+ * followed by the recovery chain. Fluid: f(t+dt) = f_c - sum_a C [F_out - F_in]
+ * + bulk viscosity (Eq. eq:rlb, R10, R11); g the same without viscosity; h:
+ * h(x, t + dt) = h_c(x - v dt) (Eq. LB_Maxwell), h_0 does not move. Returns
+ * the power-method iteration count or -1. */
+static int stream_recover_cell(const orc_sim* s, int x, int y, int z, const double* fc, const double* gc,
+                               const double* hc, double* fo, double* go, double* ho, double* po)
+{
+    const orc_params* P = &s->P;
+    const orc_lattice* L = &s->L;
+    const int64_t N = s->N;
+    const int64_t id = cell_id(P, x, y, z);
+    const double kvisc = P->alpha * P->c * orc_dt(P) / P->dx;
+    double fn[19], gn[19], hn[25], pr[ORC_NPRIM], pn[ORC_NPRIM];
+    for (int i = 0; i < 19; ++i) {
+        const double* fi = fc + (int64_t)i * N;
+        const double* gi = gc + (int64_t)i * N;
+        fn[i] = fi[id] - flux_divergence(P, L, fi, x, y, z, i);
+        if (i != 0) fn[i] += kvisc * laplacian(P, fi, x, y, z);
+        gn[i] = gi[id] - flux_divergence(P, L, gi, x, y, z, i);
+    }
+    for (int k = 0; k < 24; ++k) hn[k] = hc[(int64_t)k * N + shift_index(P, x, y, z, L->hop[k])];
+    hn[24] = hc[24 * N + id];
+
+    gather_cell(s->prim, ORC_NPRIM, N, id, pr);
+    const int it = orc_recover_cell(P, L, fn, gn, hn, pr, pn);
+    scatter_cell(fo, 19, N, id, fn);
+    scatter_cell(go, 19, N, id, gn);
+    scatter_cell(ho, 25, N, id, hn);
+    /* on failure keep the previous primitives; the failure is counted */
+    scatter_cell(po, ORC_NPRIM, N, id, it < 0 ? pr : pn);
+    return it;
+}
+
+/* Eq. eq:rlb exactly as printed (test switch ORC_IMPLICIT_AS_PRINTED): streaming
+ * and viscosity of f(t), collision implicit in f(t+dt) against f^eq(t). */
+static int update_cell_as_printed(const orc_sim* s, int x, int y, int z, const double* hc, double* fo,
+                                  double* go, double* ho, double* po)
+{
+    const orc_params* P = &s->P;
+    const orc_lattice* L = &s->L;
+    const int64_t N = s->N;
+    const int64_t id = cell_id(P, x, y, z);
+    const double c = P->c, dt_tau = 1.0 / P->tau;
+    const double kvisc = P->alpha * c * orc_dt(P) / P->dx;
+    double pr[ORC_NPRIM], pn[ORC_NPRIM], feq[19], geq[19], fn[19], gn[19], hn[25];
+    gather_cell(s->prim, ORC_NPRIM, N, id, pr);
+    orc_feq(P, L, pr[ORC_N], pr[ORC_EPS], pr + ORC_U, pr + ORC_E, pr + ORC_B, feq);
+    orc_geq(P, L, pr[ORC_N], pr + ORC_U, geq);
+    const double* u = pr + ORC_U;
+    const double gam = 1.0 / sqrt(1.0 - dot3(u, u) / (c * c));
+    for (int i = 0; i < 19; ++i) {
+        const double* fi = s->f + (int64_t)i * N;
+        const double* gi = s->g + (int64_t)i * N;
+        double fs = fi[id] - flux_divergence(P, L, fi, x, y, z, i);
+        if (i != 0) fs += kvisc * laplacian(P, fi, x, y, z);
+        const double gs = gi[id] - flux_divergence(P, L, gi, x, y, z, i);
+        double vu = 0.0;
+        for (int a = 0; a < 3; ++a) vu += (L->ca / L->ct_c0) * c * L->chat[i][a] * u[a];
+        const double K = dt_tau * gam * (1.0 - vu / (c * c));
+        fn[i] = (fs + K * feq[i]) / (1.0 + K);
+        gn[i] = (gs + dt_tau * geq[i]) / (1.0 + dt_tau);
+    }
+    for (int k = 0; k < 24; ++k) hn[k] = hc[(int64_t)k * N + shift_index(P, x, y, z, L->hop[k])];
+    hn[24] = hc[24 * N + id];
+    const int it = orc_recover_cell(P, L, fn, gn, hn, pr, pn);
+    scatter_cell(fo, 19, N, id, fn);
+    scatter_cell(go, 19, N, id, gn);
+    scatter_cell(ho, 25, N, id, hn);
+    scatter_cell(po, ORC_NPRIM, N, id, it < 0 ? pr : pn);
+    return it;
+}
+
+/* Collision of every cell into s->fc, s->gc, s->hc. */
+static void collide_all(orc_sim* s)
+{
+    const int64_t N = s->N;
+#pragma omp parallel for schedule(static)
+    for (int64_t id = 0; id < N; ++id) collide_cell(s, id, s->fc, s->gc, s->hc);
+}
+
+static int update_cell(const orc_sim* s, int x, int y, int z, double* fo, double* go, double* ho, double* po)
+{
+    if (s->P.flags & ORC_IMPLICIT_AS_PRINTED) return update_cell_as_printed(s, x, y, z, s->hc, fo, go, ho, po);
+    return stream_recover_cell(s, x, y, z, s->fc, s->gc, s->hc, fo, go, ho, po);
+}
+
+static void copy_cell_state(orc_sim* s, int64_t dst, int64_t src)
+{
+    const int64_t N = s->N;
+    for (int k = 0; k < 19; ++k) {
+        s->f[k * N + dst] = s->f[k * N + src];
+        s->g[k * N + dst] = s->g[k * N + src];
+    }
+    for (int k = 0; k < 25; ++k) s->h[k * N + dst] = s->h[k * N + src];
+    for (int k = 0; k < ORC_NPRIM; ++k) s->prim[k * N + dst] = s->prim[k * N + src];
+}
+
+/* R19: open faces copy the state of the first interior cell. */
+static void open_boundaries(orc_sim* s)
+{
+    const orc_params* P = &s->P;
+    const int n[3] = {P->nx, P->ny, P->nz};
+    for (int face = 0; face < 6; ++face) {
+        if (P->bc[face] == ORC_PERIODIC) continue;
+        const int a = face / 2, hi = face % 2;
+        if (n[a] < 3) continue;
+        const int b = hi ? n[a] - 1 : 0;
+        const int src = hi ? n[a] - 2 : 1;
+        const int a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+        for (int j2 = 0; j2 < n[a2]; ++j2)
+            for (int j1 = 0; j1 < n[a1]; ++j1) {
+                int q[3], r[3];
+                q[a] = b; q[a1] = j1; q[a2] = j2;
+                r[a] = src; r[a1] = j1; r[a2] = j2;
+                copy_cell_state(s, cell_id(P, q[0], q[1], q[2]), cell_id(P, r[0], r[1], r[2]));
+            }
+    }
+}
+
+/* R20: normal-B fix on open faces, after all copies, faces in order. */
+static void normal_b_fix(orc_sim* s)
+{
+    const orc_params* P = &s->P;
+    const orc_lattice* L = &s->L;
+    const int64_t N = s->N;
+    const int n[3] = {P->nx, P->ny, P->nz};
+    double* Bp[3] = {s->prim + (int64_t)ORC_B * N, s->prim + (int64_t)(ORC_B + 1) * N,
+                     s->prim + (int64_t)(ORC_B + 2) * N};
+    for (int face = 0; face < 6; ++face) {
+        if (P->bc[face] == ORC_PERIODIC) continue;
+        const int a = face / 2, hi = face % 2;
+        if (n[a] < 3) continue;
+        const int sgn = hi ? -1 : 1; /* inward direction */
+        const int b = hi ? n[a] - 1 : 0;
+        const int a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+        for (int j2 = 0; j2 < n[a2]; ++j2)
+            for (int j1 = 0; j1 < n[a1]; ++j1) {
+                int q[3];
+                q[a1] = j1; q[a2] = j2;
+                q[a] = b + sgn;
+                const int x1 = q[0], y1 = q[1], z1 = q[2];
+                /* tangential part of the central-difference divergence at the first interior cell */
+                double tang = 0.0;
+                const int at[2] = {a1, a2};
+                for (int t = 0; t < 2; ++t) {
+                    if (n[at[t]] == 1) continue;
+                    tang += (Bp[at[t]][nb_index(P, x1, y1, z1, at[t], 1)] -
+                             Bp[at[t]][nb_index(P, x1, y1, z1, at[t], -1)]) / (2.0 * P->dx);
+                }
+                q[a] = b + 2 * sgn;
+                const double B_far = Bp[a][cell_id(P, q[0], q[1], q[2])];
+                q[a] = b;
+                const int64_t idb = cell_id(P, q[0], q[1], q[2]);
+                /* sgn (B_far - B_b) / (2 dx) + tang = 0 */
+                const double Bn_new = B_far + sgn * 2.0 * P->dx * tang;
+                const double dB = Bn_new - Bp[a][idb];
+                Bp[a][idb] = Bn_new;
+                for (int k = 0; k < 24; ++k)
+                    if (L->b[k][a] != 0.0) s->h[(int64_t)k * N + idb] += dB * L->b[k][a] / 8.0;
+            }
+    }
+}
+
+/* R21: the drive pattern (the paper's two co-rotating photospheric vortices),
+ * on x, y in [-3, 3] mapped onto the grid, scaled to max |u| = u0. */
+void orc_drive_velocity(const orc_params* P, int x, int y, double* u)
+{
+    const double X = -3.0 + (x + 0.5) * 6.0 / P->nx;
+    const double Y = -3.0 + (y + 0.5) * 6.0 / P->ny;
+    const double xs = (X < 0.0) ? X : X - 3.0;
+    u[0] = P->drive_u0 * sin(M_PI * xs / 3.0) * cos(M_PI * Y / 6.0);
+    u[1] = P->drive_u0 * cos(M_PI * xs / 3.0) * sin(M_PI * Y / 6.0);
+    u[2] = 0.0;
+}
+
+static void drive_layers(orc_sim* s)
+{
+    const orc_params* P = &s->P;
+    if (P->bc[4] != ORC_DRIVEN || P->drive_layers <= 0) return;
+    const int64_t N = s->N;
+    const int nl = P->drive_layers < P->nz ? P->drive_layers : P->nz;
+    for (int z = 0; z < nl; ++z)
+        for (int y = 0; y < P->ny; ++y)
+            for (int x = 0; x < P->nx; ++x) {
+                const int64_t id = cell_id(P, x, y, z);
+                double pr[ORC_NPRIM], u[3], E[3];
+                gather_cell(s->prim, ORC_NPRIM, N, id, pr);
+                orc_drive_velocity(P, x, y, u);
+                cross3(u, pr + ORC_B, E);
+                for (int a = 0; a < 3; ++a) {
+                    pr[ORC_U + a] = u[a];
+                    pr[ORC_E + a] = -E[a];
+                }
+                orc_ohm_current(P, pr + ORC_E, pr + ORC_U, pr + ORC_B, pr[ORC_RHOC], pr + ORC_J);
+                scatter_cell(s->prim, ORC_NPRIM, N, id, pr);
+                set_cell_equilibrium(s, id);
+            }
+}
+
+int orc_step(orc_sim* s, int64_t nsteps)
+{
+    const orc_params* P = &s->P;
+#ifdef _OPENMP
+    if (P->threads > 0) omp_set_num_threads(P->threads);
+#endif
+    int64_t fails = 0;
+    for (int64_t t = 0; t < nsteps; ++t) {
+        int64_t it_sum = 0, it_max = s->iter_max;
+        collide_all(s);
+#pragma omp parallel for collapse(2) schedule(static) reduction(+ : fails, it_sum) reduction(max : it_max)
+        for (int z = 0; z < P->nz; ++z)
+            for (int y = 0; y < P->ny; ++y)
+                for (int x = 0; x < P->nx; ++x) {
+                    int it = update_cell(s, x, y, z, s->f2, s->g2, s->h2, s->prim2);
+                    if (it < 0)
+                        ++fails;
+                    else {
+                        it_sum += it;
+                        if (it > it_max) it_max = it;
+                    }
+                }
+        double* tmp;
+        tmp = s->f; s->f = s->f2; s->f2 = tmp;
+        tmp = s->g; s->g = s->g2; s->g2 = tmp;
+        tmp = s->h; s->h = s->h2; s->h2 = tmp;
+        tmp = s->prim; s->prim = s->prim2; s->prim2 = tmp;
+        open_boundaries(s);
+        normal_b_fix(s);
+        drive_layers(s);
+        s->iter_total += it_sum;
+        s->iter_max = it_max;
+        s->steps += 1;
+    }
+    s->recover_fail += fails;
+    return fails ? -1 : 0;
+}
+
+/* Output fields, field-major (ORC_OUT_* rows of N values):
+ * n, p, eps, u(3), E(3), B(3), rho_c, J(3). */
+void orc_get_moments(const orc_sim* s, double* out)
+{
+    const int64_t N = s->N;
+    const double* pr = s->prim;
+    for (int64_t id = 0; id < N; ++id) {
+        out[0 * N + id] = pr[ORC_N * N + id];
+        out[1 * N + id] = orc_eos_pressure(&s->P, pr[ORC_N * N + id], pr[ORC_EPS * N + id]);
+        out[2 * N + id] = pr[ORC_EPS * N + id];
+        for (int a = 0; a < 3; ++a) {
+            out[(3 + a) * N + id] = pr[(ORC_U + a) * N + id];
+            out[(6 + a) * N + id] = pr[(ORC_E + a) * N + id];
+            out[(9 + a) * N + id] = pr[(ORC_B + a) * N + id];
+            out[(13 + a) * N + id] = pr[(ORC_J + a) * N + id];
+        }
+        out[12 * N + id] = pr[ORC_RHOC * N + id];
+    }
+}
+
+void orc_get_state(const orc_sim* s, double* f, double* g, double* h, double* prim)
+{
+    const int64_t N = s->N;
+    if (f) memcpy(f, s->f, 19 * N * sizeof(double));
+    if (g) memcpy(g, s->g, 19 * N * sizeof(double));
+    if (h) memcpy(h, s->h, 25 * N * sizeof(double));
+    if (prim) memcpy(prim, s->prim, ORC_NPRIM * N * sizeof(double));
+}
+
+void orc_set_state(orc_sim* s, const double* f, const double* g, const double* h, const double* prim)
+{
+    const int64_t N = s->N;
+    if (f) memcpy(s->f, f, 19 * N * sizeof(double));
+    if (g) memcpy(s->g, g, 19 * N * sizeof(double));
+    if (h) memcpy(s->h, h, 25 * N * sizeof(double));
+    if (prim) memcpy(s->prim, prim, ORC_NPRIM * N * sizeof(double));
+}
+
+/* One-step update of selected cells only (used to check a full-size GPU step
+ * at sampled cells). Writes 19 + 19 + 25 + ORC_NPRIM values per listed cell,
+ * before any boundary or driving pass. */
+int orc_update_cells(orc_sim* s, const int64_t* cells, int64_t ncells, double* f_out, double* g_out,
+                     double* h_out, double* prim_out)
+{
+    const orc_params* P = &s->P;
+    const int64_t N = s->N;
+    collide_all(s);
+    double* fo = (double*)calloc(19 * N, sizeof(double));
+    double* go = (double*)calloc(19 * N, sizeof(double));
+    double* ho = (double*)calloc(25 * N, sizeof(double));
+    double* po = (double*)calloc(ORC_NPRIM * N, sizeof(double));
+    int rc = 0;
+    if (!fo || !go || !ho || !po) rc = -2;
+    for (int64_t m = 0; m < ncells && rc == 0; ++m) {
+        const int64_t id = cells[m];
+        const int x = (int)(id % P->nx), y = (int)((id / P->nx) % P->ny), z = (int)(id / ((int64_t)P->nx * P->ny));
+        if (update_cell(s, x, y, z, fo, go, ho, po) < 0) rc = -1;
+        for (int k = 0; k < 19; ++k) {
+            f_out[m * 19 + k] = fo[k * N + id];
+            g_out[m * 19 + k] = go[k * N + id];
+        }
+        for (int k = 0; k < 25; ++k) h_out[m * 25 + k] = ho[k * N + id];
+        for (int k = 0; k < ORC_NPRIM; ++k) prim_out[m * ORC_NPRIM + k] = po[k * N + id];
+    }
+    free(fo); free(go); free(ho); free(po);
+    return rc;
+}
+
+/* Post-collision populations of the current state (the populations that the
+ * next step streams): f_c, g_c, h_c of collide_cell, field-major. */
+void orc_get_post_collision(orc_sim* s, double* fc, double* gc, double* hc)
+{
+    const int64_t N = s->N;
+    collide_all(s);
+    if (fc) memcpy(fc, s->fc, 19 * N * sizeof(double));
+    if (gc) memcpy(gc, s->gc, 19 * N * sizeof(double));
+    if (hc) memcpy(hc, s->hc, 25 * N * sizeof(double));
+}
+
+void orc_stats(const orc_sim* s, int64_t* out4)
+{
+    out4[0] = s->steps;
+    out4[1] = s->iter_total;
+    out4[2] = s->iter_max;
+    out4[3] = s->recover_fail;
+}
+
+void orc_get_lattice(const orc_params* P, orc_lattice* L)
+{
+    orc_params Q = *P;
+    if (!(Q.nu > 0)) Q.nu = sqrt(27.0);
+    orc_lattice_init(&Q, L);
+}

@@ -1,0 +1,214 @@
+"""Whole-step pins of the oracle: invariants, analytic solutions and the numbers
+the paper prints for its validation runs (Sec. IV)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1508_03452_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+OPEN, PER = O.OPEN, O.PERIODIC
+
+
+def _sim(F, **kw):
+    P = O.make_params(F.nx, F.ny, F.nz, **{"threads": 4, **kw})
+    s = O.Sim(P)
+    s.init(F.n, F.p, F.u, F.B, F.E)
+    return s, P
+
+
+def _totals(s):
+    """Sum over cells of N^0, T^{0 nu} and rho_c from the populations."""
+    f, g, h, _ = s.state()
+    L = O.lattice(s.P)
+    p = L["p"]
+    N0 = (p[:, 0:1] * g).sum()
+    T0 = np.array([(p[:, 0:1] * p[:, m:m + 1] * f).sum() for m in range(4)])
+    rc = h.sum()
+    return N0, T0, rc
+
+
+def test_uniform_state_is_steady():
+    """A uniform ideal state (E = -u x B, rho_c = 0, J = 0) is a fixed point."""
+    N = 6 * 5 * 4
+    u = np.tile(np.array([[0.2], [-0.1], [0.05]]), N)
+    B = np.tile(np.array([[0.1], [0.05], [-0.2]]), N)
+    F = W.Fields(6, 5, 4, np.full(N, 1.3), np.full(N, 0.7), u, B)
+    s, _ = _sim(F, sigma=50.0)
+    m0 = s.moments()
+    s.step(5)
+    m = s.moments()
+    assert np.allclose(m, m0, rtol=0, atol=1e-13)
+
+
+def test_mass_and_charge_conserved_periodic():
+    """Sum of N^0 (Eq. Density_cons with the BGK g collision and n = N^0/U^0) and
+    of rho_c (Eq. Current_cons, from the h_0 update) are conserved to round-off
+    on a periodic lattice."""
+    F = W.kelvin_helmholtz(24, 24, 1, V=0.3, ratio=3.0, B0=0.1, a=2.0, noise=1e-2, seed=3)
+    s, _ = _sim(F, sigma=100.0)
+    N0a, _, rca = _totals(s)
+    s.step(30)
+    N0b, _, rcb = _totals(s)
+    assert abs(N0b - N0a) < 1e-12 * abs(N0a)
+    assert abs(rcb - rca) < 1e-12
+
+
+def test_energy_momentum_conserved_without_fields():
+    """Without electromagnetic fields the explicit Anderson-Witting collision
+    conserves T^{0 nu} exactly (Landau matching), and the flux-form streaming
+    telescopes: sum_x T^{0 nu} is conserved to round-off."""
+    N = 16 * 16
+    rng = np.random.default_rng(50)
+    x, y = np.meshgrid(np.arange(16), np.arange(16))
+    u = np.zeros((3, N))
+    u[0] = 0.2 * np.sin(2 * np.pi * y.reshape(-1) / 16)
+    u[1] = 0.1 * np.cos(2 * np.pi * x.reshape(-1) / 16)
+    F = W.Fields(16, 16, 1, 1.0 + 0.1 * rng.uniform(size=N), np.ones(N), u, np.zeros((3, N)))
+    s, _ = _sim(F, sigma=0.0)
+    _, Ta, _ = _totals(s)
+    s.step(40)
+    _, Tb, _ = _totals(s)
+    assert np.abs(Tb - Ta).max() < 1e-12 * abs(Ta[0])
+
+
+def test_one_dimensional_fields_keep_bx():
+    """With fields varying along x only the yz-plane EM populations stream onto
+    identical values, so B_x stays at its initial value (div B = 0 exactly)."""
+    F = W.alfven_wave(32, 1, 1, amp=1e-2)
+    s, _ = _sim(F, sigma=1e3)
+    s.step(50)
+    m = s.moments()
+    assert np.abs(m[9] - 0.1).max() < 1e-13
+
+
+def _alfven_right_mover(nx, flags=0):
+    F = W.alfven_wave(nx, 1, 1)
+    s, P = _sim(F, sigma=1e6, flags=flags)
+    vA, k, B0 = F.meta["vA"], 2 * np.pi / nx, F.meta["B0"]
+    nsteps = int(round(0.25 * nx / (vA * O.dt(P))))
+    mode = lambda a: np.fft.fft(a)[1]
+    m0 = s.moments()
+    s.step(nsteps)
+    m = s.moments()
+    R0 = mode(m0[11]) - (B0 / vA) * mode(m0[5])
+    R = mode(m[11]) - (B0 / vA) * mode(m[5])
+    return -np.angle(R / R0) / k / (nsteps * O.dt(P)) / vA - 1.0
+
+
+def test_alfven_wave_speed():
+    """Config-1 form (ideal limit, sigma = 1e6): the right-moving Alfven wave
+    travels at v_A = B0 c / sqrt(eps + p + B0^2), the small-amplitude limit of the
+    paper's Alfven speed; the error falls at second order with resolution."""
+    e32, e64, e128 = (abs(_alfven_right_mover(n)) for n in (32, 64, 128))
+    assert e64 < 0.03 and e128 < 0.01
+    assert e32 / e64 > 2.5 and e64 / e128 > 2.5
+
+
+def test_collision_as_printed_slows_waves():
+    """Eq. eq:rlb exactly as printed (implicit collision towards f^eq(t)) moves
+    the Alfven wave far too slowly; the reading used everywhere else does not."""
+    assert _alfven_right_mover(64, flags=O.IMPLICIT_AS_PRINTED) < -0.2
+    assert abs(_alfven_right_mover(64)) < 0.03
+
+
+@pytest.mark.parametrize("sigma", [10.0, 100.0])
+def test_current_sheet_diffusion(sigma):
+    """Config-2 form on a reduced grid: B_y follows the exact periodic solution of
+    dB/dt = sigma^-1 d^2B/dx^2 (the paper's current-sheet equation)."""
+    F = W.current_sheet(128, 1, 1, delta=8.0)
+    s, P = _sim(F, sigma=sigma)
+    B0 = s.moments()[10]
+    nsteps = 2000
+    s.step(nsteps)
+    B = s.moments()[10]
+    t = nsteps * O.dt(P)
+    k = 2 * np.pi * np.fft.fftfreq(128)
+    exact = np.real(np.fft.ifft(np.fft.fft(B0) * np.exp(-k * k * t / sigma)))
+    change = np.linalg.norm(B0 - exact)
+    assert np.linalg.norm(B - exact) < 0.05 * change
+
+
+def _paper_sheet(N, t_end=None, steps=None):
+    g = json.load(open(os.path.join(GOLDEN, "current_sheet_convergence.json")))
+    F = W.current_sheet_paper(N, sigma=g["sigma"], t0=g["t_start"], B0=g["B0"], p0=g["p"], n0=g["n"])
+    s, P = _sim(F, sigma=g["sigma"], dx=F.meta["dx"], bc=(OPEN, OPEN, PER, PER, PER, PER), threads=1)
+    dt = O.dt(P)
+    if steps is None:
+        steps = int(round((t_end - g["t_start"]) / dt))
+    s.step(steps)
+    return F, s, g["t_start"] + steps * dt, dt
+
+
+def test_paper_current_sheet_matches_erf():
+    """The paper's resistive test (100 cells, sigma = 100, open boundaries, t = 1
+    to 9) lands on B0 erf(x sqrt(sigma/t)/2) at t = 9."""
+    F, s, t, _ = _paper_sheet(100, t_end=9.0)
+    x = F.meta["x"]
+    exact = np.array([math.erf(0.5 * math.sqrt(100.0 / t) * v) for v in x])
+    By = s.moments()[10]
+    assert np.linalg.norm(By - exact) / np.linalg.norm(exact) < 0.01
+
+
+def test_paper_convergence_slope():
+    """Self-convergence of the sigma = 100 sheet against a 200-cell run (the
+    paper's error E_N): second order, near the printed slope -1.9668."""
+    g = json.load(open(os.path.join(GOLDEN, "current_sheet_convergence.json")))
+    Ns, errs = (25, 50, 100), []
+    for N in Ns:
+        _, s, t, _ = _paper_sheet(N, t_end=g["t_end"])
+        By = s.moments()[10]
+        # reference at the same time: linear interpolation between two steps
+        _, r, _, dtr = _paper_sheet(g["reference_cells"], steps=0)
+        k = int(math.floor((t - g["t_start"]) / dtr))
+        r.step(k)
+        a = r.moments()[10]
+        r.step(1)
+        b = r.moments()[10]
+        w = (t - g["t_start"] - k * dtr) / dtr
+        ref = ((1 - w) * a + w * b).reshape(N, -1).mean(axis=1)
+        errs.append(math.sqrt(np.mean((By - ref) ** 2)))
+    slope = np.polyfit(np.log(Ns), np.log(errs), 1)[0]
+    assert abs(slope - g["slope"]) < 0.25, (slope, errs)
+
+
+def test_open_boundary_copies_and_fixes_normal_b():
+    """Open faces copy the first interior cell (Sec. IV: 'copying the distribution
+    functions from the neighboring cell'); then the normal B of the boundary
+    cell is set so the central-difference div B of the first interior cell is 0."""
+    F = W.kelvin_helmholtz(16, 12, 1, V=0.2, B0=0.1, a=2.0, noise=1e-2, seed=1)
+    rng = np.random.default_rng(60)
+    F.B[1] += 0.01 * rng.uniform(-1, 1, F.N)  # give B_y a non-trivial divergence
+    s, P = _sim(F, sigma=100.0, bc=(PER, PER, OPEN, OPEN, PER, PER))
+    s.step(2)
+    m = s.moments()
+    nx, ny = 16, 12
+    Bx, By = m[9].reshape(ny, nx), m[10].reshape(ny, nx)
+    for yb, y1, y2 in ((0, 1, 2), (ny - 1, ny - 2, ny - 3)):
+        sgn = 1 if yb == 0 else -1
+        div = sgn * (By[y2] - By[yb]) / 2.0 + (np.roll(Bx[y1], -1) - np.roll(Bx[y1], 1)) / 2.0
+        assert np.abs(div).max() < 1e-14
+        for k in (0, 3, 4, 5, 6, 7, 8, 12):  # everything but B_y and J is a copy
+            assert np.array_equal(m[k].reshape(ny, nx)[yb], m[k].reshape(ny, nx)[y1])
+
+
+def test_driven_layers_hold_the_drive():
+    """Driven layers are reset to the equilibrium of the two-vortex photospheric
+    drive (max |u| = drive_u0) every step."""
+    F = W.flux_rope(12, 12, 16)
+    nl = W.drive_layers_for(16)
+    s, P = _sim(F, sigma=500.0, bc=(OPEN, OPEN, OPEN, OPEN, O.DRIVEN, OPEN), drive_u0=0.05, drive_layers=nl)
+    s.step(3)
+    m = s.moments()
+    ux = m[3].reshape(16, 12, 12)
+    uy = m[4].reshape(16, 12, 12)
+    for z in range(nl):
+        for y in range(12):
+            for x in range(12):
+                d = O.drive_velocity(P, x, y)
+                assert abs(ux[z, y, x] - d[0]) < 1e-15 and abs(uy[z, y, x] - d[1]) < 1e-15
+    assert np.sqrt(ux[0] ** 2 + uy[0] ** 2).max() <= 0.05 + 1e-15
