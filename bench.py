@@ -1,0 +1,318 @@
+"""Benchmark of the RRMHD lattice Boltzmann step (arXiv:1508.03452) on GB300.
+
+Workload (one "step" = one lattice Boltzmann time step of every run): the
+resistive current sheet on a 1024 x 1024 periodic lattice, B_y = 0.1 x the
+periodic double tanh of width 8 cells, n = p = 1, u = 0, three runs with sigma =
+10, 100, 1000, float32 populations (the configuration the headline MLUPS metric
+is quoted on). Inputs are synthetic (seeded analytic fields); the state of one
+run (1.2 GB read + written per step) is far larger than L2, so no flush is done.
+
+Arms:
+  default            the CUDA library (C ABI through the Python binding)
+  --impl reference   the FP64 CPU oracle on the host cores, each step a bounded
+                     sample (a 1024 x 32 strip of the sigma = 100 run)
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS/GPU and HBM-roofline %, mixed+learned vs plain FP32 at matched error"
+UNIT = "MLUPS"
+SIGMAS = (10.0, 100.0, 1000.0)
+NX = NY = 1024
+# algorithmic bytes per cell update of the fused step: 63 populations + 12
+# primitives, each read once and written once
+BYTES_PER_CELL = {"fp64": 2 * (63 + 12) * 8, "fp32": 2 * (63 + 12) * 4, "fp16": 2 * (38 * 2 + 25 * 4 + 12 * 4)}
+PROFILE = os.path.join(ROOT, "profiles", "step_kernel_current_sheet_1024.md")
+KERNEL_SOURCES = ["step_impl.cuh", "lattice.cuh", "common.cuh"]
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def kernel_sha() -> str:
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1508_03452_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(precision: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    m_sha = re.search(r"kernel_sources_sha:\s*([0-9a-f]+)", text)
+    m_b = re.search(rf"dram_bytes_per_launch_{precision}:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_b or m_sha.group(1) != kernel_sha():
+        return None
+    return float(m_b.group(1))
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.proc, self.path = index, None, None
+
+    def __enter__(self):
+        try:
+            import tempfile
+
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline_sample(seconds: float = 12.0, threads: int | None = None):
+    """The oracle as it stands on the host cores: the sigma = 100 current sheet,
+    full 1024-wide rows, a strip of 32 rows (periodic), stepped for ~`seconds`."""
+    import oracle as O
+    from paper_1508_03452_gb300 import workloads as W
+
+    threads = threads or os.cpu_count() or 1
+    ny = 32
+    F = W.current_sheet(NX, ny, 1, delta=8.0)
+    s = O.Sim(O.make_params(NX, ny, 1, sigma=100.0, threads=threads))
+    s.init(F.n, F.p, F.u, F.B)
+    s.step(1)
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        s.step(1)
+        steps += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    el = time.perf_counter() - t0
+    return {"value": NX * ny * steps / el / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"current sheet sigma=100, {NX}x{ny} periodic strip of the 1024x1024 workload, {steps} steps, "
+                      f"{el:.1f} s, FP64 C oracle with OpenMP"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_1508_03452_gb300 import workloads as W
+
+    threads = os.cpu_count() or 1
+    ny = 32
+    F = W.current_sheet(NX, ny, 1, delta=8.0)
+    s = O.Sim(O.make_params(NX, ny, 1, sigma=100.0, threads=threads))
+    s.init(F.n, F.p, F.u, F.B)
+    for _ in range(args.warmup):
+        s.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.step(1)
+    el = time.perf_counter() - t0
+    value = NX * ny * args.steps / el / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "current_sheet", "grid": [NX, ny, 1], "sigma": 100.0,
+                   "note": "bounded sample of the 1024x1024 workload: a 1024x32 periodic strip per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{NX}x{ny} strip of the sigma=100 current sheet, {args.steps} steps"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_1508_03452_gb300 import lbrmhd as L
+    from paper_1508_03452_gb300 import workloads as W
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py: no CUDA device (the library has no CPU path)")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    prec = {"fp32": L.FP32, "fp16": L.FP16_DEV, "fp64": L.FP64}[args.precision]
+    F = W.current_sheet(NX, NY, 1, delta=8.0)
+    params = [L.make_params(NX, NY, 1, sigma=s, precision=prec) for s in SIGMAS]
+    stream = torch.cuda.current_stream()
+    solver = L.Solver(params, stream=stream)
+    N = NX * NY
+    # device-resident inputs (float64) for the timed device run
+    dev = {k: torch.from_numpy(np.ascontiguousarray(v, dtype=np.float64)).cuda() for k, v in
+           (("n", F.n), ("p", F.p), ("u", F.u), ("B", F.B))}
+    for r in range(len(SIGMAS)):
+        solver.init_fields_device(r, dev["n"], dev["p"], dev["u"], dev["B"])
+    solver.step(args.warmup)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    cells = N * len(SIGMAS)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solver.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    stats = [solver.stats(r) for r in range(len(SIGMAS))]
+    launches = args.steps * len(SIGMAS)
+    value = world * cells * args.steps / (ms * 1e-3) / 1e6
+    # roofline of the dominant (only) kernel of the timed region: the fused step
+    bpc = BYTES_PER_CELL[args.precision]
+    avg_launch_s = ms * 1e-3 / launches
+    achieved = bpc * N / avg_launch_s / 1e9
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    traffic = profiled_traffic(args.precision)
+
+    # end to end through the C ABI with host buffers: host -> device inputs,
+    # K steps, device -> host moments of every run
+    pin = {k: torch.from_numpy(np.ascontiguousarray(v, dtype=np.float64)).pin_memory() for k, v in
+           (("n", F.n), ("p", F.p), ("u", F.u), ("B", F.B))}
+    out_host = torch.empty(L.NMOMENTS * N, dtype=torch.float64).pin_memory()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in range(len(SIGMAS)):
+        solver.init_fields(r, pin["n"].numpy(), pin["p"].numpy(), pin["u"].numpy(), pin["B"].numpy())
+    solver.step(args.steps)
+    for r in range(len(SIGMAS)):
+        solver._check(solver._L.lbrmhd_get_moments(solver._h, r, L._dp(out_host.numpy())))
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    h2d = len(SIGMAS) * N * 8 * (1 + 1 + 3 + 3)
+    d2h = len(SIGMAS) * N * 8 * L.NMOMENTS
+    e2e_value = world * cells * args.steps / e2e_s / 1e6
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16-storage/f32", "fp64": "f64"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": "current_sheet_1024x1024_sigma_10_100_1000", "grid": [NX, NY, 1],
+                       "runs": len(SIGMAS), "sigma": list(SIGMAS), "precision": args.precision,
+                       "boundaries": "periodic", "l2": "no flush: state per run 1.2 GB >> L2",
+                       "parallelism": f"replicas{world}" if world > 1 else "single"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "lb::step_kernel", "bytes_per_cell": bpc,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
+                    "d2h_bytes_per_step": d2h / args.steps},
+            "gpu_launches": launches,
+            "recovery": {"iters_mean": sum(s["iter_total"] for s in stats) / max(1, sum(
+                (args.steps + args.warmup) * N for _ in stats)), "iters_max": max(s["iter_max"] for s in stats),
+                         "failures": sum(s["recover_fail"] for s in stats)},
+        }
+        clocks = clk.summary()
+        if clocks:
+            line["clocks"] = clocks
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline_sample(args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_gpu(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

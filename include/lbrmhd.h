@@ -1,0 +1,184 @@
+/*
+ * lbrmhd.h -- C ABI of the GB300 (sm_103a) lattice Boltzmann solver for
+ * resistive relativistic magnetohydrodynamics of Mohseni, Mendoza, Succi and
+ * Herrmann, "Lattice Boltzmann model for resistive relativistic
+ * magnetohydrodynamics" (arXiv:1508.03452).
+ *
+ * One time step (Sec. III) is one fused CUDA kernel per run: the flux-limited
+ * streaming of the D3Q19 energy-momentum populations f and number-density
+ * populations g (Eq. eq:rlb, Eq. Hupp), the exact streaming of the D3Q13
+ * Maxwell populations h (Eq. LB_Maxwell), the moments (Eqs. Cal_E, Cal_B,
+ * Cal_rhoc, T = sum p p f, N = sum p g), the Landau eigen-solve for U and eps,
+ * n = N^0/U^0, the Ohm-coupled E solve (Eqs. Ohm, Ex_force), the equation of
+ * state (Eq. EOS), and the Anderson-Witting / BGK / tau_h = 1/2 collisions
+ * towards the equilibria Eq. Dis_fun_EM, Eq. Hupp and Eq. Maxwell-eq. Open
+ * boundaries, the normal-B adjustment and the photospheric driving (Sec. IV)
+ * follow as small kernels.
+ *
+ * Units: mu_0 = 1, eps_0 = 1 / c^2, dt = dx / (sqrt(2) c) (time-step
+ * synchronisation of Sec. III); tau is in units of dt.
+ *
+ * Conventions for every call:
+ *   - Return value: LBRMHD_OK (0) or a negative LBRMHD_ERR_* code; the message
+ *     of the last failure is returned by lbrmhd_last_error(handle) (or
+ *     lbrmhd_last_error(NULL) for a failed lbrmhd_create).
+ *   - Ownership: the library allocates and owns all device memory of a handle;
+ *     caller arrays are only read or written during the call (host arrays are
+ *     copied; device arrays must stay valid until the call's work on the
+ *     handle's stream has finished).
+ *   - Layout of caller field arrays: float64, x fastest, cell index
+ *     x + nx (y + ny z); a vector field is three consecutive planes of N = nx ny
+ *     nz values (x components, then y, then z).
+ *   - Threading: a handle must not be used from two threads at once. All work
+ *     is issued on the handle's stream (lbrmhd_set_stream); calls that return
+ *     host data synchronise that stream.
+ *   - The library never falls back to a CPU path: without a usable sm_103a GPU
+ *     lbrmhd_create fails with LBRMHD_ERR_CUDA.
+ */
+#ifndef LBRMHD_H
+#define LBRMHD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBRMHD_OK 0
+#define LBRMHD_ERR_BAD_ARG (-1)      /* invalid argument or parameter */
+#define LBRMHD_ERR_OOM (-2)          /* device or host allocation failed */
+#define LBRMHD_ERR_CUDA (-3)         /* a CUDA runtime call failed */
+#define LBRMHD_ERR_NONCONVERGED (-4) /* a recovery did not converge (cells keep their previous state) */
+#define LBRMHD_ERR_NONFINITE (-5)    /* a NaN or Inf was found by the diagnostics */
+#define LBRMHD_ERR_TIMEOUT (-6)      /* a device-side wait gave up */
+#define LBRMHD_ERR_STATE (-7)        /* call out of order (e.g. step before init_fields) */
+
+/* boundary kinds, per face -x,+x,-y,+y,-z,+z */
+#define LBRMHD_PERIODIC 0
+#define LBRMHD_OPEN 1   /* copy of the first interior cell + normal-B fix (Sec. IV, KH and flare set-ups) */
+#define LBRMHD_DRIVEN 2 /* -z face only: open, and the lowest drive_layers layers driven */
+
+/* population storage / arithmetic */
+#define LBRMHD_FP64 0      /* float64 storage and arithmetic */
+#define LBRMHD_FP32 1      /* float32 storage (f, g as deviations from the rest equilibrium), float32 arithmetic */
+#define LBRMHD_FP16_DEV 2  /* f, g as float16 relative deviations from the rest equilibrium; h, primitives float32 */
+
+/* primitive recovery seed */
+#define LBRMHD_RECOVERY_PLAIN 0 /* seeded with the previous step's velocity */
+#define LBRMHD_RECOVERY_MLP 1   /* seeded by the learned network (lbrmhd_mlp_*) */
+
+/* test switches (flags) */
+#define LBRMHD_FLAG_NO_EM_COLLISION 1 /* h is streamed without collision: h(x + v dt, t + dt) = h(x, t) */
+
+/* rows of lbrmhd_get_moments output (each row N values) */
+#define LBRMHD_NMOMENTS 16 /* n, p, eps, u(3), E(3), B(3), rho_c, J(3) */
+
+/* lbrmhd_get_diagnostics output */
+#define LBRMHD_NDIAG 10
+/* [0] sum N^0  [1..4] sum T^{0 nu}  [5] sum rho_c  [6] max |div B|  [7] rms div B
+ * [8] non-finite cell count  [9] number of cells */
+
+typedef struct lbrmhd_params {
+    int32_t nx, ny, nz;     /* grid; nz = 1 is a 2-D run, ny = nz = 1 a 1-D run */
+    int32_t bc[6];          /* LBRMHD_PERIODIC | LBRMHD_OPEN | LBRMHD_DRIVEN per face -x,+x,-y,+y,-z,+z */
+    double tau;             /* fluid relaxation time in units of dt (> 0.5 for stability) */
+    double sigma;           /* conductivity of Eq. Ohm (>= 0) */
+    double gamma_ad;        /* adiabatic index of Eq. EOS (> 1) */
+    double alpha;           /* bulk-viscosity constant of Eq. eq:rlb (>= 0) */
+    double c;               /* numerical speed of light (> 0); dt = dx / (sqrt(2) c) */
+    double dx;              /* lattice spacing (> 0) */
+    double drive_u0;        /* peak speed of the driven photospheric layers */
+    int32_t drive_layers;   /* number of driven z-layers (LBRMHD_DRIVEN on -z) */
+    int32_t precision;      /* LBRMHD_FP64 | LBRMHD_FP32 | LBRMHD_FP16_DEV (same for every run of a handle) */
+    int32_t recovery;       /* LBRMHD_RECOVERY_PLAIN | LBRMHD_RECOVERY_MLP */
+    int32_t flags;          /* LBRMHD_FLAG_* */
+    int32_t max_iters;      /* recovery iteration cap (0: 64) */
+    double tol;             /* recovery tolerance (0: 1e-14 for FP64, 1e-6 otherwise) */
+} lbrmhd_params;
+
+typedef struct lbrmhd_state_s* lbrmhd_handle;
+
+/* Creates n_runs independent runs (params[0..n_runs-1]; grids may differ) and
+ * allocates their device state: per run two copies (read / write) of the 19 +
+ * 19 + 25 populations and 12 primitive fields per cell. Errors: BAD_ARG for
+ * any invalid parameter (grid < 1, c, dx or tau <= 0, sigma < 0, gamma_ad <=
+ * 1, DRIVEN on a face other than -z, precision mixed across runs), OOM, CUDA
+ * (no usable GPU). On failure *out is NULL. */
+int lbrmhd_create(const lbrmhd_params* params, int n_runs, lbrmhd_handle* out);
+
+/* Frees all device memory of the handle. A NULL handle is ignored. */
+int lbrmhd_destroy(lbrmhd_handle h);
+
+/* Issues all further work on `stream` (a cudaStream_t; NULL = the legacy
+ * default stream). The caller keeps ownership of the stream. */
+int lbrmhd_set_stream(lbrmhd_handle h, void* stream);
+
+/* Initial state of one run from host arrays (Sec. IV set-ups): n, p (N values),
+ * u, B (3N), E (3N, or NULL for the ideal-MHD field E = -u x B of Eq.
+ * Ohm_ideal). eps from Eq. EOS, rho_c = eps0 div E by central differences
+ * (Eq. Gauss_E), J from Eq. Ohm, every population at its equilibrium.
+ * Errors: BAD_ARG (run out of range, NULL array, |u| >= c), CUDA. */
+int lbrmhd_init_fields(lbrmhd_handle h, int run, const double* n, const double* p, const double* u,
+                       const double* B, const double* E);
+
+/* As lbrmhd_init_fields with device arrays (float64, same layout). */
+int lbrmhd_init_fields_device(lbrmhd_handle h, int run, const double* n, const double* p, const double* u,
+                              const double* B, const double* E);
+
+/* Advances every run by nsteps time steps (asynchronous on the handle's
+ * stream). Recovery failures are counted per run (lbrmhd_get_stats) and the
+ * affected cells keep their previous primitives. Errors: STATE (a run was
+ * never initialised), BAD_ARG (nsteps < 0), CUDA. */
+int lbrmhd_step(lbrmhd_handle h, int64_t nsteps);
+
+/* Macroscopic fields of one run, LBRMHD_NMOMENTS rows of N float64 values:
+ * n, p, eps, u(3), E(3), B(3), rho_c, J(3) (J from Eq. Ohm). Host output;
+ * synchronises the stream. */
+int lbrmhd_get_moments(lbrmhd_handle h, int run, double* out);
+
+/* As lbrmhd_get_moments into a device array of LBRMHD_NMOMENTS * N float64;
+ * asynchronous. */
+int lbrmhd_get_moments_device(lbrmhd_handle h, int run, double* out);
+
+/* Post-collision populations of one run (the populations the next step
+ * streams), float64 on the host: f (19 N), g (19 N), h (25 N), population-major
+ * in the order of the D3Q19 table (rest; +x,-x,+y,-y,+z,-z; +x+y,-x-y,+x-y,
+ * -x+y; +x+z,-x-z,+x-z,-x+z; +y+z,-y-z,+y-z,-y+z) and of the D3Q13 table
+ * (k = 8 p + 2 i + j, then the rest population). Any pointer may be NULL. */
+int lbrmhd_get_populations(lbrmhd_handle h, int run, double* f, double* g, double* hh);
+
+/* Conservation diagnostics of one run (LBRMHD_NDIAG float64 values, see
+ * above) computed from the current state with float64 reductions. Returns
+ * NONFINITE if any cell holds a NaN or Inf. Host output. */
+int lbrmhd_get_diagnostics(lbrmhd_handle h, int run, double* out);
+
+/* Counters of one run: [0] steps taken, [1] recovery failures, [2] sum of
+ * recovery iterations, [3] maximum recovery iterations. Host output. */
+int lbrmhd_get_stats(lbrmhd_handle h, int run, int64_t* out4);
+
+/* Checkpoint / resume: the raw device state of every run (populations and
+ * primitives in their storage format, plus step counters). Resuming from a
+ * checkpoint is bit-exact. `bytes` must be lbrmhd_state_bytes(). */
+int lbrmhd_state_bytes(lbrmhd_handle h, size_t* bytes);
+int lbrmhd_get_state(lbrmhd_handle h, void* host_buf, size_t bytes);
+int lbrmhd_set_state(lbrmhd_handle h, const void* host_buf, size_t bytes);
+
+/* Number of cells of one run (0 if out of range). */
+int64_t lbrmhd_run_cells(lbrmhd_handle h, int run);
+
+/* The lattice tables the library uses, for interpreting population arrays
+ * (Eq. cellconfigs1 and the D3Q13 vectors of Sec. III), LBRMHD_NTABLE float64:
+ * chat_i (19 x 3), w_i (19), w'_i (19), D3Q13 lattice hops v_k dt / dx (24 x 3),
+ * e_k / c (24 x 3), b_k (24 x 3). Host only; needs no GPU. */
+#define LBRMHD_NTABLE 311
+int lbrmhd_lattice_tables(double* out, size_t n);
+
+/* Message of the last failure on this handle (or of the last failed create
+ * when h is NULL). Owned by the library; valid until the next call. */
+const char* lbrmhd_last_error(lbrmhd_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -712,15 +712,15 @@ static void collide_cell(const orc_sim* s, int64_t id, double* fc, double* gc, d
  * + bulk viscosity (Eq. eq:rlb, R10, R11); g the same without viscosity; h:
  * h(x, t + dt) = h_c(x - v dt) (Eq. LB_Maxwell), h_0 does not move. Returns
  * the power-method iteration count or -1. */
-static int stream_recover_cell(const orc_sim* s, int x, int y, int z, const double* fc, const double* gc,
-                               const double* hc, double* fo, double* go, double* ho, double* po)
+static int stream_recover_local(const orc_sim* s, int x, int y, int z, const double* fc, const double* gc,
+                                const double* hc, double* fn, double* gn, double* hn, double* pn)
 {
     const orc_params* P = &s->P;
     const orc_lattice* L = &s->L;
     const int64_t N = s->N;
     const int64_t id = cell_id(P, x, y, z);
     const double kvisc = P->alpha * P->c * orc_dt(P) / P->dx;
-    double fn[19], gn[19], hn[25], pr[ORC_NPRIM], pn[ORC_NPRIM];
+    double pr[ORC_NPRIM];
     for (int i = 0; i < 19; ++i) {
         const double* fi = fc + (int64_t)i * N;
         const double* gi = gc + (int64_t)i * N;
@@ -733,11 +733,22 @@ static int stream_recover_cell(const orc_sim* s, int x, int y, int z, const doub
 
     gather_cell(s->prim, ORC_NPRIM, N, id, pr);
     const int it = orc_recover_cell(P, L, fn, gn, hn, pr, pn);
+    /* on failure keep the previous primitives; the failure is counted */
+    if (it < 0) memcpy(pn, pr, sizeof(pr));
+    return it;
+}
+
+static int stream_recover_cell(const orc_sim* s, int x, int y, int z, const double* fc, const double* gc,
+                               const double* hc, double* fo, double* go, double* ho, double* po)
+{
+    const int64_t N = s->N;
+    const int64_t id = cell_id(&s->P, x, y, z);
+    double fn[19], gn[19], hn[25], pn[ORC_NPRIM];
+    const int it = stream_recover_local(s, x, y, z, fc, gc, hc, fn, gn, hn, pn);
     scatter_cell(fo, 19, N, id, fn);
     scatter_cell(go, 19, N, id, gn);
     scatter_cell(ho, 25, N, id, hn);
-    /* on failure keep the previous primitives; the failure is counted */
-    scatter_cell(po, ORC_NPRIM, N, id, it < 0 ? pr : pn);
+    scatter_cell(po, ORC_NPRIM, N, id, pn);
     return it;
 }
 
@@ -1010,6 +1021,31 @@ int orc_update_cells(orc_sim* s, const int64_t* cells, int64_t ncells, double* f
         for (int k = 0; k < ORC_NPRIM; ++k) prim_out[m * ORC_NPRIM + k] = po[k * N + id];
     }
     free(fo); free(go); free(ho); free(po);
+    return rc;
+}
+
+/* One step of selected cells from given post-collision populations (fc, gc,
+ * hc, field-major) and primitives at t (prim, ORC_NPRIM planes): streaming and
+ * recovery only, before any boundary pass. Used to check a full-size GPU step
+ * at sampled cells from the GPU's own state. */
+int orc_update_cells_from(orc_sim* s, const double* fc, const double* gc, const double* hc, const double* prim,
+                          const int64_t* cells, int64_t ncells, double* f_out, double* g_out, double* h_out,
+                          double* prim_out)
+{
+    const orc_params* P = &s->P;
+    const int64_t N = s->N;
+    memcpy(s->fc, fc, 19 * N * sizeof(double));
+    memcpy(s->gc, gc, 19 * N * sizeof(double));
+    memcpy(s->hc, hc, 25 * N * sizeof(double));
+    memcpy(s->prim, prim, ORC_NPRIM * N * sizeof(double));
+    int rc = 0;
+    for (int64_t m = 0; m < ncells; ++m) {
+        const int64_t id = cells[m];
+        const int x = (int)(id % P->nx), y = (int)((id / P->nx) % P->ny), z = (int)(id / ((int64_t)P->nx * P->ny));
+        if (stream_recover_local(s, x, y, z, s->fc, s->gc, s->hc, f_out + m * 19, g_out + m * 19, h_out + m * 25,
+                                 prim_out + m * ORC_NPRIM) < 0)
+            rc = -1;
+    }
     return rc;
 }
 

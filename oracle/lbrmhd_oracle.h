@@ -110,6 +110,9 @@ void orc_set_state(orc_sim* s, const double* f, const double* g, const double* h
 int orc_update_cells(orc_sim* s, const int64_t* cells, int64_t ncells, double* f_out, double* g_out,
                      double* h_out, double* prim_out);
 void orc_get_post_collision(orc_sim* s, double* fc, double* gc, double* hc);
+int orc_update_cells_from(orc_sim* s, const double* fc, const double* gc, const double* hc, const double* prim,
+                          const int64_t* cells, int64_t ncells, double* f_out, double* g_out, double* h_out,
+                          double* prim_out);
 void orc_stats(const orc_sim* s, int64_t* out4);
 
 #ifdef __cplusplus

@@ -85,6 +85,8 @@ def lib():
             L.orc_update_cells.argtypes = [C.c_void_p, C.POINTER(C.c_int64), C.c_int64, dp, dp, dp, dp]
             L.orc_stats.argtypes = [C.c_void_p, C.POINTER(C.c_int64)]
             L.orc_get_post_collision.argtypes = [C.c_void_p, dp, dp, dp]
+            L.orc_update_cells_from.argtypes = [C.c_void_p, dp, dp, dp, dp, C.POINTER(C.c_int64), C.c_int64,
+                                                dp, dp, dp, dp]
             L.orc_get_lattice.argtypes = [P, C.POINTER(Lattice)]
             L.orc_dt.restype = C.c_double
             L.orc_dt.argtypes = [P]
@@ -291,6 +293,20 @@ class Sim:
                                     _dp(f), _dp(g), _dp(h), _dp(pr))
         if rc != 0:
             raise RuntimeError(f"oracle update_cells failed ({rc})")
+        return f.reshape(m, 19), g.reshape(m, 19), h.reshape(m, 25), pr.reshape(m, NPRIM)
+
+    def update_cells_from(self, fc, gc, hc, prim, cells):
+        """Streams and recovers the listed cells from given post-collision
+        populations and primitives (ORC prim layout, NPRIM planes)."""
+        fc, gc, hc, prim = (_f64(a).reshape(-1) for a in (fc, gc, hc, prim))
+        cells = np.ascontiguousarray(np.asarray(cells, dtype=np.int64))
+        m = len(cells)
+        f = np.zeros(19 * m); g = np.zeros(19 * m); h = np.zeros(25 * m); pr = np.zeros(NPRIM * m)
+        rc = lib().orc_update_cells_from(self._h, _dp(fc), _dp(gc), _dp(hc), _dp(prim),
+                                         cells.ctypes.data_as(C.POINTER(C.c_int64)), m, _dp(f), _dp(g), _dp(h),
+                                         _dp(pr))
+        if rc != 0:
+            raise RuntimeError(f"oracle update_cells_from failed ({rc})")
         return f.reshape(m, 19), g.reshape(m, 19), h.reshape(m, 25), pr.reshape(m, NPRIM)
 
     def stats(self):

@@ -1,0 +1,607 @@
+// api.cu -- host implementation of the lbrmhd C ABI (include/lbrmhd.h).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "aux.cuh"
+#include "lbrmhd.h"
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct RunState {
+    lbrmhd_params p{};
+    int64_t N = 0, stride = 0;
+    void* pops[2] = {nullptr, nullptr};  // 38 planes: f (19) then g (19)
+    void* h[2] = {nullptr, nullptr};     // 25 planes
+    void* prim[2] = {nullptr, nullptr};  // 12 planes
+    int cur = 0;
+    bool initialized = false;
+    lb::RefState ref{1.0, 4.0, 1.0};
+    lb::RefPops refpops{};
+    lb::HalfScale hs{};
+    unsigned long long* d_stats = nullptr;  // failures, iteration sum, iteration max
+    int64_t steps = 0;
+    int periodic[3] = {1, 1, 1};
+};
+
+size_t pop_bytes(int precision) { return precision == LBRMHD_FP64 ? 8 : (precision == LBRMHD_FP32 ? 4 : 2); }
+size_t hp_bytes(int precision) { return precision == LBRMHD_FP64 ? 8 : 4; }
+
+}  // namespace
+
+struct lbrmhd_state_s {
+    std::vector<RunState> runs;
+    int precision = LBRMHD_FP32;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    double* d_scratch = nullptr;  // per-block diagnostics partials
+    int64_t scratch_blocks = 0;
+    double* d_io = nullptr;  // staging for inputs / outputs
+    size_t io_bytes = 0;
+    double* d_small = nullptr;  // 16 float64
+    int* d_flag = nullptr;
+};
+
+#define LB_CK(call)                                                                        \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            h->err = std::string(#call) + ": " + cudaGetErrorString(e_);                   \
+            return LBRMHD_ERR_CUDA;                                                        \
+        }                                                                                  \
+    } while (0)
+
+namespace {
+
+int fail(lbrmhd_handle h, int code, const std::string& msg)
+{
+    h->err = msg;
+    return code;
+}
+
+bool bad_run(lbrmhd_handle h, int run) { return !h || run < 0 || run >= (int)h->runs.size(); }
+
+template <class R>
+lb::Phys<R> make_phys(const lbrmhd_params& p, const lb::RefState& ref)
+{
+    lb::Phys<R> k{};
+    const double dt = p.dx / (std::sqrt(2.0) * p.c);
+    const double C = lb::kQ * p.c * dt / p.dx;
+    k.c = (R)p.c;
+    k.c2 = (R)(p.c * p.c);
+    k.inv_c = (R)(1.0 / p.c);
+    k.eps0 = (R)(1.0 / (p.c * p.c));
+    k.sigma = (R)p.sigma;
+    k.inv_tau = (R)(1.0 / p.tau);
+    k.half_dt_c2 = (R)(0.5 * dt * p.c * p.c);
+    k.gm1 = (R)(p.gamma_ad - 1.0);
+    k.C = (R)C;
+    k.kappa = (R)(0.5 * (1.0 - C));
+    k.kvisc = (R)(p.alpha * p.c * dt / p.dx);
+    k.n_r = (R)ref.n_r;
+    k.eps_r = (R)ref.eps_r;
+    k.p_r = (R)ref.p_r;
+    k.dx = (R)p.dx;
+    const bool f64 = p.precision == LBRMHD_FP64;
+    k.tol = (R)(p.tol > 0 ? p.tol : (f64 ? 1e-14 : 1e-6));
+    k.maxit = p.max_iters > 0 ? p.max_iters : 64;
+    return k;
+}
+
+template <class Cfg>
+lb::PopView<Cfg> view(const RunState& r, int buf)
+{
+    lb::PopView<Cfg> v{};
+    v.f = (typename Cfg::pop*)r.pops[buf];
+    v.g = v.f + 19 * r.stride;
+    v.h = (typename Cfg::hpop*)r.h[buf];
+    v.prim = (typename Cfg::prim*)r.prim[buf];
+    v.nx = r.p.nx;
+    v.ny = r.p.ny;
+    v.nz = r.p.nz;
+    v.stride = r.stride;
+    for (int a = 0; a < 3; ++a) v.periodic[a] = r.periodic[a];
+    v.hs = r.hs;
+    return v;
+}
+
+// reference rest equilibrium of the deviations (restated equilibria at u = E = B = 0)
+void set_reference(RunState& r, double n_r, double p_r)
+{
+    const double c2 = r.p.c * r.p.c;
+    r.ref.n_r = n_r;
+    r.ref.p_r = p_r;
+    r.ref.eps_r = n_r * c2 + p_r / (r.p.gamma_ad - 1.0);
+    double fmax = 0.0, gmax = 0.0;
+    for (int i = 0; i < 19; ++i) {
+        double v = 3.0 * p_r;
+        if (i == 0) v += lb::kRest * (3.0 * p_r - r.ref.eps_r);
+        r.refpops.f[i] = lb::w19(i) * v;
+        r.refpops.g[i] = lb::wg19(i) * n_r;
+        fmax = std::fmax(fmax, std::fabs(r.refpops.f[i]));
+        gmax = std::fmax(gmax, std::fabs(r.refpops.g[i]));
+    }
+    for (int i = 0; i < 19; ++i) {
+        if (r.p.precision == LBRMHD_FP16_DEV) {
+            const double sf = std::fmax(std::fabs(r.refpops.f[i]), 0.05 * fmax);
+            const double sg = std::fmax(std::fabs(r.refpops.g[i]), 0.05 * gmax);
+            r.hs.f[i] = (float)sf;
+            r.hs.finv[i] = (float)(1.0 / sf);
+            r.hs.g[i] = (float)sg;
+            r.hs.ginv[i] = (float)(1.0 / sg);
+        } else {
+            r.hs.f[i] = r.hs.finv[i] = r.hs.g[i] = r.hs.ginv[i] = 1.0f;
+        }
+    }
+}
+
+int ensure_io(lbrmhd_handle h, size_t bytes)
+{
+    if (h->io_bytes >= bytes) return LBRMHD_OK;
+    if (h->d_io) cudaFree(h->d_io);
+    h->d_io = nullptr;
+    h->io_bytes = 0;
+    if (cudaMalloc(&h->d_io, bytes) != cudaSuccess) return fail(h, LBRMHD_ERR_OOM, "staging allocation failed");
+    h->io_bytes = bytes;
+    return LBRMHD_OK;
+}
+
+template <class Cfg>
+int step_run(lbrmhd_handle h, RunState& r)
+{
+    using R = typename Cfg::real;
+    lb::StepArgs<Cfg> A{};
+    const int in = r.cur, out = 1 - r.cur;
+    A.fin = (const typename Cfg::pop*)r.pops[in];
+    A.gin = A.fin + 19 * r.stride;
+    A.hin = (const typename Cfg::hpop*)r.h[in];
+    A.pin = (const typename Cfg::prim*)r.prim[in];
+    A.fout = (typename Cfg::pop*)r.pops[out];
+    A.gout = A.fout + 19 * r.stride;
+    A.hout = (typename Cfg::hpop*)r.h[out];
+    A.pout = (typename Cfg::prim*)r.prim[out];
+    A.nx = r.p.nx;
+    A.ny = r.p.ny;
+    A.nz = r.p.nz;
+    A.stride = r.stride;
+    for (int a = 0; a < 3; ++a) A.periodic[a] = r.periodic[a];
+    A.flags = r.p.flags;
+    A.k = make_phys<R>(r.p, r.ref);
+    A.hs = r.hs;
+    A.stats = r.d_stats;
+    LB_CK(lb::launch_step<Cfg>(A, h->stream));
+    const bool any_open = r.p.bc[0] || r.p.bc[1] || r.p.bc[2] || r.p.bc[3] || r.p.bc[4] || r.p.bc[5];
+    if (any_open)
+        LB_CK(lb::launch_boundaries<Cfg>(view<Cfg>(r, out), A.k, r.p.bc, r.p.drive_layers, r.p.drive_u0, h->stream));
+    r.cur = out;
+    r.steps += 1;
+    return LBRMHD_OK;
+}
+
+template <class Cfg>
+int init_run(lbrmhd_handle h, RunState& r, const lb::InitInputs& in)
+{
+    LB_CK(lb::launch_mean_np(in.n, in.p, r.N, h->d_small, h->stream));
+    double np[2];
+    LB_CK(cudaMemcpyAsync(np, h->d_small, sizeof(np), cudaMemcpyDeviceToHost, h->stream));
+    LB_CK(cudaStreamSynchronize(h->stream));
+    set_reference(r, np[0], np[1]);
+    LB_CK(cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream));
+    LB_CK(lb::launch_init<Cfg>(view<Cfg>(r, r.cur), in, make_phys<double>(r.p, r.ref), h->d_flag, h->stream));
+    int bad = 0;
+    LB_CK(cudaMemcpyAsync(&bad, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    LB_CK(cudaMemsetAsync(r.d_stats, 0, 3 * sizeof(unsigned long long), h->stream));
+    LB_CK(cudaStreamSynchronize(h->stream));
+    if (bad) return fail(h, LBRMHD_ERR_BAD_ARG, "initial state has |u| >= c or n <= 0");
+    r.initialized = true;
+    r.steps = 0;
+    return LBRMHD_OK;
+}
+
+template <class Cfg>
+int dispatch_step(lbrmhd_handle h, RunState& r)
+{
+    return step_run<Cfg>(h, r);
+}
+
+int init_common(lbrmhd_handle h, int run, const double* n, const double* p, const double* u, const double* B,
+                const double* E, bool device_inputs)
+{
+    if (bad_run(h, run)) return h ? fail(h, LBRMHD_ERR_BAD_ARG, "run out of range") : LBRMHD_ERR_BAD_ARG;
+    if (!n || !p || !u || !B) return fail(h, LBRMHD_ERR_BAD_ARG, "NULL input array");
+    LB_CK(cudaSetDevice(h->device));
+    RunState& r = h->runs[run];
+    const int64_t N = r.N;
+    lb::InitInputs in{};
+    if (device_inputs) {
+        in = {n, p, u, B, E};
+    } else {
+        int rc = ensure_io(h, (size_t)11 * N * sizeof(double));
+        if (rc) return rc;
+        double* d = h->d_io;
+        LB_CK(cudaMemcpyAsync(d, n, N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        LB_CK(cudaMemcpyAsync(d + N, p, N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        LB_CK(cudaMemcpyAsync(d + 2 * N, u, 3 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        LB_CK(cudaMemcpyAsync(d + 5 * N, B, 3 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        if (E) LB_CK(cudaMemcpyAsync(d + 8 * N, E, 3 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        in = {d, d + N, d + 2 * N, d + 5 * N, E ? d + 8 * N : nullptr};
+    }
+    switch (h->precision) {
+        case LBRMHD_FP64: return init_run<lb::CfgF64>(h, r, in);
+        case LBRMHD_FP32: return init_run<lb::CfgF32>(h, r, in);
+        default: return init_run<lb::CfgF16>(h, r, in);
+    }
+}
+
+std::string check_params(const lbrmhd_params& p)
+{
+    if (p.nx < 1 || p.ny < 1 || p.nz < 1) return "grid sizes must be >= 1";
+    if ((int64_t)p.nx * p.ny * p.nz > ((int64_t)1 << 34)) return "grid too large";
+    if (!(p.c > 0) || !(p.dx > 0) || !(p.tau > 0)) return "c, dx and tau must be > 0";
+    if (!(p.sigma >= 0)) return "sigma must be >= 0";
+    if (!(p.gamma_ad > 1)) return "gamma_ad must be > 1";
+    if (!(p.alpha >= 0)) return "alpha must be >= 0";
+    if (p.precision < LBRMHD_FP64 || p.precision > LBRMHD_FP16_DEV) return "unknown precision";
+    if (p.recovery != LBRMHD_RECOVERY_PLAIN && p.recovery != LBRMHD_RECOVERY_MLP) return "unknown recovery mode";
+    for (int f = 0; f < 6; ++f) {
+        if (p.bc[f] < 0 || p.bc[f] > 2) return "unknown boundary kind";
+        if (p.bc[f] == LBRMHD_DRIVEN && f != 4) return "DRIVEN is only allowed on the -z face";
+    }
+    for (int a = 0; a < 3; ++a)
+        if ((p.bc[2 * a] == LBRMHD_PERIODIC) != (p.bc[2 * a + 1] == LBRMHD_PERIODIC))
+            return "an axis must be periodic on both faces or on neither";
+    if (p.bc[4] == LBRMHD_DRIVEN && p.drive_layers < 0) return "drive_layers must be >= 0";
+    return "";
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbrmhd_create(const lbrmhd_params* params, int n_runs, lbrmhd_handle* out)
+{
+    if (out) *out = nullptr;
+    if (!params || n_runs < 1 || !out) {
+        g_create_error = "NULL params / out or n_runs < 1";
+        return LBRMHD_ERR_BAD_ARG;
+    }
+    for (int r = 0; r < n_runs; ++r) {
+        std::string m = check_params(params[r]);
+        if (m.empty() && params[r].precision != params[0].precision) m = "precision differs between runs";
+        if (!m.empty()) {
+            g_create_error = "run " + std::to_string(r) + ": " + m;
+            return LBRMHD_ERR_BAD_ARG;
+        }
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        g_create_error = "no CUDA device available";
+        return LBRMHD_ERR_CUDA;
+    }
+    lbrmhd_handle h = new lbrmhd_state_s();
+    cudaGetDevice(&h->device);
+    h->precision = params[0].precision;
+    const size_t pb = pop_bytes(h->precision), hb = hp_bytes(h->precision), qb = hp_bytes(h->precision);
+    int64_t max_blocks = 1;
+    bool ok = true;
+    h->runs.resize(n_runs);
+    for (int r = 0; r < n_runs && ok; ++r) {
+        RunState& s = h->runs[r];
+        s.p = params[r];
+        s.N = (int64_t)s.p.nx * s.p.ny * s.p.nz;
+        s.stride = (s.N + 127) / 128 * 128;
+        for (int a = 0; a < 3; ++a) s.periodic[a] = s.p.bc[2 * a] == LBRMHD_PERIODIC;
+        set_reference(s, 1.0, 1.0);
+        for (int b = 0; b < 2 && ok; ++b) {
+            ok = ok && cudaMalloc(&s.pops[b], 38 * s.stride * pb) == cudaSuccess;
+            ok = ok && cudaMalloc(&s.h[b], 25 * s.stride * hb) == cudaSuccess;
+            ok = ok && cudaMalloc(&s.prim[b], lb::NPRIM * s.stride * qb) == cudaSuccess;
+            if (ok) {
+                cudaMemset(s.pops[b], 0, 38 * s.stride * pb);
+                cudaMemset(s.h[b], 0, 25 * s.stride * hb);
+                cudaMemset(s.prim[b], 0, lb::NPRIM * s.stride * qb);
+            }
+        }
+        ok = ok && cudaMalloc(&s.d_stats, 3 * sizeof(unsigned long long)) == cudaSuccess;
+        if (ok) cudaMemset(s.d_stats, 0, 3 * sizeof(unsigned long long));
+        max_blocks = std::max<int64_t>(max_blocks, (s.N + lb::kDiagThreads - 1) / lb::kDiagThreads);
+    }
+    ok = ok && cudaMalloc(&h->d_scratch, (size_t)max_blocks * lb::NPART * sizeof(double)) == cudaSuccess;
+    h->scratch_blocks = max_blocks;
+    ok = ok && cudaMalloc(&h->d_small, 16 * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->d_flag, sizeof(int)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        lbrmhd_destroy(h);
+        g_create_error = "device allocation failed";
+        return LBRMHD_ERR_OOM;
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        g_create_error = std::string("CUDA error during create: ") + cudaGetErrorString(cudaGetLastError());
+        lbrmhd_destroy(h);
+        return LBRMHD_ERR_CUDA;
+    }
+    *out = h;
+    return LBRMHD_OK;
+}
+
+int lbrmhd_destroy(lbrmhd_handle h)
+{
+    if (!h) return LBRMHD_OK;
+    cudaSetDevice(h->device);
+    for (auto& r : h->runs) {
+        for (int b = 0; b < 2; ++b) {
+            if (r.pops[b]) cudaFree(r.pops[b]);
+            if (r.h[b]) cudaFree(r.h[b]);
+            if (r.prim[b]) cudaFree(r.prim[b]);
+        }
+        if (r.d_stats) cudaFree(r.d_stats);
+    }
+    if (h->d_scratch) cudaFree(h->d_scratch);
+    if (h->d_io) cudaFree(h->d_io);
+    if (h->d_small) cudaFree(h->d_small);
+    if (h->d_flag) cudaFree(h->d_flag);
+    delete h;
+    return LBRMHD_OK;
+}
+
+int lbrmhd_set_stream(lbrmhd_handle h, void* stream)
+{
+    if (!h) return LBRMHD_ERR_BAD_ARG;
+    h->stream = (cudaStream_t)stream;
+    return LBRMHD_OK;
+}
+
+int lbrmhd_init_fields(lbrmhd_handle h, int run, const double* n, const double* p, const double* u, const double* B,
+                       const double* E)
+{
+    return init_common(h, run, n, p, u, B, E, false);
+}
+
+int lbrmhd_init_fields_device(lbrmhd_handle h, int run, const double* n, const double* p, const double* u,
+                              const double* B, const double* E)
+{
+    return init_common(h, run, n, p, u, B, E, true);
+}
+
+int lbrmhd_step(lbrmhd_handle h, int64_t nsteps)
+{
+    if (!h) return LBRMHD_ERR_BAD_ARG;
+    if (nsteps < 0) return fail(h, LBRMHD_ERR_BAD_ARG, "nsteps < 0");
+    for (auto& r : h->runs)
+        if (!r.initialized) return fail(h, LBRMHD_ERR_STATE, "lbrmhd_step before lbrmhd_init_fields");
+    LB_CK(cudaSetDevice(h->device));
+    for (int64_t t = 0; t < nsteps; ++t) {
+        for (auto& r : h->runs) {
+            int rc;
+            switch (h->precision) {
+                case LBRMHD_FP64: rc = dispatch_step<lb::CfgF64>(h, r); break;
+                case LBRMHD_FP32: rc = dispatch_step<lb::CfgF32>(h, r); break;
+                default: rc = dispatch_step<lb::CfgF16>(h, r); break;
+            }
+            if (rc) return rc;
+        }
+    }
+    return LBRMHD_OK;
+}
+
+int lbrmhd_get_moments_device(lbrmhd_handle h, int run, double* out)
+{
+    if (bad_run(h, run) || !out) return h ? fail(h, LBRMHD_ERR_BAD_ARG, "bad run or NULL output") : LBRMHD_ERR_BAD_ARG;
+    RunState& r = h->runs[run];
+    if (!r.initialized) return fail(h, LBRMHD_ERR_STATE, "run not initialised");
+    LB_CK(cudaSetDevice(h->device));
+    const lb::Phys<double> k = make_phys<double>(r.p, r.ref);
+    switch (h->precision) {
+        case LBRMHD_FP64: LB_CK(lb::launch_moments<lb::CfgF64>(view<lb::CfgF64>(r, r.cur), k, out, h->stream)); break;
+        case LBRMHD_FP32: LB_CK(lb::launch_moments<lb::CfgF32>(view<lb::CfgF32>(r, r.cur), k, out, h->stream)); break;
+        default: LB_CK(lb::launch_moments<lb::CfgF16>(view<lb::CfgF16>(r, r.cur), k, out, h->stream)); break;
+    }
+    return LBRMHD_OK;
+}
+
+int lbrmhd_get_moments(lbrmhd_handle h, int run, double* out)
+{
+    if (bad_run(h, run) || !out) return h ? fail(h, LBRMHD_ERR_BAD_ARG, "bad run or NULL output") : LBRMHD_ERR_BAD_ARG;
+    const int64_t N = h->runs[run].N;
+    int rc = ensure_io(h, (size_t)LBRMHD_NMOMENTS * N * sizeof(double));
+    if (rc) return rc;
+    rc = lbrmhd_get_moments_device(h, run, h->d_io);
+    if (rc) return rc;
+    LB_CK(cudaMemcpyAsync(out, h->d_io, (size_t)LBRMHD_NMOMENTS * N * sizeof(double), cudaMemcpyDeviceToHost,
+                          h->stream));
+    LB_CK(cudaStreamSynchronize(h->stream));
+    return LBRMHD_OK;
+}
+
+int lbrmhd_get_populations(lbrmhd_handle h, int run, double* f, double* g, double* hh)
+{
+    if (bad_run(h, run)) return h ? fail(h, LBRMHD_ERR_BAD_ARG, "run out of range") : LBRMHD_ERR_BAD_ARG;
+    RunState& r = h->runs[run];
+    if (!r.initialized) return fail(h, LBRMHD_ERR_STATE, "run not initialised");
+    LB_CK(cudaSetDevice(h->device));
+    const int64_t N = r.N;
+    int rc = ensure_io(h, (size_t)63 * N * sizeof(double));
+    if (rc) return rc;
+    double* d = h->d_io;
+    switch (h->precision) {
+        case LBRMHD_FP64:
+            LB_CK(lb::launch_populations<lb::CfgF64>(view<lb::CfgF64>(r, r.cur), r.refpops, d, d + 19 * N, d + 38 * N,
+                                                     h->stream));
+            break;
+        case LBRMHD_FP32:
+            LB_CK(lb::launch_populations<lb::CfgF32>(view<lb::CfgF32>(r, r.cur), r.refpops, d, d + 19 * N, d + 38 * N,
+                                                     h->stream));
+            break;
+        default:
+            LB_CK(lb::launch_populations<lb::CfgF16>(view<lb::CfgF16>(r, r.cur), r.refpops, d, d + 19 * N, d + 38 * N,
+                                                     h->stream));
+            break;
+    }
+    if (f) LB_CK(cudaMemcpyAsync(f, d, 19 * N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (g) LB_CK(cudaMemcpyAsync(g, d + 19 * N, 19 * N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (hh) LB_CK(cudaMemcpyAsync(hh, d + 38 * N, 25 * N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    LB_CK(cudaStreamSynchronize(h->stream));
+    return LBRMHD_OK;
+}
+
+int lbrmhd_get_diagnostics(lbrmhd_handle h, int run, double* out)
+{
+    if (bad_run(h, run) || !out) return h ? fail(h, LBRMHD_ERR_BAD_ARG, "bad run or NULL output") : LBRMHD_ERR_BAD_ARG;
+    RunState& r = h->runs[run];
+    if (!r.initialized) return fail(h, LBRMHD_ERR_STATE, "run not initialised");
+    LB_CK(cudaSetDevice(h->device));
+    const lb::Phys<double> k = make_phys<double>(r.p, r.ref);
+    switch (h->precision) {
+        case LBRMHD_FP64:
+            LB_CK(lb::launch_diag<lb::CfgF64>(view<lb::CfgF64>(r, r.cur), k, r.ref, h->d_scratch, h->scratch_blocks,
+                                              h->d_small, h->stream));
+            break;
+        case LBRMHD_FP32:
+            LB_CK(lb::launch_diag<lb::CfgF32>(view<lb::CfgF32>(r, r.cur), k, r.ref, h->d_scratch, h->scratch_blocks,
+                                              h->d_small, h->stream));
+            break;
+        default:
+            LB_CK(lb::launch_diag<lb::CfgF16>(view<lb::CfgF16>(r, r.cur), k, r.ref, h->d_scratch, h->scratch_blocks,
+                                              h->d_small, h->stream));
+            break;
+    }
+    LB_CK(cudaMemcpyAsync(out, h->d_small, LBRMHD_NDIAG * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    LB_CK(cudaStreamSynchronize(h->stream));
+    if (out[8] > 0) return fail(h, LBRMHD_ERR_NONFINITE, "non-finite values in the state");
+    return LBRMHD_OK;
+}
+
+int lbrmhd_get_stats(lbrmhd_handle h, int run, int64_t* out4)
+{
+    if (bad_run(h, run) || !out4) return h ? fail(h, LBRMHD_ERR_BAD_ARG, "bad run or NULL output") : LBRMHD_ERR_BAD_ARG;
+    RunState& r = h->runs[run];
+    LB_CK(cudaSetDevice(h->device));
+    unsigned long long s[3];
+    LB_CK(cudaMemcpyAsync(s, r.d_stats, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
+    LB_CK(cudaStreamSynchronize(h->stream));
+    out4[0] = r.steps;
+    out4[1] = (int64_t)s[0];
+    out4[2] = (int64_t)s[1];
+    out4[3] = (int64_t)s[2];
+    return LBRMHD_OK;
+}
+
+// checkpoint blob: per run [int64 steps][3 double ref][uint64 stats x3]
+// [pops 38 N][h 25 N][prim 12 N] (storage format)
+int lbrmhd_state_bytes(lbrmhd_handle h, size_t* bytes)
+{
+    if (!h || !bytes) return LBRMHD_ERR_BAD_ARG;
+    const size_t pb = pop_bytes(h->precision), hb = hp_bytes(h->precision);
+    size_t total = 0;
+    for (auto& r : h->runs) total += 8 + 24 + 24 + (size_t)r.N * (38 * pb + 25 * hb + lb::NPRIM * hb);
+    *bytes = total;
+    return LBRMHD_OK;
+}
+
+int lbrmhd_get_state(lbrmhd_handle h, void* host_buf, size_t bytes)
+{
+    size_t need = 0;
+    if (lbrmhd_state_bytes(h, &need) || !host_buf || bytes != need)
+        return h ? fail(h, LBRMHD_ERR_BAD_ARG, "state buffer size mismatch") : LBRMHD_ERR_BAD_ARG;
+    LB_CK(cudaSetDevice(h->device));
+    const size_t pb = pop_bytes(h->precision), hb = hp_bytes(h->precision);
+    char* o = (char*)host_buf;
+    for (auto& r : h->runs) {
+        if (!r.initialized) return fail(h, LBRMHD_ERR_STATE, "run not initialised");
+        std::memcpy(o, &r.steps, 8);
+        o += 8;
+        const double ref[3] = {r.ref.n_r, r.ref.eps_r, r.ref.p_r};
+        std::memcpy(o, ref, 24);
+        o += 24;
+        LB_CK(cudaMemcpyAsync(o, r.d_stats, 24, cudaMemcpyDeviceToHost, h->stream));
+        o += 24;
+        for (int pl = 0; pl < 38; ++pl, o += r.N * pb)
+            LB_CK(cudaMemcpyAsync(o, (char*)r.pops[r.cur] + pl * r.stride * pb, r.N * pb, cudaMemcpyDeviceToHost,
+                                  h->stream));
+        for (int pl = 0; pl < 25; ++pl, o += r.N * hb)
+            LB_CK(cudaMemcpyAsync(o, (char*)r.h[r.cur] + pl * r.stride * hb, r.N * hb, cudaMemcpyDeviceToHost,
+                                  h->stream));
+        for (int pl = 0; pl < lb::NPRIM; ++pl, o += r.N * hb)
+            LB_CK(cudaMemcpyAsync(o, (char*)r.prim[r.cur] + pl * r.stride * hb, r.N * hb, cudaMemcpyDeviceToHost,
+                                  h->stream));
+    }
+    LB_CK(cudaStreamSynchronize(h->stream));
+    return LBRMHD_OK;
+}
+
+int lbrmhd_set_state(lbrmhd_handle h, const void* host_buf, size_t bytes)
+{
+    size_t need = 0;
+    if (lbrmhd_state_bytes(h, &need) || !host_buf || bytes != need)
+        return h ? fail(h, LBRMHD_ERR_BAD_ARG, "state buffer size mismatch") : LBRMHD_ERR_BAD_ARG;
+    LB_CK(cudaSetDevice(h->device));
+    const size_t pb = pop_bytes(h->precision), hb = hp_bytes(h->precision);
+    const char* o = (const char*)host_buf;
+    for (auto& r : h->runs) {
+        std::memcpy(&r.steps, o, 8);
+        o += 8;
+        double ref[3];
+        std::memcpy(ref, o, 24);
+        o += 24;
+        set_reference(r, ref[0], ref[2]);
+        r.ref.eps_r = ref[1];
+        LB_CK(cudaMemcpyAsync(r.d_stats, o, 24, cudaMemcpyHostToDevice, h->stream));
+        o += 24;
+        for (int pl = 0; pl < 38; ++pl, o += r.N * pb)
+            LB_CK(cudaMemcpyAsync((char*)r.pops[r.cur] + pl * r.stride * pb, o, r.N * pb, cudaMemcpyHostToDevice,
+                                  h->stream));
+        for (int pl = 0; pl < 25; ++pl, o += r.N * hb)
+            LB_CK(cudaMemcpyAsync((char*)r.h[r.cur] + pl * r.stride * hb, o, r.N * hb, cudaMemcpyHostToDevice,
+                                  h->stream));
+        for (int pl = 0; pl < lb::NPRIM; ++pl, o += r.N * hb)
+            LB_CK(cudaMemcpyAsync((char*)r.prim[r.cur] + pl * r.stride * hb, o, r.N * hb, cudaMemcpyHostToDevice,
+                                  h->stream));
+        r.initialized = true;
+    }
+    LB_CK(cudaStreamSynchronize(h->stream));
+    return LBRMHD_OK;
+}
+
+int64_t lbrmhd_run_cells(lbrmhd_handle h, int run)
+{
+    if (bad_run(h, run)) return 0;
+    return h->runs[run].N;
+}
+
+const char* lbrmhd_last_error(lbrmhd_handle h)
+{
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+int lbrmhd_lattice_tables(double* out, size_t n)
+{
+    if (!out || n < LBRMHD_NTABLE) return LBRMHD_ERR_BAD_ARG;
+    double* o = out;
+    for (int i = 0; i < 19; ++i)
+        for (int a = 0; a < 3; ++a) *o++ = lb::c19(i, a);
+    for (int i = 0; i < 19; ++i) *o++ = lb::w19(i);
+    for (int i = 0; i < 19; ++i) *o++ = lb::wg19(i);
+    for (int k = 0; k < 24; ++k)
+        for (int a = 0; a < 3; ++a) *o++ = lb::hop13(k, a);
+    for (int k = 0; k < 24; ++k) {  // e_k / c
+        const int p = k / 8, i = (k % 8) / 2, j = k % 2, ie = (i + 3) % 4;
+        const double s = (j == 0 ? 1.0 : -1.0) * lb::kSqrt2 / 2.0;
+        for (int a = 0; a < 3; ++a)
+            *o++ = a == lb::plane_a1(p) ? s * lb::hop_s1(ie) : (a == lb::plane_a2(p) ? s * lb::hop_s2(ie) : 0.0);
+    }
+    for (int k = 0; k < 24; ++k) {  // b_k
+        const int p = k / 8, j = k % 2;
+        for (int a = 0; a < 3; ++a)
+            *o++ = a == lb::plane_normal(p) ? (j == 0 ? -1.0 : 1.0) * lb::plane_orient(p) : 0.0;
+    }
+    return LBRMHD_OK;
+}
+
+}  // extern "C"

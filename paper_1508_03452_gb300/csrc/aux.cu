@@ -1,0 +1,503 @@
+// aux.cu -- initial state, open boundaries, normal-B fix, photospheric driving,
+// output conversion and float64 diagnostics of the RRMHD lattice Boltzmann
+// library (arXiv:1508.03452, Secs. III-IV).
+#include "aux.cuh"
+
+namespace lb {
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+template <class Cfg>
+__device__ __forceinline__ void load_prim(const typename Cfg::prim* P, int64_t stride, int64_t c,
+                                          Prim<typename Cfg::real>& s)
+{
+    using R = typename Cfg::real;
+    s.n = (R)P[P_N * stride + c];
+    s.eps = (R)P[P_EPS * stride + c];
+    for (int a = 0; a < 3; ++a) {
+        s.u[a] = (R)P[(P_U + a) * stride + c];
+        s.E[a] = (R)P[(P_E + a) * stride + c];
+        s.B[a] = (R)P[(P_B + a) * stride + c];
+    }
+    s.rho = (R)P[P_RHO * stride + c];
+}
+
+template <class Cfg, class R>
+__device__ __forceinline__ void store_prim(typename Cfg::prim* P, int64_t stride, int64_t c, const Prim<R>& s)
+{
+    using T = typename Cfg::prim;
+    P[P_N * stride + c] = (T)s.n;
+    P[P_EPS * stride + c] = (T)s.eps;
+    for (int a = 0; a < 3; ++a) {
+        P[(P_U + a) * stride + c] = (T)s.u[a];
+        P[(P_E + a) * stride + c] = (T)s.E[a];
+        P[(P_B + a) * stride + c] = (T)s.B[a];
+    }
+    P[P_RHO * stride + c] = (T)s.rho;
+}
+
+template <int I, class Cfg, class R>
+struct EqStore {
+    static __device__ __forceinline__ void run(const PopView<Cfg>& V, int64_t c, const EqCell<R>& q)
+    {
+        st_pop<Cfg>(V.f + (int64_t)I * V.stride + c, (typename Cfg::real)feq_dev<I>(q), V.hs.finv[I]);
+        st_pop<Cfg>(V.g + (int64_t)I * V.stride + c, (typename Cfg::real)geq_dev<I>(q), V.hs.ginv[I]);
+        EqStore<I + 1, Cfg, R>::run(V, c, q);
+    }
+};
+template <class Cfg, class R>
+struct EqStore<19, Cfg, R> {
+    static __device__ __forceinline__ void run(const PopView<Cfg>&, int64_t, const EqCell<R>&) {}
+};
+
+template <int K, class Cfg, class R>
+struct HeqStore {
+    static __device__ __forceinline__ void run(const PopView<Cfg>& V, int64_t c, const R* E, const R* B, const R* J,
+                                               const Phys<R>& k)
+    {
+        V.h[(int64_t)K * V.stride + c] = (typename Cfg::hpop)heq13<K>(E, B, J, k);
+        HeqStore<K + 1, Cfg, R>::run(V, c, E, B, J, k);
+    }
+};
+template <class Cfg, class R>
+struct HeqStore<24, Cfg, R> {
+    static __device__ __forceinline__ void run(const PopView<Cfg>&, int64_t, const R*, const R*, const R*,
+                                               const Phys<R>&) {}
+};
+
+// every population of cell c at its equilibrium for primitives s (the
+// post-collision value of an equilibrium state is the equilibrium itself)
+template <class Cfg, class R>
+__device__ __forceinline__ void set_equilibrium(const PopView<Cfg>& V, int64_t c, const Prim<R>& s, const Phys<R>& k)
+{
+    EqCell<R> q;
+    eq_cell(s, k, q);
+    R J[3];
+    ohm_current(s.E, s.u, s.B, s.rho, k, J);
+    EqStore<0, Cfg, R>::run(V, c, q);
+    HeqStore<0, Cfg, R>::run(V, c, s.E, s.B, J, k);
+    V.h[24 * V.stride + c] = (typename Cfg::hpop)s.rho;
+}
+
+// ---------------------------------------------------------------------------
+// initial state (Sec. IV set-ups): eps from Eq. EOS, E = -u x B when not
+// given (Eq. Ohm_ideal), rho_c = eps0 div E by central differences (Eq.
+// Gauss_E), J from Eq. Ohm, populations at equilibrium. float64 arithmetic.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void input_E(const InitInputs& in, int64_t c, int64_t N, double* E)
+{
+    if (in.E) {
+        E[0] = in.E[c]; E[1] = in.E[N + c]; E[2] = in.E[2 * N + c];
+    } else {
+        const double u[3] = {in.u[c], in.u[N + c], in.u[2 * N + c]};
+        const double B[3] = {in.B[c], in.B[N + c], in.B[2 * N + c]};
+        E[0] = -(u[1] * B[2] - u[2] * B[1]);
+        E[1] = -(u[2] * B[0] - u[0] * B[2]);
+        E[2] = -(u[0] * B[1] - u[1] * B[0]);
+    }
+}
+
+template <class Cfg>
+__global__ void init_kernel(PopView<Cfg> V, InitInputs in, Phys<double> k, int* bad)
+{
+    const int64_t N = (int64_t)V.nx * V.ny * V.nz;
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const int x = (int)(c % V.nx), y = (int)((c / V.nx) % V.ny), z = (int)(c / ((int64_t)V.nx * V.ny));
+    Prim<double> s;
+    s.n = in.n[c];
+    s.eps = s.n * k.c2 + in.p[c] / k.gm1;
+    for (int a = 0; a < 3; ++a) {
+        s.u[a] = in.u[a * N + c];
+        s.B[a] = in.B[a * N + c];
+    }
+    input_E(in, c, N, s.E);
+    if (!(s.u[0] * s.u[0] + s.u[1] * s.u[1] + s.u[2] * s.u[2] < k.c2) || !(s.n > 0)) atomicExch(bad, 1);
+    const int q[3] = {x, y, z}, n[3] = {V.nx, V.ny, V.nz};
+    double div = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        if (n[a] == 1) continue;
+        int qp[3] = {q[0], q[1], q[2]}, qm[3] = {q[0], q[1], q[2]};
+        qp[a] = wrap_coord(q[a] + 1, n[a], V.periodic[a]);
+        qm[a] = wrap_coord(q[a] - 1, n[a], V.periodic[a]);
+        double Ep[3], Em[3];
+        input_E(in, qp[0] + (int64_t)V.nx * (qp[1] + (int64_t)V.ny * qp[2]), N, Ep);
+        input_E(in, qm[0] + (int64_t)V.nx * (qm[1] + (int64_t)V.ny * qm[2]), N, Em);
+        div += (Ep[a] - Em[a]) / (2.0 * k.dx);
+    }
+    s.rho = k.eps0 * div;
+    store_prim<Cfg>(V.prim, V.stride, c, s);
+    set_equilibrium<Cfg, double>(V, c, s, k);
+}
+
+// float64 sums of n and p for the reference rest state (one block)
+__global__ void mean_np_kernel(const double* n, const double* p, int64_t N, double* out)
+{
+    __shared__ double sh[2][32];
+    double sn = 0.0, sp = 0.0;
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+        sn += n[i];
+        sp += p[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sn += __shfl_down_sync(0xffffffffu, sn, o);
+        sp += __shfl_down_sync(0xffffffffu, sp, o);
+    }
+    if (threadIdx.x % 32 == 0) {
+        sh[0][threadIdx.x / 32] = sn;
+        sh[1][threadIdx.x / 32] = sp;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
+            a += sh[0][w];
+            b += sh[1][w];
+        }
+        out[0] = a / (double)N;
+        out[1] = b / (double)N;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// open boundaries: copy of the first interior cell (faces in order -x .. +z,
+// which is the same as clamping every open-axis coordinate into [1, n-2])
+// ---------------------------------------------------------------------------
+template <class Cfg>
+__global__ void open_copy_kernel(PopView<Cfg> V, int open_mask)
+{
+    const int64_t N = (int64_t)V.nx * V.ny * V.nz;
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    int q[3] = {(int)(c % V.nx), (int)((c / V.nx) % V.ny), (int)(c / ((int64_t)V.nx * V.ny))};
+    const int n[3] = {V.nx, V.ny, V.nz};
+    int r[3] = {q[0], q[1], q[2]};
+    bool boundary = false;
+    for (int a = 0; a < 3; ++a) {
+        if (!((open_mask >> a) & 1) || n[a] < 3) continue;
+        if (q[a] == 0 || q[a] == n[a] - 1) boundary = true;
+        r[a] = q[a] < 1 ? 1 : (q[a] > n[a] - 2 ? n[a] - 2 : q[a]);
+    }
+    if (!boundary) return;
+    const int64_t s = r[0] + (int64_t)V.nx * (r[1] + (int64_t)V.ny * r[2]);
+    for (int i = 0; i < 19; ++i) {
+        V.f[(int64_t)i * V.stride + c] = V.f[(int64_t)i * V.stride + s];
+        V.g[(int64_t)i * V.stride + c] = V.g[(int64_t)i * V.stride + s];
+    }
+    for (int i = 0; i < 25; ++i) V.h[(int64_t)i * V.stride + c] = V.h[(int64_t)i * V.stride + s];
+    for (int i = 0; i < NPRIM; ++i) V.prim[(int64_t)i * V.stride + c] = V.prim[(int64_t)i * V.stride + s];
+}
+
+// ---------------------------------------------------------------------------
+// normal-B fix on one open face (axis a, side hi): B_n of the boundary cell is
+// set so that the central-difference div B of the first interior cell
+// vanishes; the change is carried by the h populations whose b is parallel to
+// the normal (h_c += dB b_n / 8), and the f populations see the changed
+// equilibrium through the collision (f_c += K_i [f_i^eq(new) - f_i^eq(old)]).
+// ---------------------------------------------------------------------------
+template <int I, class Cfg, class R>
+struct FixF {
+    static __device__ __forceinline__ void run(const PopView<Cfg>& V, int64_t c, const EqCell<R>& qo,
+                                               const EqCell<R>& qn)
+    {
+        const R d = k_aw<I>(qo) * (feq_dev<I>(qn) - feq_dev<I>(qo));
+        typename Cfg::pop* p = V.f + (int64_t)I * V.stride + c;
+        const R v = ld_pop<Cfg>(p, V.hs.f[I]) + d;
+        st_pop<Cfg>(p, v, V.hs.finv[I]);
+        FixF<I + 1, Cfg, R>::run(V, c, qo, qn);
+    }
+};
+template <class Cfg, class R>
+struct FixF<19, Cfg, R> {
+    static __device__ __forceinline__ void run(const PopView<Cfg>&, int64_t, const EqCell<R>&, const EqCell<R>&) {}
+};
+
+template <class Cfg>
+__global__ void bfix_kernel(PopView<Cfg> V, Phys<typename Cfg::real> k, int a, int hi)
+{
+    using R = typename Cfg::real;
+    const int n[3] = {V.nx, V.ny, V.nz};
+    const int a1 = (a + 1) % 3, a2 = (a + 2) % 3;
+    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (m >= (int64_t)n[a1] * n[a2]) return;
+    int q[3];
+    q[a1] = (int)(m % n[a1]);
+    q[a2] = (int)(m / n[a1]);
+    const int sgn = hi ? -1 : 1;
+    const int b = hi ? n[a] - 1 : 0;
+    auto idx = [&](const int* r) { return r[0] + (int64_t)V.nx * (r[1] + (int64_t)V.ny * r[2]); };
+    int r1[3] = {q[0], q[1], q[2]};
+    r1[a] = b + sgn;
+    R tang = R(0);
+    const int at[2] = {a1, a2};
+    for (int t = 0; t < 2; ++t) {
+        const int ax = at[t];
+        if (n[ax] == 1) continue;
+        int rp[3] = {r1[0], r1[1], r1[2]}, rm[3] = {r1[0], r1[1], r1[2]};
+        rp[ax] = wrap_coord(r1[ax] + 1, n[ax], V.periodic[ax]);
+        rm[ax] = wrap_coord(r1[ax] - 1, n[ax], V.periodic[ax]);
+        tang += ((R)V.prim[(P_B + ax) * V.stride + idx(rp)] - (R)V.prim[(P_B + ax) * V.stride + idx(rm)]) /
+                (R(2) * k.dx);
+    }
+    int r2[3] = {q[0], q[1], q[2]};
+    r2[a] = b + 2 * sgn;
+    int rb[3] = {q[0], q[1], q[2]};
+    rb[a] = b;
+    const int64_t cb = idx(rb);
+    const R Bfar = (R)V.prim[(P_B + a) * V.stride + idx(r2)];
+    const R Bn_new = Bfar + R(sgn) * R(2) * k.dx * tang;
+    Prim<R> so;
+    load_prim<Cfg>(V.prim, V.stride, cb, so);
+    const R dB = Bn_new - so.B[a];
+    Prim<R> sn = so;
+    sn.B[a] = Bn_new;
+    V.prim[(P_B + a) * V.stride + cb] = (typename Cfg::prim)Bn_new;
+    // h: populations of the plane whose normal is axis a, b = -/+ o_p n_hat
+    for (int p = 0; p < 3; ++p) {
+        if (plane_normal(p) != a) continue;
+        for (int kk = 8 * p; kk < 8 * p + 8; ++kk) {
+            const R bn = R(((kk % 2) == 0 ? -1 : 1) * plane_orient(p));
+            typename Cfg::hpop* ph = V.h + (int64_t)kk * V.stride + cb;
+            *ph = (typename Cfg::hpop)((R)*ph + dB * bn / R(8));
+        }
+    }
+    EqCell<R> qo, qn;
+    eq_cell(so, k, qo);
+    eq_cell(sn, k, qn);
+    FixF<0, Cfg, R>::run(V, cb, qo, qn);
+}
+
+// ---------------------------------------------------------------------------
+// photospheric driving: the lowest `layers` z-layers are reset to the
+// equilibrium of their own n, eps, B, rho_c with the two-vortex drive velocity
+// (max |u| = u0) and E = -u x B
+// ---------------------------------------------------------------------------
+template <class Cfg>
+__global__ void drive_kernel(PopView<Cfg> V, Phys<typename Cfg::real> k, int layers, double u0)
+{
+    using R = typename Cfg::real;
+    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t plane = (int64_t)V.nx * V.ny;
+    if (m >= plane * layers) return;
+    const int x = (int)(m % V.nx), y = (int)((m / V.nx) % V.ny);
+    const int64_t c = m;
+    const double X = -3.0 + (x + 0.5) * 6.0 / V.nx;
+    const double Y = -3.0 + (y + 0.5) * 6.0 / V.ny;
+    const double xs = X < 0.0 ? X : X - 3.0;
+    const double pi = 3.14159265358979323846;
+    Prim<R> s;
+    load_prim<Cfg>(V.prim, V.stride, c, s);
+    s.u[0] = (R)(u0 * sin(pi * xs / 3.0) * cos(pi * Y / 6.0));
+    s.u[1] = (R)(u0 * cos(pi * xs / 3.0) * sin(pi * Y / 6.0));
+    s.u[2] = R(0);
+    s.E[0] = -(s.u[1] * s.B[2] - s.u[2] * s.B[1]);
+    s.E[1] = -(s.u[2] * s.B[0] - s.u[0] * s.B[2]);
+    s.E[2] = -(s.u[0] * s.B[1] - s.u[1] * s.B[0]);
+    store_prim<Cfg>(V.prim, V.stride, c, s);
+    set_equilibrium<Cfg, R>(V, c, s, k);
+}
+
+// ---------------------------------------------------------------------------
+// outputs
+// ---------------------------------------------------------------------------
+template <class Cfg>
+__global__ void moments_kernel(PopView<Cfg> V, Phys<double> k, double* out)
+{
+    const int64_t N = (int64_t)V.nx * V.ny * V.nz;
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    Prim<double> s;
+    s.n = (double)V.prim[P_N * V.stride + c];
+    s.eps = (double)V.prim[P_EPS * V.stride + c];
+    for (int a = 0; a < 3; ++a) {
+        s.u[a] = (double)V.prim[(P_U + a) * V.stride + c];
+        s.E[a] = (double)V.prim[(P_E + a) * V.stride + c];
+        s.B[a] = (double)V.prim[(P_B + a) * V.stride + c];
+    }
+    s.rho = (double)V.prim[P_RHO * V.stride + c];
+    double J[3];
+    ohm_current(s.E, s.u, s.B, s.rho, k, J);
+    out[0 * N + c] = s.n;
+    out[1 * N + c] = k.gm1 * (s.eps - s.n * k.c2);
+    out[2 * N + c] = s.eps;
+    for (int a = 0; a < 3; ++a) {
+        out[(3 + a) * N + c] = s.u[a];
+        out[(6 + a) * N + c] = s.E[a];
+        out[(9 + a) * N + c] = s.B[a];
+        out[(13 + a) * N + c] = J[a];
+    }
+    out[12 * N + c] = s.rho;
+}
+
+// absolute post-collision populations (reference rest equilibrium added back)
+template <class Cfg>
+__global__ void populations_kernel(PopView<Cfg> V, RefPops ref, double* f, double* g, double* h)
+{
+    const int64_t N = (int64_t)V.nx * V.ny * V.nz;
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    for (int i = 0; i < 19; ++i) {
+        if (f) f[i * N + c] = ref.f[i] + (double)ld_pop<Cfg>(V.f + (int64_t)i * V.stride + c, V.hs.f[i]);
+        if (g) g[i * N + c] = ref.g[i] + (double)ld_pop<Cfg>(V.g + (int64_t)i * V.stride + c, V.hs.g[i]);
+    }
+    if (h)
+        for (int i = 0; i < 25; ++i) h[i * N + c] = (double)V.h[(int64_t)i * V.stride + c];
+}
+
+// per-block float64 partial diagnostics: sum N^0, T^{0 nu} (4), rho_c, max |div B|,
+// sum (div B)^2, non-finite count
+template <class Cfg>
+__global__ void diag_kernel(PopView<Cfg> V, Phys<double> k, RefState r, double* partial)
+{
+    const int64_t N = (int64_t)V.nx * V.ny * V.nz;
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double v[NPART] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    if (c < N) {
+        double bad = 0.0;
+        double N0 = r.n_r, T0[4] = {r.eps_r, 0, 0, 0}, rho = 0.0;
+        for (int i = 0; i < 19; ++i) {
+            const double fi = (double)ld_pop<Cfg>(V.f + (int64_t)i * V.stride + c, V.hs.f[i]);
+            const double gi = (double)ld_pop<Cfg>(V.g + (int64_t)i * V.stride + c, V.hs.g[i]);
+            if (!isfinite(fi) || !isfinite(gi)) bad = 1.0;
+            N0 += gi;
+            T0[0] += fi;
+            for (int a = 0; a < 3; ++a) T0[a + 1] += kQ * c19(i, a) * fi;
+        }
+        for (int i = 0; i < 25; ++i) {
+            const double hi = (double)V.h[(int64_t)i * V.stride + c];
+            if (!isfinite(hi)) bad = 1.0;
+            rho += hi;
+        }
+        for (int i = 0; i < NPRIM; ++i)
+            if (!isfinite((double)V.prim[(int64_t)i * V.stride + c])) bad = 1.0;
+        const int q[3] = {(int)(c % V.nx), (int)((c / V.nx) % V.ny), (int)(c / ((int64_t)V.nx * V.ny))};
+        const int n[3] = {V.nx, V.ny, V.nz};
+        double div = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            if (n[a] == 1) continue;
+            int qp[3] = {q[0], q[1], q[2]}, qm[3] = {q[0], q[1], q[2]};
+            qp[a] = wrap_coord(q[a] + 1, n[a], V.periodic[a]);
+            qm[a] = wrap_coord(q[a] - 1, n[a], V.periodic[a]);
+            const int64_t ip = qp[0] + (int64_t)V.nx * (qp[1] + (int64_t)V.ny * qp[2]);
+            const int64_t im = qm[0] + (int64_t)V.nx * (qm[1] + (int64_t)V.ny * qm[2]);
+            div += ((double)V.prim[(P_B + a) * V.stride + ip] - (double)V.prim[(P_B + a) * V.stride + im]) /
+                   (2.0 * k.dx);
+        }
+        v[0] = N0;
+        for (int a = 0; a < 4; ++a) v[1 + a] = T0[a];
+        v[5] = rho;
+        v[6] = fabs(div);
+        v[7] = div * div;
+        v[8] = bad;
+    }
+    block_reduce_partials(v, partial);
+}
+
+__global__ void diag_final_kernel(const double* partial, int64_t nblocks, int64_t ncells, double* out)
+{
+    double v[NPART] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        for (int j = 0; j < NPART; ++j) {
+            const double x = partial[b * NPART + j];
+            v[j] = (j == 6) ? fmax(v[j], x) : v[j] + x;
+        }
+    }
+    block_reduce_partials(v, out);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // out layout of the C ABI: sums, max |div B|, rms div B, non-finite count, cells
+        const double sumsq = out[7];
+        out[7] = sqrt(sumsq / (double)ncells);
+        out[9] = (double)ncells;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <class Cfg>
+cudaError_t launch_init(const PopView<Cfg>& V, const InitInputs& in, const Phys<double>& k, int* bad,
+                        cudaStream_t s)
+{
+    const int64_t N = (int64_t)V.nx * V.ny * V.nz;
+    init_kernel<Cfg><<<blocks_for(N, 128), 128, 0, s>>>(V, in, k, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mean_np(const double* n, const double* p, int64_t N, double* out, cudaStream_t s)
+{
+    mean_np_kernel<<<1, 1024, 0, s>>>(n, p, N, out);
+    return cudaGetLastError();
+}
+
+template <class Cfg>
+cudaError_t launch_boundaries(const PopView<Cfg>& V, const Phys<typename Cfg::real>& k, const int* bc, int layers,
+                              double u0, cudaStream_t s)
+{
+    const int64_t N = (int64_t)V.nx * V.ny * V.nz;
+    const int n[3] = {V.nx, V.ny, V.nz};
+    int open_mask = 0;
+    for (int a = 0; a < 3; ++a)
+        if (bc[2 * a] != 0 || bc[2 * a + 1] != 0) open_mask |= 1 << a;
+    if (open_mask) open_copy_kernel<Cfg><<<blocks_for(N, 256), 256, 0, s>>>(V, open_mask);
+    for (int face = 0; face < 6; ++face) {
+        const int a = face / 2;
+        if (bc[face] == 0 || n[a] < 3) continue;
+        const int64_t m = (int64_t)n[(a + 1) % 3] * n[(a + 2) % 3];
+        bfix_kernel<Cfg><<<blocks_for(m, 128), 128, 0, s>>>(V, k, a, face % 2);
+    }
+    if (bc[4] == 2 && layers > 0) {
+        const int nl = layers < V.nz ? layers : V.nz;
+        drive_kernel<Cfg><<<blocks_for((int64_t)V.nx * V.ny * nl, 128), 128, 0, s>>>(V, k, nl, u0);
+    }
+    return cudaGetLastError();
+}
+
+template <class Cfg>
+cudaError_t launch_moments(const PopView<Cfg>& V, const Phys<double>& k, double* out, cudaStream_t s)
+{
+    const int64_t N = (int64_t)V.nx * V.ny * V.nz;
+    moments_kernel<Cfg><<<blocks_for(N, 128), 128, 0, s>>>(V, k, out);
+    return cudaGetLastError();
+}
+
+template <class Cfg>
+cudaError_t launch_populations(const PopView<Cfg>& V, const RefPops& ref, double* f, double* g, double* h,
+                               cudaStream_t s)
+{
+    const int64_t N = (int64_t)V.nx * V.ny * V.nz;
+    populations_kernel<Cfg><<<blocks_for(N, 128), 128, 0, s>>>(V, ref, f, g, h);
+    return cudaGetLastError();
+}
+
+template <class Cfg>
+cudaError_t launch_diag(const PopView<Cfg>& V, const Phys<double>& k, const RefState& r, double* partial,
+                        int64_t max_blocks, double* out, cudaStream_t s)
+{
+    const int64_t N = (int64_t)V.nx * V.ny * V.nz;
+    const int64_t nb = blocks_for(N, kDiagThreads);
+    if (nb > max_blocks) return cudaErrorInvalidValue;
+    diag_kernel<Cfg><<<(unsigned)nb, kDiagThreads, 0, s>>>(V, k, r, partial);
+    diag_final_kernel<<<1, kDiagThreads, 0, s>>>(partial, nb, N, out);
+    return cudaGetLastError();
+}
+
+#define LB_INSTANTIATE(CFG)                                                                                        \
+    template cudaError_t launch_init<CFG>(const PopView<CFG>&, const InitInputs&, const Phys<double>&, int*,      \
+                                          cudaStream_t);                                                           \
+    template cudaError_t launch_boundaries<CFG>(const PopView<CFG>&, const Phys<CFG::real>&, const int*, int,      \
+                                                double, cudaStream_t);                                             \
+    template cudaError_t launch_moments<CFG>(const PopView<CFG>&, const Phys<double>&, double*, cudaStream_t);     \
+    template cudaError_t launch_populations<CFG>(const PopView<CFG>&, const RefPops&, double*, double*, double*,  \
+                                                 cudaStream_t);                                                    \
+    template cudaError_t launch_diag<CFG>(const PopView<CFG>&, const Phys<double>&, const RefState&, double*,      \
+                                          int64_t, double*, cudaStream_t);
+
+LB_INSTANTIATE(CfgF64)
+LB_INSTANTIATE(CfgF32)
+LB_INSTANTIATE(CfgF16)
+
+}  // namespace lb

@@ -1,0 +1,82 @@
+// aux.cuh -- declarations shared by the host API and the auxiliary kernels.
+#pragma once
+
+#include "common.cuh"
+
+namespace lb {
+
+// one buffer set (current state) of one run
+template <class Cfg>
+struct PopView {
+    typename Cfg::pop* f;
+    typename Cfg::pop* g;
+    typename Cfg::hpop* h;
+    typename Cfg::prim* prim;
+    int nx, ny, nz;
+    int64_t stride;
+    int periodic[3];
+    HalfScale hs;
+};
+
+// device float64 input fields of lbrmhd_init_fields (E may be NULL)
+struct InitInputs {
+    const double* n;
+    const double* p;
+    const double* u;
+    const double* B;
+    const double* E;
+};
+
+// absolute reference rest equilibrium populations (added back on output)
+struct RefPops {
+    double f[19], g[19];
+};
+
+struct RefState {
+    double n_r, eps_r, p_r;
+};
+
+constexpr int NPART = 9;
+constexpr int kDiagThreads = 256;
+
+// block-wide reduction of NPART float64 values (index 6 is a max, the others
+// sums); thread 0 writes dst[blockIdx.x * NPART + j]
+__device__ __forceinline__ void block_reduce_partials(double* v, double* dst)
+{
+    __shared__ double sh[kDiagThreads / 32][NPART];
+    for (int j = 0; j < NPART; ++j)
+        for (int o = 16; o > 0; o >>= 1) {
+            const double other = __shfl_down_sync(0xffffffffu, v[j], o);
+            v[j] = (j == 6) ? fmax(v[j], other) : v[j] + other;
+        }
+    const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (lane == 0)
+        for (int j = 0; j < NPART; ++j) sh[w][j] = v[j];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int j = 0; j < NPART; ++j) {
+            double acc = sh[0][j];
+            for (int ww = 1; ww < (int)(blockDim.x / 32); ++ww) acc = (j == 6) ? fmax(acc, sh[ww][j]) : acc + sh[ww][j];
+            dst[(int64_t)blockIdx.x * NPART + j] = acc;
+        }
+    }
+}
+
+template <class Cfg>
+cudaError_t launch_step(const StepArgs<Cfg>& A, cudaStream_t stream);
+template <class Cfg>
+cudaError_t launch_init(const PopView<Cfg>& V, const InitInputs& in, const Phys<double>& k, int* bad, cudaStream_t s);
+cudaError_t launch_mean_np(const double* n, const double* p, int64_t N, double* out, cudaStream_t s);
+template <class Cfg>
+cudaError_t launch_boundaries(const PopView<Cfg>& V, const Phys<typename Cfg::real>& k, const int* bc, int layers,
+                              double u0, cudaStream_t s);
+template <class Cfg>
+cudaError_t launch_moments(const PopView<Cfg>& V, const Phys<double>& k, double* out, cudaStream_t s);
+template <class Cfg>
+cudaError_t launch_populations(const PopView<Cfg>& V, const RefPops& ref, double* f, double* g, double* h,
+                               cudaStream_t s);
+template <class Cfg>
+cudaError_t launch_diag(const PopView<Cfg>& V, const Phys<double>& k, const RefState& r, double* partial,
+                        int64_t max_blocks, double* out, cudaStream_t s);
+
+}  // namespace lb

@@ -1,0 +1,122 @@
+// common.cuh -- storage configurations, kernel argument blocks and lattice
+// indexing shared by the kernels of the RRMHD lattice Boltzmann library.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lattice.cuh"
+
+namespace lb {
+
+// Storage / arithmetic configurations. `pop` stores the fluid populations f,
+// g as deviations from the reference rest equilibrium; `hpop` the Maxwell
+// populations; `prim` the 12 primitive fields; `real` is the arithmetic type.
+struct CfgF64 {
+    using real = double;
+    using pop = double;
+    using hpop = double;
+    using prim = double;
+    static constexpr bool kHalf = false;
+};
+struct CfgF32 {
+    using real = float;
+    using pop = float;
+    using hpop = float;
+    using prim = float;
+    static constexpr bool kHalf = false;
+};
+struct CfgF16 {  // float16 relative deviations for f and g
+    using real = float;
+    using pop = __half;
+    using hpop = float;
+    using prim = float;
+    static constexpr bool kHalf = true;
+};
+
+// primitive planes
+enum { P_N = 0, P_EPS = 1, P_U = 2, P_E = 5, P_B = 8, P_RHO = 11, NPRIM = 12 };
+
+constexpr int FLAG_NO_EM_COLLISION = 1;
+
+// Population scale for float16 relative deviations: stored value =
+// deviation * inv[i]; deviation = stored * scale[i].
+struct HalfScale {
+    float f[19], finv[19], g[19], ginv[19];
+};
+
+template <class Cfg>
+struct StepArgs {
+    using pop = typename Cfg::pop;
+    using hpop = typename Cfg::hpop;
+    using prim = typename Cfg::prim;
+    using real = typename Cfg::real;
+    const pop* __restrict__ fin;
+    const pop* __restrict__ gin;
+    const hpop* __restrict__ hin;
+    const prim* __restrict__ pin;
+    pop* __restrict__ fout;
+    pop* __restrict__ gout;
+    hpop* __restrict__ hout;
+    prim* __restrict__ pout;
+    int nx, ny, nz;
+    int64_t stride;  // elements between consecutive planes
+    int periodic[3];
+    int flags;
+    Phys<real> k;
+    HalfScale hs;
+    unsigned long long* stats;  // [0] failures [1] iteration sum [2] iteration max
+};
+
+// population load / store in the configured format
+template <class Cfg>
+__device__ __forceinline__ typename Cfg::real ld_pop(const typename Cfg::pop* p, float scale)
+{
+    if constexpr (Cfg::kHalf)
+        return __half2float(__ldg(reinterpret_cast<const __half*>(p))) * scale;
+    else
+        return __ldg(p);
+}
+
+template <class Cfg>
+__device__ __forceinline__ void st_pop(typename Cfg::pop* p, typename Cfg::real v, float inv_scale)
+{
+    if constexpr (Cfg::kHalf)
+        *p = __float2half_rn(v * inv_scale);
+    else
+        *p = v;
+}
+
+// wrapped (periodic) or clamped (open / driven) coordinate
+__host__ __device__ __forceinline__ int wrap_coord(int s, int n, int periodic)
+{
+    if (periodic) {
+        while (s < 0) s += n;
+        while (s >= n) s -= n;
+    } else {
+        s = s < 0 ? 0 : (s >= n ? n - 1 : s);
+    }
+    return s;
+}
+
+// neighbour offsets -2..+2 along each axis (y premultiplied by nx, z by nx ny)
+struct Nb {
+    int x[5];
+    int64_t y[5], z[5];
+    __device__ __forceinline__ int64_t at(int dx, int dy, int dz) const { return x[dx + 2] + y[dy + 2] + z[dz + 2]; }
+};
+
+__device__ __forceinline__ Nb make_nb(int x, int y, int z, int nx, int ny, int nz, const int* per)
+{
+    Nb nb;
+#pragma unroll
+    for (int d = -2; d <= 2; ++d) {
+        nb.x[d + 2] = wrap_coord(x + d, nx, per[0]);
+        nb.y[d + 2] = (int64_t)wrap_coord(y + d, ny, per[1]) * nx;
+        nb.z[d + 2] = (int64_t)wrap_coord(z + d, nz, per[2]) * nx * (int64_t)ny;
+    }
+    return nb;
+}
+
+}  // namespace lb

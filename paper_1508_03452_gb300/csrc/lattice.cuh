@@ -1,0 +1,313 @@
+// lattice.cuh -- lattice constants and per-cell physics of the RRMHD lattice
+// Boltzmann step (arXiv:1508.03452, Sec. III), written for the GPU path.
+//
+// Conventions (shared with the C ABI, restated here from the paper):
+//  * D3Q19 (Eq. cellconfigs1), population order: rest; +x,-x,+y,-y,+z,-z;
+//    +x+y,-x-y,+x-y,-x+y; +x+z,-x-z,+x-z,-x+z; +y+z,-y-z,+y-z,-y+z.
+//  * The temperature parameter is nu = sqrt(27), so c_t = c_0, the momentum
+//    vectors are p_i = (1, q chat_i) with q = c_a = sqrt(19/27), and the
+//    weights are w_0 = -44/361, w_axis = 99/722, w_diag = 9/361 (nu cancels
+//    from them) and, for Eq. Hupp, w'_0 = 1/10, w'_axis = 6/95, w'_diag = 33/760.
+//  * D3Q13 (Maxwell subsection): moving population k = 8 p + 2 i + j, plane p
+//    spanned by axes (a1, a2) = (x, y), (x, z), (y, z); v_i^p = sqrt(2) c hop_i
+//    with hop_0..3 = (+,+), (-,+), (-,-), (+,-) in (a1, a2); e_{i0} = v_{(i+3)%4}/2,
+//    e_{i1} = -e_{i0}; b_{i0} = -o_p, b_{i1} = +o_p with o_p = a1 x a2 (= +z, -y,
+//    +x). Index 24 is the rest population h_0.
+//  * Fluid populations are handled as deviations from the rest equilibrium of a
+//    reference state (n_r, eps_r, p_r): d_i = f_i - f_i^eq(n_r, eps_r, 0, 0, 0),
+//    so that small flows keep full relative precision in float32.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lb {
+
+// ---------------------------------------------------------------------------
+// tables
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int c19(int i, int a)
+{
+    constexpr int t[19][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0}, {0, 0, 1},  {0, 0, -1},
+                              {1, 1, 0},  {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1},  {-1, 0, -1}, {1, 0, -1},
+                              {-1, 0, 1}, {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+    return t[i][a];
+}
+
+__host__ __device__ constexpr int c19_norm1(int i) { return (c19(i, 0) != 0) + (c19(i, 1) != 0) + (c19(i, 2) != 0); }
+
+// weight of Eq. Dis_fun_EM (nu = sqrt 27)
+__host__ __device__ constexpr double w19(int i)
+{
+    return c19_norm1(i) == 0 ? -44.0 / 361.0 : (c19_norm1(i) == 1 ? 99.0 / 722.0 : 9.0 / 361.0);
+}
+
+// weight of Eq. Hupp (nu = sqrt 27, c_a^2 = 19/27)
+__host__ __device__ constexpr double wg19(int i)
+{
+    return c19_norm1(i) == 0 ? 1.0 / 10.0 : (c19_norm1(i) == 1 ? 6.0 / 95.0 : 33.0 / 760.0);
+}
+
+// D3Q13: plane axes, hop signs, normal orientation
+__host__ __device__ constexpr int plane_a1(int p) { return p == 2 ? 1 : 0; }
+__host__ __device__ constexpr int plane_a2(int p) { return p == 0 ? 1 : 2; }
+__host__ __device__ constexpr int plane_normal(int p) { return p == 0 ? 2 : (p == 1 ? 1 : 0); }
+__host__ __device__ constexpr int plane_orient(int p) { return p == 1 ? -1 : 1; }
+__host__ __device__ constexpr int hop_s1(int i) { return (i == 0 || i == 3) ? 1 : -1; }
+__host__ __device__ constexpr int hop_s2(int i) { return (i == 0 || i == 1) ? 1 : -1; }
+// lattice hop of moving population k along axis a
+__host__ __device__ constexpr int hop13(int k, int a)
+{
+    return a == plane_a1(k / 8) ? hop_s1((k % 8) / 2) : (a == plane_a2(k / 8) ? hop_s2((k % 8) / 2) : 0);
+}
+
+// numerical constants
+constexpr double kQ = 0.838870492807861077470742756327;      // sqrt(19/27): c_a with nu = sqrt 27
+constexpr double kQ2 = 19.0 / 27.0;
+constexpr double kL1 = 3.35548197123144430988297102531;     // sqrt(19) (sqrt(27)/2 - 1) / c_0, c_0 = 3/8 (9 - 2 sqrt 3)
+constexpr double kSqrt19_3 = 2.51661147842358323241222826898; // sqrt(19/3): Poynting term, nu c_a / sqrt 3
+constexpr double kRest = 3.0 / 4.0 * 361.0 / 33.0;          // 3/4 * 361/33 (rest-population EOS term)
+constexpr double kSqrt2 = 1.41421356237309504880168872421;
+
+// ---------------------------------------------------------------------------
+// per-run constants in compute precision
+// ---------------------------------------------------------------------------
+template <class R>
+struct Phys {
+    R c, c2, inv_c, eps0;      // eps0 = 1 / c^2 (mu0 = 1)
+    R sigma, inv_tau;          // conductivity, dt / tau
+    R half_dt_c2;              // (dt/2) mu0 c^2
+    R gm1;                     // Gamma - 1
+    R C, kappa, kvisc;         // Courant number, (1 - C)/2, alpha c dt / dx
+    R n_r, eps_r, p_r;         // reference rest state of the deviations
+    R dx;                      // lattice spacing
+    R tol;                     // recovery tolerance (relative change of beta)
+    int maxit;
+};
+
+template <class R>
+struct Prim {
+    R n, eps, u[3], E[3], B[3], rho;
+};
+
+template <class R>
+__device__ __forceinline__ R sq(R a) { return a * a; }
+
+// ---------------------------------------------------------------------------
+// equilibria in deviation form (restated from Eq. Dis_fun_EM with the
+// readings of the delta_{i0} term, the sign of the nu^2/5 term, the
+// c_a^y c_a^z typo and the c in the Poynting term; and Eq. Hupp)
+//
+//   f_i^eq = w_i [ 3 p + d_{i0} (3/4)(361/33)(3p - eps) + (3/4)(eps + p) Q_i + EM_i ]
+//   Q_i  = L1 g^2 (c.b) + 19 g^2 sum_{a<b} c_a c_b b_a b_b + (4/15) g^2 (19 sum_a c_a^2 b_a^2 - 4 b^2)
+//   EM_i = eps0 [ 2.3 (c^2 B^2 + E^2) - c sqrt(19/3) (B x E).c
+//                 - 3.8 sum_a c_a^2 X_aa - 14.25 sum_{a<b} c_a c_b X_ab ],  X_ab = E_a E_b + c^2 B_a B_b
+//   g_i^eq = w'_i n g (1 + 3 q c.b + 4.5 q^2 (c.b)^2 - 1.5 b^2)
+// (b = u / c, g = Lorentz factor, c = chat_i)
+// ---------------------------------------------------------------------------
+template <class R>
+struct EqCell {
+    R g, g2, b[3], b2;
+    R three_dp, rest_dev, wq;  // 3(p - p_r), (3/4)(361/33)[(3p-eps)-(3p_r-eps_r)], (3/4)(eps + p)
+    R em_iso, em_lin[3], X[3][3];
+    R ng, dng;                 // n g, n g - n_r
+    R kf;                      // g / tau  (Anderson-Witting factor K_i = kf (1 - q c.b))
+};
+
+template <class R>
+__device__ __forceinline__ void eq_cell(const Prim<R>& s, const Phys<R>& k, EqCell<R>& q)
+{
+    const R b0 = s.u[0] * k.inv_c, b1 = s.u[1] * k.inv_c, b2 = s.u[2] * k.inv_c;
+    q.b[0] = b0; q.b[1] = b1; q.b[2] = b2;
+    q.b2 = b0 * b0 + b1 * b1 + b2 * b2;
+    q.g2 = R(1) / (R(1) - q.b2);
+    q.g = sqrt(q.g2);
+    const R p = k.gm1 * (s.eps - s.n * k.c2);
+    q.three_dp = R(3) * (p - k.p_r);
+    q.rest_dev = R(kRest) * ((R(3) * p - s.eps) - (R(3) * k.p_r - k.eps_r));
+    q.wq = R(0.75) * (s.eps + p);
+    const R* E = s.E;
+    const R* B = s.B;
+    const R BxE[3] = {B[1] * E[2] - B[2] * E[1], B[2] * E[0] - B[0] * E[2], B[0] * E[1] - B[1] * E[0]};
+    q.em_iso = k.eps0 * R(2.3) * (k.c2 * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]) + E[0] * E[0] + E[1] * E[1] + E[2] * E[2]);
+    for (int a = 0; a < 3; ++a) q.em_lin[a] = -k.eps0 * k.c * R(kSqrt19_3) * BxE[a];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) q.X[a][b] = k.eps0 * (E[a] * E[b] + k.c2 * B[a] * B[b]);
+    q.ng = s.n * q.g;
+    q.dng = q.ng - k.n_r;
+    q.kf = q.g * k.inv_tau;
+}
+
+// f_i^eq - f_i^eq(reference rest state), population I
+template <int I, class R>
+__device__ __forceinline__ R feq_dev(const EqCell<R>& q)
+{
+    constexpr int cx = c19(I, 0), cy = c19(I, 1), cz = c19(I, 2);
+    const R cb = R(cx) * q.b[0] + R(cy) * q.b[1] + R(cz) * q.b[2];
+    const R cross = R(cx * cy) * q.b[0] * q.b[1] + R(cx * cz) * q.b[0] * q.b[2] + R(cy * cz) * q.b[1] * q.b[2];
+    const R diag = R(cx * cx) * q.b[0] * q.b[0] + R(cy * cy) * q.b[1] * q.b[1] + R(cz * cz) * q.b[2] * q.b[2];
+    const R Q = q.g2 * (R(kL1) * cb + R(19) * cross + R(4.0 / 15.0) * (R(19) * diag - R(4) * q.b2));
+    const R emq = R(cx * cx) * q.X[0][0] + R(cy * cy) * q.X[1][1] + R(cz * cz) * q.X[2][2];
+    const R emx = R(cx * cy) * q.X[0][1] + R(cx * cz) * q.X[0][2] + R(cy * cz) * q.X[1][2];
+    const R em = q.em_iso + R(cx) * q.em_lin[0] + R(cy) * q.em_lin[1] + R(cz) * q.em_lin[2] - R(3.8) * emq -
+                 R(14.25) * emx;
+    R v = q.three_dp + q.wq * Q + em;
+    if (I == 0) v += q.rest_dev;
+    return R(w19(I)) * v;
+}
+
+// g_i^eq - g_i^eq(reference rest state), population I
+template <int I, class R>
+__device__ __forceinline__ R geq_dev(const EqCell<R>& q)
+{
+    constexpr int cx = c19(I, 0), cy = c19(I, 1), cz = c19(I, 2);
+    const R cb = R(kQ) * (R(cx) * q.b[0] + R(cy) * q.b[1] + R(cz) * q.b[2]);
+    return R(wg19(I)) * (q.dng + q.ng * (R(3) * cb + R(4.5) * cb * cb - R(1.5) * q.b2));
+}
+
+// Anderson-Witting collision factor K_i = (dt/tau) g (1 - v_i.u / c^2), v_i = c q chat_i
+template <int I, class R>
+__device__ __forceinline__ R k_aw(const EqCell<R>& q)
+{
+    constexpr int cx = c19(I, 0), cy = c19(I, 1), cz = c19(I, 2);
+    return q.kf * (R(1) - R(kQ) * (R(cx) * q.b[0] + R(cy) * q.b[1] + R(cz) * q.b[2]));
+}
+
+// ---------------------------------------------------------------------------
+// Maxwell equilibrium (Eq. Maxwell-eq), restated per (plane, i):
+//   h_{i0}^eq = a + e - m,  h_{i1}^eq = a - e + m
+//   a = (sqrt2 c / 16) hop_i . J,  e = (sqrt2 / (16 c)) hop_{(i+3)%4} . E,
+//   m = (1/8) o_p B_normal
+// ---------------------------------------------------------------------------
+template <int K, class R>
+__device__ __forceinline__ R heq13(const R* E, const R* B, const R* J, const Phys<R>& k)
+{
+    constexpr int p = K / 8, i = (K % 8) / 2, j = K % 2;
+    constexpr int a1 = plane_a1(p), a2 = plane_a2(p);
+    constexpr int ie = (i + 3) % 4;
+    const R a = R(kSqrt2 / 16.0) * k.c * (R(hop_s1(i)) * J[a1] + R(hop_s2(i)) * J[a2]);
+    const R e = R(kSqrt2 / 16.0) * k.inv_c * (R(hop_s1(ie)) * E[a1] + R(hop_s2(ie)) * E[a2]);
+    const R m = R(0.125) * R(plane_orient(p)) * B[plane_normal(p)];
+    return j == 0 ? a + e - m : a - e + m;
+}
+
+// EM moments of the 25 populations: E' (Eq. Cal_E), B (Eq. Cal_B), rho_c (Eq. Cal_rhoc)
+template <class R>
+__device__ __forceinline__ void em_moments(const R* h, const Phys<R>& k, R* Ep, R* B, R& rho)
+{
+    Ep[0] = Ep[1] = Ep[2] = R(0);
+    B[0] = B[1] = B[2] = R(0);
+    rho = h[24];
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        R bn = R(0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const R h0 = h[8 * p + 2 * i], h1 = h[8 * p + 2 * i + 1];
+            const R d = h0 - h1;
+            const int ie = (i + 3) % 4;
+            Ep[plane_a1(p)] += d * R(hop_s1(ie));
+            Ep[plane_a2(p)] += d * R(hop_s2(ie));
+            bn += h1 - h0;
+            rho += h0 + h1;
+        }
+        B[plane_normal(p)] = R(plane_orient(p)) * bn;
+    }
+    const R s = R(kSqrt2 / 2.0) * k.c;
+    Ep[0] *= s; Ep[1] *= s; Ep[2] *= s;
+}
+
+// ---------------------------------------------------------------------------
+// Ohm-coupled E solve (Eqs. Ohm and Ex_force, closed form) and J
+//   [(1+k) I - (k/c^2) u u^T] E = E' - k u x B - (dt/2) c^2 rho u,  k = (dt/2) c^2 sigma g
+//   E = a/(1+k) - k/(1+k) u x B + k/(1+k) (u.a) u / (c^2 (1 + k/g^2)),  a = E' - (dt/2) c^2 rho u
+// J is taken from Eq. Ex_force, J = (E' - E) / ((dt/2) mu0 c^2), which equals
+// Eq. Ohm at the solution and stays accurate at large sigma in float32.
+// ---------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ void ohm_solve(const R* Ep, const R* u, const R* B, R rho, R g2, const Phys<R>& k, R* E,
+                                          R* J)
+{
+    const R kk = k.half_dt_c2 * k.sigma * sqrt(g2);
+    const R inv1k = R(1) / (R(1) + kk);
+    const R kfrac = kk * inv1k;
+    R a[3];
+    for (int c = 0; c < 3; ++c) a[c] = Ep[c] - k.half_dt_c2 * rho * u[c];
+    const R ua = u[0] * a[0] + u[1] * a[1] + u[2] * a[2];
+    const R s = kfrac * ua / (k.c2 * (R(1) + kk / g2));
+    const R uxB[3] = {u[1] * B[2] - u[2] * B[1], u[2] * B[0] - u[0] * B[2], u[0] * B[1] - u[1] * B[0]};
+    for (int c = 0; c < 3; ++c) {
+        E[c] = a[c] * inv1k - kfrac * uxB[c] + s * u[c];
+        J[c] = (Ep[c] - E[c]) / k.half_dt_c2;
+    }
+}
+
+// J from Eq. Ohm for stored primitives (initial state, outputs, driven cells)
+template <class R>
+__device__ __forceinline__ void ohm_current(const R* E, const R* u, const R* B, R rho, const Phys<R>& k, R* J)
+{
+    const R g = R(1) / sqrt(R(1) - (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) * k.inv_c * k.inv_c);
+    const R uxB[3] = {u[1] * B[2] - u[2] * B[1], u[2] * B[0] - u[0] * B[2], u[0] * B[1] - u[1] * B[0]};
+    const R Eu = E[0] * u[0] + E[1] * u[1] + E[2] * u[2];
+    for (int c = 0; c < 3; ++c) J[c] = k.sigma * g * (E[c] + uxB[c] - Eu * u[c] * k.inv_c * k.inv_c) + rho * u[c];
+}
+
+// ---------------------------------------------------------------------------
+// Landau eigen-solve (coupling subsection): largest eigenpair of
+// A = [T - eps0 F F(E_old, B_old)] eta by a shifted power iteration
+// (shift p_old - s_old pushes the spacelike eigenvalues to ~0), seeded with
+// the previous velocity. T holds the full moments (reference added).
+// Returns the iteration count, or -1 if it failed.
+// ---------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ int landau(const R T[4][4], const Prim<R>& old, const Phys<R>& k, R beta[3], R& lambda,
+                                      R& s_old)
+{
+    const R* E = old.E;
+    const R* B = old.B;
+    const R E2 = E[0] * E[0] + E[1] * E[1] + E[2] * E[2];
+    const R B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+    const R ExB[3] = {E[1] * B[2] - E[2] * B[1], E[2] * B[0] - E[0] * B[2], E[0] * B[1] - E[1] * B[0]};
+    // S = eps0 F^{mu rho} F_rho^nu: S00 = eps0 E^2, S0a = eps0 c (E x B)_a,
+    // Sab = eps0 [-E_a E_b + c^2 (d_ab B^2 - B_a B_b)]
+    R A[4][4];
+    A[0][0] = T[0][0] - k.eps0 * E2;
+    for (int a = 0; a < 3; ++a) {
+        const R m0a = T[0][a + 1] - k.eps0 * k.c * ExB[a];
+        A[0][a + 1] = -m0a;
+        A[a + 1][0] = m0a;
+        for (int b = 0; b < 3; ++b) {
+            const R sab = k.eps0 * (-E[a] * E[b] + k.c2 * ((a == b ? B2 : R(0)) - B[a] * B[b]));
+            A[a + 1][b + 1] = -(T[a + 1][b + 1] - sab);
+        }
+    }
+    s_old = R(0.5) * k.eps0 * (k.c2 * B2 - E2);
+    const R p_old = k.gm1 * (old.eps - old.n * k.c2);
+    const R shift = p_old - s_old;
+    R v1 = old.u[0] * k.inv_c, v2 = old.u[1] * k.inv_c, v3 = old.u[2] * k.inv_c;
+    int it = 0;
+    bool done = false;
+    for (it = 1; it <= k.maxit; ++it) {
+        const R w0 = A[0][0] + A[0][1] * v1 + A[0][2] * v2 + A[0][3] * v3 + shift;
+        const R w1 = A[1][0] + (A[1][1] + shift) * v1 + A[1][2] * v2 + A[1][3] * v3;
+        const R w2 = A[2][0] + A[2][1] * v1 + (A[2][2] + shift) * v2 + A[2][3] * v3;
+        const R w3 = A[3][0] + A[3][1] * v1 + A[3][2] * v2 + (A[3][3] + shift) * v3;
+        const R iw = R(1) / w0;
+        const R n1 = w1 * iw, n2 = w2 * iw, n3 = w3 * iw;
+        const R d2 = sq(n1 - v1) + sq(n2 - v2) + sq(n3 - v3);
+        const R b2 = n1 * n1 + n2 * n2 + n3 * n3;
+        v1 = n1; v2 = n2; v3 = n3;
+        if (it >= 2 && (d2 <= k.tol * k.tol * b2 || d2 == R(0))) {
+            done = true;
+            break;
+        }
+    }
+    if (!done) return -1;
+    lambda = A[0][0] + A[0][1] * v1 + A[0][2] * v2 + A[0][3] * v3;
+    beta[0] = v1; beta[1] = v2; beta[2] = v3;
+    const R b2 = v1 * v1 + v2 * v2 + v3 * v3;
+    if (!(b2 < R(1)) || !(lambda == lambda)) return -1;
+    return it;
+}
+
+}  // namespace lb

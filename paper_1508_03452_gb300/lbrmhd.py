@@ -1,0 +1,225 @@
+"""Python binding of the lbrmhd C ABI (include/lbrmhd.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library
+liblbrmhd.so. There is no CPU fallback: if the library cannot be built or
+loaded, or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+OK = 0
+ERR_BAD_ARG, ERR_OOM, ERR_CUDA, ERR_NONCONVERGED, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE = -1, -2, -3, -4, -5, -6, -7
+PERIODIC, OPEN, DRIVEN = 0, 1, 2
+FP64, FP32, FP16_DEV = 0, 1, 2
+RECOVERY_PLAIN, RECOVERY_MLP = 0, 1
+FLAG_NO_EM_COLLISION = 1
+NMOMENTS, NDIAG, NTABLE = 16, 10, 311
+MOMENT_NAMES = ["n", "p", "eps", "ux", "uy", "uz", "Ex", "Ey", "Ez", "Bx", "By", "Bz", "rho_c", "Jx", "Jy", "Jz"]
+DIAG_NAMES = ["N0", "T00", "T01", "T02", "T03", "rho_c", "divB_max", "divB_rms", "nonfinite", "cells"]
+
+EXPORTED = [
+    "lbrmhd_create", "lbrmhd_destroy", "lbrmhd_set_stream", "lbrmhd_init_fields", "lbrmhd_init_fields_device",
+    "lbrmhd_step", "lbrmhd_get_moments", "lbrmhd_get_moments_device", "lbrmhd_get_populations",
+    "lbrmhd_get_diagnostics", "lbrmhd_get_stats", "lbrmhd_state_bytes", "lbrmhd_get_state", "lbrmhd_set_state",
+    "lbrmhd_run_cells", "lbrmhd_last_error", "lbrmhd_lattice_tables",
+]
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+        ("bc", C.c_int32 * 6),
+        ("tau", C.c_double), ("sigma", C.c_double), ("gamma_ad", C.c_double), ("alpha", C.c_double),
+        ("c", C.c_double), ("dx", C.c_double), ("drive_u0", C.c_double),
+        ("drive_layers", C.c_int32), ("precision", C.c_int32), ("recovery", C.c_int32), ("flags", C.c_int32),
+        ("max_iters", C.c_int32), ("tol", C.c_double),
+    ]
+
+
+def make_params(nx, ny=1, nz=1, *, bc=(PERIODIC,) * 6, tau=1.0, sigma=100.0, gamma_ad=4.0 / 3.0, alpha=0.1, c=1.0,
+                dx=1.0, drive_u0=0.0, drive_layers=0, precision=FP32, recovery=RECOVERY_PLAIN, flags=0, max_iters=0,
+                tol=0.0) -> Params:
+    P = Params()
+    P.nx, P.ny, P.nz = int(nx), int(ny), int(nz)
+    for k in range(6):
+        P.bc[k] = int(bc[k])
+    P.tau, P.sigma, P.gamma_ad, P.alpha, P.c, P.dx = tau, sigma, gamma_ad, alpha, c, dx
+    P.drive_u0, P.drive_layers = drive_u0, int(drive_layers)
+    P.precision, P.recovery, P.flags, P.max_iters, P.tol = int(precision), int(recovery), int(flags), int(max_iters), tol
+    return P
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+class LbrmhdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"lbrmhd error {code}: {msg}")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_missing: bool = True):
+    """Loads liblbrmhd.so (building it with nvcc first if needed)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB_PATH
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing; run __graft_entry__.build()")
+        L = C.CDLL(path)
+        vp, dp, i64 = C.c_void_p, C.POINTER(C.c_double), C.c_int64
+        L.lbrmhd_create.argtypes = [C.POINTER(Params), C.c_int, C.POINTER(C.c_void_p)]
+        L.lbrmhd_destroy.argtypes = [vp]
+        L.lbrmhd_set_stream.argtypes = [vp, vp]
+        L.lbrmhd_init_fields.argtypes = [vp, C.c_int, dp, dp, dp, dp, dp]
+        L.lbrmhd_init_fields_device.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp]
+        L.lbrmhd_step.argtypes = [vp, i64]
+        L.lbrmhd_get_moments.argtypes = [vp, C.c_int, dp]
+        L.lbrmhd_get_moments_device.argtypes = [vp, C.c_int, vp]
+        L.lbrmhd_get_populations.argtypes = [vp, C.c_int, dp, dp, dp]
+        L.lbrmhd_get_diagnostics.argtypes = [vp, C.c_int, dp]
+        L.lbrmhd_get_stats.argtypes = [vp, C.c_int, C.POINTER(i64)]
+        L.lbrmhd_state_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
+        L.lbrmhd_get_state.argtypes = [vp, vp, C.c_size_t]
+        L.lbrmhd_set_state.argtypes = [vp, vp, C.c_size_t]
+        L.lbrmhd_run_cells.argtypes = [vp, C.c_int]
+        L.lbrmhd_run_cells.restype = i64
+        L.lbrmhd_last_error.argtypes = [vp]
+        L.lbrmhd_last_error.restype = C.c_char_p
+        L.lbrmhd_lattice_tables.argtypes = [dp, C.c_size_t]
+        _lib = L
+        return L
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f64(a, n) -> np.ndarray:
+    out = np.ascontiguousarray(np.asarray(a, dtype=np.float64)).reshape(-1)
+    if out.size != n:
+        raise ValueError(f"expected {n} values, got {out.size}")
+    return out
+
+
+def lattice_tables() -> dict:
+    """The lattice tables compiled into the library (needs no GPU)."""
+    out = np.zeros(NTABLE)
+    rc = load().lbrmhd_lattice_tables(_dp(out), NTABLE)
+    if rc != OK:
+        raise LbrmhdError(rc, "lattice_tables")
+    o = 0
+
+    def take(n, shape):
+        nonlocal o
+        v = out[o:o + n].reshape(shape)
+        o += n
+        return v
+
+    return {"chat": take(57, (19, 3)), "w": take(19, (19,)), "wg": take(19, (19,)), "hop": take(72, (24, 3)),
+            "e_over_c": take(72, (24, 3)), "b": take(72, (24, 3))}
+
+
+class Solver:
+    """One handle of the library: n_runs independent runs advanced together."""
+
+    def __init__(self, params, stream=None):
+        L = load()
+        plist = params if isinstance(params, (list, tuple)) else [params]
+        arr = (Params * len(plist))(*plist)
+        h = C.c_void_p()
+        rc = L.lbrmhd_create(arr, len(plist), C.byref(h))
+        if rc != OK:
+            raise LbrmhdError(rc, L.lbrmhd_last_error(None).decode())
+        self._L, self._h, self.params = L, h, list(plist)
+        self.cells = [int(L.lbrmhd_run_cells(h, r)) for r in range(len(plist))]
+        if stream is not None:
+            self.set_stream(stream)
+
+    def _check(self, rc):
+        if rc != OK:
+            raise LbrmhdError(rc, self._L.lbrmhd_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.lbrmhd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, an integer cudaStream_t or None."""
+        ptr = getattr(stream, "cuda_stream", stream)
+        self._check(self._L.lbrmhd_set_stream(self._h, C.c_void_p(ptr or 0)))
+
+    def init_fields(self, run, n, p, u, B, E=None):
+        N = self.cells[run]
+        n, p, u, B = _f64(n, N), _f64(p, N), _f64(u, 3 * N), _f64(B, 3 * N)
+        Ep = None if E is None else _f64(E, 3 * N)
+        self._check(self._L.lbrmhd_init_fields(self._h, run, _dp(n), _dp(p), _dp(u), _dp(B),
+                                               None if Ep is None else _dp(Ep)))
+
+    def init_fields_device(self, run, n, p, u, B, E=None):
+        """Device float64 arrays: torch tensors (contiguous, cuda) or integer pointers."""
+        ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr() if hasattr(t, "data_ptr") else int(t))
+        self._check(self._L.lbrmhd_init_fields_device(self._h, run, ptr(n), ptr(p), ptr(u), ptr(B), ptr(E)))
+
+    def step(self, nsteps=1):
+        self._check(self._L.lbrmhd_step(self._h, int(nsteps)))
+
+    def moments(self, run=0) -> np.ndarray:
+        out = np.zeros(NMOMENTS * self.cells[run])
+        self._check(self._L.lbrmhd_get_moments(self._h, run, _dp(out)))
+        return out.reshape(NMOMENTS, self.cells[run])
+
+    def moments_device(self, run, out_ptr):
+        ptr = out_ptr.data_ptr() if hasattr(out_ptr, "data_ptr") else int(out_ptr)
+        self._check(self._L.lbrmhd_get_moments_device(self._h, run, C.c_void_p(ptr)))
+
+    def populations(self, run=0):
+        N = self.cells[run]
+        f, g, h = np.zeros(19 * N), np.zeros(19 * N), np.zeros(25 * N)
+        self._check(self._L.lbrmhd_get_populations(self._h, run, _dp(f), _dp(g), _dp(h)))
+        return f.reshape(19, N), g.reshape(19, N), h.reshape(25, N)
+
+    def diagnostics(self, run=0, check=True) -> np.ndarray:
+        out = np.zeros(NDIAG)
+        rc = self._L.lbrmhd_get_diagnostics(self._h, run, _dp(out))
+        if check or rc not in (OK, ERR_NONFINITE):
+            self._check(rc)
+        return out
+
+    def stats(self, run=0) -> dict:
+        out = (C.c_int64 * 4)()
+        self._check(self._L.lbrmhd_get_stats(self._h, run, out))
+        return {"steps": out[0], "recover_fail": out[1], "iter_total": out[2], "iter_max": out[3]}
+
+    def get_state(self) -> bytes:
+        n = C.c_size_t()
+        self._check(self._L.lbrmhd_state_bytes(self._h, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        self._check(self._L.lbrmhd_get_state(self._h, buf, n.value))
+        return buf.raw
+
+    def set_state(self, blob: bytes):
+        buf = C.create_string_buffer(blob, len(blob))
+        self._check(self._L.lbrmhd_set_state(self._h, buf, len(blob)))

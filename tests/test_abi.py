@@ -1,0 +1,65 @@
+"""CPU checks of the C-ABI library: it builds, loads and exports every symbol
+its header declares; its compiled-in lattice tables agree with the oracle's
+independently written ones; and without a GPU it refuses to run (no CPU
+fallback)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1508_03452_gb300 import lbrmhd as L
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(lbrmhd_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_header_symbols_are_exported():
+    lib = L.load()
+    names = declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(L.EXPORTED) <= set(names)
+
+
+def test_lattice_tables_match_oracle():
+    t = L.lattice_tables()
+    lat = O.lattice(O.make_params(c=1.0))
+    assert np.array_equal(t["chat"], lat["chat"])
+    assert np.allclose(t["w"], lat["w"], rtol=0, atol=1e-15)
+    assert np.allclose(t["wg"], lat["wg"], rtol=0, atol=1e-15)
+    assert np.array_equal(t["hop"], lat["hop"])
+    assert np.allclose(t["e_over_c"], lat["e"], rtol=0, atol=1e-15)
+    assert np.allclose(t["b"], lat["b"], rtol=0, atol=1e-15)
+
+
+def test_bad_parameters_are_rejected():
+    with pytest.raises(L.LbrmhdError) as e:
+        L.Solver(L.make_params(0, 4, 1))
+    assert e.value.code == L.ERR_BAD_ARG
+    with pytest.raises(L.LbrmhdError) as e:
+        L.Solver(L.make_params(8, 4, 4, bc=(L.DRIVEN, L.DRIVEN, 0, 0, 0, 0)))
+    assert e.value.code == L.ERR_BAD_ARG
+    with pytest.raises(L.LbrmhdError) as e:
+        L.Solver(L.make_params(8, 4, 4, bc=(L.OPEN, L.PERIODIC, 0, 0, 0, 0)))
+    assert e.value.code == L.ERR_BAD_ARG
+
+
+def test_no_cpu_fallback_without_gpu():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(L.LbrmhdError) as e:
+        L.Solver(L.make_params(8, 8, 1))
+    assert e.value.code == L.ERR_CUDA

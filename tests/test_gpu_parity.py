@@ -1,0 +1,234 @@
+"""GPU parity: the CUDA library, called through its C ABI, against the FP64
+CPU oracle on the same seeded inputs.
+
+Bars: relative L2 per field group <= 1e-10 for the float64 build and <= 1e-5 for
+the float32 build after the stated step counts; the float16-deviation build has
+no bar (its error against the oracle is reported by the benchmark) beyond a
+sanity bound. Integer-like checks (the EM permutation) are bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1508_03452_gb300 import lbrmhd as L
+from paper_1508_03452_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+GROUPS = {"n": (0,), "p": (1,), "eps": (2,), "u": (3, 4, 5), "E": (6, 7, 8), "B": (9, 10, 11), "rho_c": (12,)}
+TOL = {L.FP64: 1e-10, L.FP32: 1e-5}
+BC_ORC = {L.PERIODIC: O.PERIODIC, L.OPEN: O.OPEN, L.DRIVEN: O.DRIVEN}
+
+
+def rel_errors(mg, mo, floor=1e-300):
+    out = {}
+    for name, rows in GROUPS.items():
+        a, b = mg[list(rows)], mo[list(rows)]
+        nb = np.linalg.norm(b)
+        out[name] = np.linalg.norm(a - b) / nb if nb > floor else np.linalg.norm(a - b)
+    return out
+
+
+def run_pair(F, steps, precision, *, bc=(L.PERIODIC,) * 6, check_groups=None, **kw):
+    okw = {k: v for k, v in kw.items() if k in ("sigma", "tau", "alpha", "c", "dx", "drive_u0", "drive_layers")}
+    ref = O.Sim(O.make_params(F.nx, F.ny, F.nz, bc=tuple(BC_ORC[b] for b in bc), threads=8, **okw))
+    ref.init(F.n, F.p, F.u, F.B, F.E)
+    ref.step(steps)
+    s = L.Solver(L.make_params(F.nx, F.ny, F.nz, bc=bc, precision=precision, **kw))
+    s.init_fields(0, F.n, F.p, F.u, F.B, F.E)
+    s.step(steps)
+    errs = rel_errors(s.moments(), ref.moments())
+    st = s.stats()
+    s.close()
+    assert st["recover_fail"] == 0, st
+    return errs, ref
+
+
+def assert_parity(errs, tol, skip=()):
+    bad = {k: v for k, v in errs.items() if k not in skip and not v <= tol}
+    assert not bad, (bad, errs)
+
+
+@pytest.mark.parametrize("precision", [L.FP64, L.FP32])
+def test_alfven_config1(precision):
+    """Config 1 in full: 64 x 64 periodic Alfven wave, sigma = 1e6, 500 steps."""
+    F = W.alfven_wave(64, 64, 1)
+    errs, _ = run_pair(F, 500, precision, sigma=1e6)
+    # rho_c stays at round-off level in this problem; u, E, B carry the wave
+    assert_parity(errs, TOL[precision], skip=("rho_c",))
+
+
+@pytest.mark.parametrize("precision", [L.FP64, L.FP32])
+def test_current_sheet_reduced(precision):
+    """Config 2 on a reduced, ragged grid (160 x 12, several 128-wide tiles and
+    a tail), sigma = 100, 2000 steps."""
+    F = W.current_sheet(160, 12, 1, delta=8.0)
+    errs, _ = run_pair(F, 2000, precision, sigma=100.0)
+    assert_parity(errs, TOL[precision], skip=("rho_c",))
+
+
+@pytest.mark.parametrize("precision", [L.FP64, L.FP32])
+def test_kelvin_helmholtz_short_horizon(precision):
+    """Config 3 form (shear +-V, density ratio 10, sigma = 1e3, seeded noise) on
+    a 136 x 72 grid for 150 steps (the flow is chaotic: short horizon)."""
+    F = W.kelvin_helmholtz(136, 72, 1, V=0.3, ratio=10.0, B0=0.1, a=2.0, noise=1e-3, seed=3)
+    errs, _ = run_pair(F, 150, precision, sigma=1e3)
+    assert_parity(errs, TOL[precision] * (10 if precision == L.FP32 else 1))
+
+
+def test_three_dimensional_periodic_fp64():
+    """A 3-D periodic state with every population moving (24 x 20 x 18)."""
+    rng = np.random.default_rng(70)
+    nx, ny, nz = 24, 20, 18
+    N = nx * ny * nz
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    u = np.zeros((3, N))
+    u[0] = 0.2 * np.sin(2 * np.pi * y.reshape(-1) / ny)
+    u[1] = 0.1 * np.sin(2 * np.pi * z.reshape(-1) / nz)
+    u[2] = 0.15 * np.cos(2 * np.pi * x.reshape(-1) / nx)
+    B = 0.05 * rng.uniform(-1, 1, (3, N)) + np.array([[0.1], [0.0], [0.05]])
+    F = W.Fields(nx, ny, nz, 1.0 + 0.05 * rng.uniform(size=N), np.ones(N), u, B)
+    errs, _ = run_pair(F, 40, L.FP64, sigma=50.0)
+    assert_parity(errs, 1e-10)
+
+
+def test_open_boundaries_fp64():
+    """Open y faces with the normal-B fix (the paper's KH boundaries)."""
+    F = W.kelvin_helmholtz(48, 40, 1, V=0.2, ratio=3.0, B0=0.1, a=2.0, noise=1e-2, seed=5)
+    rng = np.random.default_rng(71)
+    F.B[1] += 0.005 * rng.uniform(-1, 1, F.N)
+    errs, _ = run_pair(F, 60, L.FP64, bc=(L.PERIODIC, L.PERIODIC, L.OPEN, L.OPEN, L.PERIODIC, L.PERIODIC),
+                       sigma=100.0)
+    assert_parity(errs, 1e-10)
+
+
+def test_flux_rope_open_and_driven_fp64():
+    """Config 5 form on a small grid: open faces, driven photosphere."""
+    F = W.flux_rope(20, 16, 24)
+    nl = W.drive_layers_for(24)
+    errs, _ = run_pair(F, 25, L.FP64, bc=(L.OPEN, L.OPEN, L.OPEN, L.OPEN, L.DRIVEN, L.OPEN), sigma=500.0,
+                       drive_u0=0.05, drive_layers=nl)
+    assert_parity(errs, 1e-10)
+
+
+def test_fp16_deviation_storage_is_close():
+    """float16 relative-deviation storage of f, g: no parity bar, only a sanity
+    bound on the error against the oracle (reported in full by the benchmark)."""
+    F = W.current_sheet(160, 12, 1, delta=8.0)
+    errs, _ = run_pair(F, 400, L.FP16_DEV, sigma=100.0)
+    assert errs["B"] < 1e-2 and errs["n"] < 1e-2 and errs["eps"] < 1e-2, errs
+
+
+@pytest.mark.parametrize("precision", [L.FP64, L.FP32])
+def test_em_streaming_permutation_bit_exact(precision):
+    """With the EM collision switched off, h after n steps is the initial h
+    rolled by n lattice hops, bit for bit (ragged 3-D grid)."""
+    nx, ny, nz = 37, 11, 6
+    N = nx * ny * nz
+    rng = np.random.default_rng(72)
+    s = L.Solver(L.make_params(nx, ny, nz, sigma=10.0, precision=precision, flags=L.FLAG_NO_EM_COLLISION))
+    s.init_fields(0, np.ones(N), np.ones(N), rng.uniform(-0.1, 0.1, (3, N)), rng.uniform(-0.1, 0.1, (3, N)))
+    _, _, h0 = s.populations()
+    n = 5
+    s.step(n)
+    _, _, h1 = s.populations()
+    hop = L.lattice_tables()["hop"].astype(int)
+    for k in range(24):
+        expect = np.roll(h0[k].reshape(nz, ny, nx), (n * hop[k][2], n * hop[k][1], n * hop[k][0]), axis=(0, 1, 2))
+        assert np.array_equal(h1[k].reshape(nz, ny, nx), expect), k
+    assert np.array_equal(h1[24], h0[24])
+
+
+def test_mass_and_charge_conserved_fp64():
+    F = W.kelvin_helmholtz(64, 48, 1, V=0.3, ratio=3.0, B0=0.1, a=2.0, noise=1e-2, seed=9)
+    s = L.Solver(L.make_params(F.nx, F.ny, F.nz, sigma=100.0, precision=L.FP64))
+    s.init_fields(0, F.n, F.p, F.u, F.B)
+    d0 = s.diagnostics()
+    s.step(100)
+    d1 = s.diagnostics()
+    assert abs(d1[0] - d0[0]) < 1e-12 * d0[0]
+    assert abs(d1[5] - d0[5]) < 1e-12
+    assert d1[8] == 0 and d1[9] == F.N
+
+
+def test_diagnostics_match_oracle_totals():
+    """Sums of N^0 and rho_c of the post-collision state equal the oracle's
+    (the g collision conserves N^0 and the h_0 update conserves charge)."""
+    F = W.kelvin_helmholtz(40, 32, 1, V=0.3, ratio=3.0, B0=0.1, a=2.0, noise=1e-2, seed=11)
+    ref = O.Sim(O.make_params(F.nx, F.ny, 1, sigma=100.0, threads=8))
+    ref.init(F.n, F.p, F.u, F.B)
+    ref.step(20)
+    f, g, h, _ = ref.state()
+    lat = O.lattice(ref.P)
+    s = L.Solver(L.make_params(F.nx, F.ny, 1, sigma=100.0, precision=L.FP64))
+    s.init_fields(0, F.n, F.p, F.u, F.B)
+    s.step(20)
+    d = s.diagnostics()
+    assert abs(d[0] - (lat["p"][:, 0:1] * g).sum()) < 1e-11 * d[0]
+    assert abs(d[5] - h.sum()) < 1e-11
+
+
+def test_checkpoint_resume_bit_exact():
+    F = W.kelvin_helmholtz(48, 40, 1, V=0.3, ratio=3.0, B0=0.1, a=2.0, noise=1e-2, seed=13)
+    P = L.make_params(F.nx, F.ny, 1, sigma=100.0, precision=L.FP32)
+    a = L.Solver(P)
+    a.init_fields(0, F.n, F.p, F.u, F.B)
+    a.step(20)
+    b = L.Solver(P)
+    b.init_fields(0, F.n, F.p, F.u, F.B)
+    b.step(9)
+    blob = b.get_state()
+    c = L.Solver(P)
+    c.set_state(blob)
+    c.step(11)
+    assert np.array_equal(a.moments(), c.moments())
+    fa, ga, ha = a.populations()
+    fc, gc, hc = c.populations()
+    assert np.array_equal(fa, fc) and np.array_equal(ga, gc) and np.array_equal(ha, hc)
+    assert c.stats()["steps"] == 20
+
+
+def test_uniform_state_stays_uniform_fp32():
+    N = 40 * 30
+    u = np.tile(np.array([[0.2], [-0.1], [0.0]]), N)
+    B = np.tile(np.array([[0.1], [0.05], [0.0]]), N)
+    s = L.Solver(L.make_params(40, 30, 1, sigma=50.0, precision=L.FP32))
+    s.init_fields(0, np.full(N, 1.3), np.full(N, 0.7), u, B)
+    m0 = s.moments()
+    s.step(50)
+    m = s.moments()
+    assert np.abs(m - m0).max() < 1e-6
+    assert np.all(m.std(axis=1) <= 1e-7 * (1 + np.abs(m).max(axis=1)))
+
+
+def test_full_size_sampled_step_fp32():
+    """Config 2 at its full size (1024 x 1024, sigma = 100, float32) in the
+    launch configuration the benchmark times: one GPU step checked at 400
+    sampled cells against the oracle's step of the same (GPU) state."""
+    nx = ny = 1024
+    F = W.current_sheet(nx, ny, 1, delta=8.0)
+    s = L.Solver(L.make_params(nx, ny, 1, sigma=100.0, precision=L.FP32))
+    s.init_fields(0, F.n, F.p, F.u, F.B)
+    s.step(3)
+    fc, gc, hc = s.populations()
+    m = s.moments()
+    prim = np.zeros((O.NPRIM, F.N))
+    prim[O.N_] = m[0]
+    prim[O.EPS_] = m[2]
+    prim[O.U_:O.U_ + 3] = m[3:6]
+    prim[O.E_:O.E_ + 3] = m[6:9]
+    prim[O.B_:O.B_ + 3] = m[9:12]
+    prim[O.RHOC_] = m[12]
+    prim[O.J_:O.J_ + 3] = m[13:16]
+    rng = np.random.default_rng(73)
+    cells = np.unique(np.concatenate([rng.integers(0, F.N, 392), [0, nx - 1, F.N - 1, F.N - nx, 1023 * nx + 5]]))
+    ref = O.Sim(O.make_params(nx, ny, 1, sigma=100.0, threads=8))
+    _, _, _, pr = ref.update_cells_from(fc, gc, hc, prim, cells)
+    s.step(1)
+    m1 = s.moments()[:, cells]
+    for name, rows in (("n", [0]), ("eps", [2]), ("u", [3, 4, 5]), ("E", [6, 7, 8]), ("B", [9, 10, 11])):
+        orows = {"n": [O.N_], "eps": [O.EPS_], "u": [2, 3, 4], "E": [5, 6, 7], "B": [8, 9, 10]}[name]
+        a, b = m1[rows], pr[:, orows].T
+        nb = np.linalg.norm(b)
+        err = np.linalg.norm(a - b) / nb if nb > 0 else np.linalg.norm(a - b)
+        assert err <= 1e-5 or np.linalg.norm(a - b) < 1e-9, (name, err)
