@@ -45,7 +45,8 @@
  *   R13 both the subtraction before the eigen-solve and the eigenvalue shift use
  *       E, B of the previous step; "F^{mu rho} F^nu_rho" is the first term of
  *       T_EM with the index placement that gives T^00_EM = eps0 (E^2+c^2B^2)/2.
- *   R14 power method to ||dU||/||U|| <= 1e-14, seeded with the previous U.
+ *   R14 power method until the change of the spatial part of U is at most
+ *       1e-14 of its size (or zero), seeded with the previous U.
  *   R15 n = N^0 / U^0.
  *   R16 the 3x3 Ohm system is solved in closed form (Sherman-Morrison).
  *   R17 initial populations are the equilibria of the initial fields.
@@ -62,6 +63,8 @@
  *       Parity: UNPINNED (the paper's forcing scheme is not stated).
  *   R22 nu (the temperature parameter, not given in the paper) only changes the
  *       number-density lattice weights w'_i; nu = sqrt(27), i.e. c_t = c_0.
+ *   R23 after the E solve, J is taken from Eq. Ex_force (equal to Eq. Ohm at
+ *       the solution, and well conditioned at large sigma).
  *
  * Units: mu_0 = 1, eps_0 = 1/(mu_0 c^2); dt = dx / (sqrt(2) c) (Sec. III,
  * time-step synchronisation).
@@ -390,10 +393,10 @@ int orc_landau(const orc_params* P, const double* T16, const double* E_prev, con
         for (int m = 0; m < 4; ++m) {
             V[m] /= v0;
             diff += (V[m] - U[m]) * (V[m] - U[m]);
-            nrm += V[m] * V[m];
+            if (m > 0) nrm += V[m] * V[m];
             U[m] = V[m];
         }
-        if (sqrt(diff) <= P->power_tol * sqrt(nrm)) break;
+        if (diff == 0.0 || sqrt(diff) <= P->power_tol * sqrt(nrm)) break;
     }
     const double norm2 = U[0] * U[0] - (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]);
     if (it > P->max_power_iters || !(norm2 > 0.0)) return -1;
@@ -427,7 +430,10 @@ int orc_recover_cell(const orc_params* P, const orc_lattice* L, const double* f,
     double u[3] = {c * U[1] / U[0], c * U[2] / U[0], c * U[3] / U[0]};
     double E[3], J[3];
     orc_ohm_solve(P, Ep, u, B, rho_c, E);
-    orc_ohm_current(P, E, u, B, rho_c, J);
+    /* R23: J at the solution of Eq. Ex_force, J = (E' - E) / ((dt/2) mu0 c^2),
+     * which equals Eq. Ohm there; Eq. Ohm evaluated directly loses
+     * log10(sigma |u x B| / |J|) digits at large sigma. */
+    for (int a = 0; a < 3; ++a) J[a] = (Ep[a] - E[a]) / (0.5 * orc_dt(P) * c * c);
     prim_out[ORC_N] = n;
     prim_out[ORC_EPS] = eps;
     for (int a = 0; a < 3; ++a) {

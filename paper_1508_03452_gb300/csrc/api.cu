@@ -22,6 +22,9 @@ struct RunState {
     int cur = 0;
     bool initialized = false;
     lb::RefState ref{1.0, 4.0, 1.0};
+    double means[lb::NMEANS] = {};               // reference-state means (see means_kernel)
+    double Er[3] = {0, 0, 0}, Br[3] = {0, 0, 0};  // reference fields of the h deviations
+    double Xr[3][3] = {}, Yr[3] = {};            // reference EM terms of the f deviations
     lb::RefPops refpops{};
     lb::HalfScale hs{};
     unsigned long long* d_stats = nullptr;  // failures, iteration sum, iteration max
@@ -40,11 +43,11 @@ struct lbrmhd_state_s {
     int device = 0;
     cudaStream_t stream = nullptr;
     std::string err;
-    double* d_scratch = nullptr;  // per-block diagnostics partials
+    double* d_scratch = nullptr;  // per-block partial sums (diagnostics, reference means)
     int64_t scratch_blocks = 0;
     double* d_io = nullptr;  // staging for inputs / outputs
     size_t io_bytes = 0;
-    double* d_small = nullptr;  // 16 float64
+    double* d_small = nullptr;  // 32 float64
     int* d_flag = nullptr;
 };
 
@@ -67,9 +70,17 @@ int fail(lbrmhd_handle h, int code, const std::string& msg)
 
 bool bad_run(lbrmhd_handle h, int run) { return !h || run < 0 || run >= (int)h->runs.size(); }
 
+struct RunRef {
+    const double *Er, *Br;
+    const double (*Xr)[3];
+    const double* Yr;
+};
+
 template <class R>
-lb::Phys<R> make_phys(const lbrmhd_params& p, const lb::RefState& ref)
+lb::Phys<R> make_phys(const lbrmhd_params& p, const lb::RefState& ref, const RunRef& rr)
 {
+    const double* Er = rr.Er;
+    const double* Br = rr.Br;
     lb::Phys<R> k{};
     const double dt = p.dx / (std::sqrt(2.0) * p.c);
     const double C = lb::kQ * p.c * dt / p.dx;
@@ -88,11 +99,30 @@ lb::Phys<R> make_phys(const lbrmhd_params& p, const lb::RefState& ref)
     k.eps_r = (R)ref.eps_r;
     k.p_r = (R)ref.p_r;
     k.dx = (R)p.dx;
+    const double eps0 = 1.0 / (p.c * p.c);
+    for (int a = 0; a < 3; ++a) {
+        k.Er[a] = (R)Er[a];
+        k.Br[a] = (R)Br[a];
+        for (int b = 0; b < 3; ++b)
+            k.dXr[a][b] = (R)(rr.Xr[a][b] - eps0 * (Er[a] * Er[b] + p.c * p.c * Br[a] * Br[b]));
+    }
+    const double BxE[3] = {Br[1] * Er[2] - Br[2] * Er[1], Br[2] * Er[0] - Br[0] * Er[2], Br[0] * Er[1] - Br[1] * Er[0]};
+    for (int a = 0; a < 3; ++a) k.dYr[a] = (R)(rr.Yr[a] - eps0 * p.c * BxE[a]);
+    // moments of the reference EM terms: T^00 = tr X / 2, T^0a = -Y_a, T^ab = -X_ab + tr X / 2 d_ab
+    const double tr = rr.Xr[0][0] + rr.Xr[1][1] + rr.Xr[2][2];
+    k.Tem[0] = (R)(0.5 * tr);
+    for (int a = 0; a < 3; ++a) k.Tem[1 + a] = (R)(-rr.Yr[a]);
+    for (int a = 0; a < 3; ++a) k.Tem[4 + a] = (R)(-rr.Xr[a][a] + 0.5 * tr);
+    k.Tem[7] = (R)(-rr.Xr[0][1]);
+    k.Tem[8] = (R)(-rr.Xr[0][2]);
+    k.Tem[9] = (R)(-rr.Xr[1][2]);
     const bool f64 = p.precision == LBRMHD_FP64;
     k.tol = (R)(p.tol > 0 ? p.tol : (f64 ? 1e-14 : 1e-6));
     k.maxit = p.max_iters > 0 ? p.max_iters : 64;
     return k;
 }
+
+RunRef runref(const RunState& r) { return RunRef{r.Er, r.Br, r.Xr, r.Yr}; }
 
 template <class Cfg>
 lb::PopView<Cfg> view(const RunState& r, int buf)
@@ -111,17 +141,47 @@ lb::PopView<Cfg> view(const RunState& r, int buf)
     return v;
 }
 
-// reference rest equilibrium of the deviations (restated equilibria at u = E = B = 0)
-void set_reference(RunState& r, double n_r, double p_r)
+// reference state of the deviations, from the means of the initial fields
+// (means_kernel layout): the rest equilibrium of (n_r, p_r) plus the mean EM
+// terms X = eps0 <E_a E_b + c^2 B_a B_b>, Y = eps0 c <B x E> for f and g, and
+// the Maxwell equilibrium of (Er, Br) = (<E>, <B>), J = 0, rho_c = 0 for h
+void set_reference(RunState& r, const double* means)
 {
-    const double c2 = r.p.c * r.p.c;
+    for (int j = 0; j < lb::NMEANS; ++j) r.means[j] = means[j];
+    const double c = r.p.c, c2 = c * c, eps0 = 1.0 / c2;
+    const double n_r = means[0], p_r = means[1];
     r.ref.n_r = n_r;
     r.ref.p_r = p_r;
     r.ref.eps_r = n_r * c2 + p_r / (r.p.gamma_ad - 1.0);
+    const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+    for (int a = 0; a < 3; ++a) {
+        r.Er[a] = means[2 + a];
+        r.Br[a] = means[5 + a];
+        r.Yr[a] = eps0 * c * means[20 + a];
+    }
+    for (int m = 0; m < 6; ++m) {
+        const double x = eps0 * (means[8 + m] + c2 * means[14 + m]);
+        r.Xr[ia[m]][ib[m]] = r.Xr[ib[m]][ia[m]] = x;
+    }
+    const double* Er = r.Er;
+    const double* Br = r.Br;
+    for (int kk = 0; kk < 24; ++kk) {
+        const int p = kk / 8, i = (kk % 8) / 2, j = kk % 2, ie = (i + 3) % 4;
+        const int a1 = lb::plane_a1(p), a2 = lb::plane_a2(p);
+        const double e = lb::kSqrt2 / (16.0 * c) * (lb::hop_s1(ie) * Er[a1] + lb::hop_s2(ie) * Er[a2]);
+        const double m = 0.125 * lb::plane_orient(p) * Br[lb::plane_normal(p)];
+        r.refpops.h[kk] = j == 0 ? e - m : m - e;
+    }
+    r.refpops.h[24] = 0.0;
+    const double tr = r.Xr[0][0] + r.Xr[1][1] + r.Xr[2][2];
     double fmax = 0.0, gmax = 0.0;
     for (int i = 0; i < 19; ++i) {
+        const int cx = lb::c19(i, 0), cy = lb::c19(i, 1), cz = lb::c19(i, 2);
         double v = 3.0 * p_r;
         if (i == 0) v += lb::kRest * (3.0 * p_r - r.ref.eps_r);
+        v += 2.3 * tr - lb::kSqrt19_3 * (cx * r.Yr[0] + cy * r.Yr[1] + cz * r.Yr[2]) -
+             3.8 * (cx * cx * r.Xr[0][0] + cy * cy * r.Xr[1][1] + cz * cz * r.Xr[2][2]) -
+             14.25 * (cx * cy * r.Xr[0][1] + cx * cz * r.Xr[0][2] + cy * cz * r.Xr[1][2]);
         r.refpops.f[i] = lb::w19(i) * v;
         r.refpops.g[i] = lb::wg19(i) * n_r;
         fmax = std::fmax(fmax, std::fabs(r.refpops.f[i]));
@@ -172,7 +232,7 @@ int step_run(lbrmhd_handle h, RunState& r)
     A.stride = r.stride;
     for (int a = 0; a < 3; ++a) A.periodic[a] = r.periodic[a];
     A.flags = r.p.flags;
-    A.k = make_phys<R>(r.p, r.ref);
+    A.k = make_phys<R>(r.p, r.ref, runref(r));
     A.hs = r.hs;
     A.stats = r.d_stats;
     LB_CK(lb::launch_step<Cfg>(A, h->stream));
@@ -187,13 +247,13 @@ int step_run(lbrmhd_handle h, RunState& r)
 template <class Cfg>
 int init_run(lbrmhd_handle h, RunState& r, const lb::InitInputs& in)
 {
-    LB_CK(lb::launch_mean_np(in.n, in.p, r.N, h->d_small, h->stream));
-    double np[2];
-    LB_CK(cudaMemcpyAsync(np, h->d_small, sizeof(np), cudaMemcpyDeviceToHost, h->stream));
+    LB_CK(lb::launch_means(in, r.N, h->d_scratch, h->d_small, h->stream));
+    double mean[lb::NMEANS];
+    LB_CK(cudaMemcpyAsync(mean, h->d_small, sizeof(mean), cudaMemcpyDeviceToHost, h->stream));
     LB_CK(cudaStreamSynchronize(h->stream));
-    set_reference(r, np[0], np[1]);
+    set_reference(r, mean);
     LB_CK(cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream));
-    LB_CK(lb::launch_init<Cfg>(view<Cfg>(r, r.cur), in, make_phys<double>(r.p, r.ref), h->d_flag, h->stream));
+    LB_CK(lb::launch_init<Cfg>(view<Cfg>(r, r.cur), in, make_phys<double>(r.p, r.ref, runref(r)), h->d_flag, h->stream));
     int bad = 0;
     LB_CK(cudaMemcpyAsync(&bad, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     LB_CK(cudaMemsetAsync(r.d_stats, 0, 3 * sizeof(unsigned long long), h->stream));
@@ -297,7 +357,8 @@ int lbrmhd_create(const lbrmhd_params* params, int n_runs, lbrmhd_handle* out)
         s.N = (int64_t)s.p.nx * s.p.ny * s.p.nz;
         s.stride = (s.N + 127) / 128 * 128;
         for (int a = 0; a < 3; ++a) s.periodic[a] = s.p.bc[2 * a] == LBRMHD_PERIODIC;
-        set_reference(s, 1.0, 1.0);
+        double m0[lb::NMEANS] = {1.0, 1.0};
+        set_reference(s, m0);
         for (int b = 0; b < 2 && ok; ++b) {
             ok = ok && cudaMalloc(&s.pops[b], 38 * s.stride * pb) == cudaSuccess;
             ok = ok && cudaMalloc(&s.h[b], 25 * s.stride * hb) == cudaSuccess;
@@ -312,9 +373,10 @@ int lbrmhd_create(const lbrmhd_params* params, int n_runs, lbrmhd_handle* out)
         if (ok) cudaMemset(s.d_stats, 0, 3 * sizeof(unsigned long long));
         max_blocks = std::max<int64_t>(max_blocks, (s.N + lb::kDiagThreads - 1) / lb::kDiagThreads);
     }
-    ok = ok && cudaMalloc(&h->d_scratch, (size_t)max_blocks * lb::NPART * sizeof(double)) == cudaSuccess;
+    const size_t scratch = std::max<size_t>((size_t)max_blocks * lb::NPART, (size_t)lb::kMeansBlocks * lb::NMEANS);
+    ok = ok && cudaMalloc(&h->d_scratch, scratch * sizeof(double)) == cudaSuccess;
     h->scratch_blocks = max_blocks;
-    ok = ok && cudaMalloc(&h->d_small, 16 * sizeof(double)) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->d_small, 32 * sizeof(double)) == cudaSuccess;
     ok = ok && cudaMalloc(&h->d_flag, sizeof(int)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -397,7 +459,7 @@ int lbrmhd_get_moments_device(lbrmhd_handle h, int run, double* out)
     RunState& r = h->runs[run];
     if (!r.initialized) return fail(h, LBRMHD_ERR_STATE, "run not initialised");
     LB_CK(cudaSetDevice(h->device));
-    const lb::Phys<double> k = make_phys<double>(r.p, r.ref);
+    const lb::Phys<double> k = make_phys<double>(r.p, r.ref, runref(r));
     switch (h->precision) {
         case LBRMHD_FP64: LB_CK(lb::launch_moments<lb::CfgF64>(view<lb::CfgF64>(r, r.cur), k, out, h->stream)); break;
         case LBRMHD_FP32: LB_CK(lb::launch_moments<lb::CfgF32>(view<lb::CfgF32>(r, r.cur), k, out, h->stream)); break;
@@ -457,7 +519,7 @@ int lbrmhd_get_diagnostics(lbrmhd_handle h, int run, double* out)
     RunState& r = h->runs[run];
     if (!r.initialized) return fail(h, LBRMHD_ERR_STATE, "run not initialised");
     LB_CK(cudaSetDevice(h->device));
-    const lb::Phys<double> k = make_phys<double>(r.p, r.ref);
+    const lb::Phys<double> k = make_phys<double>(r.p, r.ref, runref(r));
     switch (h->precision) {
         case LBRMHD_FP64:
             LB_CK(lb::launch_diag<lb::CfgF64>(view<lb::CfgF64>(r, r.cur), k, r.ref, h->d_scratch, h->scratch_blocks,
@@ -493,14 +555,14 @@ int lbrmhd_get_stats(lbrmhd_handle h, int run, int64_t* out4)
     return LBRMHD_OK;
 }
 
-// checkpoint blob: per run [int64 steps][3 double ref][uint64 stats x3]
+// checkpoint blob: per run [int64 steps][NMEANS double reference means][uint64 stats x3]
 // [pops 38 N][h 25 N][prim 12 N] (storage format)
 int lbrmhd_state_bytes(lbrmhd_handle h, size_t* bytes)
 {
     if (!h || !bytes) return LBRMHD_ERR_BAD_ARG;
     const size_t pb = pop_bytes(h->precision), hb = hp_bytes(h->precision);
     size_t total = 0;
-    for (auto& r : h->runs) total += 8 + 24 + 24 + (size_t)r.N * (38 * pb + 25 * hb + lb::NPRIM * hb);
+    for (auto& r : h->runs) total += 8 + 8 * lb::NMEANS + 24 + (size_t)r.N * (38 * pb + 25 * hb + lb::NPRIM * hb);
     *bytes = total;
     return LBRMHD_OK;
 }
@@ -517,9 +579,8 @@ int lbrmhd_get_state(lbrmhd_handle h, void* host_buf, size_t bytes)
         if (!r.initialized) return fail(h, LBRMHD_ERR_STATE, "run not initialised");
         std::memcpy(o, &r.steps, 8);
         o += 8;
-        const double ref[3] = {r.ref.n_r, r.ref.eps_r, r.ref.p_r};
-        std::memcpy(o, ref, 24);
-        o += 24;
+        std::memcpy(o, r.means, 8 * lb::NMEANS);
+        o += 8 * lb::NMEANS;
         LB_CK(cudaMemcpyAsync(o, r.d_stats, 24, cudaMemcpyDeviceToHost, h->stream));
         o += 24;
         for (int pl = 0; pl < 38; ++pl, o += r.N * pb)
@@ -547,11 +608,10 @@ int lbrmhd_set_state(lbrmhd_handle h, const void* host_buf, size_t bytes)
     for (auto& r : h->runs) {
         std::memcpy(&r.steps, o, 8);
         o += 8;
-        double ref[3];
-        std::memcpy(ref, o, 24);
-        o += 24;
-        set_reference(r, ref[0], ref[2]);
-        r.ref.eps_r = ref[1];
+        double means[lb::NMEANS];
+        std::memcpy(means, o, 8 * lb::NMEANS);
+        o += 8 * lb::NMEANS;
+        set_reference(r, means);
         LB_CK(cudaMemcpyAsync(r.d_stats, o, 24, cudaMemcpyHostToDevice, h->stream));
         o += 24;
         for (int pl = 0; pl < 38; ++pl, o += r.N * pb)

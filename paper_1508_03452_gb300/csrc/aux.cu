@@ -76,7 +76,9 @@ __device__ __forceinline__ void set_equilibrium(const PopView<Cfg>& V, int64_t c
     R J[3];
     ohm_current(s.E, s.u, s.B, s.rho, k, J);
     EqStore<0, Cfg, R>::run(V, c, q);
-    HeqStore<0, Cfg, R>::run(V, c, s.E, s.B, J, k);
+    const R dE[3] = {s.E[0] - k.Er[0], s.E[1] - k.Er[1], s.E[2] - k.Er[2]};
+    const R dB[3] = {s.B[0] - k.Br[0], s.B[1] - k.Br[1], s.B[2] - k.Br[2]};
+    HeqStore<0, Cfg, R>::run(V, c, dE, dB, J, k);
     V.h[24 * V.stride + c] = (typename Cfg::hpop)s.rho;
 }
 
@@ -131,32 +133,53 @@ __global__ void init_kernel(PopView<Cfg> V, InitInputs in, Phys<double> k, int* 
     set_equilibrium<Cfg, double>(V, c, s, k);
 }
 
-// float64 sums of n and p for the reference rest state (one block)
-__global__ void mean_np_kernel(const double* n, const double* p, int64_t N, double* out)
+// float64 means for the reference state: n, p, E (3), B (3), E_a E_b (6: xx yy
+// zz xy xz yz), B_a B_b (6), B x E (3). Pass 1: per-block partial sums
+// (grid-stride); pass 2: one block adds the partials in block order, so the
+// result does not depend on scheduling.
+__global__ void means_partial_kernel(InitInputs in, int64_t N, double* partial)
 {
-    __shared__ double sh[2][32];
-    double sn = 0.0, sp = 0.0;
-    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
-        sn += n[i];
-        sp += p[i];
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        sn += __shfl_down_sync(0xffffffffu, sn, o);
-        sp += __shfl_down_sync(0xffffffffu, sp, o);
-    }
-    if (threadIdx.x % 32 == 0) {
-        sh[0][threadIdx.x / 32] = sn;
-        sh[1][threadIdx.x / 32] = sp;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
-            a += sh[0][w];
-            b += sh[1][w];
+    constexpr int M = NMEANS;
+    __shared__ double sh[M][kMeansThreads / 32];
+    double acc[M];
+    for (int j = 0; j < M; ++j) acc[j] = 0.0;
+    const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        double E[3], B[3];
+        input_E(in, i, N, E);
+        for (int a = 0; a < 3; ++a) B[a] = in.B[a * N + i];
+        acc[0] += in.n[i];
+        acc[1] += in.p[i];
+        for (int a = 0; a < 3; ++a) {
+            acc[2 + a] += E[a];
+            acc[5 + a] += B[a];
         }
-        out[0] = a / (double)N;
-        out[1] = b / (double)N;
+        for (int m = 0; m < 6; ++m) {
+            acc[8 + m] += E[ia[m]] * E[ib[m]];
+            acc[14 + m] += B[ia[m]] * B[ib[m]];
+        }
+        acc[20] += B[1] * E[2] - B[2] * E[1];
+        acc[21] += B[2] * E[0] - B[0] * E[2];
+        acc[22] += B[0] * E[1] - B[1] * E[0];
+    }
+    for (int j = 0; j < M; ++j)
+        for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_down_sync(0xffffffffu, acc[j], o);
+    if (threadIdx.x % 32 == 0)
+        for (int j = 0; j < M; ++j) sh[j][threadIdx.x / 32] = acc[j];
+    __syncthreads();
+    if (threadIdx.x < M) {
+        double a = 0.0;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) a += sh[threadIdx.x][w];
+        partial[(int64_t)blockIdx.x * M + threadIdx.x] = a;
+    }
+}
+
+__global__ void means_final_kernel(const double* partial, int nblocks, int64_t N, double* out)
+{
+    if (threadIdx.x < NMEANS) {
+        double a = 0.0;
+        for (int b = 0; b < nblocks; ++b) a += partial[(int64_t)b * NMEANS + threadIdx.x];
+        out[threadIdx.x] = a / (double)N;
     }
 }
 
@@ -342,7 +365,7 @@ __global__ void populations_kernel(PopView<Cfg> V, RefPops ref, double* f, doubl
         if (g) g[i * N + c] = ref.g[i] + (double)ld_pop<Cfg>(V.g + (int64_t)i * V.stride + c, V.hs.g[i]);
     }
     if (h)
-        for (int i = 0; i < 25; ++i) h[i * N + c] = (double)V.h[(int64_t)i * V.stride + c];
+        for (int i = 0; i < 25; ++i) h[i * N + c] = ref.h[i] + (double)V.h[(int64_t)i * V.stride + c];
 }
 
 // per-block float64 partial diagnostics: sum N^0, T^{0 nu} (4), rho_c, max |div B|,
@@ -427,9 +450,12 @@ cudaError_t launch_init(const PopView<Cfg>& V, const InitInputs& in, const Phys<
     return cudaGetLastError();
 }
 
-cudaError_t launch_mean_np(const double* n, const double* p, int64_t N, double* out, cudaStream_t s)
+cudaError_t launch_means(const InitInputs& in, int64_t N, double* partial, double* out, cudaStream_t s)
 {
-    mean_np_kernel<<<1, 1024, 0, s>>>(n, p, N, out);
+    int nb = (int)((N + kMeansThreads - 1) / kMeansThreads);
+    nb = nb < kMeansBlocks ? nb : kMeansBlocks;
+    means_partial_kernel<<<nb, kMeansThreads, 0, s>>>(in, N, partial);
+    means_final_kernel<<<1, 32, 0, s>>>(partial, nb, N, out);
     return cudaGetLastError();
 }
 

@@ -29,7 +29,7 @@ struct InitInputs {
 
 // absolute reference rest equilibrium populations (added back on output)
 struct RefPops {
-    double f[19], g[19];
+    double f[19], g[19], h[25];
 };
 
 struct RefState {
@@ -37,6 +37,8 @@ struct RefState {
 };
 
 constexpr int NPART = 9;
+constexpr int NMEANS = 23;  // entries of the reference-state means
+constexpr int kMeansThreads = 256, kMeansBlocks = 608;
 constexpr int kDiagThreads = 256;
 
 // block-wide reduction of NPART float64 values (index 6 is a max, the others
@@ -66,7 +68,7 @@ template <class Cfg>
 cudaError_t launch_step(const StepArgs<Cfg>& A, cudaStream_t stream);
 template <class Cfg>
 cudaError_t launch_init(const PopView<Cfg>& V, const InitInputs& in, const Phys<double>& k, int* bad, cudaStream_t s);
-cudaError_t launch_mean_np(const double* n, const double* p, int64_t N, double* out, cudaStream_t s);
+cudaError_t launch_means(const InitInputs& in, int64_t N, double* partial, double* out, cudaStream_t s);
 template <class Cfg>
 cudaError_t launch_boundaries(const PopView<Cfg>& V, const Phys<typename Cfg::real>& k, const int* bc, int layers,
                               double u0, cudaStream_t s);

@@ -81,6 +81,9 @@ struct Phys {
     R C, kappa, kvisc;         // Courant number, (1 - C)/2, alpha c dt / dx
     R n_r, eps_r, p_r;         // reference rest state of the deviations
     R dx;                      // lattice spacing
+    R Er[3], Br[3];            // reference fields of the h deviations (h_ref = h^eq(Er, Br, J = 0, rho = 0))
+    R dXr[3][3], dYr[3];       // reference EM terms of the f deviations minus their values at (Er, Br)
+    R Tem[10];                 // moments of the reference EM terms: T^00, T^0a (3), T^ab (xx, yy, zz, xy, xz, yz)
     R tol;                     // recovery tolerance (relative change of beta)
     int maxit;
 };
@@ -100,8 +103,12 @@ __device__ __forceinline__ R sq(R a) { return a * a; }
 //
 //   f_i^eq = w_i [ 3 p + d_{i0} (3/4)(361/33)(3p - eps) + (3/4)(eps + p) Q_i + EM_i ]
 //   Q_i  = L1 g^2 (c.b) + 19 g^2 sum_{a<b} c_a c_b b_a b_b + (4/15) g^2 (19 sum_a c_a^2 b_a^2 - 4 b^2)
-//   EM_i = eps0 [ 2.3 (c^2 B^2 + E^2) - c sqrt(19/3) (B x E).c
-//                 - 3.8 sum_a c_a^2 X_aa - 14.25 sum_{a<b} c_a c_b X_ab ],  X_ab = E_a E_b + c^2 B_a B_b
+//   EM_i = 2.3 tr X - sqrt(19/3) Y.c - 3.8 sum_a c_a^2 X_aa - 14.25 sum_{a<b} c_a c_b X_ab,
+//          X_ab = eps0 (E_a E_b + c^2 B_a B_b), Y = eps0 c (B x E)
+// The deviations subtract the reference rest state and a reference (Xr, Yr)
+// of the EM terms; X - Xr and Y - Yr are formed from the field deviations
+// dE = E - Er, dB = B - Br so that a uniform background field costs no
+// float32 precision.
 //   g_i^eq = w'_i n g (1 + 3 q c.b + 4.5 q^2 (c.b)^2 - 1.5 b^2)
 // (b = u / c, g = Lorentz factor, c = chat_i)
 // ---------------------------------------------------------------------------
@@ -114,28 +121,49 @@ struct EqCell {
     R kf;                      // g / tau  (Anderson-Witting factor K_i = kf (1 - q c.b))
 };
 
+// n_dev = n - n_r, eps_dev = eps - eps_r, dE = E - Er and dB = B - Br are passed
+// separately so that the float32 path never rounds the large reference values
+// into the deviations.
 template <class R>
-__device__ __forceinline__ void eq_cell(const Prim<R>& s, const Phys<R>& k, EqCell<R>& q)
+__device__ __forceinline__ void eq_cell(const Prim<R>& s, R n_dev, R eps_dev, const R* dE, const R* dB,
+                                        const Phys<R>& k, EqCell<R>& q)
 {
     const R b0 = s.u[0] * k.inv_c, b1 = s.u[1] * k.inv_c, b2 = s.u[2] * k.inv_c;
     q.b[0] = b0; q.b[1] = b1; q.b[2] = b2;
     q.b2 = b0 * b0 + b1 * b1 + b2 * b2;
     q.g2 = R(1) / (R(1) - q.b2);
     q.g = sqrt(q.g2);
-    const R p = k.gm1 * (s.eps - s.n * k.c2);
-    q.three_dp = R(3) * (p - k.p_r);
-    q.rest_dev = R(kRest) * ((R(3) * p - s.eps) - (R(3) * k.p_r - k.eps_r));
+    const R p_dev = k.gm1 * (eps_dev - n_dev * k.c2);
+    const R p = k.p_r + p_dev;
+    q.three_dp = R(3) * p_dev;
+    q.rest_dev = R(kRest) * (R(3) * p_dev - eps_dev);
     q.wq = R(0.75) * (s.eps + p);
     const R* E = s.E;
     const R* B = s.B;
-    const R BxE[3] = {B[1] * E[2] - B[2] * E[1], B[2] * E[0] - B[0] * E[2], B[0] * E[1] - B[1] * E[0]};
-    q.em_iso = k.eps0 * R(2.3) * (k.c2 * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]) + E[0] * E[0] + E[1] * E[1] + E[2] * E[2]);
-    for (int a = 0; a < 3; ++a) q.em_lin[a] = -k.eps0 * k.c * R(kSqrt19_3) * BxE[a];
+    // X - Xr = eps0 [dE_a E_b + Er_a dE_b + c^2 (dB_a B_b + Br_a dB_b)] - dXr
     for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) q.X[a][b] = k.eps0 * (E[a] * E[b] + k.c2 * B[a] * B[b]);
+        for (int b = 0; b < 3; ++b)
+            q.X[a][b] = k.eps0 * (dE[a] * E[b] + k.Er[a] * dE[b] + k.c2 * (dB[a] * B[b] + k.Br[a] * dB[b])) -
+                        k.dXr[a][b];
+    // Y - Yr = eps0 c (dB x E + Br x dE) - dYr
+    const R Yd[3] = {
+        k.eps0 * k.c * (dB[1] * E[2] - dB[2] * E[1] + k.Br[1] * dE[2] - k.Br[2] * dE[1]) - k.dYr[0],
+        k.eps0 * k.c * (dB[2] * E[0] - dB[0] * E[2] + k.Br[2] * dE[0] - k.Br[0] * dE[2]) - k.dYr[1],
+        k.eps0 * k.c * (dB[0] * E[1] - dB[1] * E[0] + k.Br[0] * dE[1] - k.Br[1] * dE[0]) - k.dYr[2]};
+    q.em_iso = R(2.3) * (q.X[0][0] + q.X[1][1] + q.X[2][2]);
+    for (int a = 0; a < 3; ++a) q.em_lin[a] = -R(kSqrt19_3) * Yd[a];
     q.ng = s.n * q.g;
-    q.dng = q.ng - k.n_r;
+    // n g - n_r = n_dev g + n_r (g - 1), g - 1 = g^2 b^2 / (g + 1)
+    q.dng = n_dev * q.g + k.n_r * (q.g2 * q.b2 / (q.g + R(1)));
     q.kf = q.g * k.inv_tau;
+}
+
+template <class R>
+__device__ __forceinline__ void eq_cell(const Prim<R>& s, const Phys<R>& k, EqCell<R>& q)
+{
+    const R dE[3] = {s.E[0] - k.Er[0], s.E[1] - k.Er[1], s.E[2] - k.Er[2]};
+    const R dB[3] = {s.B[0] - k.Br[0], s.B[1] - k.Br[1], s.B[2] - k.Br[2]};
+    eq_cell(s, s.n - k.n_r, s.eps - k.eps_r, dE, dB, k, q);
 }
 
 // f_i^eq - f_i^eq(reference rest state), population I
@@ -191,7 +219,9 @@ __device__ __forceinline__ R heq13(const R* E, const R* B, const R* J, const Phy
     return j == 0 ? a + e - m : a - e + m;
 }
 
-// EM moments of the 25 populations: E' (Eq. Cal_E), B (Eq. Cal_B), rho_c (Eq. Cal_rhoc)
+// EM moments of the 25 populations (Eqs. Cal_E, Cal_B, Cal_rhoc) for h stored as
+// deviations from h_ref = h^eq(Er, Br, 0, 0): returns E' - Er, B - Br and rho_c
+// (h_ref carries no charge)
 template <class R>
 __device__ __forceinline__ void em_moments(const R* h, const Phys<R>& k, R* Ep, R* B, R& rho)
 {
@@ -256,8 +286,9 @@ __device__ __forceinline__ void ohm_current(const R* E, const R* u, const R* B, 
 // Landau eigen-solve (coupling subsection): largest eigenpair of
 // A = [T - eps0 F F(E_old, B_old)] eta by a shifted power iteration
 // (shift p_old - s_old pushes the spacelike eigenvalues to ~0), seeded with
-// the previous velocity. T holds the full moments (reference added).
-// Returns the iteration count, or -1 if it failed.
+// the previous velocity. T holds the moments with eps_r taken out of T^00
+// (the reference rest state's other entries included); the returned lambda is
+// the eigenvalue minus eps_r. Returns the iteration count, or -1 if it failed.
 // ---------------------------------------------------------------------------
 template <class R>
 __device__ __forceinline__ int landau(const R T[4][4], const Prim<R>& old, const Phys<R>& k, R beta[3], R& lambda,
@@ -270,6 +301,7 @@ __device__ __forceinline__ int landau(const R T[4][4], const Prim<R>& old, const
     const R ExB[3] = {E[1] * B[2] - E[2] * B[1], E[2] * B[0] - E[0] * B[2], E[0] * B[1] - E[1] * B[0]};
     // S = eps0 F^{mu rho} F_rho^nu: S00 = eps0 E^2, S0a = eps0 c (E x B)_a,
     // Sab = eps0 [-E_a E_b + c^2 (d_ab B^2 - B_a B_b)]
+    // T[0][0] holds T^00 - eps_r: A[0][0] and lambda are deviations from eps_r
     R A[4][4];
     A[0][0] = T[0][0] - k.eps0 * E2;
     for (int a = 0; a < 3; ++a) {
@@ -284,11 +316,12 @@ __device__ __forceinline__ int landau(const R T[4][4], const Prim<R>& old, const
     s_old = R(0.5) * k.eps0 * (k.c2 * B2 - E2);
     const R p_old = k.gm1 * (old.eps - old.n * k.c2);
     const R shift = p_old - s_old;
+    const R a00_full = k.eps_r + shift;  // eps_r restored in the first row only
     R v1 = old.u[0] * k.inv_c, v2 = old.u[1] * k.inv_c, v3 = old.u[2] * k.inv_c;
     int it = 0;
     bool done = false;
     for (it = 1; it <= k.maxit; ++it) {
-        const R w0 = A[0][0] + A[0][1] * v1 + A[0][2] * v2 + A[0][3] * v3 + shift;
+        const R w0 = A[0][0] + A[0][1] * v1 + A[0][2] * v2 + A[0][3] * v3 + a00_full;
         const R w1 = A[1][0] + (A[1][1] + shift) * v1 + A[1][2] * v2 + A[1][3] * v3;
         const R w2 = A[2][0] + A[2][1] * v1 + (A[2][2] + shift) * v2 + A[2][3] * v3;
         const R w3 = A[3][0] + A[3][1] * v1 + A[3][2] * v2 + (A[3][3] + shift) * v3;

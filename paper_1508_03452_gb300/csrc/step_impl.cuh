@@ -174,31 +174,41 @@ __global__ void __launch_bounds__(128) step_kernel(const StepArgs<Cfg> A)
     // 2. moments (reference rest state added back)
     const R qq = R(kQ), q2 = R(kQ2);
     R T[4][4];
-    T[0][0] = k.eps_r + Tm[0];
-    T[0][1] = T[1][0] = qq * Tm[1];
-    T[0][2] = T[2][0] = qq * Tm[2];
-    T[0][3] = T[3][0] = qq * Tm[3];
-    T[1][1] = k.p_r + q2 * Tm[4];
-    T[2][2] = k.p_r + q2 * Tm[5];
-    T[3][3] = k.p_r + q2 * Tm[6];
-    T[1][2] = T[2][1] = q2 * Tm[7];
-    T[1][3] = T[3][1] = q2 * Tm[8];
-    T[2][3] = T[3][2] = q2 * Tm[9];
-    const R N0 = k.n_r + Nm[0];
-    R Ep[3], Bn[3], rho;
-    em_moments(h, k, Ep, Bn, rho);
+    // reference moments: rest state (eps_r, p_r) plus the reference EM terms k.Tem
+    T[0][0] = k.Tem[0] + Tm[0];  // T^00 - eps_r
+    T[0][1] = T[1][0] = k.Tem[1] + qq * Tm[1];
+    T[0][2] = T[2][0] = k.Tem[2] + qq * Tm[2];
+    T[0][3] = T[3][0] = k.Tem[3] + qq * Tm[3];
+    T[1][1] = k.p_r + k.Tem[4] + q2 * Tm[4];
+    T[2][2] = k.p_r + k.Tem[5] + q2 * Tm[5];
+    T[3][3] = k.p_r + k.Tem[6] + q2 * Tm[6];
+    T[1][2] = T[2][1] = k.Tem[7] + q2 * Tm[7];
+    T[1][3] = T[3][1] = k.Tem[8] + q2 * Tm[8];
+    T[2][3] = T[3][2] = k.Tem[9] + q2 * Tm[9];
+    const R dN0 = Nm[0];  // N^0 - n_r
+    R dEp[3], dB[3], Ep[3], Bn[3], rho;
+    em_moments(h, k, dEp, dB, rho);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        Ep[a] = k.Er[a] + dEp[a];
+        Bn[a] = k.Br[a] + dB[a];
+    }
 
     // 3. recovery
     R beta[3], lambda, s_old;
     const int it = landau(T, old, k, beta, lambda, s_old);
     Prim<R> nw;
-    R J[3];
+    R J[3], n_dev, eps_dev;
     const bool ok = it > 0;
     if (ok) {
         const R b2 = beta[0] * beta[0] + beta[1] * beta[1] + beta[2] * beta[2];
         const R g2 = R(1) / (R(1) - b2);
-        nw.eps = lambda - s_old;
-        nw.n = N0 / sqrt(g2);
+        const R g = sqrt(g2);
+        eps_dev = lambda - s_old;
+        // n = N^0 / U^0: n - n_r = (dN0 - n_r (g - 1)) / g, g - 1 = g^2 b^2 / (g + 1)
+        n_dev = (dN0 - k.n_r * (g2 * b2 / (g + R(1)))) / g;
+        nw.eps = k.eps_r + eps_dev;
+        nw.n = k.n_r + n_dev;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             nw.u[a] = k.c * beta[a];
@@ -208,15 +218,24 @@ __global__ void __launch_bounds__(128) step_kernel(const StepArgs<Cfg> A)
         ohm_solve(Ep, nw.u, nw.B, rho, g2, k, nw.E, J);
     } else {
         nw = old;
+        n_dev = old.n - k.n_r;
+        eps_dev = old.eps - k.eps_r;
         ohm_current(old.E, old.u, old.B, old.rho, k, J);
     }
 
     // 4. collisions and stores
+    R dE[3], dBn[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        dE[a] = nw.E[a] - k.Er[a];
+        dBn[a] = ok ? dB[a] : nw.B[a] - k.Br[a];
+    }
     EqCell<R> q;
-    eq_cell(nw, k, q);
+    eq_cell(nw, n_dev, eps_dev, dE, dBn, k, q);
     CollideFG<0, Cfg>::run(A, c, fd, gd, q);
     const bool em_coll = (A.flags & FLAG_NO_EM_COLLISION) == 0;
-    CollideH<0, Cfg>::run(A, c, h, nw.E, nw.B, J, em_coll);
+    // h_c - h_ref = 2 h^eq(E - Er, B - Br, J) - (h - h_ref)  (Eq. Maxwell-eq is linear)
+    CollideH<0, Cfg>::run(A, c, h, dE, dBn, J, em_coll);
     A.hout[24 * A.stride + c] = (typename Cfg::hpop)(em_coll ? R(2) * nw.rho - h[24] : h[24]);
 
     A.pout[P_N * A.stride + c] = (typename Cfg::prim)nw.n;
