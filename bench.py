@@ -297,6 +297,23 @@ def run_gpu(args, world, rank, local):
         dist.destroy_process_group()
 
 
+def run_profile_case(args):
+    """Small profiling case (no timing): one 1024 x 1024 current-sheet run
+    (sigma = 100) in the chosen precision, init + `--steps` steps."""
+    import torch
+
+    from paper_1508_03452_gb300 import lbrmhd as L
+    from paper_1508_03452_gb300 import workloads as W
+
+    prec = {"fp32": L.FP32, "fp16": L.FP16_DEV, "fp64": L.FP64}[args.precision]
+    F = W.current_sheet(NX, NY, 1, delta=8.0)
+    s = L.Solver(L.make_params(NX, NY, 1, sigma=100.0, precision=prec), stream=torch.cuda.current_stream())
+    s.init_fields(0, F.n, F.p, F.u, F.B)
+    s.step(args.steps)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": args.precision, "steps": args.steps, "stats": s.stats()}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -306,9 +323,12 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--profile-case", action="store_true", help="untimed 1024^2 single-run case for ncu captures")
     args = ap.parse_args()
     world, rank, local = dist_env()
-    if args.impl == "reference":
+    if args.profile_case:
+        run_profile_case(args)
+    elif args.impl == "reference":
         run_reference(args, world, rank)
     else:
         run_gpu(args, world, rank, local)
