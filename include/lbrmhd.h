@@ -153,6 +153,40 @@ int lbrmhd_get_populations(lbrmhd_handle h, int run, double* f, double* g, doubl
  * NONFINITE if any cell holds a NaN or Inf. Host output. */
 int lbrmhd_get_diagnostics(lbrmhd_handle h, int run, double* out);
 
+/* Diagnostics for callers that cannot allocate device memory when they need
+ * them: for instance a monitor running while another framework's memory pool
+ * owns the free device memory (a new cudaMalloc could fail even though the
+ * reduction needs only a few kilobytes), or a time-critical loop that must not
+ * pay the device-wide synchronisation that cudaMalloc / cudaFree may imply.
+ * The paper has no counterpart; this is a library facility.
+ *
+ * Same values as lbrmhd_get_diagnostics (LBRMHD_NDIAG float64, same order),
+ * but this call allocates nothing and copies nothing to the host: the
+ * per-block partial sums of the reduction live in a fixed static device array
+ * of this library (4.7 MB on every GPU that loads the library, held until the
+ * process exits), and the results are written to d_out, a caller-owned device
+ * array of at least LBRMHD_NDIAG float64. The work is queued on the handle's
+ * stream and the call returns without waiting; d_out is valid once that
+ * stream reaches this point.
+ *
+ * Limits and rules:
+ *   - runs of at most 16,777,216 cells (256^3); larger runs are rejected with
+ *     LBRMHD_ERR_BAD_ARG and a message naming the limit.
+ *   - The first call on a device looks up the device address of the static
+ *     array (once per device, with that device current); make that first call
+ *     before any stream capture.
+ *   - Every call shares the one array, which keeps the previous call's
+ *     contents; each call writes every entry it later reads, so no clearing is
+ *     needed. Calls whose work overlaps on the GPU (other streams, other
+ *     threads, other handles on the same device) race on the array and must be
+ *     serialised by the caller.
+ *   - The non-finite count is returned in d_out[8]; unlike
+ *     lbrmhd_get_diagnostics this call cannot report NONFINITE in its return
+ *     value, since it does not wait for the result.
+ * Errors: BAD_ARG (run out of range, NULL d_out, run above the limit), STATE
+ * (run not initialised), CUDA. */
+int lbrmhd_get_diagnostics_noalloc(lbrmhd_handle h, int run, double* d_out);
+
 /* Counters of one run: [0] steps taken, [1] recovery failures, [2] sum of
  * recovery iterations, [3] maximum recovery iterations. Host output. */
 int lbrmhd_get_stats(lbrmhd_handle h, int run, int64_t* out4);

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -320,6 +321,42 @@ std::string check_params(const lbrmhd_params& p)
     return "";
 }
 
+// ---------------------------------------------------------------------------
+// Scratch for lbrmhd_get_diagnostics_noalloc: a fixed, file-scope device array
+// instead of any allocation. It holds the per-block partial sums of the
+// diagnostics reduction (NPART float64 per block of kDiagThreads cells), for
+// at most kNoAllocMaxBlocks blocks, i.e. runs of up to
+// kNoAllocMaxBlocks * kDiagThreads = 16,777,216 cells (256^3): 4.7 MB that every
+// GPU that loads this library keeps until the process exits.
+// ---------------------------------------------------------------------------
+constexpr int64_t kNoAllocMaxBlocks = 65536;
+constexpr int64_t kNoAllocMaxCells = kNoAllocMaxBlocks * lb::kDiagThreads;
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxBlocks * lb::NPART];
+
+// The host-side name g_noalloc_partials is only a stand-in for the device
+// array, not its address; a kernel handed it would fault or, on systems where
+// the GPU can reach host memory, silently use the wrong memory. The device
+// address is looked up once per device, with that device current, and cached.
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[kMaxDevices] = {};
+
+int noalloc_scratch(lbrmhd_handle h, double** out)
+{
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (h->device < 0 || h->device >= kMaxDevices) return fail(h, LBRMHD_ERR_BAD_ARG, "device id out of range");
+    if (!g_noalloc_ptr[h->device]) {
+        double* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_noalloc_partials);
+        if (e != cudaSuccess || !p)
+            return fail(h, LBRMHD_ERR_CUDA, std::string("cudaGetSymbolAddress(g_noalloc_partials): ") +
+                                                cudaGetErrorString(e));
+        g_noalloc_ptr[h->device] = p;
+    }
+    *out = g_noalloc_ptr[h->device];
+    return LBRMHD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -537,6 +574,37 @@ int lbrmhd_get_diagnostics(lbrmhd_handle h, int run, double* out)
     LB_CK(cudaMemcpyAsync(out, h->d_small, LBRMHD_NDIAG * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     LB_CK(cudaStreamSynchronize(h->stream));
     if (out[8] > 0) return fail(h, LBRMHD_ERR_NONFINITE, "non-finite values in the state");
+    return LBRMHD_OK;
+}
+
+int lbrmhd_get_diagnostics_noalloc(lbrmhd_handle h, int run, double* d_out)
+{
+    if (bad_run(h, run) || !d_out) return h ? fail(h, LBRMHD_ERR_BAD_ARG, "bad run or NULL output") : LBRMHD_ERR_BAD_ARG;
+    RunState& r = h->runs[run];
+    if (!r.initialized) return fail(h, LBRMHD_ERR_STATE, "run not initialised");
+    if (r.N > kNoAllocMaxCells)
+        return fail(h, LBRMHD_ERR_BAD_ARG,
+                    "lbrmhd_get_diagnostics_noalloc: run has " + std::to_string(r.N) + " cells, above the limit of " +
+                        std::to_string(kNoAllocMaxCells) + " of its static scratch; use lbrmhd_get_diagnostics");
+    LB_CK(cudaSetDevice(h->device));
+    double* partial = nullptr;
+    const int rc = noalloc_scratch(h, &partial);
+    if (rc) return rc;
+    const lb::Phys<double> k = make_phys<double>(r.p, r.ref, runref(r));
+    switch (h->precision) {
+        case LBRMHD_FP64:
+            LB_CK(lb::launch_diag<lb::CfgF64>(view<lb::CfgF64>(r, r.cur), k, r.ref, partial, kNoAllocMaxBlocks, d_out,
+                                              h->stream));
+            break;
+        case LBRMHD_FP32:
+            LB_CK(lb::launch_diag<lb::CfgF32>(view<lb::CfgF32>(r, r.cur), k, r.ref, partial, kNoAllocMaxBlocks, d_out,
+                                              h->stream));
+            break;
+        default:
+            LB_CK(lb::launch_diag<lb::CfgF16>(view<lb::CfgF16>(r, r.cur), k, r.ref, partial, kNoAllocMaxBlocks, d_out,
+                                              h->stream));
+            break;
+    }
     return LBRMHD_OK;
 }
 

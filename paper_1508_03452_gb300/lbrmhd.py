@@ -28,7 +28,7 @@ EXPORTED = [
     "lbrmhd_create", "lbrmhd_destroy", "lbrmhd_set_stream", "lbrmhd_init_fields", "lbrmhd_init_fields_device",
     "lbrmhd_step", "lbrmhd_get_moments", "lbrmhd_get_moments_device", "lbrmhd_get_populations",
     "lbrmhd_get_diagnostics", "lbrmhd_get_stats", "lbrmhd_state_bytes", "lbrmhd_get_state", "lbrmhd_set_state",
-    "lbrmhd_run_cells", "lbrmhd_last_error", "lbrmhd_lattice_tables",
+    "lbrmhd_run_cells", "lbrmhd_last_error", "lbrmhd_lattice_tables", "lbrmhd_get_diagnostics_noalloc",
 ]
 
 
@@ -93,6 +93,7 @@ def load(build_if_missing: bool = True):
         L.lbrmhd_get_moments_device.argtypes = [vp, C.c_int, vp]
         L.lbrmhd_get_populations.argtypes = [vp, C.c_int, dp, dp, dp]
         L.lbrmhd_get_diagnostics.argtypes = [vp, C.c_int, dp]
+        L.lbrmhd_get_diagnostics_noalloc.argtypes = [vp, C.c_int, vp]
         L.lbrmhd_get_stats.argtypes = [vp, C.c_int, C.POINTER(i64)]
         L.lbrmhd_state_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
         L.lbrmhd_get_state.argtypes = [vp, vp, C.c_size_t]
