@@ -36,28 +36,48 @@ __device__ __forceinline__ R flux_diff(R um2, R um1, R u0, R up1, R kappa)
     return Fout - Fin;
 }
 
-// One streamed fluid population (pre-collision value at t + dt).
+// Relative element offsets of the neighbours d = -2..+2 of one cell along each
+// axis (index 2 is the cell itself), with the periodic wrap or the open-face
+// clamp already applied; y offsets include the factor nx, z offsets nx ny.
+struct Off {
+    int x[5], y[5], z[5];
+};
+
+__device__ __forceinline__ Off make_off(int x, int y, int z, int nx, int ny, int nz, const int* per)
+{
+    Off o;
+#pragma unroll
+    for (int d = -2; d <= 2; ++d) {
+        o.x[d + 2] = wrap_coord(x + d, nx, per[0]) - x;
+        o.y[d + 2] = (wrap_coord(y + d, ny, per[1]) - y) * nx;
+        o.z[d + 2] = (wrap_coord(z + d, nz, per[2]) - z) * nx * ny;
+    }
+    return o;
+}
+
+// One streamed fluid population (pre-collision value at t + dt); p points at
+// this cell in the population's plane.
 template <int I, bool IS3D, bool VISC, class Cfg>
-__device__ __forceinline__ typename Cfg::real stream_pop(const typename Cfg::pop* __restrict__ plane, const Nb& nb,
+__device__ __forceinline__ typename Cfg::real stream_pop(const typename Cfg::pop* __restrict__ p, const Off& o,
                                                          const Phys<typename Cfg::real>& k, float scale)
 {
     using R = typename Cfg::real;
     constexpr int s[3] = {c19(I, 0), c19(I, 1), c19(I, 2)};
-    const R v0 = ld_pop<Cfg>(plane + nb.at(0, 0, 0), scale);
+    const R v0 = ld_pop<Cfg>(p, scale);
     R flux = R(0), lap = R(0);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (a == 2 && !IS3D) continue;
+        const int* oa = a == 0 ? o.x : (a == 1 ? o.y : o.z);
         const int sa = s[a];
-        auto at = [&](int d) {
-            return ld_pop<Cfg>(plane + nb.at(a == 0 ? d : 0, a == 1 ? d : 0, a == 2 ? d : 0), scale);
-        };
         if (sa != 0) {
-            const R um2 = at(-2 * sa), um1 = at(-sa), up1 = at(sa);
+            const R um2 = ld_pop<Cfg>(p + oa[2 - 2 * sa], scale);
+            const R um1 = ld_pop<Cfg>(p + oa[2 - sa], scale);
+            const R up1 = ld_pop<Cfg>(p + oa[2 + sa], scale);
             flux += flux_diff(um2, um1, v0, up1, k.kappa);
             if (VISC) lap += (um1 + up1) - R(2) * v0;
         } else if (VISC) {
-            lap += (at(-1) + at(1)) - R(2) * v0;
+            lap += (ld_pop<Cfg>(p + oa[1], scale) + ld_pop<Cfg>(p + oa[3], scale)) - R(2) * v0;
         }
     }
     R out = v0 - k.C * flux;
@@ -65,16 +85,19 @@ __device__ __forceinline__ typename Cfg::real stream_pop(const typename Cfg::pop
     return out;
 }
 
+// Streams f and g (population I onwards) into the shared-memory buffer `sp`
+// (slot I for f, 19 + I for g) and accumulates their moments.
 template <int I, bool IS3D, class Cfg>
 struct StreamAll {
     using R = typename Cfg::real;
-    static __device__ __forceinline__ void run(const StepArgs<Cfg>& A, const Nb& nb, R* fd, R* gd, R (&Tm)[10],
-                                               R (&Nm)[1])
+    static __device__ __forceinline__ void run(const StepArgs<Cfg>& A, const Off& o, int64_t c, R* sp, int nth,
+                                               R (&Tm)[10], R& Nm)
     {
-        fd[I] = stream_pop<I, IS3D, true, Cfg>(A.fin + (int64_t)I * A.stride, nb, A.k, A.hs.f[I]);
-        gd[I] = stream_pop<I, IS3D, false, Cfg>(A.gin + (int64_t)I * A.stride, nb, A.k, A.hs.g[I]);
+        const R f = stream_pop<I, IS3D, true, Cfg>(A.fin + (int64_t)I * A.stride + c, o, A.k, A.hs.f[I]);
+        const R g = stream_pop<I, IS3D, false, Cfg>(A.gin + (int64_t)I * A.stride + c, o, A.k, A.hs.g[I]);
+        sp[I * nth] = f;
+        sp[(19 + I) * nth] = g;
         constexpr int cx = c19(I, 0), cy = c19(I, 1), cz = c19(I, 2);
-        const R f = fd[I];
         // T^{mu nu} of the deviations: p = (1, q chat)
         Tm[0] += f;
         if (cx) Tm[1] += R(cx) * f;
@@ -86,80 +109,123 @@ struct StreamAll {
         if (cx * cy) Tm[7] += R(cx * cy) * f;
         if (cx * cz) Tm[8] += R(cx * cz) * f;
         if (cy * cz) Tm[9] += R(cy * cz) * f;
-        Nm[0] += gd[I];
-        StreamAll<I + 1, IS3D, Cfg>::run(A, nb, fd, gd, Tm, Nm);
+        Nm += g;
+        StreamAll<I + 1, IS3D, Cfg>::run(A, o, c, sp, nth, Tm, Nm);
     }
 };
 template <bool IS3D, class Cfg>
 struct StreamAll<19, IS3D, Cfg> {
     using R = typename Cfg::real;
-    static __device__ __forceinline__ void run(const StepArgs<Cfg>&, const Nb&, R*, R*, R (&)[10], R (&)[1]) {}
+    static __device__ __forceinline__ void run(const StepArgs<Cfg>&, const Off&, int64_t, R*, int, R (&)[10], R&) {}
+};
+
+// Exact D3Q13 pull h_k(x) = h_c,k(x - hop_k) into slot 38 + k, accumulating
+// E' - Er (before the sqrt(2) c / 2 factor), the plane-normal B - Br sums and rho_c.
+template <int K, bool IS3D, class Cfg>
+struct PullH {
+    using R = typename Cfg::real;
+    static __device__ __forceinline__ void run(const StepArgs<Cfg>& A, const Off& o, int64_t c, R* sp, int nth,
+                                               R (&dEp)[3], R (&bn)[3], R& rho)
+    {
+        constexpr int p = K / 8, i = (K % 8) / 2, j = K % 2, ie = (i + 3) % 4;
+        int off = o.x[2 - hop13(K, 0)] + o.y[2 - hop13(K, 1)];
+        if (IS3D) off += o.z[2 - hop13(K, 2)];
+        const R hv = (R)A.hin[(int64_t)K * A.stride + c + off];
+        sp[(38 + K) * nth] = hv;
+        rho += hv;
+        constexpr int se = j == 0 ? 1 : -1;  // e_{i1} = -e_{i0}
+        dEp[plane_a1(p)] += R(se * hop_s1(ie)) * hv;
+        dEp[plane_a2(p)] += R(se * hop_s2(ie)) * hv;
+        bn[plane_normal(p)] += R(-se * plane_orient(p)) * hv;  // b_{i0} = -o_p, b_{i1} = +o_p
+        PullH<K + 1, IS3D, Cfg>::run(A, o, c, sp, nth, dEp, bn, rho);
+    }
+};
+template <bool IS3D, class Cfg>
+struct PullH<24, IS3D, Cfg> {
+    using R = typename Cfg::real;
+    static __device__ __forceinline__ void run(const StepArgs<Cfg>&, const Off&, int64_t, R*, int, R (&)[3], R (&)[3],
+                                               R&) {}
 };
 
 template <int I, class Cfg>
 struct CollideFG {
     using R = typename Cfg::real;
-    static __device__ __forceinline__ void run(const StepArgs<Cfg>& A, int64_t c, const R* fd, const R* gd,
+    static __device__ __forceinline__ void run(const StepArgs<Cfg>& A, int64_t c, const R* sp, int nth,
                                                const EqCell<R>& q)
     {
+        const R fd = sp[I * nth], gd = sp[(19 + I) * nth];
         const R K = k_aw<I>(q);
-        const R fo = fd[I] - K * (fd[I] - feq_dev<I>(q));
-        const R go = gd[I] - A.k.inv_tau * (gd[I] - geq_dev<I>(q));
+        const R fo = fd - K * (fd - feq_dev<I>(q));
+        const R go = gd - A.k.inv_tau * (gd - geq_dev<I>(q));
         st_pop<Cfg>(A.fout + (int64_t)I * A.stride + c, fo, A.hs.finv[I]);
         st_pop<Cfg>(A.gout + (int64_t)I * A.stride + c, go, A.hs.ginv[I]);
-        CollideFG<I + 1, Cfg>::run(A, c, fd, gd, q);
+        CollideFG<I + 1, Cfg>::run(A, c, sp, nth, q);
     }
 };
 template <class Cfg>
 struct CollideFG<19, Cfg> {
     using R = typename Cfg::real;
-    static __device__ __forceinline__ void run(const StepArgs<Cfg>&, int64_t, const R*, const R*, const EqCell<R>&) {}
+    static __device__ __forceinline__ void run(const StepArgs<Cfg>&, int64_t, const R*, int, const EqCell<R>&) {}
 };
 
 template <int K, class Cfg>
 struct CollideH {
     using R = typename Cfg::real;
-    static __device__ __forceinline__ void run(const StepArgs<Cfg>& A, int64_t c, const R* h, const R* E,
+    static __device__ __forceinline__ void run(const StepArgs<Cfg>& A, int64_t c, const R* sp, int nth, const R* E,
                                                const R* B, const R* J, bool em_coll)
     {
-        const R v = em_coll ? R(2) * heq13<K>(E, B, J, A.k) - h[K] : h[K];
+        const R hv = sp[(38 + K) * nth];
+        const R v = em_coll ? R(2) * heq13<K>(E, B, J, A.k) - hv : hv;
         A.hout[(int64_t)K * A.stride + c] = (typename Cfg::hpop)v;
-        CollideH<K + 1, Cfg>::run(A, c, h, E, B, J, em_coll);
+        CollideH<K + 1, Cfg>::run(A, c, sp, nth, E, B, J, em_coll);
     }
 };
 template <class Cfg>
 struct CollideH<24, Cfg> {
     using R = typename Cfg::real;
-    static __device__ __forceinline__ void run(const StepArgs<Cfg>&, int64_t, const R*, const R*, const R*, const R*,
-                                               bool) {}
+    static __device__ __forceinline__ void run(const StepArgs<Cfg>&, int64_t, const R*, int, const R*, const R*,
+                                               const R*, bool) {}
+};
+
+constexpr int kStepThreads = 128;
+constexpr int kStepSlots = 63;  // 19 f + 19 g + 25 h pre-collision values per cell in shared memory
+#ifndef LB_STEP_MIN_BLOCKS
+#define LB_STEP_MIN_BLOCKS 4  // resident 128-thread blocks per SM targeted for float32 arithmetic
+#endif
+#ifndef LB_STEP_BX
+#define LB_STEP_BX 128  // block width along x (the block is LB_STEP_BX x 128 / LB_STEP_BX)
+#endif
+template <class Cfg>
+struct StepMinBlocks {
+    static constexpr int value = sizeof(typename Cfg::real) == 8 ? 2 : LB_STEP_MIN_BLOCKS;
 };
 
 template <class Cfg, bool IS3D>
-__global__ void __launch_bounds__(128) step_kernel(const StepArgs<Cfg> A)
+__global__ void __launch_bounds__(kStepThreads, StepMinBlocks<Cfg>::value) step_kernel(const StepArgs<Cfg> A)
 {
     using R = typename Cfg::real;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nth = blockDim.x * blockDim.y;
+    R* sp = reinterpret_cast<R*>(smem_raw) + (threadIdx.x + threadIdx.y * blockDim.x);
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
-    if (x >= A.nx || y >= A.ny) return;
-    const Nb nb = make_nb(x, y, z, A.nx, A.ny, A.nz, A.periodic);
-    const int64_t c = nb.at(0, 0, 0);
+    if (x >= A.nx || y >= A.ny) return;  // the kernel has no block-wide barrier
+    const Off o = make_off(x, y, z, A.nx, A.ny, A.nz, A.periodic);
+    const int64_t c = x + (int64_t)A.nx * (y + (int64_t)A.ny * z);
     const Phys<R>& k = A.k;
 
-    // 1. streaming of f and g, with their moments
-    R fd[19], gd[19];
+    // 1. streaming of f and g (with their moments) and of h (with its moments)
     R Tm[10] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
-    R Nm[1] = {R(0)};
-    StreamAll<0, IS3D, Cfg>::run(A, nb, fd, gd, Tm, Nm);
+    R Nm = R(0);
+    StreamAll<0, IS3D, Cfg>::run(A, o, c, sp, nth, Tm, Nm);
+    R dEp[3] = {R(0), R(0), R(0)}, bn[3] = {R(0), R(0), R(0)}, rho = R(0);
+    PullH<0, IS3D, Cfg>::run(A, o, c, sp, nth, dEp, bn, rho);
+    const R h24 = (R)A.hin[24 * A.stride + c];
+    sp[62 * nth] = h24;
+    rho += h24;
 
-    // 1b. exact streaming of h: h_k(x) = h_c,k(x - hop_k)
-    R h[25];
-#pragma unroll
-    for (int kk = 0; kk < 24; ++kk)
-        h[kk] = (R)A.hin[(int64_t)kk * A.stride + nb.at(-hop13(kk, 0), -hop13(kk, 1), -hop13(kk, 2))];
-    h[24] = (R)A.hin[24 * A.stride + c];
-
-    // previous primitives
+    // previous primitives used by the recovery
     Prim<R> old;
     old.n = (R)A.pin[P_N * A.stride + c];
     old.eps = (R)A.pin[P_EPS * A.stride + c];
@@ -169,12 +235,12 @@ __global__ void __launch_bounds__(128) step_kernel(const StepArgs<Cfg> A)
         old.E[a] = (R)A.pin[(P_E + a) * A.stride + c];
         old.B[a] = (R)A.pin[(P_B + a) * A.stride + c];
     }
-    old.rho = (R)A.pin[P_RHO * A.stride + c];
+    old.rho = R(0);
 
-    // 2. moments (reference rest state added back)
+    // 2. moments (reference state added back): rest state (eps_r, p_r) and the
+    // reference EM terms k.Tem
     const R qq = R(kQ), q2 = R(kQ2);
     R T[4][4];
-    // reference moments: rest state (eps_r, p_r) plus the reference EM terms k.Tem
     T[0][0] = k.Tem[0] + Tm[0];  // T^00 - eps_r
     T[0][1] = T[1][0] = k.Tem[1] + qq * Tm[1];
     T[0][2] = T[2][0] = k.Tem[2] + qq * Tm[2];
@@ -185,11 +251,13 @@ __global__ void __launch_bounds__(128) step_kernel(const StepArgs<Cfg> A)
     T[1][2] = T[2][1] = k.Tem[7] + q2 * Tm[7];
     T[1][3] = T[3][1] = k.Tem[8] + q2 * Tm[8];
     T[2][3] = T[3][2] = k.Tem[9] + q2 * Tm[9];
-    const R dN0 = Nm[0];  // N^0 - n_r
-    R dEp[3], dB[3], Ep[3], Bn[3], rho;
-    em_moments(h, k, dEp, dB, rho);
+    const R dN0 = Nm;  // N^0 - n_r
+    R Ep[3], Bn[3], dB[3];
+    const R es = R(kSqrt2 / 2.0) * k.c;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
+        dEp[a] *= es;
+        dB[a] = bn[a];
         Ep[a] = k.Er[a] + dEp[a];
         Bn[a] = k.Br[a] + dB[a];
     }
@@ -217,26 +285,27 @@ __global__ void __launch_bounds__(128) step_kernel(const StepArgs<Cfg> A)
         nw.rho = rho;
         ohm_solve(Ep, nw.u, nw.B, rho, g2, k, nw.E, J);
     } else {
+        // keep the previous primitives (the failure is counted)
         nw = old;
-        n_dev = old.n - k.n_r;
-        eps_dev = old.eps - k.eps_r;
-        ohm_current(old.E, old.u, old.B, old.rho, k, J);
+        nw.rho = (R)A.pin[P_RHO * A.stride + c];
+        n_dev = nw.n - k.n_r;
+        eps_dev = nw.eps - k.eps_r;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) dB[a] = nw.B[a] - k.Br[a];
+        ohm_current(nw.E, nw.u, nw.B, nw.rho, k, J);
     }
 
-    // 4. collisions and stores
-    R dE[3], dBn[3];
+    // 4. collisions at the new time level and stores
+    R dE[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        dE[a] = nw.E[a] - k.Er[a];
-        dBn[a] = ok ? dB[a] : nw.B[a] - k.Br[a];
-    }
+    for (int a = 0; a < 3; ++a) dE[a] = nw.E[a] - k.Er[a];
     EqCell<R> q;
-    eq_cell(nw, n_dev, eps_dev, dE, dBn, k, q);
-    CollideFG<0, Cfg>::run(A, c, fd, gd, q);
+    eq_cell(nw, n_dev, eps_dev, dE, dB, k, q);
+    CollideFG<0, Cfg>::run(A, c, sp, nth, q);
     const bool em_coll = (A.flags & FLAG_NO_EM_COLLISION) == 0;
     // h_c - h_ref = 2 h^eq(E - Er, B - Br, J) - (h - h_ref)  (Eq. Maxwell-eq is linear)
-    CollideH<0, Cfg>::run(A, c, h, dE, dBn, J, em_coll);
-    A.hout[24 * A.stride + c] = (typename Cfg::hpop)(em_coll ? R(2) * nw.rho - h[24] : h[24]);
+    CollideH<0, Cfg>::run(A, c, sp, nth, dE, dB, J, em_coll);
+    A.hout[24 * A.stride + c] = (typename Cfg::hpop)(em_coll ? R(2) * nw.rho - sp[62 * nth] : sp[62 * nth]);
 
     A.pout[P_N * A.stride + c] = (typename Cfg::prim)nw.n;
     A.pout[P_EPS * A.stride + c] = (typename Cfg::prim)nw.eps;
@@ -263,14 +332,24 @@ __global__ void __launch_bounds__(128) step_kernel(const StepArgs<Cfg> A)
 template <class Cfg>
 cudaError_t launch_step(const StepArgs<Cfg>& A, cudaStream_t stream)
 {
-    const int bx = A.nx >= 128 ? 128 : (A.nx >= 64 ? 64 : 32);
-    const int by = 128 / bx;
+    using R = typename Cfg::real;
+    const int bx = A.nx >= LB_STEP_BX ? LB_STEP_BX : (A.nx >= 64 ? 64 : 32);
+    const int by = kStepThreads / bx;
+    const size_t smem = (size_t)kStepSlots * sizeof(R) * kStepThreads;
+    static bool configured = false;  // one attribute call per instantiation
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(step_kernel<Cfg, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(step_kernel<Cfg, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
     dim3 block(bx, by, 1);
     dim3 grid((A.nx + bx - 1) / bx, (A.ny + by - 1) / by, A.nz);
     if (A.nz > 1)
-        step_kernel<Cfg, true><<<grid, block, 0, stream>>>(A);
+        step_kernel<Cfg, true><<<grid, block, smem, stream>>>(A);
     else
-        step_kernel<Cfg, false><<<grid, block, 0, stream>>>(A);
+        step_kernel<Cfg, false><<<grid, block, smem, stream>>>(A);
     return cudaGetLastError();
 }
 
