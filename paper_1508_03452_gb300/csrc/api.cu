@@ -92,6 +92,7 @@ lb::Phys<R> make_phys(const lbrmhd_params& p, const lb::RefState& ref, const Run
     k.sigma = (R)p.sigma;
     k.inv_tau = (R)(1.0 / p.tau);
     k.half_dt_c2 = (R)(0.5 * dt * p.c * p.c);
+    k.inv_half_dt_c2 = (R)(1.0 / (0.5 * dt * p.c * p.c));
     k.gm1 = (R)(p.gamma_ad - 1.0);
     k.C = (R)C;
     k.kappa = (R)(0.5 * (1.0 - C));

@@ -77,6 +77,7 @@ struct Phys {
     R c, c2, inv_c, eps0;      // eps0 = 1 / c^2 (mu0 = 1)
     R sigma, inv_tau;          // conductivity, dt / tau
     R half_dt_c2;              // (dt/2) mu0 c^2
+    R inv_half_dt_c2;          // 1 / ((dt/2) mu0 c^2)
     R gm1;                     // Gamma - 1
     R C, kappa, kvisc;         // Courant number, (1 - C)/2, alpha c dt / dx
     R n_r, eps_r, p_r;         // reference rest state of the deviations
@@ -112,13 +113,19 @@ __device__ __forceinline__ R sq(R a) { return a * a; }
 //   g_i^eq = w'_i n g (1 + 3 q c.b + 4.5 q^2 (c.b)^2 - 1.5 b^2)
 // (b = u / c, g = Lorentz factor, c = chat_i)
 // ---------------------------------------------------------------------------
+// Per-cell terms of the equilibria. With chat_i having one (axis a, sign s) or
+// two (axes a < b, signs s_a, s_b) non-zero components:
+//   f^eq - W = w_i (even + s odd_a)                                    axis
+//            = w_i (even_ab + s_a odd_a + s_b odd_b + s_a s_b cross_ab)   diagonal
+//            = w_0 rest                                                rest
+// with odd_a = (3/4)(eps + p) g^2 L1 b_a + EM_lin_a, and the even parts
+// collecting 3 (p - p_r), the quadratic velocity terms and the EM terms; the
+// same split for g^eq (base, lin_a, sq_a, x_ab) and for K_i = kf - sum s_a kq_a.
 template <class R>
 struct EqCell {
-    R g, g2, b[3], b2;
-    R three_dp, rest_dev, wq;  // 3(p - p_r), (3/4)(361/33)[(3p-eps)-(3p_r-eps_r)], (3/4)(eps + p)
-    R em_iso, em_lin[3], X[3][3];
-    R ng, dng;                 // n g, n g - n_r
-    R kf;                      // g / tau  (Anderson-Witting factor K_i = kf (1 - q c.b))
+    R f_rest, f_even_ax[3], f_odd[3], f_even_dg[3], f_cross[3];
+    R g_base, g_lin[3], g_sq[3], g_x[3];
+    R kf, kq[3];
 };
 
 // n_dev = n - n_r, eps_dev = eps - eps_r, dE = E - Er and dB = B - Br are passed
@@ -128,34 +135,52 @@ template <class R>
 __device__ __forceinline__ void eq_cell(const Prim<R>& s, R n_dev, R eps_dev, const R* dE, const R* dB,
                                         const Phys<R>& k, EqCell<R>& q)
 {
-    const R b0 = s.u[0] * k.inv_c, b1 = s.u[1] * k.inv_c, b2 = s.u[2] * k.inv_c;
-    q.b[0] = b0; q.b[1] = b1; q.b[2] = b2;
-    q.b2 = b0 * b0 + b1 * b1 + b2 * b2;
-    q.g2 = R(1) / (R(1) - q.b2);
-    q.g = sqrt(q.g2);
+    const R b[3] = {s.u[0] * k.inv_c, s.u[1] * k.inv_c, s.u[2] * k.inv_c};
+    const R b2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+    const R g2 = R(1) / (R(1) - b2);
+    const R g = sqrt(g2);
     const R p_dev = k.gm1 * (eps_dev - n_dev * k.c2);
-    const R p = k.p_r + p_dev;
-    q.three_dp = R(3) * p_dev;
-    q.rest_dev = R(kRest) * (R(3) * p_dev - eps_dev);
-    q.wq = R(0.75) * (s.eps + p);
+    const R three_dp = R(3) * p_dev;
+    const R rest_dev = R(kRest) * (R(3) * p_dev - eps_dev);
+    const R wq = R(0.75) * (s.eps + k.p_r + p_dev);
     const R* E = s.E;
     const R* B = s.B;
     // X - Xr = eps0 [dE_a E_b + Er_a dE_b + c^2 (dB_a B_b + Br_a dB_b)] - dXr
+    R X[3][3];
     for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b)
-            q.X[a][b] = k.eps0 * (dE[a] * E[b] + k.Er[a] * dE[b] + k.c2 * (dB[a] * B[b] + k.Br[a] * dB[b])) -
-                        k.dXr[a][b];
+        for (int c = 0; c < 3; ++c)
+            X[a][c] = k.eps0 * (dE[a] * E[c] + k.Er[a] * dE[c] + k.c2 * (dB[a] * B[c] + k.Br[a] * dB[c])) - k.dXr[a][c];
     // Y - Yr = eps0 c (dB x E + Br x dE) - dYr
     const R Yd[3] = {
         k.eps0 * k.c * (dB[1] * E[2] - dB[2] * E[1] + k.Br[1] * dE[2] - k.Br[2] * dE[1]) - k.dYr[0],
         k.eps0 * k.c * (dB[2] * E[0] - dB[0] * E[2] + k.Br[2] * dE[0] - k.Br[0] * dE[2]) - k.dYr[1],
         k.eps0 * k.c * (dB[0] * E[1] - dB[1] * E[0] + k.Br[0] * dE[1] - k.Br[1] * dE[0]) - k.dYr[2]};
-    q.em_iso = R(2.3) * (q.X[0][0] + q.X[1][1] + q.X[2][2]);
-    for (int a = 0; a < 3; ++a) q.em_lin[a] = -R(kSqrt19_3) * Yd[a];
-    q.ng = s.n * q.g;
+    const R em_iso = R(2.3) * (X[0][0] + X[1][1] + X[2][2]);
+    const R qd = g2 * R(16.0 / 15.0) * b2;  // Q of the rest population is -qd
+    R qs[3];
+    for (int a = 0; a < 3; ++a) {
+        qs[a] = g2 * R(4.0 / 15.0) * (R(19) * b[a] * b[a] - R(4) * b2);
+        q.f_even_ax[a] = three_dp + wq * qs[a] + em_iso - R(3.8) * X[a][a];
+        q.f_odd[a] = wq * g2 * R(kL1) * b[a] - R(kSqrt19_3) * Yd[a];
+    }
+    q.f_rest = three_dp + rest_dev - wq * qd + em_iso;
+    const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
+    for (int m = 0; m < 3; ++m) {
+        const int a = pa[m], c = pb[m];
+        q.f_even_dg[m] = three_dp + wq * (qs[a] + qs[c] + qd) + em_iso - R(3.8) * (X[a][a] + X[c][c]);
+        q.f_cross[m] = wq * R(19) * g2 * b[a] * b[c] - R(14.25) * X[a][c];
+    }
+    const R ng = s.n * g;
     // n g - n_r = n_dev g + n_r (g - 1), g - 1 = g^2 b^2 / (g + 1)
-    q.dng = n_dev * q.g + k.n_r * (q.g2 * q.b2 / (q.g + R(1)));
-    q.kf = q.g * k.inv_tau;
+    const R dng = n_dev * g + k.n_r * (g2 * b2 / (g + R(1)));
+    q.g_base = dng - R(1.5) * ng * b2;
+    for (int a = 0; a < 3; ++a) {
+        q.g_lin[a] = R(3) * R(kQ) * ng * b[a];
+        q.g_sq[a] = R(4.5) * R(kQ2) * ng * b[a] * b[a];
+    }
+    for (int m = 0; m < 3; ++m) q.g_x[m] = R(9) * R(kQ2) * ng * b[pa[m]] * b[pb[m]];
+    q.kf = g * k.inv_tau;
+    for (int a = 0; a < 3; ++a) q.kq[a] = q.kf * R(kQ) * b[a];
 }
 
 template <class R>
@@ -166,39 +191,58 @@ __device__ __forceinline__ void eq_cell(const Prim<R>& s, const Phys<R>& k, EqCe
     eq_cell(s, s.n - k.n_r, s.eps - k.eps_r, dE, dB, k, q);
 }
 
-// f_i^eq - f_i^eq(reference rest state), population I
+// axes of population I: first and second non-zero component (-1 if none)
+__host__ __device__ constexpr int ax1(int i) { return c19(i, 0) ? 0 : (c19(i, 1) ? 1 : (c19(i, 2) ? 2 : -1)); }
+__host__ __device__ constexpr int ax2(int i)
+{
+    return ax1(i) < 0 ? -1 : (ax1(i) < 1 && c19(i, 1) ? 1 : (ax1(i) < 2 && c19(i, 2) ? 2 : -1));
+}
+
+// f_i^eq - f_i^eq(reference state), population I
 template <int I, class R>
 __device__ __forceinline__ R feq_dev(const EqCell<R>& q)
 {
-    constexpr int cx = c19(I, 0), cy = c19(I, 1), cz = c19(I, 2);
-    const R cb = R(cx) * q.b[0] + R(cy) * q.b[1] + R(cz) * q.b[2];
-    const R cross = R(cx * cy) * q.b[0] * q.b[1] + R(cx * cz) * q.b[0] * q.b[2] + R(cy * cz) * q.b[1] * q.b[2];
-    const R diag = R(cx * cx) * q.b[0] * q.b[0] + R(cy * cy) * q.b[1] * q.b[1] + R(cz * cz) * q.b[2] * q.b[2];
-    const R Q = q.g2 * (R(kL1) * cb + R(19) * cross + R(4.0 / 15.0) * (R(19) * diag - R(4) * q.b2));
-    const R emq = R(cx * cx) * q.X[0][0] + R(cy * cy) * q.X[1][1] + R(cz * cz) * q.X[2][2];
-    const R emx = R(cx * cy) * q.X[0][1] + R(cx * cz) * q.X[0][2] + R(cy * cz) * q.X[1][2];
-    const R em = q.em_iso + R(cx) * q.em_lin[0] + R(cy) * q.em_lin[1] + R(cz) * q.em_lin[2] - R(3.8) * emq -
-                 R(14.25) * emx;
-    R v = q.three_dp + q.wq * Q + em;
-    if (I == 0) v += q.rest_dev;
-    return R(w19(I)) * v;
+    constexpr int a = ax1(I), b = ax2(I);
+    if constexpr (a < 0) {
+        return R(w19(I)) * q.f_rest;
+    } else if constexpr (b < 0) {
+        constexpr int sa = c19(I, a);
+        return R(w19(I)) * (q.f_even_ax[a] + R(sa) * q.f_odd[a]);
+    } else {
+        constexpr int sa = c19(I, a), sb = c19(I, b), m = a + b - 1;
+        return R(w19(I)) * (q.f_even_dg[m] + R(sa) * q.f_odd[a] + R(sb) * q.f_odd[b] + R(sa * sb) * q.f_cross[m]);
+    }
 }
 
-// g_i^eq - g_i^eq(reference rest state), population I
+// g_i^eq - g_i^eq(reference state), population I
 template <int I, class R>
 __device__ __forceinline__ R geq_dev(const EqCell<R>& q)
 {
-    constexpr int cx = c19(I, 0), cy = c19(I, 1), cz = c19(I, 2);
-    const R cb = R(kQ) * (R(cx) * q.b[0] + R(cy) * q.b[1] + R(cz) * q.b[2]);
-    return R(wg19(I)) * (q.dng + q.ng * (R(3) * cb + R(4.5) * cb * cb - R(1.5) * q.b2));
+    constexpr int a = ax1(I), b = ax2(I);
+    if constexpr (a < 0) {
+        return R(wg19(I)) * q.g_base;
+    } else if constexpr (b < 0) {
+        constexpr int sa = c19(I, a);
+        return R(wg19(I)) * (q.g_base + q.g_sq[a] + R(sa) * q.g_lin[a]);
+    } else {
+        constexpr int sa = c19(I, a), sb = c19(I, b), m = a + b - 1;
+        return R(wg19(I)) * (q.g_base + q.g_sq[a] + q.g_sq[b] + R(sa * sb) * q.g_x[m] + R(sa) * q.g_lin[a] +
+                             R(sb) * q.g_lin[b]);
+    }
 }
 
 // Anderson-Witting collision factor K_i = (dt/tau) g (1 - v_i.u / c^2), v_i = c q chat_i
 template <int I, class R>
 __device__ __forceinline__ R k_aw(const EqCell<R>& q)
 {
-    constexpr int cx = c19(I, 0), cy = c19(I, 1), cz = c19(I, 2);
-    return q.kf * (R(1) - R(kQ) * (R(cx) * q.b[0] + R(cy) * q.b[1] + R(cz) * q.b[2]));
+    constexpr int a = ax1(I), b = ax2(I);
+    if constexpr (a < 0) {
+        return q.kf;
+    } else if constexpr (b < 0) {
+        return q.kf - R(c19(I, a)) * q.kq[a];
+    } else {
+        return q.kf - R(c19(I, a)) * q.kq[a] - R(c19(I, b)) * q.kq[b];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -268,7 +312,7 @@ __device__ __forceinline__ void ohm_solve(const R* Ep, const R* u, const R* B, R
     const R uxB[3] = {u[1] * B[2] - u[2] * B[1], u[2] * B[0] - u[0] * B[2], u[0] * B[1] - u[1] * B[0]};
     for (int c = 0; c < 3; ++c) {
         E[c] = a[c] * inv1k - kfrac * uxB[c] + s * u[c];
-        J[c] = (Ep[c] - E[c]) / k.half_dt_c2;
+        J[c] = (Ep[c] - E[c]) * k.inv_half_dt_c2;
     }
 }
 

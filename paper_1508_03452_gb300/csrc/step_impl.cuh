@@ -25,6 +25,7 @@ namespace lb {
 template <class R>
 __device__ __forceinline__ R minmod(R a, R b)
 {
+    // the argument of smaller magnitude when both have the same sign, else 0
     return (a > R(0) && b > R(0)) ? fmin(a, b) : ((a < R(0) && b < R(0)) ? fmax(a, b) : R(0));
 }
 
@@ -317,6 +318,7 @@ __global__ void __launch_bounds__(kStepThreads, StepMinBlocks<Cfg>::value) step_
     }
     A.pout[P_RHO * A.stride + c] = (typename Cfg::prim)nw.rho;
 
+#ifndef LB_NO_STATS
     // recovery counters, aggregated per warp
     const unsigned mask = __activemask();
     const unsigned fail = __reduce_add_sync(mask, ok ? 0u : 1u);
@@ -327,6 +329,7 @@ __global__ void __launch_bounds__(kStepThreads, StepMinBlocks<Cfg>::value) step_
         atomicAdd(&A.stats[1], (unsigned long long)isum);
         atomicMax(&A.stats[2], (unsigned long long)imax);
     }
+#endif
 }
 
 template <class Cfg>
