@@ -192,3 +192,16 @@ def flux_rope(nx=256, ny=256, nz=256, *, B_bg=0.05, B_tor=0.2, c_b=0.2534, h=2.0
 def drive_layers_for(nz: int) -> int:
     """Driven photosphere thickness: the paper forces z <= 0.2343 of a 6-high box."""
     return int(math.ceil(0.2343 / 6.0 * nz))
+
+
+def mlp_init_params(seed: int = 0) -> np.ndarray:
+    """Seeded initial parameters of the 20-64-64-64-4 seed network (float32,
+    layout W1[64][20] b1[64] W2[64][64] b2[64] W3[64][64] b3[64] W4[4][64]
+    b4[4]): weights normal with variance 2 / fan_in (He et al., 2015), output
+    layer scaled by 0.1, biases zero."""
+    r = np.random.default_rng(seed)
+    parts = []
+    for fan_out, fan_in, scale in ((64, 20, 1.0), (64, 64, 1.0), (64, 64, 1.0), (4, 64, 0.1)):
+        parts.append(r.normal(0.0, scale * math.sqrt(2.0 / fan_in), size=fan_out * fan_in))
+        parts.append(np.zeros(fan_out))
+    return np.concatenate(parts).astype(np.float32)
