@@ -64,12 +64,16 @@ extern "C" {
 #define LBRMHD_FP32 1      /* float32 storage (f, g as deviations from the rest equilibrium), float32 arithmetic */
 #define LBRMHD_FP16_DEV 2  /* f, g as float16 relative deviations from the rest equilibrium; h, primitives float32 */
 
-/* primitive recovery seed */
+/* primitive recovery seed: the starting vector of the Landau eigen-solve of
+ * Sec. III (coupling). Every mode iterates to the same tolerance, so the seed
+ * changes the iteration count, not the converged primitives. */
 #define LBRMHD_RECOVERY_PLAIN 0 /* seeded with the previous step's velocity */
-#define LBRMHD_RECOVERY_MLP 1   /* seeded by the learned network (lbrmhd_mlp_*) */
+#define LBRMHD_RECOVERY_MLP 1   /* seeded by the learned network (lbrmhd_set_mlp_weights) */
+#define LBRMHD_RECOVERY_COLD 2  /* seeded with zero velocity (no history) */
 
-/* test switches (flags) */
+/* switches (flags) */
 #define LBRMHD_FLAG_NO_EM_COLLISION 1 /* h is streamed without collision: h(x + v dt, t + dt) = h(x, t) */
+#define LBRMHD_FLAG_UNSHIFTED_POWER 2 /* recovery by the plain power method (no spectral shift) */
 
 /* rows of lbrmhd_get_moments output (each row N values) */
 #define LBRMHD_NMOMENTS 16 /* n, p, eps, u(3), E(3), B(3), rho_c, J(3) */
@@ -91,7 +95,7 @@ typedef struct lbrmhd_params {
     double drive_u0;        /* peak speed of the driven photospheric layers */
     int32_t drive_layers;   /* number of driven z-layers (LBRMHD_DRIVEN on -z) */
     int32_t precision;      /* LBRMHD_FP64 | LBRMHD_FP32 | LBRMHD_FP16_DEV (same for every run of a handle) */
-    int32_t recovery;       /* LBRMHD_RECOVERY_PLAIN | LBRMHD_RECOVERY_MLP */
+    int32_t recovery;       /* LBRMHD_RECOVERY_PLAIN | LBRMHD_RECOVERY_MLP | LBRMHD_RECOVERY_COLD */
     int32_t flags;          /* LBRMHD_FLAG_* */
     int32_t max_iters;      /* recovery iteration cap (0: 64) */
     double tol;             /* recovery tolerance (0: 1e-14 for FP64, 1e-6 otherwise) */
@@ -207,6 +211,73 @@ int64_t lbrmhd_run_cells(lbrmhd_handle h, int run);
  * e_k / c (24 x 3), b_k (24 x 3). Host only; needs no GPU. */
 #define LBRMHD_NTABLE 311
 int lbrmhd_lattice_tables(double* out, size_t n);
+
+/* ------------------------------------------------------------------------
+ * Learned recovery seed. The paper has no counterpart: it fixes the
+ * eigenproblem (Sec. III, coupling), not where its iteration starts. A
+ * 20-64-64-64-4 ReLU network maps normalised moments of a cell to a guess of
+ * beta = u / c (and eps / T^00 - 1); the step kernel evaluates it on the
+ * tensor cores (bf16 operands, float32 accumulation) and uses the guess,
+ * clamped to |beta| <= 0.9, as the starting vector of the same eigen-solve.
+ *
+ * Parameters: LBRMHD_MLP_NPARAM float32 values, W1[64][20] b1[64]
+ * W2[64][64] b2[64] W3[64][64] b3[64] W4[4][64] b4[4] (W[out][in]).
+ * Features (20 float32 per cell): T^{0a}/T^00 (3), T^{xx,yy,zz,xy,xz,yz}/T^00
+ * (6), N^a/N^0 (3), N^0/T^00, E/sqrt(T^00) (3), B/sqrt(T^00) (3), 1, with T,
+ * N the streamed moments (Eqs. Cal_T, Cal_N) and E, B the previous step's.
+ * A training sample is one row of 24 float32: the 20 features, then the
+ * converged beta (3) and eps / T^00 - 1.
+ * ---------------------------------------------------------------------- */
+#define LBRMHD_MLP_NPARAM 9924
+#define LBRMHD_MLP_NFEAT 20
+#define LBRMHD_MLP_ROW 24
+
+/* LBRMHD_MLP_NPARAM and the size in bytes of the packed inference blob. */
+int lbrmhd_mlp_nparams(void);
+int lbrmhd_mlp_blob_bytes(void);
+
+/* Packs float32 parameters (device) into a caller-allocated device blob of
+ * lbrmhd_mlp_blob_bytes() bytes (bf16 weights, zero-padded rows, float32
+ * biases). Asynchronous on `stream`. Errors: BAD_ARG (NULL pointer), CUDA. */
+int lbrmhd_mlp_pack(const float* d_params, void* d_blob, void* stream);
+
+/* Network outputs (n x 4 float32, device) for n feature rows (n x 20 float32,
+ * device) with a packed blob; the same tensor-core code as the step kernel.
+ * Asynchronous. Errors: BAD_ARG (NULL pointer, n < 0), CUDA. */
+int lbrmhd_mlp_infer(const void* d_blob, const float* d_features, int64_t n, float* d_out, void* stream);
+
+/* Loss and gradient over n samples (n x 24 float32, device) in float32:
+ * loss = (1/n) sum_s sum_o (y_o(x_s) - t_so)^2. d_grad (device) receives
+ * LBRMHD_MLP_NPARAM gradient values then the loss. Allocates a scratch array
+ * and synchronises `stream`. Errors: BAD_ARG, OOM, CUDA. */
+int lbrmhd_mlp_grad(const float* d_params, const float* d_data, int64_t n, float* d_grad, void* stream);
+
+/* `steps` Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on
+ * mini-batches of `batch` samples drawn with replacement from the n samples
+ * (row = splitmix64 hash of (seed, step, j) mod n). d_params (device,
+ * updated in place), d_adam (device, 2 x LBRMHD_MLP_NPARAM: first then second
+ * moments, zero for a fresh start; updated), d_loss (device, `steps` float32:
+ * the mini-batch loss before each update, or NULL). Deterministic for given
+ * inputs. Allocates scratch and synchronises `stream`. Errors: BAD_ARG, OOM,
+ * CUDA. */
+int lbrmhd_mlp_train(float* d_params, float* d_adam, const float* d_data, int64_t n, int steps, int batch, float lr,
+                     uint64_t seed, float* d_loss, void* stream);
+
+/* Gives the handle's runs with LBRMHD_RECOVERY_MLP their network: packs
+ * d_params (device float32, LBRMHD_MLP_NPARAM; read on the handle's stream,
+ * not retained) into the handle's own blob. lbrmhd_step returns STATE for an
+ * MLP run before this call. Errors: BAD_ARG, CUDA. */
+int lbrmhd_set_mlp_weights(lbrmhd_handle h, const float* d_params);
+
+/* Attaches a caller-owned device buffer of N x LBRMHD_MLP_ROW float32 to one
+ * run (NULL detaches it). Each following step writes, for every cell whose
+ * recovery converged, its training sample (row = cell index); rows of cells
+ * that failed are left as they were. Samples are written by the cold-seed
+ * and learned-seed kernels only: a run with LBRMHD_RECOVERY_PLAIN recovers
+ * from zero velocity while a buffer is attached (same tolerance, so the same
+ * primitives up to it). The buffer must outlive its attachment. Errors:
+ * BAD_ARG (run out of range). */
+int lbrmhd_set_mlp_samples(lbrmhd_handle h, int run, float* d_samples);
 
 /* Message of the last failure on this handle (or of the last failed create
  * when h is NULL). Owned by the library; valid until the next call. */

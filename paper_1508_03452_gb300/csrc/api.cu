@@ -31,6 +31,7 @@ struct RunState {
     unsigned long long* d_stats = nullptr;  // failures, iteration sum, iteration max
     int64_t steps = 0;
     int periodic[3] = {1, 1, 1};
+    float* d_samples = nullptr;  // caller-owned training-sample buffer (or NULL)
 };
 
 size_t pop_bytes(int precision) { return precision == LBRMHD_FP64 ? 8 : (precision == LBRMHD_FP32 ? 4 : 2); }
@@ -50,6 +51,8 @@ struct lbrmhd_state_s {
     size_t io_bytes = 0;
     double* d_small = nullptr;  // 32 float64
     int* d_flag = nullptr;
+    unsigned char* d_mlp = nullptr;  // packed network of the learned seed
+    bool mlp_set = false;
 };
 
 #define LB_CK(call)                                                                        \
@@ -237,6 +240,11 @@ int step_run(lbrmhd_handle h, RunState& r)
     A.k = make_phys<R>(r.p, r.ref, runref(r));
     A.hs = r.hs;
     A.stats = r.d_stats;
+    A.mlp = h->d_mlp;
+    A.dump = r.d_samples;
+    A.seed = r.p.recovery == LBRMHD_RECOVERY_MLP ? lb::SEED_MLP
+             : (r.p.recovery == LBRMHD_RECOVERY_COLD || r.d_samples) ? lb::SEED_COLD
+                                                                     : lb::SEED_PREV;
     LB_CK(lb::launch_step<Cfg>(A, h->stream));
     const bool any_open = r.p.bc[0] || r.p.bc[1] || r.p.bc[2] || r.p.bc[3] || r.p.bc[4] || r.p.bc[5];
     if (any_open)
@@ -310,7 +318,9 @@ std::string check_params(const lbrmhd_params& p)
     if (!(p.gamma_ad > 1)) return "gamma_ad must be > 1";
     if (!(p.alpha >= 0)) return "alpha must be >= 0";
     if (p.precision < LBRMHD_FP64 || p.precision > LBRMHD_FP16_DEV) return "unknown precision";
-    if (p.recovery != LBRMHD_RECOVERY_PLAIN && p.recovery != LBRMHD_RECOVERY_MLP) return "unknown recovery mode";
+    if (p.recovery != LBRMHD_RECOVERY_PLAIN && p.recovery != LBRMHD_RECOVERY_MLP && p.recovery != LBRMHD_RECOVERY_COLD)
+        return "unknown recovery mode";
+    if (p.flags & ~(LBRMHD_FLAG_NO_EM_COLLISION | LBRMHD_FLAG_UNSHIFTED_POWER)) return "unknown flag";
     for (int f = 0; f < 6; ++f) {
         if (p.bc[f] < 0 || p.bc[f] > 2) return "unknown boundary kind";
         if (p.bc[f] == LBRMHD_DRIVEN && f != 4) return "DRIVEN is only allowed on the -z face";
@@ -447,6 +457,7 @@ int lbrmhd_destroy(lbrmhd_handle h)
     if (h->d_io) cudaFree(h->d_io);
     if (h->d_small) cudaFree(h->d_small);
     if (h->d_flag) cudaFree(h->d_flag);
+    if (h->d_mlp) cudaFree(h->d_mlp);
     delete h;
     return LBRMHD_OK;
 }
@@ -474,8 +485,11 @@ int lbrmhd_step(lbrmhd_handle h, int64_t nsteps)
 {
     if (!h) return LBRMHD_ERR_BAD_ARG;
     if (nsteps < 0) return fail(h, LBRMHD_ERR_BAD_ARG, "nsteps < 0");
-    for (auto& r : h->runs)
+    for (auto& r : h->runs) {
         if (!r.initialized) return fail(h, LBRMHD_ERR_STATE, "lbrmhd_step before lbrmhd_init_fields");
+        if (r.p.recovery == LBRMHD_RECOVERY_MLP && !h->mlp_set)
+            return fail(h, LBRMHD_ERR_STATE, "learned-seed run without weights (lbrmhd_set_mlp_weights)");
+    }
     LB_CK(cudaSetDevice(h->device));
     for (int64_t t = 0; t < nsteps; ++t) {
         for (auto& r : h->runs) {
@@ -702,6 +716,28 @@ int64_t lbrmhd_run_cells(lbrmhd_handle h, int run)
 {
     if (bad_run(h, run)) return 0;
     return h->runs[run].N;
+}
+
+int lbrmhd_set_mlp_weights(lbrmhd_handle h, const float* d_params)
+{
+    if (!h) return LBRMHD_ERR_BAD_ARG;
+    if (!d_params) return fail(h, LBRMHD_ERR_BAD_ARG, "NULL parameters");
+    LB_CK(cudaSetDevice(h->device));
+    if (!h->d_mlp && cudaMalloc(&h->d_mlp, lbrmhd_mlp_blob_bytes()) != cudaSuccess) {
+        h->d_mlp = nullptr;
+        return fail(h, LBRMHD_ERR_OOM, "network blob allocation failed");
+    }
+    const int rc = lbrmhd_mlp_pack(d_params, h->d_mlp, h->stream);
+    if (rc) return fail(h, rc, "packing the network failed");
+    h->mlp_set = true;
+    return LBRMHD_OK;
+}
+
+int lbrmhd_set_mlp_samples(lbrmhd_handle h, int run, float* d_samples)
+{
+    if (bad_run(h, run)) return h ? fail(h, LBRMHD_ERR_BAD_ARG, "run out of range") : LBRMHD_ERR_BAD_ARG;
+    h->runs[run].d_samples = d_samples;
+    return LBRMHD_OK;
 }
 
 const char* lbrmhd_last_error(lbrmhd_handle h)

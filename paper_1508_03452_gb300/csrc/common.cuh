@@ -39,6 +39,8 @@ struct CfgF16 {  // float16 relative deviations for f and g
 enum { P_N = 0, P_EPS = 1, P_U = 2, P_E = 5, P_B = 8, P_RHO = 11, NPRIM = 12 };
 
 constexpr int FLAG_NO_EM_COLLISION = 1;
+constexpr int FLAG_UNSHIFTED_POWER = 2;
+enum { SEED_PREV = 0, SEED_MLP = 1, SEED_COLD = 2 };
 
 // Population scale for float16 relative deviations: stored value =
 // deviation * inv[i]; deviation = stored * scale[i].
@@ -67,6 +69,9 @@ struct StepArgs {
     Phys<real> k;
     HalfScale hs;
     unsigned long long* stats;  // [0] failures [1] iteration sum [2] iteration max
+    const unsigned char* mlp;   // device inference blob of the learned seed (SEED_MLP)
+    float* dump;                // optional: per cell 20 features + 4 targets of the learned seed
+    int seed;                   // SEED_PREV | SEED_MLP | SEED_COLD
 };
 
 // population load / store in the configured format

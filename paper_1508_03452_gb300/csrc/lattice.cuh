@@ -328,15 +328,16 @@ __device__ __forceinline__ void ohm_current(const R* E, const R* u, const R* B, 
 
 // ---------------------------------------------------------------------------
 // Landau eigen-solve (coupling subsection): largest eigenpair of
-// A = [T - eps0 F F(E_old, B_old)] eta by a shifted power iteration
-// (shift p_old - s_old pushes the spacelike eigenvalues to ~0), seeded with
-// the previous velocity. T holds the moments with eps_r taken out of T^00
+// A = [T - eps0 F F(E_old, B_old)] eta by a power iteration, shifted by
+// p_old - s_old (which pushes the spacelike eigenvalues to ~0) unless
+// `shifted` is false (the paper's plain power method), started from the
+// velocity `seed` (beta). T holds the moments with eps_r taken out of T^00
 // (the reference rest state's other entries included); the returned lambda is
 // the eigenvalue minus eps_r. Returns the iteration count, or -1 if it failed.
 // ---------------------------------------------------------------------------
 template <class R>
 __device__ __forceinline__ int landau(const R T[4][4], const Prim<R>& old, const Phys<R>& k, R beta[3], R& lambda,
-                                      R& s_old)
+                                      R& s_old, const R* seed, bool shifted)
 {
     const R* E = old.E;
     const R* B = old.B;
@@ -359,9 +360,9 @@ __device__ __forceinline__ int landau(const R T[4][4], const Prim<R>& old, const
     }
     s_old = R(0.5) * k.eps0 * (k.c2 * B2 - E2);
     const R p_old = k.gm1 * (old.eps - old.n * k.c2);
-    const R shift = p_old - s_old;
+    const R shift = shifted ? p_old - s_old : R(0);
     const R a00_full = k.eps_r + shift;  // eps_r restored in the first row only
-    R v1 = old.u[0] * k.inv_c, v2 = old.u[1] * k.inv_c, v3 = old.u[2] * k.inv_c;
+    R v1 = seed[0], v2 = seed[1], v3 = seed[2];
     int it = 0;
     bool done = false;
     for (it = 1; it <= k.maxit; ++it) {

@@ -16,6 +16,7 @@
 //      primitives.
 #pragma once
 #include "common.cuh"
+#include "mlp.cuh"
 
 namespace lb {
 
@@ -92,7 +93,7 @@ template <int I, bool IS3D, class Cfg>
 struct StreamAll {
     using R = typename Cfg::real;
     static __device__ __forceinline__ void run(const StepArgs<Cfg>& A, const Off& o, int64_t c, R* sp, int nth,
-                                               R (&Tm)[10], R& Nm)
+                                               R (&Tm)[10], R& Nm, R (&Na)[3])
     {
         const R f = stream_pop<I, IS3D, true, Cfg>(A.fin + (int64_t)I * A.stride + c, o, A.k, A.hs.f[I]);
         const R g = stream_pop<I, IS3D, false, Cfg>(A.gin + (int64_t)I * A.stride + c, o, A.k, A.hs.g[I]);
@@ -111,13 +112,17 @@ struct StreamAll {
         if (cx * cz) Tm[8] += R(cx * cz) * f;
         if (cy * cz) Tm[9] += R(cy * cz) * f;
         Nm += g;
-        StreamAll<I + 1, IS3D, Cfg>::run(A, o, c, sp, nth, Tm, Nm);
+        if (cx) Na[0] += R(cx) * g;
+        if (cy) Na[1] += R(cy) * g;
+        if (cz) Na[2] += R(cz) * g;
+        StreamAll<I + 1, IS3D, Cfg>::run(A, o, c, sp, nth, Tm, Nm, Na);
     }
 };
 template <bool IS3D, class Cfg>
 struct StreamAll<19, IS3D, Cfg> {
     using R = typename Cfg::real;
-    static __device__ __forceinline__ void run(const StepArgs<Cfg>&, const Off&, int64_t, R*, int, R (&)[10], R&) {}
+    static __device__ __forceinline__ void run(const StepArgs<Cfg>&, const Off&, int64_t, R*, int, R (&)[10], R&,
+                                               R (&)[3]) {}
 };
 
 // Exact D3Q13 pull h_k(x) = h_c,k(x - hop_k) into slot 38 + k, accumulating
@@ -201,25 +206,34 @@ struct StepMinBlocks {
     static constexpr int value = sizeof(typename Cfg::real) == 8 ? 2 : LB_STEP_MIN_BLOCKS;
 };
 
-template <class Cfg, bool IS3D>
+template <class Cfg, bool IS3D, int SEED>
 __global__ void __launch_bounds__(kStepThreads, StepMinBlocks<Cfg>::value) step_kernel(const StepArgs<Cfg> A)
 {
     using R = typename Cfg::real;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nth = blockDim.x * blockDim.y;
-    R* sp = reinterpret_cast<R*>(smem_raw) + (threadIdx.x + threadIdx.y * blockDim.x);
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    R* sp = reinterpret_cast<R*>(smem_raw) + tid;
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
-    if (x >= A.nx || y >= A.ny) return;  // the kernel has no block-wide barrier
+    const bool active = x < A.nx && y < A.ny;
+    if constexpr (SEED != SEED_MLP) {
+        if (!active) return;  // the kernel has no block-wide barrier
+    } else {
+        // the warp-wide tensor-core MMA of the learned seed needs every lane:
+        // out-of-range lanes work on a clamped cell and store nothing
+        x = x < A.nx ? x : A.nx - 1;
+        y = y < A.ny ? y : A.ny - 1;
+    }
     const Off o = make_off(x, y, z, A.nx, A.ny, A.nz, A.periodic);
     const int64_t c = x + (int64_t)A.nx * (y + (int64_t)A.ny * z);
     const Phys<R>& k = A.k;
 
     // 1. streaming of f and g (with their moments) and of h (with its moments)
     R Tm[10] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
-    R Nm = R(0);
-    StreamAll<0, IS3D, Cfg>::run(A, o, c, sp, nth, Tm, Nm);
+    R Nm = R(0), Na[3] = {R(0), R(0), R(0)};
+    StreamAll<0, IS3D, Cfg>::run(A, o, c, sp, nth, Tm, Nm, Na);
     R dEp[3] = {R(0), R(0), R(0)}, bn[3] = {R(0), R(0), R(0)}, rho = R(0);
     PullH<0, IS3D, Cfg>::run(A, o, c, sp, nth, dEp, bn, rho);
     const R h24 = (R)A.hin[24 * A.stride + c];
@@ -263,9 +277,43 @@ __global__ void __launch_bounds__(kStepThreads, StepMinBlocks<Cfg>::value) step_
         Bn[a] = k.Br[a] + dB[a];
     }
 
-    // 3. recovery
+    // 3. recovery, seeded with the previous velocity, the learned guess or zero
+    R seed[3];
+    float feat[MLP_IN];
+    // the training-data dump exists only in the cold-seed and learned-seed
+    // variants (the seed does not change the converged result)
+    constexpr bool kCanDump = SEED != SEED_PREV;
+    const bool want_feat = SEED == SEED_MLP || (kCanDump && A.dump != nullptr);
+    if (want_feat) {
+        const R T0a[3] = {T[0][1], T[0][2], T[0][3]};
+        const R Tab[6] = {T[1][1], T[2][2], T[3][3], T[1][2], T[1][3], T[2][3]};
+        const R Nq[3] = {qq * Na[0], qq * Na[1], qq * Na[2]};
+        mlp_features(k.eps_r + T[0][0], T0a, Tab, k.n_r + dN0, Nq, old.E, old.B, feat);
+    }
+    if constexpr (SEED == SEED_MLP) {
+        __nv_bfloat16* act =
+            reinterpret_cast<__nv_bfloat16*>(smem_raw + (size_t)kStepSlots * sizeof(R) * nth);
+        float* out_f = reinterpret_cast<float*>(smem_raw + (size_t)kStepSlots * sizeof(R) * nth +
+                                                (size_t)MLP_ACT_BYTES_PER_CELL * nth);
+        __nv_bfloat16* row = act + tid * MLP_HS;
+#pragma unroll
+        for (int j = 0; j < 32; j += 2)
+            *reinterpret_cast<__nv_bfloat162*>(row + j) =
+                __floats2bfloat162_rn(j < MLP_IN ? feat[j] : 0.0f, j + 1 < MLP_IN ? feat[j + 1] : 0.0f);
+        __syncwarp();
+        mlp_forward_warp(act, A.mlp, out_f);
+        R sb[3] = {(R)out_f[tid * 8], (R)out_f[tid * 8 + 1], (R)out_f[tid * 8 + 2]};
+        const R sb2 = sb[0] * sb[0] + sb[1] * sb[1] + sb[2] * sb[2];
+        const R lim = R(0.9);  // keep the guess well inside the light cone
+        const R scale = sb2 > lim * lim ? lim / sqrt(sb2) : R(1);
+        for (int a = 0; a < 3; ++a) seed[a] = sb[a] * scale;
+    } else if constexpr (SEED == SEED_COLD) {
+        seed[0] = seed[1] = seed[2] = R(0);
+    } else {
+        for (int a = 0; a < 3; ++a) seed[a] = old.u[a] * k.inv_c;
+    }
     R beta[3], lambda, s_old;
-    const int it = landau(T, old, k, beta, lambda, s_old);
+    const int it = landau(T, old, k, beta, lambda, s_old, seed, (A.flags & FLAG_UNSHIFTED_POWER) == 0);
     Prim<R> nw;
     R J[3], n_dev, eps_dev;
     const bool ok = it > 0;
@@ -294,6 +342,14 @@ __global__ void __launch_bounds__(kStepThreads, StepMinBlocks<Cfg>::value) step_
 #pragma unroll
         for (int a = 0; a < 3; ++a) dB[a] = nw.B[a] - k.Br[a];
         ohm_current(nw.E, nw.u, nw.B, nw.rho, k, J);
+    }
+
+    if (!active) return;  // (only reached by clamped lanes of the learned-seed variant)
+    if (kCanDump && A.dump != nullptr && ok) {
+        float* d = A.dump + c * (MLP_IN + MLP_OUT);
+        for (int j = 0; j < MLP_IN; ++j) d[j] = feat[j];
+        for (int a = 0; a < 3; ++a) d[MLP_IN + a] = (float)beta[a];
+        d[MLP_IN + 3] = (float)((nw.eps) / (k.eps_r + T[0][0]) - R(1));
     }
 
     // 4. collisions at the new time level and stores
@@ -338,21 +394,37 @@ cudaError_t launch_step(const StepArgs<Cfg>& A, cudaStream_t stream)
     using R = typename Cfg::real;
     const int bx = A.nx >= LB_STEP_BX ? LB_STEP_BX : (A.nx >= 64 ? 64 : 32);
     const int by = kStepThreads / bx;
-    const size_t smem = (size_t)kStepSlots * sizeof(R) * kStepThreads;
+    const size_t smem_base = (size_t)kStepSlots * sizeof(R) * kStepThreads;
+    const size_t smem_mlp = smem_base + (size_t)(MLP_ACT_BYTES_PER_CELL + 8 * sizeof(float)) * kStepThreads;
     static bool configured = false;  // one attribute call per instantiation
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(step_kernel<Cfg, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(step_kernel<Cfg, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const int b = (int)smem_base, m = (int)smem_mlp;
+        cudaError_t e = cudaFuncSetAttribute(step_kernel<Cfg, true, SEED_PREV>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<Cfg, false, SEED_PREV>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<Cfg, true, SEED_COLD>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<Cfg, false, SEED_COLD>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<Cfg, true, SEED_MLP>, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<Cfg, false, SEED_MLP>, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
         if (e != cudaSuccess) return e;
         configured = true;
     }
     dim3 block(bx, by, 1);
     dim3 grid((A.nx + bx - 1) / bx, (A.ny + by - 1) / by, A.nz);
-    if (A.nz > 1)
-        step_kernel<Cfg, true><<<grid, block, smem, stream>>>(A);
-    else
-        step_kernel<Cfg, false><<<grid, block, smem, stream>>>(A);
+    const bool d3 = A.nz > 1;
+    switch (A.seed) {
+        case SEED_MLP:
+            if (d3) step_kernel<Cfg, true, SEED_MLP><<<grid, block, smem_mlp, stream>>>(A);
+            else step_kernel<Cfg, false, SEED_MLP><<<grid, block, smem_mlp, stream>>>(A);
+            break;
+        case SEED_COLD:
+            if (d3) step_kernel<Cfg, true, SEED_COLD><<<grid, block, smem_base, stream>>>(A);
+            else step_kernel<Cfg, false, SEED_COLD><<<grid, block, smem_base, stream>>>(A);
+            break;
+        default:
+            if (d3) step_kernel<Cfg, true, SEED_PREV><<<grid, block, smem_base, stream>>>(A);
+            else step_kernel<Cfg, false, SEED_PREV><<<grid, block, smem_base, stream>>>(A);
+            break;
+    }
     return cudaGetLastError();
 }
 

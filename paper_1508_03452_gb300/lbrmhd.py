@@ -18,8 +18,9 @@ OK = 0
 ERR_BAD_ARG, ERR_OOM, ERR_CUDA, ERR_NONCONVERGED, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE = -1, -2, -3, -4, -5, -6, -7
 PERIODIC, OPEN, DRIVEN = 0, 1, 2
 FP64, FP32, FP16_DEV = 0, 1, 2
-RECOVERY_PLAIN, RECOVERY_MLP = 0, 1
-FLAG_NO_EM_COLLISION = 1
+RECOVERY_PLAIN, RECOVERY_MLP, RECOVERY_COLD = 0, 1, 2
+FLAG_NO_EM_COLLISION, FLAG_UNSHIFTED_POWER = 1, 2
+MLP_NPARAM, MLP_NFEAT, MLP_ROW = 9924, 20, 24
 NMOMENTS, NDIAG, NTABLE = 16, 10, 311
 MOMENT_NAMES = ["n", "p", "eps", "ux", "uy", "uz", "Ex", "Ey", "Ez", "Bx", "By", "Bz", "rho_c", "Jx", "Jy", "Jz"]
 DIAG_NAMES = ["N0", "T00", "T01", "T02", "T03", "rho_c", "divB_max", "divB_rms", "nonfinite", "cells"]
@@ -29,6 +30,8 @@ EXPORTED = [
     "lbrmhd_step", "lbrmhd_get_moments", "lbrmhd_get_moments_device", "lbrmhd_get_populations",
     "lbrmhd_get_diagnostics", "lbrmhd_get_stats", "lbrmhd_state_bytes", "lbrmhd_get_state", "lbrmhd_set_state",
     "lbrmhd_run_cells", "lbrmhd_last_error", "lbrmhd_lattice_tables", "lbrmhd_get_diagnostics_noalloc",
+    "lbrmhd_mlp_nparams", "lbrmhd_mlp_blob_bytes", "lbrmhd_mlp_pack", "lbrmhd_mlp_infer", "lbrmhd_mlp_grad",
+    "lbrmhd_mlp_train", "lbrmhd_set_mlp_weights", "lbrmhd_set_mlp_samples",
 ]
 
 
@@ -103,6 +106,14 @@ def load(build_if_missing: bool = True):
         L.lbrmhd_last_error.argtypes = [vp]
         L.lbrmhd_last_error.restype = C.c_char_p
         L.lbrmhd_lattice_tables.argtypes = [dp, C.c_size_t]
+        L.lbrmhd_mlp_nparams.argtypes = []
+        L.lbrmhd_mlp_blob_bytes.argtypes = []
+        L.lbrmhd_mlp_pack.argtypes = [vp, vp, vp]
+        L.lbrmhd_mlp_infer.argtypes = [vp, vp, i64, vp, vp]
+        L.lbrmhd_mlp_grad.argtypes = [vp, vp, i64, vp, vp]
+        L.lbrmhd_mlp_train.argtypes = [vp, vp, vp, i64, C.c_int, C.c_int, C.c_float, C.c_uint64, vp, vp]
+        L.lbrmhd_set_mlp_weights.argtypes = [vp, vp]
+        L.lbrmhd_set_mlp_samples.argtypes = [vp, C.c_int, vp]
         _lib = L
         return L
 
@@ -134,6 +145,80 @@ def lattice_tables() -> dict:
 
     return {"chat": take(57, (19, 3)), "w": take(19, (19,)), "wg": take(19, (19,)), "hop": take(72, (24, 3)),
             "e_over_c": take(72, (24, 3)), "b": take(72, (24, 3))}
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor (contiguous) or an integer address."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        if not t.is_contiguous():
+            raise ValueError("device arrays must be contiguous")
+        return C.c_void_p(t.data_ptr())
+    return C.c_void_p(int(t))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(getattr(stream, "cuda_stream", stream) or 0)
+
+
+def _need_f32(t, n, what):
+    import torch
+    if t.dtype != torch.float32 or not t.is_cuda or t.numel() != n:
+        raise ValueError(f"{what}: expected a cuda float32 tensor of {n} values")
+
+
+def _rc(rc, what):
+    if rc != OK:
+        raise LbrmhdError(rc, what)
+
+
+def mlp_pack(params, stream=None):
+    """Packed inference blob (uint8 cuda tensor) of float32 parameters."""
+    import torch
+    _need_f32(params, MLP_NPARAM, "params")
+    L = load()
+    blob = torch.empty(L.lbrmhd_mlp_blob_bytes(), dtype=torch.uint8, device=params.device)
+    _rc(L.lbrmhd_mlp_pack(_ptr(params), _ptr(blob), _stream_ptr(stream)), "mlp_pack")
+    return blob
+
+
+def mlp_infer(blob, features, stream=None):
+    """Network outputs (n x 4) for feature rows (n x 20, cuda float32)."""
+    import torch
+    n = features.numel() // MLP_NFEAT
+    _need_f32(features, n * MLP_NFEAT, "features")
+    out = torch.empty((n, 4), dtype=torch.float32, device=features.device)
+    _rc(load().lbrmhd_mlp_infer(_ptr(blob), _ptr(features), n, _ptr(out), _stream_ptr(stream)), "mlp_infer")
+    return out
+
+
+def mlp_grad(params, data, stream=None):
+    """(loss, gradient) of the mean squared error over the sample rows (n x 24)."""
+    import torch
+    n = data.numel() // MLP_ROW
+    _need_f32(params, MLP_NPARAM, "params")
+    _need_f32(data, n * MLP_ROW, "data")
+    g = torch.empty(MLP_NPARAM + 1, dtype=torch.float32, device=data.device)
+    _rc(load().lbrmhd_mlp_grad(_ptr(params), _ptr(data), n, _ptr(g), _stream_ptr(stream)), "mlp_grad")
+    return float(g[MLP_NPARAM]), g[:MLP_NPARAM]
+
+
+def mlp_train(params, adam, data, steps, batch, lr, seed=1, stream=None):
+    """Adam steps on mini-batches of the sample rows; updates params and adam
+    (2 x MLP_NPARAM) in place and returns the per-step mini-batch losses."""
+    import torch
+    n = data.numel() // MLP_ROW
+    _need_f32(params, MLP_NPARAM, "params")
+    _need_f32(adam, 2 * MLP_NPARAM, "adam")
+    _need_f32(data, n * MLP_ROW, "data")
+    loss = torch.empty(max(int(steps), 1), dtype=torch.float32, device=data.device)
+    _rc(load().lbrmhd_mlp_train(_ptr(params), _ptr(adam), _ptr(data), n, int(steps), int(batch), float(lr),
+                                int(seed), _ptr(loss), _stream_ptr(stream)), "mlp_train")
+    return loss[:int(steps)]
 
 
 class Solver:
@@ -224,3 +309,16 @@ class Solver:
     def set_state(self, blob: bytes):
         buf = C.create_string_buffer(blob, len(blob))
         self._check(self._L.lbrmhd_set_state(self._h, buf, len(blob)))
+
+    def set_mlp_weights(self, params):
+        """Network of the learned recovery seed (cuda float32, MLP_NPARAM)."""
+        _need_f32(params, MLP_NPARAM, "params")
+        self._check(self._L.lbrmhd_set_mlp_weights(self._h, _ptr(params)))
+
+    def set_mlp_samples(self, run, samples):
+        """Attaches a cuda float32 buffer of cells x 24 that each following
+        step fills with training samples (None detaches)."""
+        if samples is not None:
+            _need_f32(samples, self.cells[run] * MLP_ROW, "samples")
+        self._check(self._L.lbrmhd_set_mlp_samples(self._h, run, _ptr(samples)))
+        self._samples = samples  # keep the buffer alive while attached
