@@ -12,6 +12,12 @@ Arms:
   --impl reference   the FP64 CPU oracle on the host cores, each step a bounded
                      sample (a 1024 x 32 strip of the sigma = 100 run)
 
+The default arm also reports, under "learned_seed", the same workload with the
+recovery seeded by the learned network (trained on the GPU, before that leg's
+timed region, from samples of the method's own current-sheet and
+Kelvin-Helmholtz runs): its MLUPS and eigen-solve iterations per cell beside
+the plain path's, and both float32 arms' errors against the float64 GPU build.
+
 Prints one JSON line (rank 0).
 """
 from __future__ import annotations
@@ -36,7 +42,8 @@ NX = NY = 1024
 # primitives, each read once and written once
 BYTES_PER_CELL = {"fp64": 2 * (63 + 12) * 8, "fp32": 2 * (63 + 12) * 4, "fp16": 2 * (38 * 2 + 25 * 4 + 12 * 4)}
 PROFILE = os.path.join(ROOT, "profiles", "step_kernel_current_sheet_1024.md")
-KERNEL_SOURCES = ["step_impl.cuh", "lattice.cuh", "common.cuh"]
+KERNEL_SOURCES = ["step_impl.cuh", "lattice.cuh", "common.cuh", "mlp.cuh"]
+GROUPS = {"n": (0,), "p": (1,), "eps": (2,), "u": (3, 4, 5), "E": (6, 7, 8), "B": (9, 10, 11)}
 
 
 def dist_env():
@@ -186,6 +193,95 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def hist_quantile(hist, q):
+    """Iteration count at quantile q of a recovery histogram (bin k = k + 1
+    iterations; the last bin is open-ended and reported as its lower edge)."""
+    import numpy as np
+    c = np.cumsum(hist)
+    if c[-1] == 0:
+        return None
+    return int(np.searchsorted(c, q * c[-1]) + 1)
+
+
+def rel_errors(m, ref):
+    import numpy as np
+    return {k: float(np.linalg.norm(m[list(r)] - ref[list(r)]) / max(np.linalg.norm(ref[list(r)]), 1e-300))
+            for k, r in GROUPS.items()}
+
+
+def learned_seed_leg(args, stream, plain_moments, plain_iters, steps_total):
+    """The same workload with the recovery seeded by the learned network:
+    samples from the method's own current-sheet and Kelvin-Helmholtz runs,
+    training on the GPU, then the timed steps. Errors of both float32 arms
+    are taken against a float64 GPU run of the sigma = 100 run."""
+    import numpy as np
+    import torch
+
+    from paper_1508_03452_gb300 import lbrmhd as L
+    from paper_1508_03452_gb300 import workloads as W
+
+    prec = {"fp32": L.FP32, "fp16": L.FP16_DEV, "fp64": L.FP64}[args.precision]
+    t0 = time.perf_counter()
+    cases = [(W.current_sheet(256, 64, 1, delta=8.0), 100.0)] + [
+        (W.kelvin_helmholtz(256, 128, 1, V=0.2, ratio=10.0, B0=0.1, a=2.0, noise=1e-3, seed=s), 1e3) for s in (11, 12)]
+    chunks = []
+    for F, sigma in cases:
+        s = L.Solver(L.make_params(F.nx, F.ny, 1, sigma=sigma, precision=prec, recovery=L.RECOVERY_COLD),
+                     stream=stream)
+        s.init_fields(0, F.n, F.p, F.u, F.B)
+        buf = torch.full((F.N, L.MLP_ROW), float("nan"), dtype=torch.float32, device="cuda")
+        s.set_mlp_samples(0, buf)
+        for t in range(40):
+            s.step(1)
+            if t % 4 == 3:
+                chunks.append(buf.clone())
+        s.close()
+    data = torch.cat(chunks)
+    data = data[torch.isfinite(data).all(1)].contiguous()
+    P = torch.tensor(W.mlp_init_params(1), device="cuda")
+    adam = torch.zeros(2 * L.MLP_NPARAM, device="cuda")
+    train_steps = 3000
+    losses = L.mlp_train(P, adam, data, train_steps, 1024, 1e-3, seed=7).cpu().numpy()
+    train_s = time.perf_counter() - t0
+
+    F = W.current_sheet(NX, NY, 1, delta=8.0)
+    N = NX * NY
+    solver = L.Solver([L.make_params(NX, NY, 1, sigma=sg, precision=prec, recovery=L.RECOVERY_MLP) for sg in SIGMAS],
+                      stream=stream)
+    solver.set_mlp_weights(P)
+    for r in range(len(SIGMAS)):
+        solver.init_fields(r, F.n, F.p, F.u, F.B)
+    solver.step(args.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solver.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    stats = [solver.stats(r) for r in range(len(SIGMAS))]
+    hist = sum(solver.iteration_histogram(r) for r in range(len(SIGMAS)))
+    m_mlp = solver.moments(1)
+    solver.close()
+    ref = L.Solver(L.make_params(NX, NY, 1, sigma=SIGMAS[1], precision=L.FP64), stream=stream)
+    ref.init_fields(0, F.n, F.p, F.u, F.B)
+    ref.step(steps_total)
+    m64 = ref.moments(0)
+    ref.close()
+    return {
+        "value": len(SIGMAS) * N * args.steps / (ms * 1e-3) / 1e6, "unit": UNIT,
+        "iters_per_cell": sum(s["iter_total"] for s in stats) / (len(SIGMAS) * N * steps_total),
+        "iters_p99": hist_quantile(hist, 0.99),
+        "plain_iters_per_cell": plain_iters,
+        "failures": sum(s["recover_fail"] for s in stats),
+        "err_vs_fp64": rel_errors(m_mlp, m64), "plain_err_vs_fp64": rel_errors(plain_moments, m64),
+        "error_run": f"sigma={SIGMAS[1]}, {steps_total} steps, relative L2 per field against the float64 GPU build",
+        "train": {"samples": int(data.shape[0]), "adam_steps": train_steps, "batch": 1024,
+                  "loss_first": float(losses[:10].mean()), "loss_last": float(losses[-100:].mean()),
+                  "seconds_incl_sampling": train_s},
+    }
+
+
 def run_gpu(args, world, rank, local):
     import numpy as np
     import torch
@@ -235,6 +331,10 @@ def run_gpu(args, world, rank, local):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     stats = [solver.stats(r) for r in range(len(SIGMAS))]
+    steps_total = args.warmup + args.steps
+    plain_iters = sum(s["iter_total"] for s in stats) / (len(SIGMAS) * N * steps_total)
+    plain_hist = sum(solver.iteration_histogram(r) for r in range(len(SIGMAS)))
+    plain_moments = solver.moments(1) if (rank == 0 and not args.no_learned_seed) else None
     launches = args.steps * len(SIGMAS)
     value = world * cells * args.steps / (ms * 1e-3) / 1e6
     # roofline of the dominant (only) kernel of the timed region: the fused step
@@ -282,10 +382,12 @@ def run_gpu(args, world, rank, local):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
                     "d2h_bytes_per_step": d2h / args.steps},
             "gpu_launches": launches,
-            "recovery": {"iters_mean": sum(s["iter_total"] for s in stats) / max(1, sum(
-                (args.steps + args.warmup) * N for _ in stats)), "iters_max": max(s["iter_max"] for s in stats),
+            "recovery": {"iters_mean": plain_iters, "iters_p99": hist_quantile(plain_hist, 0.99),
+                         "iters_max": max(s["iter_max"] for s in stats),
                          "failures": sum(s["recover_fail"] for s in stats)},
         }
+        if plain_moments is not None:
+            line["learned_seed"] = learned_seed_leg(args, stream, plain_moments, plain_iters, steps_total)
         clocks = clk.summary()
         if clocks:
             line["clocks"] = clocks
@@ -322,6 +424,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned-seed", action="store_true", help="skip the learned-seed comparison leg")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--profile-case", action="store_true", help="untimed 1024^2 single-run case for ncu captures")
     args = ap.parse_args()

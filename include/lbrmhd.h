@@ -195,6 +195,14 @@ int lbrmhd_get_diagnostics_noalloc(lbrmhd_handle h, int run, double* d_out);
  * recovery iterations, [3] maximum recovery iterations. Host output. */
 int lbrmhd_get_stats(lbrmhd_handle h, int run, int64_t* out4);
 
+/* Histogram of recovery iteration counts of one run since its
+ * initialisation, LBRMHD_NHIST int64 host values: out[k] (k < LBRMHD_NHIST -
+ * 1) counts cell updates whose eigen-solve converged in k + 1 iterations,
+ * out[LBRMHD_NHIST - 1] those that needed LBRMHD_NHIST or more (failures are
+ * counted by lbrmhd_get_stats only). Synchronises the handle's stream. */
+#define LBRMHD_NHIST 17
+int lbrmhd_get_iteration_histogram(lbrmhd_handle h, int run, int64_t* out);
+
 /* Checkpoint / resume: the raw device state of every run (populations and
  * primitives in their storage format, plus step counters). Resuming from a
  * checkpoint is bit-exact. `bytes` must be lbrmhd_state_bytes(). */

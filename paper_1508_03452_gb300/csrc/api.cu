@@ -28,11 +28,13 @@ struct RunState {
     double Xr[3][3] = {}, Yr[3] = {};            // reference EM terms of the f deviations
     lb::RefPops refpops{};
     lb::HalfScale hs{};
-    unsigned long long* d_stats = nullptr;  // failures, iteration sum, iteration max
+    unsigned long long* d_stats = nullptr;  // lb::kNumStats recovery counters
     int64_t steps = 0;
     int periodic[3] = {1, 1, 1};
     float* d_samples = nullptr;  // caller-owned training-sample buffer (or NULL)
 };
+
+constexpr size_t kStatsBytes = lb::kNumStats * sizeof(unsigned long long);
 
 size_t pop_bytes(int precision) { return precision == LBRMHD_FP64 ? 8 : (precision == LBRMHD_FP32 ? 4 : 2); }
 size_t hp_bytes(int precision) { return precision == LBRMHD_FP64 ? 8 : 4; }
@@ -266,7 +268,7 @@ int init_run(lbrmhd_handle h, RunState& r, const lb::InitInputs& in)
     LB_CK(lb::launch_init<Cfg>(view<Cfg>(r, r.cur), in, make_phys<double>(r.p, r.ref, runref(r)), h->d_flag, h->stream));
     int bad = 0;
     LB_CK(cudaMemcpyAsync(&bad, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    LB_CK(cudaMemsetAsync(r.d_stats, 0, 3 * sizeof(unsigned long long), h->stream));
+    LB_CK(cudaMemsetAsync(r.d_stats, 0, lb::kNumStats * sizeof(unsigned long long), h->stream));
     LB_CK(cudaStreamSynchronize(h->stream));
     if (bad) return fail(h, LBRMHD_ERR_BAD_ARG, "initial state has |u| >= c or n <= 0");
     r.initialized = true;
@@ -417,8 +419,8 @@ int lbrmhd_create(const lbrmhd_params* params, int n_runs, lbrmhd_handle* out)
                 cudaMemset(s.prim[b], 0, lb::NPRIM * s.stride * qb);
             }
         }
-        ok = ok && cudaMalloc(&s.d_stats, 3 * sizeof(unsigned long long)) == cudaSuccess;
-        if (ok) cudaMemset(s.d_stats, 0, 3 * sizeof(unsigned long long));
+        ok = ok && cudaMalloc(&s.d_stats, lb::kNumStats * sizeof(unsigned long long)) == cudaSuccess;
+        if (ok) cudaMemset(s.d_stats, 0, lb::kNumStats * sizeof(unsigned long long));
         max_blocks = std::max<int64_t>(max_blocks, (s.N + lb::kDiagThreads - 1) / lb::kDiagThreads);
     }
     const size_t scratch = std::max<size_t>((size_t)max_blocks * lb::NPART, (size_t)lb::kMeansBlocks * lb::NMEANS);
@@ -638,14 +640,26 @@ int lbrmhd_get_stats(lbrmhd_handle h, int run, int64_t* out4)
     return LBRMHD_OK;
 }
 
-// checkpoint blob: per run [int64 steps][NMEANS double reference means][uint64 stats x3]
+int lbrmhd_get_iteration_histogram(lbrmhd_handle h, int run, int64_t* out)
+{
+    if (bad_run(h, run) || !out) return h ? fail(h, LBRMHD_ERR_BAD_ARG, "bad run or NULL output") : LBRMHD_ERR_BAD_ARG;
+    RunState& r = h->runs[run];
+    LB_CK(cudaSetDevice(h->device));
+    unsigned long long s[lb::kNumStats];
+    LB_CK(cudaMemcpyAsync(s, r.d_stats, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
+    LB_CK(cudaStreamSynchronize(h->stream));
+    for (int b = 0; b < lb::kHistBins; ++b) out[b] = (int64_t)s[3 + b];
+    return LBRMHD_OK;
+}
+
+// checkpoint blob: per run [int64 steps][NMEANS double reference means][uint64 stats x kNumStats]
 // [pops 38 N][h 25 N][prim 12 N] (storage format)
 int lbrmhd_state_bytes(lbrmhd_handle h, size_t* bytes)
 {
     if (!h || !bytes) return LBRMHD_ERR_BAD_ARG;
     const size_t pb = pop_bytes(h->precision), hb = hp_bytes(h->precision);
     size_t total = 0;
-    for (auto& r : h->runs) total += 8 + 8 * lb::NMEANS + 24 + (size_t)r.N * (38 * pb + 25 * hb + lb::NPRIM * hb);
+    for (auto& r : h->runs) total += 8 + 8 * lb::NMEANS + kStatsBytes + (size_t)r.N * (38 * pb + 25 * hb + lb::NPRIM * hb);
     *bytes = total;
     return LBRMHD_OK;
 }
@@ -664,8 +678,8 @@ int lbrmhd_get_state(lbrmhd_handle h, void* host_buf, size_t bytes)
         o += 8;
         std::memcpy(o, r.means, 8 * lb::NMEANS);
         o += 8 * lb::NMEANS;
-        LB_CK(cudaMemcpyAsync(o, r.d_stats, 24, cudaMemcpyDeviceToHost, h->stream));
-        o += 24;
+        LB_CK(cudaMemcpyAsync(o, r.d_stats, kStatsBytes, cudaMemcpyDeviceToHost, h->stream));
+        o += kStatsBytes;
         for (int pl = 0; pl < 38; ++pl, o += r.N * pb)
             LB_CK(cudaMemcpyAsync(o, (char*)r.pops[r.cur] + pl * r.stride * pb, r.N * pb, cudaMemcpyDeviceToHost,
                                   h->stream));
@@ -695,8 +709,8 @@ int lbrmhd_set_state(lbrmhd_handle h, const void* host_buf, size_t bytes)
         std::memcpy(means, o, 8 * lb::NMEANS);
         o += 8 * lb::NMEANS;
         set_reference(r, means);
-        LB_CK(cudaMemcpyAsync(r.d_stats, o, 24, cudaMemcpyHostToDevice, h->stream));
-        o += 24;
+        LB_CK(cudaMemcpyAsync(r.d_stats, o, kStatsBytes, cudaMemcpyHostToDevice, h->stream));
+        o += kStatsBytes;
         for (int pl = 0; pl < 38; ++pl, o += r.N * pb)
             LB_CK(cudaMemcpyAsync((char*)r.pops[r.cur] + pl * r.stride * pb, o, r.N * pb, cudaMemcpyHostToDevice,
                                   h->stream));

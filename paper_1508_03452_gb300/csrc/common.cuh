@@ -38,6 +38,12 @@ struct CfgF16 {  // float16 relative deviations for f and g
 // primitive planes
 enum { P_N = 0, P_EPS = 1, P_U = 2, P_E = 5, P_B = 8, P_RHO = 11, NPRIM = 12 };
 
+// per-run recovery counters: [0] failures [1] iteration sum [2] iteration max,
+// then kHistBins bins: cells that converged in 1, 2, ..., kHistBins - 1
+// iterations, and in kHistBins or more
+constexpr int kHistBins = 17;
+constexpr int kNumStats = 3 + kHistBins;
+
 constexpr int FLAG_NO_EM_COLLISION = 1;
 constexpr int FLAG_UNSHIFTED_POWER = 2;
 enum { SEED_PREV = 0, SEED_MLP = 1, SEED_COLD = 2 };
@@ -68,7 +74,7 @@ struct StepArgs {
     int flags;
     Phys<real> k;
     HalfScale hs;
-    unsigned long long* stats;  // [0] failures [1] iteration sum [2] iteration max
+    unsigned long long* stats;  // kNumStats counters (see kHistBins)
     const unsigned char* mlp;   // device inference blob of the learned seed (SEED_MLP)
     float* dump;                // optional: per cell 20 features + 4 targets of the learned seed
     int seed;                   // SEED_PREV | SEED_MLP | SEED_COLD

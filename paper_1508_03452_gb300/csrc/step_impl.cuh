@@ -196,18 +196,20 @@ struct CollideH<24, Cfg> {
 constexpr int kStepThreads = 128;
 constexpr int kStepSlots = 63;  // 19 f + 19 g + 25 h pre-collision values per cell in shared memory
 #ifndef LB_STEP_MIN_BLOCKS
-#define LB_STEP_MIN_BLOCKS 4  // resident 128-thread blocks per SM targeted for float32 arithmetic
+#define LB_STEP_MIN_BLOCKS 5  // resident 128-thread blocks per SM targeted for float32 arithmetic (96 registers)
 #endif
 #ifndef LB_STEP_BX
 #define LB_STEP_BX 128  // block width along x (the block is LB_STEP_BX x 128 / LB_STEP_BX)
 #endif
-template <class Cfg>
+// float64: 2 blocks; the learned-seed variant: 4 (its shared-memory tiles
+// allow no more, so it keeps 128 registers)
+template <class Cfg, int SEED>
 struct StepMinBlocks {
-    static constexpr int value = sizeof(typename Cfg::real) == 8 ? 2 : LB_STEP_MIN_BLOCKS;
+    static constexpr int value = sizeof(typename Cfg::real) == 8 ? 2 : (SEED == SEED_MLP ? 4 : LB_STEP_MIN_BLOCKS);
 };
 
 template <class Cfg, bool IS3D, int SEED>
-__global__ void __launch_bounds__(kStepThreads, StepMinBlocks<Cfg>::value) step_kernel(const StepArgs<Cfg> A)
+__global__ void __launch_bounds__(kStepThreads, StepMinBlocks<Cfg, SEED>::value) step_kernel(const StepArgs<Cfg> A)
 {
     using R = typename Cfg::real;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -380,10 +382,18 @@ __global__ void __launch_bounds__(kStepThreads, StepMinBlocks<Cfg>::value) step_
     const unsigned fail = __reduce_add_sync(mask, ok ? 0u : 1u);
     const unsigned isum = __reduce_add_sync(mask, ok ? (unsigned)it : 0u);
     const unsigned imax = __reduce_max_sync(mask, ok ? (unsigned)it : 0u);
-    if ((threadIdx.x + threadIdx.y * blockDim.x) % 32 == (unsigned)(__ffs(mask) - 1)) {
+    const bool leader = (threadIdx.x + threadIdx.y * blockDim.x) % 32 == (unsigned)(__ffs(mask) - 1);
+    if (leader) {
         if (fail) atomicAdd(&A.stats[0], (unsigned long long)fail);
         atomicAdd(&A.stats[1], (unsigned long long)isum);
         atomicMax(&A.stats[2], (unsigned long long)imax);
+    }
+    // iteration histogram
+#pragma unroll
+    for (int b = 0; b < kHistBins; ++b) {
+        const bool in = ok && (b == kHistBins - 1 ? it >= kHistBins : it == b + 1);
+        const unsigned cnt = __popc(__ballot_sync(mask, in));
+        if (leader && cnt) atomicAdd(&A.stats[3 + b], (unsigned long long)cnt);
     }
 #endif
 }

@@ -21,7 +21,7 @@ FP64, FP32, FP16_DEV = 0, 1, 2
 RECOVERY_PLAIN, RECOVERY_MLP, RECOVERY_COLD = 0, 1, 2
 FLAG_NO_EM_COLLISION, FLAG_UNSHIFTED_POWER = 1, 2
 MLP_NPARAM, MLP_NFEAT, MLP_ROW = 9924, 20, 24
-NMOMENTS, NDIAG, NTABLE = 16, 10, 311
+NMOMENTS, NDIAG, NTABLE, NHIST = 16, 10, 311, 17
 MOMENT_NAMES = ["n", "p", "eps", "ux", "uy", "uz", "Ex", "Ey", "Ez", "Bx", "By", "Bz", "rho_c", "Jx", "Jy", "Jz"]
 DIAG_NAMES = ["N0", "T00", "T01", "T02", "T03", "rho_c", "divB_max", "divB_rms", "nonfinite", "cells"]
 
@@ -31,7 +31,7 @@ EXPORTED = [
     "lbrmhd_get_diagnostics", "lbrmhd_get_stats", "lbrmhd_state_bytes", "lbrmhd_get_state", "lbrmhd_set_state",
     "lbrmhd_run_cells", "lbrmhd_last_error", "lbrmhd_lattice_tables", "lbrmhd_get_diagnostics_noalloc",
     "lbrmhd_mlp_nparams", "lbrmhd_mlp_blob_bytes", "lbrmhd_mlp_pack", "lbrmhd_mlp_infer", "lbrmhd_mlp_grad",
-    "lbrmhd_mlp_train", "lbrmhd_set_mlp_weights", "lbrmhd_set_mlp_samples",
+    "lbrmhd_mlp_train", "lbrmhd_set_mlp_weights", "lbrmhd_set_mlp_samples", "lbrmhd_get_iteration_histogram",
 ]
 
 
@@ -114,6 +114,7 @@ def load(build_if_missing: bool = True):
         L.lbrmhd_mlp_train.argtypes = [vp, vp, vp, i64, C.c_int, C.c_int, C.c_float, C.c_uint64, vp, vp]
         L.lbrmhd_set_mlp_weights.argtypes = [vp, vp]
         L.lbrmhd_set_mlp_samples.argtypes = [vp, C.c_int, vp]
+        L.lbrmhd_get_iteration_histogram.argtypes = [vp, C.c_int, C.POINTER(i64)]
         _lib = L
         return L
 
@@ -298,6 +299,13 @@ class Solver:
         out = (C.c_int64 * 4)()
         self._check(self._L.lbrmhd_get_stats(self._h, run, out))
         return {"steps": out[0], "recover_fail": out[1], "iter_total": out[2], "iter_max": out[3]}
+
+    def iteration_histogram(self, run=0) -> np.ndarray:
+        """Recovery iteration counts since init: [k] = cell updates converged in
+        k + 1 iterations (last bin: NHIST or more)."""
+        out = (C.c_int64 * NHIST)()
+        self._check(self._L.lbrmhd_get_iteration_histogram(self._h, run, out))
+        return np.array(out[:], dtype=np.int64)
 
     def get_state(self) -> bytes:
         n = C.c_size_t()

@@ -249,3 +249,22 @@ def test_learned_seed_gain(trained, flags):
     rows = [3, 4, 5]
     d = np.linalg.norm(m_mlp[rows] - m_cold[rows]) / np.linalg.norm(m_cold[rows])
     assert d < 1e-4, d
+
+
+@pytest.mark.parametrize("recovery", [L.RECOVERY_PLAIN, L.RECOVERY_COLD])
+def test_iteration_histogram_matches_counters(recovery):
+    """The histogram counts every converged cell update once and, below its
+    overflow bin, reproduces the iteration sum and maximum."""
+    F = W.kelvin_helmholtz(96, 40, 1, V=0.2, ratio=10.0, B0=0.1, a=2.0, noise=1e-3, seed=8)
+    steps = 7
+    s = _solver(F, L.FP32, recovery, flags=L.FLAG_UNSHIFTED_POWER, sigma=1e3)
+    s.step(steps)
+    hist, st = s.iteration_histogram(0), s.stats(0)
+    s.close()
+    assert hist.sum() + st["recover_fail"] == steps * F.N
+    k = np.arange(1, L.NHIST + 1)
+    if hist[-1] == 0:
+        assert int((k * hist).sum()) == st["iter_total"]
+        assert int(k[hist > 0].max()) == st["iter_max"]
+    else:
+        assert int((k[:-1] * hist[:-1]).sum()) + L.NHIST * int(hist[-1]) <= st["iter_total"]
