@@ -16,7 +16,10 @@ The default arm also reports, under "learned_seed", the same workload with the
 recovery seeded by the learned network (trained on the GPU, before that leg's
 timed region, from samples of the method's own current-sheet and
 Kelvin-Helmholtz runs): its MLUPS and eigen-solve iterations per cell beside
-the plain path's, and both float32 arms' errors against the float64 GPU build.
+the plain path's, and both float32 arms' errors against the float64 GPU build;
+and, under "batched_sweep", the 64-run uneven-grid Kelvin-Helmholtz sweep in
+one handle: one launch per run per step against the autotuned schedule
+replayed from CUDA graphs.
 
 Prints one JSON line (rank 0).
 """
@@ -282,6 +285,54 @@ def learned_seed_leg(args, stream, plain_moments, plain_iters, steps_total):
     }
 
 
+def batched_sweep_leg(args, stream, steps=10):
+    """The batched sweep: 64 independent Kelvin-Helmholtz runs of uneven square
+    grids (sides 256..1024 step 128, sigma log-uniform [10, 1e4], V in [0.1,
+    0.5] c, density ratio {1, 3, 10}; seeded) in one handle, timed with one
+    launch per run per step on one stream, then with the autotuned schedule
+    replayed from CUDA graphs. Short horizon: sheared magnetised flows are
+    unstable in the scheme within a few hundred steps."""
+    import torch
+
+    from paper_1508_03452_gb300 import lbrmhd as L
+    from paper_1508_03452_gb300 import workloads as W
+
+    prec = {"fp32": L.FP32, "fp16": L.FP16_DEV, "fp64": L.FP64}[args.precision]
+    specs = W.kh_sweep(64)
+    solver = L.Solver([L.make_params(sp.nx, sp.ny, 1, sigma=sp.sigma, precision=prec) for sp in specs],
+                      stream=stream)
+    for r, sp in enumerate(specs):
+        F = W.kelvin_helmholtz(sp.nx, sp.ny, 1, V=sp.V, ratio=sp.ratio, B0=0.1, noise=1e-3, seed=sp.seed)
+        solver.init_fields(r, F.n, F.p, F.u, F.B)
+    cells = sum(sp.nx * sp.ny for sp in specs)
+
+    def timed(k):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solver.step(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    solver.step(3)
+    ms_plain = timed(steps)
+    best, tune_ms = solver.autotune(3)
+    graph_steps = 10
+    sched = L.make_schedule(best.kind, best.bx, best.waves, best.order, best.streams, graph_steps)
+    solver.set_schedule(sched)
+    solver.step(graph_steps)  # captures the graphs
+    ms_tuned = timed(steps)
+    fails = sum(solver.stats(r)["recover_fail"] for r in range(len(specs)))
+    solver.close()
+    return {
+        "workload": "kh_sweep_64_runs_sides_256_1024", "runs": len(specs), "cells_per_step": cells, "steps": steps,
+        "value": cells * steps / (ms_tuned * 1e-3) / 1e6, "unit": UNIT,
+        "per_run_one_stream_mlups": cells * steps / (ms_plain * 1e-3) / 1e6,
+        "schedule": sched.as_dict(), "autotune_ms_per_step": tune_ms, "recover_fail": fails,
+    }
+
+
 def run_gpu(args, world, rank, local):
     import numpy as np
     import torch
@@ -388,6 +439,8 @@ def run_gpu(args, world, rank, local):
         }
         if plain_moments is not None:
             line["learned_seed"] = learned_seed_leg(args, stream, plain_moments, plain_iters, steps_total)
+        if not args.no_sweep:
+            line["batched_sweep"] = batched_sweep_leg(args, stream)
         clocks = clk.summary()
         if clocks:
             line["clocks"] = clocks
@@ -425,6 +478,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned-seed", action="store_true", help="skip the learned-seed comparison leg")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the 64-run batched sweep leg")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--profile-case", action="store_true", help="untimed 1024^2 single-run case for ncu captures")
     args = ap.parse_args()

@@ -221,6 +221,48 @@ int64_t lbrmhd_run_cells(lbrmhd_handle h, int run);
 int lbrmhd_lattice_tables(double* out, size_t n);
 
 /* ------------------------------------------------------------------------
+ * Launch schedule of the runs of a handle. The paper runs one problem at a
+ * time; the schedule only decides how the same cell updates are grouped into
+ * kernel launches, so every schedule gives bit-identical results.
+ * ---------------------------------------------------------------------- */
+#define LBRMHD_SCHED_PER_RUN 0 /* one launch per run per step (a grid over the run's cells) */
+#define LBRMHD_SCHED_BATCH 1   /* one launch per step over the tiles of every run (per kernel variant:
+                                  2-D / 3-D runs, recovery seed) */
+
+typedef struct lbrmhd_schedule {
+    int32_t kind;        /* LBRMHD_SCHED_PER_RUN | LBRMHD_SCHED_BATCH */
+    int32_t bx;          /* BATCH: tile width 32 | 64 | 128 (a tile is bx x 128 / bx cells) */
+    int32_t waves;       /* BATCH: 0 = one block per tile; w > 0 = persistent grid of w waves of
+                            resident blocks, each block walking the tile list */
+    int32_t order;       /* BATCH: 0 = tiles run after run, 1 = tiles interleaved across runs */
+    int32_t streams;     /* PER_RUN: the runs are spread round-robin over this many streams of the
+                            handle (1..32; 1 = the handle's stream), so that kernels of different
+                            runs overlap; each run's steps stay in order on its stream */
+    int32_t graph_steps; /* > 0: lbrmhd_step replays a CUDA graph of this many steps (captured on
+                            first use on a stream of the handle, ordered after and before the
+                            handle's stream); 0: direct launches */
+} lbrmhd_schedule;
+
+/* Sets the schedule. Default (never set): PER_RUN, 1 stream, no graph.
+ * Errors: BAD_ARG. */
+int lbrmhd_set_schedule(lbrmhd_handle h, const lbrmhd_schedule* sched);
+int lbrmhd_get_schedule(lbrmhd_handle h, lbrmhd_schedule* sched);
+
+/* Autotuner: times PER_RUN on 1, 4 and up to 16 streams and every BATCH
+ * combination of bx {128, 64, 32}, waves {0, 1}, order {0, 1} on the
+ * handle's current state with `trials` dry
+ * steps each (steps whose output buffers are discarded: the state, the step
+ * counters and the recovery counters are left as they were; attached sample
+ * buffers are written), sets the fastest (keeping graph_steps) and returns
+ * it and its time per step in ms. When the environment variable
+ * LBRMHD_TUNE_CACHE names a file, a schedule stored there for the same batch
+ * (precision, grids, kernel variants) is taken without timing, and a newly
+ * tuned one is appended. Synchronises the handle's stream. Errors: BAD_ARG
+ * (trials outside 1..100), STATE (a run not initialised, a learned-seed run
+ * without weights), CUDA. */
+int lbrmhd_autotune(lbrmhd_handle h, int trials, lbrmhd_schedule* best, double* best_ms);
+
+/* ------------------------------------------------------------------------
  * Learned recovery seed. The paper has no counterpart: it fixes the
  * eigenproblem (Sec. III, coupling), not where its iteration starts. A
  * 20-64-64-64-4 ReLU network maps normalised moments of a cell to a guess of

@@ -2,8 +2,11 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
 #include <mutex>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -28,13 +31,14 @@ struct RunState {
     double Xr[3][3] = {}, Yr[3] = {};            // reference EM terms of the f deviations
     lb::RefPops refpops{};
     lb::HalfScale hs{};
-    unsigned long long* d_stats = nullptr;  // lb::kNumStats recovery counters
+    unsigned long long* d_stats = nullptr;  // lb::kStatSlots x lb::kNumStats recovery counters
     int64_t steps = 0;
     int periodic[3] = {1, 1, 1};
     float* d_samples = nullptr;  // caller-owned training-sample buffer (or NULL)
 };
 
-constexpr size_t kStatsBytes = lb::kNumStats * sizeof(unsigned long long);
+constexpr size_t kStatsBytes = lb::kNumStats * sizeof(unsigned long long);  // totals (checkpoint)
+constexpr size_t kStatsAlloc = (size_t)lb::kStatSlots * kStatsBytes;       // per-slot copies on the device
 
 size_t pop_bytes(int precision) { return precision == LBRMHD_FP64 ? 8 : (precision == LBRMHD_FP32 ? 4 : 2); }
 size_t hp_bytes(int precision) { return precision == LBRMHD_FP64 ? 8 : 4; }
@@ -55,6 +59,28 @@ struct lbrmhd_state_s {
     int* d_flag = nullptr;
     unsigned char* d_mlp = nullptr;  // packed network of the learned seed
     bool mlp_set = false;
+    // launch schedule (lbrmhd_set_schedule / lbrmhd_autotune)
+    lbrmhd_schedule sched{LBRMHD_SCHED_PER_RUN, 128, 0, 0, 1, 0};
+    // streams of the multi-stream per-run schedule, with their fork / join events
+    std::vector<cudaStream_t> aux;
+    std::vector<cudaEvent_t> aux_join;
+    cudaEvent_t ev_fork = nullptr;
+    // batched launches: per-run arguments for both input buffers, tile list
+    void* d_args = nullptr;       // 2 x runs StepArgs<Cfg> records (input buffer 0, then 1), 16-byte stride
+    bool args_dirty = true;
+    int4* d_tiles = nullptr;
+    size_t tiles_cap = 0;
+    struct Group {
+        bool is3d;
+        int seed, first, count;
+    };
+    std::vector<Group> groups;
+    bool tiles_dirty = true;
+    // CUDA graphs of graph_steps steps, one per starting input buffer
+    cudaStream_t cap_stream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int graph_len = 0;
 };
 
 #define LB_CK(call)                                                                        \
@@ -219,12 +245,25 @@ int ensure_io(lbrmhd_handle h, size_t bytes)
     return LBRMHD_OK;
 }
 
+int run_seed(const RunState& r)
+{
+    return r.p.recovery == LBRMHD_RECOVERY_MLP ? lb::SEED_MLP
+           : (r.p.recovery == LBRMHD_RECOVERY_COLD || r.d_samples) ? lb::SEED_COLD
+                                                                   : lb::SEED_PREV;
+}
+
+bool has_open(const RunState& r)
+{
+    return r.p.bc[0] || r.p.bc[1] || r.p.bc[2] || r.p.bc[3] || r.p.bc[4] || r.p.bc[5];
+}
+
+// kernel arguments of one run reading input buffer `in`
 template <class Cfg>
-int step_run(lbrmhd_handle h, RunState& r)
+lb::StepArgs<Cfg> make_args(lbrmhd_handle h, const RunState& r, int in)
 {
     using R = typename Cfg::real;
     lb::StepArgs<Cfg> A{};
-    const int in = r.cur, out = 1 - r.cur;
+    const int out = 1 - in;
     A.fin = (const typename Cfg::pop*)r.pops[in];
     A.gin = A.fin + 19 * r.stride;
     A.hin = (const typename Cfg::hpop*)r.h[in];
@@ -244,15 +283,250 @@ int step_run(lbrmhd_handle h, RunState& r)
     A.stats = r.d_stats;
     A.mlp = h->d_mlp;
     A.dump = r.d_samples;
-    A.seed = r.p.recovery == LBRMHD_RECOVERY_MLP ? lb::SEED_MLP
-             : (r.p.recovery == LBRMHD_RECOVERY_COLD || r.d_samples) ? lb::SEED_COLD
-                                                                     : lb::SEED_PREV;
-    LB_CK(lb::launch_step<Cfg>(A, h->stream));
-    const bool any_open = r.p.bc[0] || r.p.bc[1] || r.p.bc[2] || r.p.bc[3] || r.p.bc[4] || r.p.bc[5];
-    if (any_open)
-        LB_CK(lb::launch_boundaries<Cfg>(view<Cfg>(r, out), A.k, r.p.bc, r.p.drive_layers, r.p.drive_u0, h->stream));
-    r.cur = out;
-    r.steps += 1;
+    A.seed = run_seed(r);
+    return A;
+}
+
+lbrmhd_schedule effective_schedule(lbrmhd_handle h) { return h->sched; }
+
+// tile list of the batched schedule, grouped by kernel variant (2-D / 3-D,
+// recovery seed); within a group tiles follow the runs in order (order 0) or
+// are interleaved across runs (order 1)
+int build_tiles(lbrmhd_handle h, const lbrmhd_schedule& sc)
+{
+    const int bx = sc.bx, by = lb::kStepThreads / sc.bx;
+    std::vector<int4> all;
+    h->groups.clear();
+    for (int is3d = 0; is3d < 2; ++is3d)
+        for (int seed = 0; seed < 3; ++seed) {
+            std::vector<std::vector<int4>> per;
+            for (int ri = 0; ri < (int)h->runs.size(); ++ri) {
+                const RunState& r = h->runs[ri];
+                if ((r.p.nz > 1) != (is3d == 1) || run_seed(r) != seed) continue;
+                std::vector<int4> t;
+                for (int z = 0; z < r.p.nz; ++z)
+                    for (int y0 = 0; y0 < r.p.ny; y0 += by)
+                        for (int x0 = 0; x0 < r.p.nx; x0 += bx) t.push_back(make_int4(ri, x0, y0, z));
+                per.push_back(std::move(t));
+            }
+            if (per.empty()) continue;
+            const int first = (int)all.size();
+            if (sc.order == 0) {
+                for (auto& t : per) all.insert(all.end(), t.begin(), t.end());
+            } else {
+                size_t longest = 0;
+                for (auto& t : per) longest = std::max(longest, t.size());
+                for (size_t i = 0; i < longest; ++i)
+                    for (auto& t : per)
+                        if (i < t.size()) all.push_back(t[i]);
+            }
+            h->groups.push_back({is3d == 1, seed, first, (int)all.size() - first});
+        }
+    if (all.size() > (size_t)0x7fffffff) return fail(h, LBRMHD_ERR_BAD_ARG, "too many tiles for one launch");
+    if (all.size() > h->tiles_cap) {
+        if (h->d_tiles) cudaFree(h->d_tiles);
+        h->d_tiles = nullptr;
+        h->tiles_cap = 0;
+        if (cudaMalloc(&h->d_tiles, all.size() * sizeof(int4)) != cudaSuccess)
+            return fail(h, LBRMHD_ERR_OOM, "tile list allocation failed");
+        h->tiles_cap = all.size();
+    }
+    LB_CK(cudaMemcpy(h->d_tiles, all.data(), all.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    h->tiles_dirty = false;
+    return LBRMHD_OK;
+}
+
+template <class Cfg>
+int upload_args(lbrmhd_handle h)
+{
+    const size_t n = h->runs.size(), stride = lb::batch_args_stride<Cfg>();
+    std::vector<unsigned char> a(2 * n * stride, 0);
+    for (int in = 0; in < 2; ++in)
+        for (size_t ri = 0; ri < n; ++ri) {
+            const lb::StepArgs<Cfg> A = make_args<Cfg>(h, h->runs[ri], in);
+            std::memcpy(a.data() + (in * n + ri) * stride, &A, sizeof(A));
+        }
+    if (!h->d_args && cudaMalloc(&h->d_args, a.size()) != cudaSuccess) {
+        h->d_args = nullptr;
+        return fail(h, LBRMHD_ERR_OOM, "argument array allocation failed");
+    }
+    LB_CK(cudaMemcpy(h->d_args, a.data(), a.size(), cudaMemcpyHostToDevice));
+    h->args_dirty = false;
+    return LBRMHD_OK;
+}
+
+// everything a batched launch needs, refreshed when the runs or the schedule changed
+template <class Cfg>
+int prepare_batch(lbrmhd_handle h, const lbrmhd_schedule& sc)
+{
+    if (sc.kind != LBRMHD_SCHED_BATCH) return LBRMHD_OK;
+    int rc = LBRMHD_OK;
+    if (h->tiles_dirty) rc = build_tiles(h, sc);
+    if (!rc && h->args_dirty) rc = upload_args<Cfg>(h);
+    return rc;
+}
+
+// one time step of every run reading input buffer `in` (the same for all
+// runs), issued on stream `s`; the host state (cur, step counters) is not
+// touched, so a caller can also issue a dry step whose output is discarded
+template <class Cfg>
+int issue_step(lbrmhd_handle h, const lbrmhd_schedule& sc, int in, cudaStream_t s)
+{
+    using R = typename Cfg::real;
+    const int out = 1 - in;
+    if (sc.kind == LBRMHD_SCHED_BATCH) {
+        const unsigned char* args = (const unsigned char*)h->d_args + (size_t)in * h->runs.size() * lb::batch_args_stride<Cfg>();
+        int dev_sms = 0;
+        LB_CK(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, h->device));
+        for (const auto& g : h->groups) {
+            int grid = 0;  // one block per tile
+            if (sc.waves > 0) grid = sc.waves * dev_sms * std::max(1, lb::batch_blocks_per_sm<Cfg>(g.is3d, g.seed));
+            LB_CK(lb::launch_step_batch<Cfg>(args, h->d_tiles + g.first, g.count, sc.bx, grid, g.is3d, g.seed, s));
+        }
+    } else {
+        for (const auto& r : h->runs) LB_CK(lb::launch_step<Cfg>(make_args<Cfg>(h, r, in), s));
+    }
+    for (const auto& r : h->runs)
+        if (has_open(r))
+            LB_CK(lb::launch_boundaries<Cfg>(view<Cfg>(r, out), make_phys<R>(r.p, r.ref, runref(r)), r.p.bc,
+                                             r.p.drive_layers, r.p.drive_u0, s));
+    return LBRMHD_OK;
+}
+
+int ensure_aux(lbrmhd_handle h, int n)
+{
+    if (!h->ev_fork) LB_CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    while ((int)h->aux.size() < n) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        LB_CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        h->aux.push_back(st);
+        LB_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        h->aux_join.push_back(ev);
+    }
+    return LBRMHD_OK;
+}
+
+// n steps of every run from input buffer `in`, issued after and completed
+// before the work of stream `s` (host state untouched, as issue_step)
+template <class Cfg>
+int issue_steps(lbrmhd_handle h, const lbrmhd_schedule& sc, int in, int64_t n, cudaStream_t s)
+{
+    using R = typename Cfg::real;
+    const int S = sc.kind == LBRMHD_SCHED_PER_RUN ? std::min<int>(sc.streams, (int)h->runs.size()) : 1;
+    if (S <= 1) {
+        for (int64_t t = 0; t < n; ++t) {
+            const int rc = issue_step<Cfg>(h, sc, (int)((in + t) & 1), s);
+            if (rc) return rc;
+        }
+        return LBRMHD_OK;
+    }
+    int rc = ensure_aux(h, S);
+    if (rc) return rc;
+    LB_CK(cudaEventRecord(h->ev_fork, s));
+    for (int i = 0; i < S; ++i) LB_CK(cudaStreamWaitEvent(h->aux[i], h->ev_fork, 0));
+    for (int64_t t = 0; t < n; ++t) {
+        const int cin = (int)((in + t) & 1);
+        for (size_t ri = 0; ri < h->runs.size(); ++ri) {
+            const RunState& r = h->runs[ri];
+            cudaStream_t st = h->aux[ri % S];
+            LB_CK(lb::launch_step<Cfg>(make_args<Cfg>(h, r, cin), st));
+            if (has_open(r))
+                LB_CK(lb::launch_boundaries<Cfg>(view<Cfg>(r, 1 - cin), make_phys<R>(r.p, r.ref, runref(r)), r.p.bc,
+                                                 r.p.drive_layers, r.p.drive_u0, st));
+        }
+    }
+    for (int i = 0; i < S; ++i) {
+        LB_CK(cudaEventRecord(h->aux_join[i], h->aux[i]));
+        LB_CK(cudaStreamWaitEvent(s, h->aux_join[i], 0));
+    }
+    return LBRMHD_OK;
+}
+
+void drop_graphs(lbrmhd_handle h)
+{
+    for (auto& g : h->graph) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+    h->graph_len = 0;
+}
+
+// the runs' state changed (init, checkpoint, sample buffer): arguments and graphs are stale
+void runs_changed(lbrmhd_handle h)
+{
+    h->args_dirty = true;
+    h->tiles_dirty = true;  // a sample buffer can move a run to another kernel variant
+    drop_graphs(h);
+}
+
+template <class Cfg>
+int capture_graph(lbrmhd_handle h, const lbrmhd_schedule& sc, int in)
+{
+    if (!h->cap_stream) {
+        LB_CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+        LB_CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+        LB_CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+    }
+    for (const auto& g : h->groups) lb::batch_blocks_per_sm<Cfg>(g.is3d, g.seed);  // attributes set before capture
+    if (sc.kind == LBRMHD_SCHED_PER_RUN && sc.streams > 1) {
+        const int rc0 = ensure_aux(h, std::min<int>(sc.streams, (int)h->runs.size()));  // created outside the capture
+        if (rc0) return rc0;
+    }
+    LB_CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = issue_steps<Cfg>(h, sc, in, sc.graph_steps, h->cap_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(h, LBRMHD_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    const cudaError_t ei = cudaGraphInstantiate(&h->graph[in], g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+        h->graph[in] = nullptr;
+        return fail(h, LBRMHD_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+    }
+    h->graph_len = sc.graph_steps;
+    return LBRMHD_OK;
+}
+
+// n steps of every run; whole graphs first (when enabled), then direct launches
+template <class Cfg>
+int step_all(lbrmhd_handle h, int64_t n)
+{
+    const lbrmhd_schedule sc = effective_schedule(h);
+    int rc = prepare_batch<Cfg>(h, sc);
+    if (rc) return rc;
+    int in = h->runs[0].cur;
+    int64_t done = 0;
+    if (sc.graph_steps > 0 && n >= sc.graph_steps) {
+        if (h->graph_len != sc.graph_steps) drop_graphs(h);
+        if (!h->graph[in]) rc = capture_graph<Cfg>(h, sc, in);
+        if (rc) return rc;
+        LB_CK(cudaEventRecord(h->ev_in, h->stream));
+        LB_CK(cudaStreamWaitEvent(h->cap_stream, h->ev_in, 0));
+        for (; done + sc.graph_steps <= n; done += sc.graph_steps) {
+            if (!h->graph[in]) {
+                rc = capture_graph<Cfg>(h, sc, in);
+                if (rc) return rc;
+            }
+            LB_CK(cudaGraphLaunch(h->graph[in], h->cap_stream));
+            in = (in + sc.graph_steps) & 1;
+        }
+        LB_CK(cudaEventRecord(h->ev_out, h->cap_stream));
+        LB_CK(cudaStreamWaitEvent(h->stream, h->ev_out, 0));
+    }
+    if (done < n) {
+        rc = issue_steps<Cfg>(h, sc, in, n - done, h->stream);
+        if (rc) return rc;
+        in = (int)((in + (n - done)) & 1);
+    }
+    for (auto& r : h->runs) {
+        r.cur = in;
+        r.steps += n;
+    }
     return LBRMHD_OK;
 }
 
@@ -268,18 +542,13 @@ int init_run(lbrmhd_handle h, RunState& r, const lb::InitInputs& in)
     LB_CK(lb::launch_init<Cfg>(view<Cfg>(r, r.cur), in, make_phys<double>(r.p, r.ref, runref(r)), h->d_flag, h->stream));
     int bad = 0;
     LB_CK(cudaMemcpyAsync(&bad, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    LB_CK(cudaMemsetAsync(r.d_stats, 0, lb::kNumStats * sizeof(unsigned long long), h->stream));
+    LB_CK(cudaMemsetAsync(r.d_stats, 0, kStatsAlloc, h->stream));
     LB_CK(cudaStreamSynchronize(h->stream));
     if (bad) return fail(h, LBRMHD_ERR_BAD_ARG, "initial state has |u| >= c or n <= 0");
     r.initialized = true;
+    runs_changed(h);
     r.steps = 0;
     return LBRMHD_OK;
-}
-
-template <class Cfg>
-int dispatch_step(lbrmhd_handle h, RunState& r)
-{
-    return step_run<Cfg>(h, r);
 }
 
 int init_common(lbrmhd_handle h, int run, const double* n, const double* p, const double* u, const double* B,
@@ -370,6 +639,146 @@ int noalloc_scratch(lbrmhd_handle h, double** out)
     return LBRMHD_OK;
 }
 
+// totals of the per-slot recovery counters of one run (synchronises the stream)
+int read_stats(lbrmhd_handle h, const RunState& r, unsigned long long* tot)
+{
+    std::vector<unsigned long long> all((size_t)lb::kStatSlots * lb::kNumStats);
+    LB_CK(cudaMemcpyAsync(all.data(), r.d_stats, kStatsAlloc, cudaMemcpyDeviceToHost, h->stream));
+    LB_CK(cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < lb::kNumStats; ++i) tot[i] = 0;
+    for (int sl = 0; sl < lb::kStatSlots; ++sl) {
+        const unsigned long long* v = all.data() + (size_t)sl * lb::kNumStats;
+        for (int i = 0; i < lb::kNumStats; ++i) tot[i] = i == 2 ? std::max(tot[i], v[i]) : tot[i] + v[i];
+    }
+    return LBRMHD_OK;
+}
+
+// writes checkpointed totals back: slot 0 holds them, the other slots zero
+int write_stats(lbrmhd_handle h, const RunState& r, const unsigned long long* tot)
+{
+    LB_CK(cudaMemsetAsync(r.d_stats, 0, kStatsAlloc, h->stream));
+    LB_CK(cudaMemcpyAsync(r.d_stats, tot, kStatsBytes, cudaMemcpyHostToDevice, h->stream));
+    LB_CK(cudaStreamSynchronize(h->stream));
+    return LBRMHD_OK;
+}
+
+std::string check_schedule(const lbrmhd_schedule& s)
+{
+    if (s.kind != LBRMHD_SCHED_PER_RUN && s.kind != LBRMHD_SCHED_BATCH) return "unknown schedule kind";
+    if (s.bx != 32 && s.bx != 64 && s.bx != 128) return "tile width must be 32, 64 or 128";
+    if (s.waves < 0 || s.waves > 8) return "waves must be in 0..8";
+    if (s.order != 0 && s.order != 1) return "order must be 0 or 1";
+    if (s.streams < 1 || s.streams > 32) return "streams must be in 1..32";
+    if (s.graph_steps < 0 || s.graph_steps > 4096) return "graph_steps must be in 0..4096";
+    return "";
+}
+
+// key of a batch for the autotuner cache: precision and, per run, the grid
+// and the kernel variant
+std::string batch_signature(lbrmhd_handle h)
+{
+    std::ostringstream o;
+    o << "p" << h->precision;
+    for (const auto& r : h->runs)
+        o << "_" << r.p.nx << "x" << r.p.ny << "x" << r.p.nz << "s" << run_seed(r) << (has_open(r) ? "o" : "");
+    return o.str();
+}
+
+bool cache_lookup(const std::string& path, const std::string& sig, lbrmhd_schedule* sc, double* ms)
+{
+    std::ifstream f(path);
+    std::string line;
+    bool found = false;
+    while (std::getline(f, line)) {  // the last entry of a signature wins
+        std::istringstream in(line);
+        std::string key;
+        lbrmhd_schedule c{};
+        double t = 0;
+        if (in >> key >> c.kind >> c.bx >> c.waves >> c.order >> c.streams >> t && key == sig &&
+            check_schedule(c).empty()) {
+            *sc = c;
+            *ms = t;
+            found = true;
+        }
+    }
+    return found;
+}
+
+template <class Cfg>
+int autotune(lbrmhd_handle h, int trials, lbrmhd_schedule* best_out, double* best_ms_out)
+{
+    for (auto& r : h->runs) {
+        if (!r.initialized) return fail(h, LBRMHD_ERR_STATE, "autotune before lbrmhd_init_fields");
+        if (r.p.recovery == LBRMHD_RECOVERY_MLP && !h->mlp_set)
+            return fail(h, LBRMHD_ERR_STATE, "learned-seed run without weights (lbrmhd_set_mlp_weights)");
+        if (r.cur != h->runs[0].cur) return fail(h, LBRMHD_ERR_STATE, "runs out of step");
+    }
+    const lbrmhd_schedule cur = effective_schedule(h);
+    const char* cache = std::getenv("LBRMHD_TUNE_CACHE");
+    const std::string sig = batch_signature(h);
+    lbrmhd_schedule best = cur;
+    double best_ms = -1.0;
+    if (!(cache && *cache && cache_lookup(cache, sig, &best, &best_ms))) {
+        std::vector<lbrmhd_schedule> cand;
+        const int nr = (int)h->runs.size();
+        cand.push_back({LBRMHD_SCHED_PER_RUN, 128, 0, 0, 1, 0});
+        if (nr > 1) cand.push_back({LBRMHD_SCHED_PER_RUN, 128, 0, 0, std::min(nr, 4), 0});
+        if (nr > 4) cand.push_back({LBRMHD_SCHED_PER_RUN, 128, 0, 0, std::min(nr, 16), 0});
+        for (int bx : {128, 64, 32})
+            for (int waves : {0, 1})
+                for (int order : {0, 1})
+                    if (nr > 1 || order == 0) cand.push_back({LBRMHD_SCHED_BATCH, bx, waves, order, 1, 0});
+        // the counters are restored afterwards: dry steps only write the
+        // scratch (output) buffers
+        std::vector<std::vector<unsigned long long>> saved(h->runs.size(),
+                                                           std::vector<unsigned long long>(lb::kNumStats));
+        for (size_t i = 0; i < h->runs.size(); ++i) {
+            const int rc = read_stats(h, h->runs[i], saved[i].data());
+            if (rc) return rc;
+        }
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        LB_CK(cudaEventCreate(&e0));
+        LB_CK(cudaEventCreate(&e1));
+        const int in = h->runs[0].cur;
+        int rc = LBRMHD_OK;
+        for (const auto& c : cand) {
+            h->tiles_dirty = true;
+            rc = prepare_batch<Cfg>(h, c);
+            if (!rc) rc = issue_steps<Cfg>(h, c, in, 1, h->stream);  // warm-up (dry: the state stays at `in`)
+            if (rc) break;
+            if (cudaEventRecord(e0, h->stream) != cudaSuccess) rc = fail(h, LBRMHD_ERR_CUDA, "event record");
+            for (int t = 0; t < trials && !rc; ++t) rc = issue_steps<Cfg>(h, c, in, 1, h->stream);
+            if (!rc && cudaEventRecord(e1, h->stream) != cudaSuccess) rc = fail(h, LBRMHD_ERR_CUDA, "event record");
+            if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = fail(h, LBRMHD_ERR_CUDA, "autotune step failed");
+            if (rc) break;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            const double per = ms / trials;
+            if (best_ms < 0 || per < best_ms) {
+                best_ms = per;
+                best = c;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        for (size_t i = 0; i < h->runs.size() && !rc; ++i) rc = write_stats(h, h->runs[i], saved[i].data());
+        if (rc) return rc;
+        if (cache && *cache) {
+            std::ofstream f(cache, std::ios::app);
+            f << sig << " " << best.kind << " " << best.bx << " " << best.waves << " " << best.order << " "
+              << best.streams << " " << best_ms
+              << "\n";
+        }
+    }
+    best.graph_steps = cur.graph_steps;
+    h->sched = best;
+    h->tiles_dirty = true;
+    drop_graphs(h);
+    if (best_out) *best_out = best;
+    if (best_ms_out) *best_ms_out = best_ms;
+    return LBRMHD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -419,8 +828,8 @@ int lbrmhd_create(const lbrmhd_params* params, int n_runs, lbrmhd_handle* out)
                 cudaMemset(s.prim[b], 0, lb::NPRIM * s.stride * qb);
             }
         }
-        ok = ok && cudaMalloc(&s.d_stats, lb::kNumStats * sizeof(unsigned long long)) == cudaSuccess;
-        if (ok) cudaMemset(s.d_stats, 0, lb::kNumStats * sizeof(unsigned long long));
+        ok = ok && cudaMalloc(&s.d_stats, kStatsAlloc) == cudaSuccess;
+        if (ok) cudaMemset(s.d_stats, 0, kStatsAlloc);
         max_blocks = std::max<int64_t>(max_blocks, (s.N + lb::kDiagThreads - 1) / lb::kDiagThreads);
     }
     const size_t scratch = std::max<size_t>((size_t)max_blocks * lb::NPART, (size_t)lb::kMeansBlocks * lb::NMEANS);
@@ -460,6 +869,15 @@ int lbrmhd_destroy(lbrmhd_handle h)
     if (h->d_small) cudaFree(h->d_small);
     if (h->d_flag) cudaFree(h->d_flag);
     if (h->d_mlp) cudaFree(h->d_mlp);
+    drop_graphs(h);
+    if (h->d_args) cudaFree(h->d_args);
+    if (h->d_tiles) cudaFree(h->d_tiles);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
+    for (auto st : h->aux) cudaStreamDestroy(st);
+    for (auto ev : h->aux_join) cudaEventDestroy(ev);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     delete h;
     return LBRMHD_OK;
 }
@@ -492,19 +910,15 @@ int lbrmhd_step(lbrmhd_handle h, int64_t nsteps)
         if (r.p.recovery == LBRMHD_RECOVERY_MLP && !h->mlp_set)
             return fail(h, LBRMHD_ERR_STATE, "learned-seed run without weights (lbrmhd_set_mlp_weights)");
     }
+    for (auto& r : h->runs)
+        if (r.cur != h->runs[0].cur) return fail(h, LBRMHD_ERR_STATE, "runs out of step");
+    if (nsteps == 0) return LBRMHD_OK;
     LB_CK(cudaSetDevice(h->device));
-    for (int64_t t = 0; t < nsteps; ++t) {
-        for (auto& r : h->runs) {
-            int rc;
-            switch (h->precision) {
-                case LBRMHD_FP64: rc = dispatch_step<lb::CfgF64>(h, r); break;
-                case LBRMHD_FP32: rc = dispatch_step<lb::CfgF32>(h, r); break;
-                default: rc = dispatch_step<lb::CfgF16>(h, r); break;
-            }
-            if (rc) return rc;
-        }
+    switch (h->precision) {
+        case LBRMHD_FP64: return step_all<lb::CfgF64>(h, nsteps);
+        case LBRMHD_FP32: return step_all<lb::CfgF32>(h, nsteps);
+        default: return step_all<lb::CfgF16>(h, nsteps);
     }
-    return LBRMHD_OK;
 }
 
 int lbrmhd_get_moments_device(lbrmhd_handle h, int run, double* out)
@@ -630,9 +1044,9 @@ int lbrmhd_get_stats(lbrmhd_handle h, int run, int64_t* out4)
     if (bad_run(h, run) || !out4) return h ? fail(h, LBRMHD_ERR_BAD_ARG, "bad run or NULL output") : LBRMHD_ERR_BAD_ARG;
     RunState& r = h->runs[run];
     LB_CK(cudaSetDevice(h->device));
-    unsigned long long s[3];
-    LB_CK(cudaMemcpyAsync(s, r.d_stats, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
-    LB_CK(cudaStreamSynchronize(h->stream));
+    unsigned long long s[lb::kNumStats];
+    const int rc = read_stats(h, r, s);
+    if (rc) return rc;
     out4[0] = r.steps;
     out4[1] = (int64_t)s[0];
     out4[2] = (int64_t)s[1];
@@ -646,8 +1060,8 @@ int lbrmhd_get_iteration_histogram(lbrmhd_handle h, int run, int64_t* out)
     RunState& r = h->runs[run];
     LB_CK(cudaSetDevice(h->device));
     unsigned long long s[lb::kNumStats];
-    LB_CK(cudaMemcpyAsync(s, r.d_stats, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
-    LB_CK(cudaStreamSynchronize(h->stream));
+    const int rc = read_stats(h, r, s);
+    if (rc) return rc;
     for (int b = 0; b < lb::kHistBins; ++b) out[b] = (int64_t)s[3 + b];
     return LBRMHD_OK;
 }
@@ -678,7 +1092,10 @@ int lbrmhd_get_state(lbrmhd_handle h, void* host_buf, size_t bytes)
         o += 8;
         std::memcpy(o, r.means, 8 * lb::NMEANS);
         o += 8 * lb::NMEANS;
-        LB_CK(cudaMemcpyAsync(o, r.d_stats, kStatsBytes, cudaMemcpyDeviceToHost, h->stream));
+        unsigned long long tot[lb::kNumStats];
+        const int rc = read_stats(h, r, tot);
+        if (rc) return rc;
+        std::memcpy(o, tot, kStatsBytes);
         o += kStatsBytes;
         for (int pl = 0; pl < 38; ++pl, o += r.N * pb)
             LB_CK(cudaMemcpyAsync(o, (char*)r.pops[r.cur] + pl * r.stride * pb, r.N * pb, cudaMemcpyDeviceToHost,
@@ -709,7 +1126,10 @@ int lbrmhd_set_state(lbrmhd_handle h, const void* host_buf, size_t bytes)
         std::memcpy(means, o, 8 * lb::NMEANS);
         o += 8 * lb::NMEANS;
         set_reference(r, means);
-        LB_CK(cudaMemcpyAsync(r.d_stats, o, kStatsBytes, cudaMemcpyHostToDevice, h->stream));
+        unsigned long long tot[lb::kNumStats];
+        std::memcpy(tot, o, kStatsBytes);
+        const int rc = write_stats(h, r, tot);
+        if (rc) return rc;
         o += kStatsBytes;
         for (int pl = 0; pl < 38; ++pl, o += r.N * pb)
             LB_CK(cudaMemcpyAsync((char*)r.pops[r.cur] + pl * r.stride * pb, o, r.N * pb, cudaMemcpyHostToDevice,
@@ -721,6 +1141,7 @@ int lbrmhd_set_state(lbrmhd_handle h, const void* host_buf, size_t bytes)
             LB_CK(cudaMemcpyAsync((char*)r.prim[r.cur] + pl * r.stride * hb, o, r.N * hb, cudaMemcpyHostToDevice,
                                   h->stream));
         r.initialized = true;
+        runs_changed(h);
     }
     LB_CK(cudaStreamSynchronize(h->stream));
     return LBRMHD_OK;
@@ -744,6 +1165,7 @@ int lbrmhd_set_mlp_weights(lbrmhd_handle h, const float* d_params)
     const int rc = lbrmhd_mlp_pack(d_params, h->d_mlp, h->stream);
     if (rc) return fail(h, rc, "packing the network failed");
     h->mlp_set = true;
+    runs_changed(h);  // the kernel arguments carry the blob pointer
     return LBRMHD_OK;
 }
 
@@ -751,7 +1173,39 @@ int lbrmhd_set_mlp_samples(lbrmhd_handle h, int run, float* d_samples)
 {
     if (bad_run(h, run)) return h ? fail(h, LBRMHD_ERR_BAD_ARG, "run out of range") : LBRMHD_ERR_BAD_ARG;
     h->runs[run].d_samples = d_samples;
+    runs_changed(h);
     return LBRMHD_OK;
+}
+
+int lbrmhd_set_schedule(lbrmhd_handle h, const lbrmhd_schedule* sched)
+{
+    if (!h) return LBRMHD_ERR_BAD_ARG;
+    if (!sched) return fail(h, LBRMHD_ERR_BAD_ARG, "NULL schedule");
+    const std::string m = check_schedule(*sched);
+    if (!m.empty()) return fail(h, LBRMHD_ERR_BAD_ARG, m);
+    h->sched = *sched;
+    h->tiles_dirty = true;
+    drop_graphs(h);
+    return LBRMHD_OK;
+}
+
+int lbrmhd_get_schedule(lbrmhd_handle h, lbrmhd_schedule* sched)
+{
+    if (!h || !sched) return h ? fail(h, LBRMHD_ERR_BAD_ARG, "NULL schedule") : LBRMHD_ERR_BAD_ARG;
+    *sched = effective_schedule(h);
+    return LBRMHD_OK;
+}
+
+int lbrmhd_autotune(lbrmhd_handle h, int trials, lbrmhd_schedule* best, double* best_ms)
+{
+    if (!h) return LBRMHD_ERR_BAD_ARG;
+    if (trials < 1 || trials > 100) return fail(h, LBRMHD_ERR_BAD_ARG, "trials must be in 1..100");
+    LB_CK(cudaSetDevice(h->device));
+    switch (h->precision) {
+        case LBRMHD_FP64: return autotune<lb::CfgF64>(h, trials, best, best_ms);
+        case LBRMHD_FP32: return autotune<lb::CfgF32>(h, trials, best, best_ms);
+        default: return autotune<lb::CfgF16>(h, trials, best, best_ms);
+    }
 }
 
 const char* lbrmhd_last_error(lbrmhd_handle h)

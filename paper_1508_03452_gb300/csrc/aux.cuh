@@ -67,6 +67,17 @@ __device__ __forceinline__ void block_reduce_partials(double* v, double* dst)
 template <class Cfg>
 cudaError_t launch_step(const StepArgs<Cfg>& A, cudaStream_t stream);
 template <class Cfg>
+cudaError_t launch_step_batch(const unsigned char* d_args, const int4* d_tiles, int ntiles, int bx, int grid,
+                              bool is3d, int seed, cudaStream_t stream);
+template <class Cfg>
+int batch_blocks_per_sm(bool is3d, int seed);
+// device stride of the per-run argument records of the batched kernel
+template <class Cfg>
+constexpr size_t batch_args_stride()
+{
+    return (sizeof(StepArgs<Cfg>) + 15) / 16 * 16;
+}
+template <class Cfg>
 cudaError_t launch_init(const PopView<Cfg>& V, const InitInputs& in, const Phys<double>& k, int* bad, cudaStream_t s);
 cudaError_t launch_means(const InitInputs& in, int64_t N, double* partial, double* out, cudaStream_t s);
 template <class Cfg>

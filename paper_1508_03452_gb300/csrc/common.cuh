@@ -43,6 +43,12 @@ enum { P_N = 0, P_EPS = 1, P_U = 2, P_E = 5, P_B = 8, P_RHO = 11, NPRIM = 12 };
 // iterations, and in kHistBins or more
 constexpr int kHistBins = 17;
 constexpr int kNumStats = 3 + kHistBins;
+// the counters are kept in kStatSlots copies (slot = block index mod
+// kStatSlots) so that the warps' atomics do not all meet on one address; the
+// host sums the copies (maximum for [2])
+constexpr int kStatSlots = 128;
+
+constexpr int kStepThreads = 128;  // threads (cells) per block of the step kernels
 
 constexpr int FLAG_NO_EM_COLLISION = 1;
 constexpr int FLAG_UNSHIFTED_POWER = 2;
@@ -74,7 +80,7 @@ struct StepArgs {
     int flags;
     Phys<real> k;
     HalfScale hs;
-    unsigned long long* stats;  // kNumStats counters (see kHistBins)
+    unsigned long long* stats;  // kStatSlots x kNumStats counters (see kHistBins)
     const unsigned char* mlp;   // device inference blob of the learned seed (SEED_MLP)
     float* dump;                // optional: per cell 20 features + 4 targets of the learned seed
     int seed;                   // SEED_PREV | SEED_MLP | SEED_COLD

@@ -3,4 +3,7 @@
 
 namespace lb {
 template cudaError_t launch_step<CfgF32>(const StepArgs<CfgF32>&, cudaStream_t);
+template cudaError_t launch_step_batch<CfgF32>(const unsigned char*, const int4*, int, int, int, bool, int,
+                                                  cudaStream_t);
+template int batch_blocks_per_sm<CfgF32>(bool, int);
 }  // namespace lb

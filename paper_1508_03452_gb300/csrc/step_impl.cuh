@@ -193,7 +193,6 @@ struct CollideH<24, Cfg> {
                                                const R*, bool) {}
 };
 
-constexpr int kStepThreads = 128;
 constexpr int kStepSlots = 63;  // 19 f + 19 g + 25 h pre-collision values per cell in shared memory
 #ifndef LB_STEP_MIN_BLOCKS
 #define LB_STEP_MIN_BLOCKS 5  // resident 128-thread blocks per SM targeted for float32 arithmetic (96 registers)
@@ -208,20 +207,20 @@ struct StepMinBlocks {
     static constexpr int value = sizeof(typename Cfg::real) == 8 ? 2 : (SEED == SEED_MLP ? 4 : LB_STEP_MIN_BLOCKS);
 };
 
+// One cell update (x, y, z) of one run; `tid` is the thread's index in its
+// block of `nth` threads (its rows of the shared-memory buffers). Threads of
+// cells outside the grid return at once, except in the learned-seed variant,
+// whose warp-wide MMA needs all 32 lanes: there they work on a clamped cell
+// and store nothing.
 template <class Cfg, bool IS3D, int SEED>
-__global__ void __launch_bounds__(kStepThreads, StepMinBlocks<Cfg, SEED>::value) step_kernel(const StepArgs<Cfg> A)
+__device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, const int z, const int tid,
+                                          const int nth, unsigned char* smem_raw)
 {
     using R = typename Cfg::real;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nth = blockDim.x * blockDim.y;
-    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     R* sp = reinterpret_cast<R*>(smem_raw) + tid;
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
     const bool active = x < A.nx && y < A.ny;
     if constexpr (SEED != SEED_MLP) {
-        if (!active) return;  // the kernel has no block-wide barrier
+        if (!active) return;  // no block-wide barrier follows
     } else {
         // the warp-wide tensor-core MMA of the learned seed needs every lane:
         // out-of-range lanes work on a clamped cell and store nothing
@@ -383,41 +382,167 @@ __global__ void __launch_bounds__(kStepThreads, StepMinBlocks<Cfg, SEED>::value)
     const unsigned isum = __reduce_add_sync(mask, ok ? (unsigned)it : 0u);
     const unsigned imax = __reduce_max_sync(mask, ok ? (unsigned)it : 0u);
     const bool leader = (threadIdx.x + threadIdx.y * blockDim.x) % 32 == (unsigned)(__ffs(mask) - 1);
+    const unsigned slot = (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)) % kStatSlots;
+    unsigned long long* st = A.stats + (size_t)slot * kNumStats;
     if (leader) {
-        if (fail) atomicAdd(&A.stats[0], (unsigned long long)fail);
-        atomicAdd(&A.stats[1], (unsigned long long)isum);
-        atomicMax(&A.stats[2], (unsigned long long)imax);
+        if (fail) atomicAdd(&st[0], (unsigned long long)fail);
+        atomicAdd(&st[1], (unsigned long long)isum);
+        atomicMax(&st[2], (unsigned long long)imax);
     }
-    // iteration histogram
-#pragma unroll
-    for (int b = 0; b < kHistBins; ++b) {
-        const bool in = ok && (b == kHistBins - 1 ? it >= kHistBins : it == b + 1);
-        const unsigned cnt = __popc(__ballot_sync(mask, in));
-        if (leader && cnt) atomicAdd(&A.stats[3 + b], (unsigned long long)cnt);
+    // iteration histogram over the warp's own range of counts (usually 1-2 bins)
+    const unsigned ib = ok ? (unsigned)(it < kHistBins ? it : kHistBins) : 0u;
+    const unsigned bmin = __reduce_min_sync(mask, ok ? ib : 0xffffffffu);
+    const unsigned bmax = __reduce_max_sync(mask, ib);
+    for (unsigned b = bmin; b <= bmax; ++b) {
+        const unsigned cnt = __popc(__ballot_sync(mask, ib == b));
+        if (leader && cnt) atomicAdd(&st[2 + b], (unsigned long long)cnt);
     }
 #endif
+}
+
+// one run: a 2-D grid of blocks over (x, y) and z
+template <class Cfg, bool IS3D, int SEED>
+__global__ void __launch_bounds__(kStepThreads, StepMinBlocks<Cfg, SEED>::value) step_kernel(const StepArgs<Cfg> A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    step_cell<Cfg, IS3D, SEED>(A, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y,
+                               blockIdx.z, threadIdx.x + threadIdx.y * blockDim.x, blockDim.x * blockDim.y, smem_raw);
+}
+
+template <class Cfg>
+__host__ __device__ constexpr size_t step_cell_smem(int seed)
+{
+    return seed == SEED_MLP ? (size_t)kStepSlots * sizeof(typename Cfg::real) * kStepThreads +
+                                  (size_t)(MLP_ACT_BYTES_PER_CELL + 8 * sizeof(float)) * kStepThreads
+                            : (size_t)kStepSlots * sizeof(typename Cfg::real) * kStepThreads;
+}
+
+// the batched kernel keeps the arguments of its current run in shared memory,
+// after the per-cell buffers; in device memory they are stored with this
+// (16-byte) stride
+template <class Cfg>
+__host__ __device__ constexpr size_t batch_args_bytes()
+{
+    return (sizeof(StepArgs<Cfg>) + 15) / 16 * 16;
+}
+
+// Many runs in one launch: a list of tiles (run, x0, y0, z) of bx x
+// (kStepThreads / bx) cells each, walked by the blocks with stride gridDim.x
+// (persistent when the grid is one wave of resident blocks). A block copies
+// the arguments of a tile's run from device memory into shared memory when
+// the run changes from its previous tile.
+template <class Cfg, bool IS3D, int SEED>
+__global__ void __launch_bounds__(kStepThreads, StepMinBlocks<Cfg, SEED>::value)
+    step_batch_kernel(const unsigned char* __restrict__ args, const int4* __restrict__ tiles, int ntiles, int bx)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    StepArgs<Cfg>* sA = reinterpret_cast<StepArgs<Cfg>*>(smem_raw + step_cell_smem<Cfg>(SEED));
+    const int tid = threadIdx.x;
+    const int tx = tid % bx, ty = tid / bx;
+    int run = -1;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int4 td = __ldg(tiles + t);  // block-uniform
+        if (td.x != run) {
+            __syncthreads();  // the previous tile's readers are done
+            const int4* src = reinterpret_cast<const int4*>(args + (size_t)td.x * batch_args_bytes<Cfg>());
+            int4* dst = reinterpret_cast<int4*>(sA);
+            for (int i = tid; i < (int)(batch_args_bytes<Cfg>() / 16); i += kStepThreads) dst[i] = __ldg(src + i);
+            __syncthreads();
+            run = td.x;
+        }
+        __syncwarp();  // every lane starts a tile together (the learned seed's MMA)
+        step_cell<Cfg, IS3D, SEED>(*sA, td.y + tx, td.z + ty, td.w, tid, kStepThreads, smem_raw);
+    }
+}
+
+template <class Cfg>
+size_t step_smem_bytes(int seed)
+{
+    return step_cell_smem<Cfg>(seed);
+}
+
+template <class Cfg>
+size_t batch_smem_bytes(int seed)
+{
+    return step_cell_smem<Cfg>(seed) + batch_args_bytes<Cfg>();
+}
+
+template <class Cfg>
+cudaError_t configure_step_kernels()
+{
+    static bool configured = false;  // one attribute call per instantiation
+    if (configured) return cudaSuccess;
+    const int b = (int)step_smem_bytes<Cfg>(SEED_PREV), m = (int)step_smem_bytes<Cfg>(SEED_MLP);
+    const int bb = (int)batch_smem_bytes<Cfg>(SEED_PREV), bm = (int)batch_smem_bytes<Cfg>(SEED_MLP);
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<Cfg, true, SEED_PREV>, a, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<Cfg, false, SEED_PREV>, a, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<Cfg, true, SEED_COLD>, a, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<Cfg, false, SEED_COLD>, a, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<Cfg, true, SEED_MLP>, a, m);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<Cfg, false, SEED_MLP>, a, m);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_batch_kernel<Cfg, true, SEED_PREV>, a, bb);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_batch_kernel<Cfg, false, SEED_PREV>, a, bb);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_batch_kernel<Cfg, true, SEED_COLD>, a, bb);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_batch_kernel<Cfg, false, SEED_COLD>, a, bb);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_batch_kernel<Cfg, true, SEED_MLP>, a, bm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_batch_kernel<Cfg, false, SEED_MLP>, a, bm);
+    if (e == cudaSuccess) configured = true;
+    return e;
+}
+
+// resident blocks per SM of the batched kernel (for a one-wave persistent grid)
+template <class Cfg>
+int batch_blocks_per_sm(bool is3d, int seed)
+{
+    cudaError_t e = configure_step_kernels<Cfg>();
+    if (e != cudaSuccess) return 0;
+    int nb = 0;
+    const size_t smem = batch_smem_bytes<Cfg>(seed);
+    if (seed == SEED_MLP)
+        e = is3d ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_batch_kernel<Cfg, true, SEED_MLP>, kStepThreads, smem)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_batch_kernel<Cfg, false, SEED_MLP>, kStepThreads, smem);
+    else if (seed == SEED_COLD)
+        e = is3d ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_batch_kernel<Cfg, true, SEED_COLD>, kStepThreads, smem)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_batch_kernel<Cfg, false, SEED_COLD>, kStepThreads, smem);
+    else
+        e = is3d ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_batch_kernel<Cfg, true, SEED_PREV>, kStepThreads, smem)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_batch_kernel<Cfg, false, SEED_PREV>, kStepThreads, smem);
+    return e == cudaSuccess ? nb : 0;
+}
+
+template <class Cfg>
+cudaError_t launch_step_batch(const unsigned char* d_args, const int4* d_tiles, int ntiles, int bx, int grid,
+                              bool is3d, int seed, cudaStream_t stream)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    if (bx != 32 && bx != 64 && bx != 128) return cudaErrorInvalidValue;
+    cudaError_t e = configure_step_kernels<Cfg>();
+    if (e != cudaSuccess) return e;
+    const size_t smem = batch_smem_bytes<Cfg>(seed);
+    const int g = grid > 0 && grid < ntiles ? grid : ntiles;
+    if (seed == SEED_MLP) {
+        if (is3d) step_batch_kernel<Cfg, true, SEED_MLP><<<g, kStepThreads, smem, stream>>>(d_args, d_tiles, ntiles, bx);
+        else step_batch_kernel<Cfg, false, SEED_MLP><<<g, kStepThreads, smem, stream>>>(d_args, d_tiles, ntiles, bx);
+    } else if (seed == SEED_COLD) {
+        if (is3d) step_batch_kernel<Cfg, true, SEED_COLD><<<g, kStepThreads, smem, stream>>>(d_args, d_tiles, ntiles, bx);
+        else step_batch_kernel<Cfg, false, SEED_COLD><<<g, kStepThreads, smem, stream>>>(d_args, d_tiles, ntiles, bx);
+    } else {
+        if (is3d) step_batch_kernel<Cfg, true, SEED_PREV><<<g, kStepThreads, smem, stream>>>(d_args, d_tiles, ntiles, bx);
+        else step_batch_kernel<Cfg, false, SEED_PREV><<<g, kStepThreads, smem, stream>>>(d_args, d_tiles, ntiles, bx);
+    }
+    return cudaGetLastError();
 }
 
 template <class Cfg>
 cudaError_t launch_step(const StepArgs<Cfg>& A, cudaStream_t stream)
 {
-    using R = typename Cfg::real;
     const int bx = A.nx >= LB_STEP_BX ? LB_STEP_BX : (A.nx >= 64 ? 64 : 32);
     const int by = kStepThreads / bx;
-    const size_t smem_base = (size_t)kStepSlots * sizeof(R) * kStepThreads;
-    const size_t smem_mlp = smem_base + (size_t)(MLP_ACT_BYTES_PER_CELL + 8 * sizeof(float)) * kStepThreads;
-    static bool configured = false;  // one attribute call per instantiation
-    if (!configured) {
-        const int b = (int)smem_base, m = (int)smem_mlp;
-        cudaError_t e = cudaFuncSetAttribute(step_kernel<Cfg, true, SEED_PREV>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<Cfg, false, SEED_PREV>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<Cfg, true, SEED_COLD>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<Cfg, false, SEED_COLD>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<Cfg, true, SEED_MLP>, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<Cfg, false, SEED_MLP>, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    const size_t smem_base = step_smem_bytes<Cfg>(SEED_PREV), smem_mlp = step_smem_bytes<Cfg>(SEED_MLP);
+    const cudaError_t ce = configure_step_kernels<Cfg>();
+    if (ce != cudaSuccess) return ce;
     dim3 block(bx, by, 1);
     dim3 grid((A.nx + bx - 1) / bx, (A.ny + by - 1) / by, A.nz);
     const bool d3 = A.nz > 1;

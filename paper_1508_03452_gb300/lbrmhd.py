@@ -21,6 +21,7 @@ FP64, FP32, FP16_DEV = 0, 1, 2
 RECOVERY_PLAIN, RECOVERY_MLP, RECOVERY_COLD = 0, 1, 2
 FLAG_NO_EM_COLLISION, FLAG_UNSHIFTED_POWER = 1, 2
 MLP_NPARAM, MLP_NFEAT, MLP_ROW = 9924, 20, 24
+SCHED_PER_RUN, SCHED_BATCH = 0, 1
 NMOMENTS, NDIAG, NTABLE, NHIST = 16, 10, 311, 17
 MOMENT_NAMES = ["n", "p", "eps", "ux", "uy", "uz", "Ex", "Ey", "Ez", "Bx", "By", "Bz", "rho_c", "Jx", "Jy", "Jz"]
 DIAG_NAMES = ["N0", "T00", "T01", "T02", "T03", "rho_c", "divB_max", "divB_rms", "nonfinite", "cells"]
@@ -32,6 +33,7 @@ EXPORTED = [
     "lbrmhd_run_cells", "lbrmhd_last_error", "lbrmhd_lattice_tables", "lbrmhd_get_diagnostics_noalloc",
     "lbrmhd_mlp_nparams", "lbrmhd_mlp_blob_bytes", "lbrmhd_mlp_pack", "lbrmhd_mlp_infer", "lbrmhd_mlp_grad",
     "lbrmhd_mlp_train", "lbrmhd_set_mlp_weights", "lbrmhd_set_mlp_samples", "lbrmhd_get_iteration_histogram",
+    "lbrmhd_set_schedule", "lbrmhd_get_schedule", "lbrmhd_autotune",
 ]
 
 
@@ -44,6 +46,18 @@ class Params(C.Structure):
         ("drive_layers", C.c_int32), ("precision", C.c_int32), ("recovery", C.c_int32), ("flags", C.c_int32),
         ("max_iters", C.c_int32), ("tol", C.c_double),
     ]
+
+
+class Schedule(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("bx", C.c_int32), ("waves", C.c_int32), ("order", C.c_int32),
+                ("streams", C.c_int32), ("graph_steps", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def make_schedule(kind=SCHED_BATCH, bx=128, waves=0, order=0, streams=1, graph_steps=0) -> Schedule:
+    return Schedule(int(kind), int(bx), int(waves), int(order), int(streams), int(graph_steps))
 
 
 def make_params(nx, ny=1, nz=1, *, bc=(PERIODIC,) * 6, tau=1.0, sigma=100.0, gamma_ad=4.0 / 3.0, alpha=0.1, c=1.0,
@@ -115,6 +129,9 @@ def load(build_if_missing: bool = True):
         L.lbrmhd_set_mlp_weights.argtypes = [vp, vp]
         L.lbrmhd_set_mlp_samples.argtypes = [vp, C.c_int, vp]
         L.lbrmhd_get_iteration_histogram.argtypes = [vp, C.c_int, C.POINTER(i64)]
+        L.lbrmhd_set_schedule.argtypes = [vp, C.POINTER(Schedule)]
+        L.lbrmhd_get_schedule.argtypes = [vp, C.POINTER(Schedule)]
+        L.lbrmhd_autotune.argtypes = [vp, C.c_int, C.POINTER(Schedule), C.POINTER(C.c_double)]
         _lib = L
         return L
 
@@ -317,6 +334,23 @@ class Solver:
     def set_state(self, blob: bytes):
         buf = C.create_string_buffer(blob, len(blob))
         self._check(self._L.lbrmhd_set_state(self._h, buf, len(blob)))
+
+    def set_schedule(self, sched: Schedule | None = None, **kw):
+        """Launch schedule (see lbrmhd_schedule); keyword arguments build one."""
+        sched = sched if sched is not None else make_schedule(**kw)
+        self._check(self._L.lbrmhd_set_schedule(self._h, C.byref(sched)))
+
+    def schedule(self) -> Schedule:
+        out = Schedule()
+        self._check(self._L.lbrmhd_get_schedule(self._h, C.byref(out)))
+        return out
+
+    def autotune(self, trials=3):
+        """Times the candidate schedules on dry steps, keeps the fastest;
+        returns (schedule, ms per step)."""
+        best, ms = Schedule(), C.c_double()
+        self._check(self._L.lbrmhd_autotune(self._h, int(trials), C.byref(best), C.byref(ms)))
+        return best, ms.value
 
     def set_mlp_weights(self, params):
         """Network of the learned recovery seed (cuda float32, MLP_NPARAM)."""
