@@ -375,13 +375,12 @@ __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, 
     }
     A.pout[P_RHO * A.stride + c] = (typename Cfg::prim)nw.rho;
 
-#ifndef LB_NO_STATS
     // recovery counters, aggregated per warp
     const unsigned mask = __activemask();
     const unsigned fail = __reduce_add_sync(mask, ok ? 0u : 1u);
     const unsigned isum = __reduce_add_sync(mask, ok ? (unsigned)it : 0u);
     const unsigned imax = __reduce_max_sync(mask, ok ? (unsigned)it : 0u);
-    const bool leader = (threadIdx.x + threadIdx.y * blockDim.x) % 32 == (unsigned)(__ffs(mask) - 1);
+    const bool leader = (tid & 31) == __ffs(mask) - 1;
     const unsigned slot = (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)) % kStatSlots;
     unsigned long long* st = A.stats + (size_t)slot * kNumStats;
     if (leader) {
@@ -397,7 +396,6 @@ __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, 
         const unsigned cnt = __popc(__ballot_sync(mask, ib == b));
         if (leader && cnt) atomicAdd(&st[2 + b], (unsigned long long)cnt);
     }
-#endif
 }
 
 // one run: a 2-D grid of blocks over (x, y) and z
