@@ -93,7 +93,7 @@ class ClockSampler:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index: int):
-        self.index, self.proc, self.path = index, None, None
+        self.index, self.proc, self.path, self.skip = index, None, None, 0
 
     def __enter__(self):
         try:
@@ -103,7 +103,12 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "50"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            # the timed region starts once the sampler is running
+            t0 = time.time()
+            while time.time() - t0 < 5.0 and self.proc.poll() is None and os.path.getsize(self.path) == 0:
+                time.sleep(0.02)
+            self.skip = sum(1 for _ in open(self.path))
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
@@ -121,7 +126,9 @@ class ClockSampler:
             return None
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for k, line in enumerate(open(self.path)):
+            if k < self.skip:  # taken before the timed region
+                continue
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
