@@ -26,16 +26,17 @@ namespace lb {
 template <class R>
 __device__ __forceinline__ R minmod(R a, R b)
 {
-    // the argument of smaller magnitude when both have the same sign, else 0
-    return (a > R(0) && b > R(0)) ? fmin(a, b) : ((a < R(0) && b < R(0)) ? fmax(a, b) : R(0));
+    // the argument of smaller magnitude when both have the same sign, else 0:
+    // the median of (a, b, 0), as four min / max operations
+    return fmax(fmin(a, b), fmin(fmax(a, b), R(0)));
 }
 
 template <class R>
 __device__ __forceinline__ R flux_diff(R um2, R um1, R u0, R up1, R kappa)
 {
-    const R Fout = u0 + kappa * minmod(up1 - u0, u0 - um1);
-    const R Fin = um1 + kappa * minmod(u0 - um1, um1 - um2);
-    return Fout - Fin;
+    // Fout - Fin = (u0 - um1) + kappa [minmod(up1 - u0, u0 - um1) - minmod(u0 - um1, um1 - um2)]
+    const R d0 = u0 - um1;
+    return d0 + kappa * (minmod(up1 - u0, d0) - minmod(d0, um1 - um2));
 }
 
 // Relative element offsets of the neighbours d = -2..+2 of one cell along each
@@ -208,14 +209,15 @@ struct StepMinBlocks {
 };
 
 // One cell update (x, y, z) of one run; `tid` is the thread's index in its
-// block of `nth` threads (its rows of the shared-memory buffers). Threads of
+// block of kStepThreads threads (its rows of the shared-memory buffers). Threads of
 // cells outside the grid return at once, except in the learned-seed variant,
 // whose warp-wide MMA needs all 32 lanes: there they work on a clamped cell
 // and store nothing.
 template <class Cfg, bool IS3D, int SEED>
 __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, const int z, const int tid,
-                                          const int nth, unsigned char* smem_raw)
+                                          unsigned char* smem_raw)
 {
+    constexpr int nth = kStepThreads;  // a compile-time stride of the shared-memory slots
     using R = typename Cfg::real;
     R* sp = reinterpret_cast<R*>(smem_raw) + tid;
     const bool active = x < A.nx && y < A.ny;
@@ -404,7 +406,7 @@ __global__ void __launch_bounds__(kStepThreads, StepMinBlocks<Cfg, SEED>::value)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     step_cell<Cfg, IS3D, SEED>(A, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y,
-                               blockIdx.z, threadIdx.x + threadIdx.y * blockDim.x, blockDim.x * blockDim.y, smem_raw);
+                               blockIdx.z, threadIdx.x + threadIdx.y * blockDim.x, smem_raw);
 }
 
 template <class Cfg>
@@ -449,7 +451,7 @@ __global__ void __launch_bounds__(kStepThreads, StepMinBlocks<Cfg, SEED>::value)
             run = td.x;
         }
         __syncwarp();  // every lane starts a tile together (the learned seed's MMA)
-        step_cell<Cfg, IS3D, SEED>(*sA, td.y + tx, td.z + ty, td.w, tid, kStepThreads, smem_raw);
+        step_cell<Cfg, IS3D, SEED>(*sA, td.y + tx, td.z + ty, td.w, tid, smem_raw);
     }
 }
 
