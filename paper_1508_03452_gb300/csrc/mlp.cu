@@ -187,30 +187,30 @@ __global__ void mlp_adam_kernel(float* __restrict__ P, float* __restrict__ m, fl
     P[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
-// float32 parameters -> padded bf16 inference blob (zero padding)
+// float32 parameters -> bf16 inference blob in fragment order (zero padding)
 __global__ void mlp_pack_kernel(const float* __restrict__ P, unsigned char* __restrict__ blob)
 {
     __nv_bfloat16* W = reinterpret_cast<__nv_bfloat16*>(blob);
     float* bias = reinterpret_cast<float*>(blob + MLPD_NBF16 * 2);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < MLPD_NBF16 + MLPD_NBIAS; i += gridDim.x * blockDim.x) {
-        if (i < MLPD_NBF16) {
-            float val = 0.0f;
-            if (i < MLPD_W2) {
-                const int o = i / MLP_XS, k = i % MLP_XS;
-                if (k < MLP_IN) val = P[MLP_W1 + o * MLP_IN + k];
-            } else if (i < MLPD_W3) {
-                const int o = (i - MLPD_W2) / MLP_HS, k = (i - MLPD_W2) % MLP_HS;
-                if (k < MLP_H) val = P[MLP_W2 + o * MLP_H + k];
-            } else if (i < MLPD_W4) {
-                const int o = (i - MLPD_W3) / MLP_HS, k = (i - MLPD_W3) % MLP_HS;
-                if (k < MLP_H) val = P[MLP_W3 + o * MLP_H + k];
-            } else {
-                const int o = (i - MLPD_W4) / MLP_HS, k = (i - MLPD_W4) % MLP_HS;
-                if (o < MLP_OUT && k < MLP_H) val = P[MLP_W4 + o * MLP_H + k];
-            }
-            W[i] = __float2bfloat16_rn(val);
+    const int total = MLP_H * MLP_K1 + 2 * MLP_H * MLP_H + 8 * MLP_H + MLPD_NBIAS;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        // i enumerates (layer, r, k) in row-major order, then the biases
+        if (i < MLP_H * MLP_K1) {
+            const int r = i / MLP_K1, k = i % MLP_K1;
+            W[MLPD_W1 + mlpd_frag_index(r, k, MLP_K1)] =
+                __float2bfloat16_rn(k < MLP_IN ? P[MLP_W1 + r * MLP_IN + k] : 0.0f);
+        } else if (i < MLP_H * MLP_K1 + MLP_H * MLP_H) {
+            const int j = i - MLP_H * MLP_K1, r = j / MLP_H, k = j % MLP_H;
+            W[MLPD_W2 + mlpd_frag_index(r, k, MLP_H)] = __float2bfloat16_rn(P[MLP_W2 + r * MLP_H + k]);
+        } else if (i < MLP_H * MLP_K1 + 2 * MLP_H * MLP_H) {
+            const int j = i - MLP_H * MLP_K1 - MLP_H * MLP_H, r = j / MLP_H, k = j % MLP_H;
+            W[MLPD_W3 + mlpd_frag_index(r, k, MLP_H)] = __float2bfloat16_rn(P[MLP_W3 + r * MLP_H + k]);
+        } else if (i < MLP_H * MLP_K1 + 2 * MLP_H * MLP_H + 8 * MLP_H) {
+            const int j = i - MLP_H * MLP_K1 - 2 * MLP_H * MLP_H, r = j / MLP_H, k = j % MLP_H;
+            W[MLPD_W4 + mlpd_frag_index(r, k, MLP_H)] =
+                __float2bfloat16_rn(r < MLP_OUT ? P[MLP_W4 + r * MLP_H + k] : 0.0f);
         } else {
-            const int j = i - MLPD_NBF16;
+            const int j = i - (MLP_H * MLP_K1 + 2 * MLP_H * MLP_H + 8 * MLP_H);
             float val = 0.0f;
             if (j < 64) val = P[MLP_B1 + j];
             else if (j < 128) val = P[MLP_B2 + j - 64];

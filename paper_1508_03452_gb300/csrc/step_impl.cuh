@@ -46,14 +46,24 @@ struct Off {
     int x[5], y[5], z[5];
 };
 
+// neighbour coordinate s = x + d, |d| <= 2, wrapped (periodic) or clamped:
+// one branch-free correction when the axis has at least 2 cells
+__device__ __forceinline__ int near_coord(int s, int n, int periodic)
+{
+    if (n < 2) return wrap_coord(s, n, periodic);
+    if (periodic) return s < 0 ? s + n : (s >= n ? s - n : s);
+    return s < 0 ? 0 : (s >= n ? n - 1 : s);
+}
+
+template <bool IS3D>
 __device__ __forceinline__ Off make_off(int x, int y, int z, int nx, int ny, int nz, const int* per)
 {
     Off o;
 #pragma unroll
     for (int d = -2; d <= 2; ++d) {
-        o.x[d + 2] = wrap_coord(x + d, nx, per[0]) - x;
-        o.y[d + 2] = (wrap_coord(y + d, ny, per[1]) - y) * nx;
-        o.z[d + 2] = (wrap_coord(z + d, nz, per[2]) - z) * nx * ny;
+        o.x[d + 2] = near_coord(x + d, nx, per[0]) - x;
+        o.y[d + 2] = (near_coord(y + d, ny, per[1]) - y) * nx;
+        o.z[d + 2] = IS3D ? (near_coord(z + d, nz, per[2]) - z) * nx * ny : 0;  // unused in 2-D runs
     }
     return o;
 }
@@ -229,7 +239,7 @@ __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, 
         x = x < A.nx ? x : A.nx - 1;
         y = y < A.ny ? y : A.ny - 1;
     }
-    const Off o = make_off(x, y, z, A.nx, A.ny, A.nz, A.periodic);
+    const Off o = make_off<IS3D>(x, y, z, A.nx, A.ny, A.nz, A.periodic);
     const int64_t c = x + (int64_t)A.nx * (y + (int64_t)A.ny * z);
     const Phys<R>& k = A.k;
 

@@ -37,9 +37,9 @@ def test_learned_seed_layout_constants_need_no_gpu():
     from oracle import mlp_ref as M
     lib = L.load()
     assert lib.lbrmhd_mlp_nparams() == L.MLP_NPARAM == M.NPARAM
-    # bf16 weights with padded rows (W1 64 x 40, W2 and W3 64 x 72, W4 8 x 72)
-    # then 200 float32 biases
-    assert lib.lbrmhd_mlp_blob_bytes() == 2 * (64 * 40 + 2 * 64 * 72 + 8 * 72) + 4 * 200
+    # bf16 weights in fragment order (W1 64 x 32 with zero-padded inputs, W2 and
+    # W3 64 x 64, W4 8 x 64 with zero-padded outputs), then 200 float32 biases
+    assert lib.lbrmhd_mlp_blob_bytes() == 2 * (64 * 32 + 2 * 64 * 64 + 8 * 64) + 4 * 200
     assert lib.lbrmhd_mlp_pack(None, None, None) == L.ERR_BAD_ARG
     assert lib.lbrmhd_mlp_infer(None, None, 1, None, None) == L.ERR_BAD_ARG
     assert lib.lbrmhd_mlp_grad(None, None, 1, None, None) == L.ERR_BAD_ARG
