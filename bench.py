@@ -56,6 +56,23 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The largest of the ranks' values (the job is as slow as its slowest rank)."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(world: int, cells_per_rank: int, steps: int, seconds: float) -> float:
+    """Cell updates of all ranks per second, in millions (weak scaling: every
+    rank runs the same workload)."""
+    return world * cells_per_rank * steps / seconds / 1e6
+
+
 def kernel_sha() -> str:
     h = hashlib.sha256()
     for name in KERNEL_SOURCES:
@@ -383,18 +400,14 @@ def run_gpu(args, world, rank, local):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     stats = [solver.stats(r) for r in range(len(SIGMAS))]
     steps_total = args.warmup + args.steps
     plain_iters = sum(s["iter_total"] for s in stats) / (len(SIGMAS) * N * steps_total)
     plain_hist = sum(solver.iteration_histogram(r) for r in range(len(SIGMAS)))
     plain_moments = solver.moments(1) if (rank == 0 and not args.no_learned_seed) else None
     launches = args.steps * len(SIGMAS)
-    value = world * cells * args.steps / (ms * 1e-3) / 1e6
+    value = whole_job_mlups(world, cells, args.steps, ms * 1e-3)
     # roofline of the dominant (only) kernel of the timed region: the fused step
     bpc = BYTES_PER_CELL[args.precision]
     avg_launch_s = ms * 1e-3 / launches
@@ -417,11 +430,11 @@ def run_gpu(args, world, rank, local):
     for r in range(len(SIGMAS)):
         solver._check(solver._L.lbrmhd_get_moments(solver._h, r, L._dp(out_host.numpy())))
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     barrier()
     h2d = len(SIGMAS) * N * 8 * (1 + 1 + 3 + 3)
     d2h = len(SIGMAS) * N * 8 * L.NMOMENTS
-    e2e_value = world * cells * args.steps / e2e_s / 1e6
+    e2e_value = whole_job_mlups(world, cells, args.steps, e2e_s)
 
     if rank == 0:
         line = {
@@ -469,7 +482,11 @@ def run_profile_case(args):
 
     prec = {"fp32": L.FP32, "fp16": L.FP16_DEV, "fp64": L.FP64}[args.precision]
     F = W.current_sheet(NX, NY, 1, delta=8.0)
-    s = L.Solver(L.make_params(NX, NY, 1, sigma=100.0, precision=prec), stream=torch.cuda.current_stream())
+    rec = L.RECOVERY_MLP if args.profile_learned else L.RECOVERY_PLAIN
+    s = L.Solver(L.make_params(NX, NY, 1, sigma=100.0, precision=prec, recovery=rec),
+                 stream=torch.cuda.current_stream())
+    if args.profile_learned:  # untrained weights: the inference cost, not the seed quality
+        s.set_mlp_weights(torch.tensor(W.mlp_init_params(1), device="cuda"))
     s.init_fields(0, F.n, F.p, F.u, F.B)
     s.step(args.steps)
     torch.cuda.synchronize()
@@ -488,6 +505,7 @@ def main():
     ap.add_argument("--no-sweep", action="store_true", help="skip the 64-run batched sweep leg")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--profile-case", action="store_true", help="untimed 1024^2 single-run case for ncu captures")
+    ap.add_argument("--profile-learned", action="store_true", help="--profile-case with the learned-seed kernel")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if args.profile_case:
