@@ -191,6 +191,18 @@ int lbrmhd_get_diagnostics(lbrmhd_handle h, int run, double* out);
  * (run not initialised), CUDA. */
 int lbrmhd_get_diagnostics_noalloc(lbrmhd_handle h, int run, double* d_out);
 
+/* Reconnection rate of a 2-D run (Sec. IV, Kelvin-Helmholtz-driven
+ * reconnection): R = (E^z - E^z_0) / B0 at the null point, E^z_0 being the
+ * out-of-plane electric field of the run's initial state (kept from
+ * lbrmhd_init_fields, and in checkpoints). The null point is the cell of
+ * smallest B_x^2 + B_y^2 in rows y_lo <= y < y_hi (the band names one current
+ * layer; ties go to the lowest cell index), found again at every call, so it
+ * follows the layer as it moves. out4 (host): R, x, y and |B_in-plane| at the
+ * null (NaN if the band holds no finite field). Synchronises the handle's
+ * stream. Errors: BAD_ARG (run out of range, 3-D run, empty or out-of-grid
+ * band, B0 zero or not finite), STATE (run not initialised), CUDA. */
+int lbrmhd_reconnection_rate(lbrmhd_handle h, int run, int y_lo, int y_hi, double B0, double* out4);
+
 /* Counters of one run: [0] steps taken, [1] recovery failures, [2] sum of
  * recovery iterations, [3] maximum recovery iterations. Host output. */
 int lbrmhd_get_stats(lbrmhd_handle h, int run, int64_t* out4);

@@ -35,6 +35,7 @@ struct RunState {
     int64_t steps = 0;
     int periodic[3] = {1, 1, 1};
     float* d_samples = nullptr;  // caller-owned training-sample buffer (or NULL)
+    void* d_ez0 = nullptr;       // E^z of the initial state (primitive type, N), for the reconnection rate
 };
 
 constexpr size_t kStatsBytes = lb::kNumStats * sizeof(unsigned long long);  // totals (checkpoint)
@@ -545,6 +546,9 @@ int init_run(lbrmhd_handle h, RunState& r, const lb::InitInputs& in)
     LB_CK(cudaMemsetAsync(r.d_stats, 0, kStatsAlloc, h->stream));
     LB_CK(cudaStreamSynchronize(h->stream));
     if (bad) return fail(h, LBRMHD_ERR_BAD_ARG, "initial state has |u| >= c or n <= 0");
+    const size_t qb = sizeof(typename Cfg::prim);
+    LB_CK(cudaMemcpyAsync(r.d_ez0, (const char*)r.prim[r.cur] + (size_t)(lb::P_E + 2) * r.stride * qb, r.N * qb,
+                          cudaMemcpyDeviceToDevice, h->stream));
     r.initialized = true;
     runs_changed(h);
     r.steps = 0;
@@ -828,6 +832,7 @@ int lbrmhd_create(const lbrmhd_params* params, int n_runs, lbrmhd_handle* out)
                 cudaMemset(s.prim[b], 0, lb::NPRIM * s.stride * qb);
             }
         }
+        ok = ok && cudaMalloc(&s.d_ez0, s.N * qb) == cudaSuccess;
         ok = ok && cudaMalloc(&s.d_stats, kStatsAlloc) == cudaSuccess;
         if (ok) cudaMemset(s.d_stats, 0, kStatsAlloc);
         max_blocks = std::max<int64_t>(max_blocks, (s.N + lb::kDiagThreads - 1) / lb::kDiagThreads);
@@ -863,6 +868,7 @@ int lbrmhd_destroy(lbrmhd_handle h)
             if (r.prim[b]) cudaFree(r.prim[b]);
         }
         if (r.d_stats) cudaFree(r.d_stats);
+        if (r.d_ez0) cudaFree(r.d_ez0);
     }
     if (h->d_scratch) cudaFree(h->d_scratch);
     if (h->d_io) cudaFree(h->d_io);
@@ -1067,13 +1073,14 @@ int lbrmhd_get_iteration_histogram(lbrmhd_handle h, int run, int64_t* out)
 }
 
 // checkpoint blob: per run [int64 steps][NMEANS double reference means][uint64 stats x kNumStats]
-// [pops 38 N][h 25 N][prim 12 N] (storage format)
+// [pops 38 N][h 25 N][prim 12 N][initial E^z N] (storage format)
 int lbrmhd_state_bytes(lbrmhd_handle h, size_t* bytes)
 {
     if (!h || !bytes) return LBRMHD_ERR_BAD_ARG;
     const size_t pb = pop_bytes(h->precision), hb = hp_bytes(h->precision);
     size_t total = 0;
-    for (auto& r : h->runs) total += 8 + 8 * lb::NMEANS + kStatsBytes + (size_t)r.N * (38 * pb + 25 * hb + lb::NPRIM * hb);
+    for (auto& r : h->runs)
+        total += 8 + 8 * lb::NMEANS + kStatsBytes + (size_t)r.N * (38 * pb + 25 * hb + (lb::NPRIM + 1) * hb);
     *bytes = total;
     return LBRMHD_OK;
 }
@@ -1106,6 +1113,8 @@ int lbrmhd_get_state(lbrmhd_handle h, void* host_buf, size_t bytes)
         for (int pl = 0; pl < lb::NPRIM; ++pl, o += r.N * hb)
             LB_CK(cudaMemcpyAsync(o, (char*)r.prim[r.cur] + pl * r.stride * hb, r.N * hb, cudaMemcpyDeviceToHost,
                                   h->stream));
+        LB_CK(cudaMemcpyAsync(o, r.d_ez0, r.N * hb, cudaMemcpyDeviceToHost, h->stream));
+        o += r.N * hb;
     }
     LB_CK(cudaStreamSynchronize(h->stream));
     return LBRMHD_OK;
@@ -1140,6 +1149,8 @@ int lbrmhd_set_state(lbrmhd_handle h, const void* host_buf, size_t bytes)
         for (int pl = 0; pl < lb::NPRIM; ++pl, o += r.N * hb)
             LB_CK(cudaMemcpyAsync((char*)r.prim[r.cur] + pl * r.stride * hb, o, r.N * hb, cudaMemcpyHostToDevice,
                                   h->stream));
+        LB_CK(cudaMemcpyAsync(r.d_ez0, o, r.N * hb, cudaMemcpyHostToDevice, h->stream));
+        o += r.N * hb;
         r.initialized = true;
         runs_changed(h);
     }
@@ -1206,6 +1217,37 @@ int lbrmhd_autotune(lbrmhd_handle h, int trials, lbrmhd_schedule* best, double* 
         case LBRMHD_FP32: return autotune<lb::CfgF32>(h, trials, best, best_ms);
         default: return autotune<lb::CfgF16>(h, trials, best, best_ms);
     }
+}
+
+int lbrmhd_reconnection_rate(lbrmhd_handle h, int run, int y_lo, int y_hi, double B0, double* out4)
+{
+    if (bad_run(h, run) || !out4) return h ? fail(h, LBRMHD_ERR_BAD_ARG, "bad run or NULL output") : LBRMHD_ERR_BAD_ARG;
+    RunState& r = h->runs[run];
+    if (r.p.nz != 1) return fail(h, LBRMHD_ERR_BAD_ARG, "the reconnection rate is defined for 2-D runs");
+    if (y_lo < 0 || y_hi > r.p.ny || y_lo >= y_hi) return fail(h, LBRMHD_ERR_BAD_ARG, "empty or out-of-grid row band");
+    if (!(B0 != 0.0) || !std::isfinite(B0)) return fail(h, LBRMHD_ERR_BAD_ARG, "B0 must be finite and non-zero");
+    if (!r.initialized) return fail(h, LBRMHD_ERR_STATE, "run not initialised");
+    LB_CK(cudaSetDevice(h->device));
+    const int64_t scratch = std::max<int64_t>(h->scratch_blocks * lb::NPART, (int64_t)lb::kMeansBlocks * lb::NMEANS);
+    cudaError_t e;
+    switch (h->precision) {
+        case LBRMHD_FP64:
+            e = lb::launch_null<lb::CfgF64>(view<lb::CfgF64>(r, r.cur), y_lo, y_hi, (const double*)r.d_ez0, B0,
+                                            h->d_scratch, scratch, h->d_small, h->stream);
+            break;
+        case LBRMHD_FP32:
+            e = lb::launch_null<lb::CfgF32>(view<lb::CfgF32>(r, r.cur), y_lo, y_hi, (const float*)r.d_ez0, B0,
+                                            h->d_scratch, scratch, h->d_small, h->stream);
+            break;
+        default:
+            e = lb::launch_null<lb::CfgF16>(view<lb::CfgF16>(r, r.cur), y_lo, y_hi, (const float*)r.d_ez0, B0,
+                                            h->d_scratch, scratch, h->d_small, h->stream);
+            break;
+    }
+    LB_CK(e);
+    LB_CK(cudaMemcpyAsync(out4, h->d_small, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    LB_CK(cudaStreamSynchronize(h->stream));
+    return LBRMHD_OK;
 }
 
 const char* lbrmhd_last_error(lbrmhd_handle h)

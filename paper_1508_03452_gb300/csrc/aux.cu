@@ -1,6 +1,10 @@
 // aux.cu -- initial state, open boundaries, normal-B fix, photospheric driving,
 // output conversion and float64 diagnostics of the RRMHD lattice Boltzmann
 // library (arXiv:1508.03452, Secs. III-IV).
+#include <math_constants.h>
+
+#include <climits>
+
 #include "aux.cuh"
 
 namespace lb {
@@ -437,6 +441,86 @@ __global__ void diag_final_kernel(const double* partial, int64_t nblocks, int64_
 }
 
 // ---------------------------------------------------------------------------
+// reconnection rate at the null point (Sec. IV, KH-driven reconnection):
+// argmin of B_x^2 + B_y^2 over rows [y_lo, y_hi) of a 2-D run, ties to the
+// lowest cell index (the reduction is exact, so its order does not matter)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void min_pair(double& v, long long& i, double v2, long long i2)
+{
+    if (v2 < v || (v2 == v && i2 < i)) {
+        v = v2;
+        i = i2;
+    }
+}
+
+__device__ __forceinline__ void block_min_pair(double& v, long long& i)
+{
+    __shared__ double sv[32];
+    __shared__ long long si[32];
+    for (int o = 16; o > 0; o >>= 1)
+        min_pair(v, i, __shfl_down_sync(0xffffffffu, v, o), __shfl_down_sync(0xffffffffu, i, o));
+    const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (lane == 0) {
+        sv[w] = v;
+        si[w] = i;
+    }
+    __syncthreads();
+    if (w == 0) {
+        const int nw = (int)(blockDim.x / 32);
+        v = lane < nw ? sv[lane] : CUDART_INF;
+        i = lane < nw ? si[lane] : LLONG_MAX;
+        for (int o = 16; o > 0; o >>= 1)
+            min_pair(v, i, __shfl_down_sync(0xffffffffu, v, o), __shfl_down_sync(0xffffffffu, i, o));
+    }
+}
+
+template <class Cfg>
+__global__ void null_partial_kernel(PopView<Cfg> V, int y_lo, int y_hi, double* part_v, long long* part_i)
+{
+    const int64_t nb = (int64_t)V.nx * (y_hi - y_lo);
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double v = CUDART_INF;
+    long long i = LLONG_MAX;
+    if (t < nb) {
+        const long long c = (long long)y_lo * V.nx + t;
+        const double bx = (double)V.prim[P_B * V.stride + c], by = (double)V.prim[(P_B + 1) * V.stride + c];
+        const double b2 = __dadd_rn(__dmul_rn(bx, bx), __dmul_rn(by, by));  // no FMA: rounds as written
+        if (b2 == b2) {  // NaN never wins
+            v = b2;
+            i = c;
+        }
+    }
+    block_min_pair(v, i);
+    if (threadIdx.x == 0) {
+        part_v[blockIdx.x] = v;
+        part_i[blockIdx.x] = i;
+    }
+}
+
+// out: R, x, y, |B| at the null (NaN when the band holds no finite field)
+template <class Cfg>
+__global__ void null_final_kernel(const double* part_v, const long long* part_i, int64_t nblocks, PopView<Cfg> V,
+                                  const typename Cfg::prim* ez0, double B0, double* out)
+{
+    double v = CUDART_INF;
+    long long i = LLONG_MAX;
+    for (int64_t b = threadIdx.x; b < nblocks; b += blockDim.x) min_pair(v, i, part_v[b], part_i[b]);
+    block_min_pair(v, i);
+    if (threadIdx.x == 0) {
+        const int64_t N = (int64_t)V.nx * V.ny;
+        if (i >= 0 && i < N) {
+            const double ez = (double)V.prim[(P_E + 2) * V.stride + i];
+            out[0] = (ez - (double)ez0[i]) / B0;
+            out[1] = (double)(i % V.nx);
+            out[2] = (double)(i / V.nx);
+            out[3] = sqrt(v);
+        } else {
+            out[0] = out[1] = out[2] = out[3] = CUDART_NAN;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
 static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -511,6 +595,19 @@ cudaError_t launch_diag(const PopView<Cfg>& V, const Phys<double>& k, const RefS
     return cudaGetLastError();
 }
 
+template <class Cfg>
+cudaError_t launch_null(const PopView<Cfg>& V, int y_lo, int y_hi, const typename Cfg::prim* ez0, double B0,
+                        double* scratch, int64_t scratch_doubles, double* out, cudaStream_t s)
+{
+    const int64_t nb = blocks_for((int64_t)V.nx * (y_hi - y_lo), kDiagThreads);
+    if (2 * nb > scratch_doubles) return cudaErrorInvalidValue;
+    double* pv = scratch;
+    long long* pi = reinterpret_cast<long long*>(scratch + nb);
+    null_partial_kernel<Cfg><<<(unsigned)nb, kDiagThreads, 0, s>>>(V, y_lo, y_hi, pv, pi);
+    null_final_kernel<Cfg><<<1, kDiagThreads, 0, s>>>(pv, pi, nb, V, ez0, B0, out);
+    return cudaGetLastError();
+}
+
 #define LB_INSTANTIATE(CFG)                                                                                        \
     template cudaError_t launch_init<CFG>(const PopView<CFG>&, const InitInputs&, const Phys<double>&, int*,      \
                                           cudaStream_t);                                                           \
@@ -520,6 +617,8 @@ cudaError_t launch_diag(const PopView<Cfg>& V, const Phys<double>& k, const RefS
     template cudaError_t launch_populations<CFG>(const PopView<CFG>&, const RefPops&, double*, double*, double*,  \
                                                  cudaStream_t);                                                    \
     template cudaError_t launch_diag<CFG>(const PopView<CFG>&, const Phys<double>&, const RefState&, double*,      \
+                                          int64_t, double*, cudaStream_t);                                         \
+    template cudaError_t launch_null<CFG>(const PopView<CFG>&, int, int, const CFG::prim*, double, double*,       \
                                           int64_t, double*, cudaStream_t);
 
 LB_INSTANTIATE(CfgF64)

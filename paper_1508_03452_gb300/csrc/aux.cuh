@@ -71,6 +71,9 @@ cudaError_t launch_step_batch(const unsigned char* d_args, const int4* d_tiles, 
                               bool is3d, int seed, cudaStream_t stream);
 template <class Cfg>
 int batch_blocks_per_sm(bool is3d, int seed);
+template <class Cfg>
+cudaError_t launch_null(const PopView<Cfg>& V, int y_lo, int y_hi, const typename Cfg::prim* ez0, double B0,
+                        double* scratch, int64_t scratch_doubles, double* out, cudaStream_t s);
 // device stride of the per-run argument records of the batched kernel
 template <class Cfg>
 constexpr size_t batch_args_stride()

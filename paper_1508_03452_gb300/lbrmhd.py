@@ -33,7 +33,7 @@ EXPORTED = [
     "lbrmhd_run_cells", "lbrmhd_last_error", "lbrmhd_lattice_tables", "lbrmhd_get_diagnostics_noalloc",
     "lbrmhd_mlp_nparams", "lbrmhd_mlp_blob_bytes", "lbrmhd_mlp_pack", "lbrmhd_mlp_infer", "lbrmhd_mlp_grad",
     "lbrmhd_mlp_train", "lbrmhd_set_mlp_weights", "lbrmhd_set_mlp_samples", "lbrmhd_get_iteration_histogram",
-    "lbrmhd_set_schedule", "lbrmhd_get_schedule", "lbrmhd_autotune",
+    "lbrmhd_set_schedule", "lbrmhd_get_schedule", "lbrmhd_autotune", "lbrmhd_reconnection_rate",
 ]
 
 
@@ -132,6 +132,7 @@ def load(build_if_missing: bool = True):
         L.lbrmhd_set_schedule.argtypes = [vp, C.POINTER(Schedule)]
         L.lbrmhd_get_schedule.argtypes = [vp, C.POINTER(Schedule)]
         L.lbrmhd_autotune.argtypes = [vp, C.c_int, C.POINTER(Schedule), C.POINTER(C.c_double)]
+        L.lbrmhd_reconnection_rate.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_double, dp]
         _lib = L
         return L
 
@@ -323,6 +324,13 @@ class Solver:
         out = (C.c_int64 * NHIST)()
         self._check(self._L.lbrmhd_get_iteration_histogram(self._h, run, out))
         return np.array(out[:], dtype=np.int64)
+
+    def reconnection_rate(self, run, y_lo, y_hi, B0) -> dict:
+        """R = (E^z - E^z_0) / B0 at the null point of rows [y_lo, y_hi) (2-D runs)."""
+        out = np.zeros(4)
+        self._check(self._L.lbrmhd_reconnection_rate(self._h, run, int(y_lo), int(y_hi), float(B0), _dp(out)))
+        return {"R": out[0], "x": int(out[1]) if np.isfinite(out[1]) else -1,
+                "y": int(out[2]) if np.isfinite(out[2]) else -1, "B": out[3]}
 
     def get_state(self) -> bytes:
         n = C.c_size_t()

@@ -49,6 +49,7 @@ def test_learned_seed_layout_constants_need_no_gpu():
     assert lib.lbrmhd_set_schedule(None, None) == L.ERR_BAD_ARG
     assert lib.lbrmhd_get_schedule(None, None) == L.ERR_BAD_ARG
     assert lib.lbrmhd_autotune(None, 1, None, None) == L.ERR_BAD_ARG
+    assert lib.lbrmhd_reconnection_rate(None, 0, 0, 1, 1.0, None) == L.ERR_BAD_ARG
 
 
 def test_lattice_tables_match_oracle():
