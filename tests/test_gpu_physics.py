@@ -1,0 +1,61 @@
+"""The paper's validation runs (Sec. IV) on the GPU, checked against the
+analytic solutions the paper compares with (not only against the oracle):
+the resistive current sheet against B0 erf(x sqrt(sigma / t) / 2), and the
+Alfven wave against its phase speed."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1508_03452_gb300 import lbrmhd as L
+from paper_1508_03452_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+OPEN_X = (L.OPEN, L.OPEN, L.PERIODIC, L.PERIODIC, L.PERIODIC, L.PERIODIC)
+
+
+@pytest.mark.parametrize("precision", [L.FP64, L.FP32])
+def test_paper_current_sheet_matches_erf_on_gpu(precision):
+    """100 cells on [-1.5, 1.5], sigma = 100, p = 50, open faces, from the erf
+    profile at t = 1 to t = 9: within 1 % of the exact self-similar solution."""
+    g = json.load(open(os.path.join(GOLDEN, "current_sheet_convergence.json")))
+    F = W.current_sheet_paper(100, sigma=g["sigma"], t0=g["t_start"], B0=g["B0"], p0=g["p"], n0=g["n"])
+    dx = F.meta["dx"]
+    s = L.Solver(L.make_params(F.nx, 1, 1, sigma=g["sigma"], dx=dx, bc=OPEN_X, precision=precision))
+    s.init_fields(0, F.n, F.p, F.u, F.B)
+    dt = dx / math.sqrt(2.0)
+    steps = int(round((g["t_end"] - g["t_start"]) / dt))
+    s.step(steps)
+    t = g["t_start"] + steps * dt
+    By = s.moments()[10]
+    st = s.stats()
+    s.close()
+    exact = np.array([math.erf(0.5 * math.sqrt(g["sigma"] / t) * v) for v in F.meta["x"]])
+    assert st["recover_fail"] == 0
+    assert np.linalg.norm(By - exact) / np.linalg.norm(exact) < 0.01
+
+
+@pytest.mark.parametrize("precision", [L.FP64, L.FP32])
+def test_alfven_phase_speed_on_gpu(precision):
+    """The right-moving Alfven mode of the config-1 set-up (64 cells, sigma =
+    1e6) travels at v_A within 3 % after a quarter box."""
+    nx = 64
+    F = W.alfven_wave(nx, 1, 1)
+    vA, k, B0 = F.meta["vA"], 2 * np.pi / nx, F.meta["B0"]
+    s = L.Solver(L.make_params(nx, 1, 1, sigma=1e6, precision=precision))
+    s.init_fields(0, F.n, F.p, F.u, F.B)
+    dt = 1.0 / math.sqrt(2.0)
+    nsteps = int(round(0.25 * nx / (vA * dt)))
+    mode = lambda a: np.fft.fft(a)[1]
+    m0 = s.moments()
+    s.step(nsteps)
+    m = s.moments()
+    s.close()
+    R0 = mode(m0[11]) - (B0 / vA) * mode(m0[5])
+    R = mode(m[11]) - (B0 / vA) * mode(m[5])
+    err = -np.angle(R / R0) / k / (nsteps * dt) / vA - 1.0
+    assert abs(err) < 0.03, err
