@@ -72,7 +72,7 @@ struct lbrmhd_state_s {
     int4* d_tiles = nullptr;
     size_t tiles_cap = 0;
     struct Group {
-        bool is3d;
+        bool is3d, open;
         int seed, first, count;
     };
     std::vector<Group> groups;
@@ -278,6 +278,9 @@ lb::StepArgs<Cfg> make_args(lbrmhd_handle h, const RunState& r, int in)
     A.nz = r.p.nz;
     A.stride = r.stride;
     for (int a = 0; a < 3; ++a) A.periodic[a] = r.periodic[a];
+    A.open_mask = 0;
+    for (int a = 0; a < 3; ++a)
+        if (r.p.bc[2 * a] != 0 || r.p.bc[2 * a + 1] != 0) A.open_mask |= 1 << a;
     A.flags = r.p.flags;
     A.k = make_phys<R>(r.p, r.ref, runref(r));
     A.hs = r.hs;
@@ -299,11 +302,12 @@ int build_tiles(lbrmhd_handle h, const lbrmhd_schedule& sc)
     std::vector<int4> all;
     h->groups.clear();
     for (int is3d = 0; is3d < 2; ++is3d)
-        for (int seed = 0; seed < 3; ++seed) {
+        for (int seed = 0; seed < 3; ++seed)
+        for (int open = 0; open < 2; ++open) {
             std::vector<std::vector<int4>> per;
             for (int ri = 0; ri < (int)h->runs.size(); ++ri) {
                 const RunState& r = h->runs[ri];
-                if ((r.p.nz > 1) != (is3d == 1) || run_seed(r) != seed) continue;
+                if ((r.p.nz > 1) != (is3d == 1) || run_seed(r) != seed || has_open(r) != (open == 1)) continue;
                 std::vector<int4> t;
                 for (int z = 0; z < r.p.nz; ++z)
                     for (int y0 = 0; y0 < r.p.ny; y0 += by)
@@ -321,7 +325,7 @@ int build_tiles(lbrmhd_handle h, const lbrmhd_schedule& sc)
                     for (auto& t : per)
                         if (i < t.size()) all.push_back(t[i]);
             }
-            h->groups.push_back({is3d == 1, seed, first, (int)all.size() - first});
+            h->groups.push_back({is3d == 1, open == 1, seed, first, (int)all.size() - first});
         }
     if (all.size() > (size_t)0x7fffffff) return fail(h, LBRMHD_ERR_BAD_ARG, "too many tiles for one launch");
     if (all.size() > h->tiles_cap) {
@@ -381,8 +385,10 @@ int issue_step(lbrmhd_handle h, const lbrmhd_schedule& sc, int in, cudaStream_t 
         LB_CK(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, h->device));
         for (const auto& g : h->groups) {
             int grid = 0;  // one block per tile
-            if (sc.waves > 0) grid = sc.waves * dev_sms * std::max(1, lb::batch_blocks_per_sm<Cfg>(g.is3d, g.seed));
-            LB_CK(lb::launch_step_batch<Cfg>(args, h->d_tiles + g.first, g.count, sc.bx, grid, g.is3d, g.seed, s));
+            if (sc.waves > 0)
+                grid = sc.waves * dev_sms * std::max(1, lb::batch_blocks_per_sm<Cfg>(g.is3d, g.seed, g.open));
+            LB_CK(lb::launch_step_batch<Cfg>(args, h->d_tiles + g.first, g.count, sc.bx, grid, g.is3d, g.seed, g.open,
+                                             s));
         }
     } else {
         for (const auto& r : h->runs) LB_CK(lb::launch_step<Cfg>(make_args<Cfg>(h, r, in), s));
@@ -469,7 +475,7 @@ int capture_graph(lbrmhd_handle h, const lbrmhd_schedule& sc, int in)
         LB_CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
         LB_CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
     }
-    for (const auto& g : h->groups) lb::batch_blocks_per_sm<Cfg>(g.is3d, g.seed);  // attributes set before capture
+    for (const auto& g : h->groups) lb::batch_blocks_per_sm<Cfg>(g.is3d, g.seed, g.open);  // attributes set before capture
     if (sc.kind == LBRMHD_SCHED_PER_RUN && sc.streams > 1) {
         const int rc0 = ensure_aux(h, std::min<int>(sc.streams, (int)h->runs.size()));  // created outside the capture
         if (rc0) return rc0;

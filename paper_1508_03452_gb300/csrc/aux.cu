@@ -191,31 +191,6 @@ __global__ void means_final_kernel(const double* partial, int nblocks, int64_t N
 // open boundaries: copy of the first interior cell (faces in order -x .. +z,
 // which is the same as clamping every open-axis coordinate into [1, n-2])
 // ---------------------------------------------------------------------------
-template <class Cfg>
-__global__ void open_copy_kernel(PopView<Cfg> V, int open_mask)
-{
-    const int64_t N = (int64_t)V.nx * V.ny * V.nz;
-    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (c >= N) return;
-    int q[3] = {(int)(c % V.nx), (int)((c / V.nx) % V.ny), (int)(c / ((int64_t)V.nx * V.ny))};
-    const int n[3] = {V.nx, V.ny, V.nz};
-    int r[3] = {q[0], q[1], q[2]};
-    bool boundary = false;
-    for (int a = 0; a < 3; ++a) {
-        if (!((open_mask >> a) & 1) || n[a] < 3) continue;
-        if (q[a] == 0 || q[a] == n[a] - 1) boundary = true;
-        r[a] = q[a] < 1 ? 1 : (q[a] > n[a] - 2 ? n[a] - 2 : q[a]);
-    }
-    if (!boundary) return;
-    const int64_t s = r[0] + (int64_t)V.nx * (r[1] + (int64_t)V.ny * r[2]);
-    for (int i = 0; i < 19; ++i) {
-        V.f[(int64_t)i * V.stride + c] = V.f[(int64_t)i * V.stride + s];
-        V.g[(int64_t)i * V.stride + c] = V.g[(int64_t)i * V.stride + s];
-    }
-    for (int i = 0; i < 25; ++i) V.h[(int64_t)i * V.stride + c] = V.h[(int64_t)i * V.stride + s];
-    for (int i = 0; i < NPRIM; ++i) V.prim[(int64_t)i * V.stride + c] = V.prim[(int64_t)i * V.stride + s];
-}
-
 // ---------------------------------------------------------------------------
 // normal-B fix on one open face (axis a, side hi): B_n of the boundary cell is
 // set so that the central-difference div B of the first interior cell
@@ -223,31 +198,41 @@ __global__ void open_copy_kernel(PopView<Cfg> V, int open_mask)
 // the normal (h_c += dB b_n / 8), and the f populations see the changed
 // equilibrium through the collision (f_c += K_i [f_i^eq(new) - f_i^eq(old)]).
 // ---------------------------------------------------------------------------
+// f_c += K_i [f_i^eq(new) - f_i^eq(old)] for the 19 populations; `fv` holds
+// their values, loaded before any store (the planes are distinct, which the
+// compiler cannot prove)
 template <int I, class Cfg, class R>
 struct FixF {
     static __device__ __forceinline__ void run(const PopView<Cfg>& V, int64_t c, const EqCell<R>& qo,
-                                               const EqCell<R>& qn)
+                                               const EqCell<R>& qn, const R* fv)
     {
         const R d = k_aw<I>(qo) * (feq_dev<I>(qn) - feq_dev<I>(qo));
-        typename Cfg::pop* p = V.f + (int64_t)I * V.stride + c;
-        const R v = ld_pop<Cfg>(p, V.hs.f[I]) + d;
-        st_pop<Cfg>(p, v, V.hs.finv[I]);
-        FixF<I + 1, Cfg, R>::run(V, c, qo, qn);
+        st_pop<Cfg>(V.f + (int64_t)I * V.stride + c, fv[I] + d, V.hs.finv[I]);
+        FixF<I + 1, Cfg, R>::run(V, c, qo, qn, fv);
     }
 };
 template <class Cfg, class R>
 struct FixF<19, Cfg, R> {
-    static __device__ __forceinline__ void run(const PopView<Cfg>&, int64_t, const EqCell<R>&, const EqCell<R>&) {}
+    static __device__ __forceinline__ void run(const PopView<Cfg>&, int64_t, const EqCell<R>&, const EqCell<R>&,
+                                               const R*)
+    {
+    }
 };
 
+// nfaces = 1: the face `hi` of axis a; nfaces = 2: both faces of axis a in one
+// launch (independent when the axis has at least 4 cells: a face writes its
+// boundary layer and reads the two layers inside it)
 template <class Cfg>
-__global__ void bfix_kernel(PopView<Cfg> V, Phys<typename Cfg::real> k, int a, int hi)
+__global__ void bfix_kernel(PopView<Cfg> V, Phys<typename Cfg::real> k, int a, int hi_first, int nfaces)
 {
     using R = typename Cfg::real;
     const int n[3] = {V.nx, V.ny, V.nz};
     const int a1 = (a + 1) % 3, a2 = (a + 2) % 3;
-    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (m >= (int64_t)n[a1] * n[a2]) return;
+    const int64_t face = (int64_t)n[a1] * n[a2];
+    const int64_t mm = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (mm >= nfaces * face) return;
+    const int hi = nfaces == 2 ? (int)(mm / face) : hi_first;
+    const int64_t m = mm % face;
     int q[3];
     q[a1] = (int)(m % n[a1]);
     q[a2] = (int)(m / n[a1]);
@@ -276,23 +261,29 @@ __global__ void bfix_kernel(PopView<Cfg> V, Phys<typename Cfg::real> k, int a, i
     const R Bn_new = Bfar + R(sgn) * R(2) * k.dx * tang;
     Prim<R> so;
     load_prim<Cfg>(V.prim, V.stride, cb, so);
+    R fv[19], hv[8];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) fv[i] = ld_pop<Cfg>(V.f + (int64_t)i * V.stride + cb, V.hs.f[i]);
+    int hp = 0;  // the plane whose normal is axis a
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+        if (plane_normal(p) == a) hp = p;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) hv[j] = (R)V.h[(int64_t)(8 * hp + j) * V.stride + cb];
     const R dB = Bn_new - so.B[a];
     Prim<R> sn = so;
     sn.B[a] = Bn_new;
     V.prim[(P_B + a) * V.stride + cb] = (typename Cfg::prim)Bn_new;
     // h: populations of the plane whose normal is axis a, b = -/+ o_p n_hat
-    for (int p = 0; p < 3; ++p) {
-        if (plane_normal(p) != a) continue;
-        for (int kk = 8 * p; kk < 8 * p + 8; ++kk) {
-            const R bn = R(((kk % 2) == 0 ? -1 : 1) * plane_orient(p));
-            typename Cfg::hpop* ph = V.h + (int64_t)kk * V.stride + cb;
-            *ph = (typename Cfg::hpop)((R)*ph + dB * bn / R(8));
-        }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const R bn = R(((j % 2) == 0 ? -1 : 1) * plane_orient(hp));
+        V.h[(int64_t)(8 * hp + j) * V.stride + cb] = (typename Cfg::hpop)(hv[j] + dB * bn / R(8));
     }
     EqCell<R> qo, qn;
     eq_cell(so, k, qo);
     eq_cell(sn, k, qn);
-    FixF<0, Cfg, R>::run(V, cb, qo, qn);
+    FixF<0, Cfg, R>::run(V, cb, qo, qn, fv);
 }
 
 // ---------------------------------------------------------------------------
@@ -547,17 +538,18 @@ template <class Cfg>
 cudaError_t launch_boundaries(const PopView<Cfg>& V, const Phys<typename Cfg::real>& k, const int* bc, int layers,
                               double u0, cudaStream_t s)
 {
-    const int64_t N = (int64_t)V.nx * V.ny * V.nz;
     const int n[3] = {V.nx, V.ny, V.nz};
-    int open_mask = 0;
-    for (int a = 0; a < 3; ++a)
-        if (bc[2 * a] != 0 || bc[2 * a + 1] != 0) open_mask |= 1 << a;
-    if (open_mask) open_copy_kernel<Cfg><<<blocks_for(N, 256), 256, 0, s>>>(V, open_mask);
-    for (int face = 0; face < 6; ++face) {
-        const int a = face / 2;
-        if (bc[face] == 0 || n[a] < 3) continue;
+    // (the copy of the interior neighbour into the open faces is done by the
+    // step kernel itself; here the normal-B fix and the driving follow it)
+    for (int a = 0; a < 3; ++a) {
+        const bool lo = bc[2 * a] != 0 && n[a] >= 3, hi = bc[2 * a + 1] != 0 && n[a] >= 3;
         const int64_t m = (int64_t)n[(a + 1) % 3] * n[(a + 2) % 3];
-        bfix_kernel<Cfg><<<blocks_for(m, 128), 128, 0, s>>>(V, k, a, face % 2);
+        if (lo && hi && n[a] >= 4) {
+            bfix_kernel<Cfg><<<blocks_for(2 * m, 128), 128, 0, s>>>(V, k, a, 0, 2);
+        } else {
+            if (lo) bfix_kernel<Cfg><<<blocks_for(m, 128), 128, 0, s>>>(V, k, a, 0, 1);
+            if (hi) bfix_kernel<Cfg><<<blocks_for(m, 128), 128, 0, s>>>(V, k, a, 1, 1);
+        }
     }
     if (bc[4] == 2 && layers > 0) {
         const int nl = layers < V.nz ? layers : V.nz;

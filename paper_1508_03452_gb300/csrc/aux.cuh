@@ -68,9 +68,9 @@ template <class Cfg>
 cudaError_t launch_step(const StepArgs<Cfg>& A, cudaStream_t stream);
 template <class Cfg>
 cudaError_t launch_step_batch(const unsigned char* d_args, const int4* d_tiles, int ntiles, int bx, int grid,
-                              bool is3d, int seed, cudaStream_t stream);
+                              bool is3d, int seed, bool open, cudaStream_t stream);
 template <class Cfg>
-int batch_blocks_per_sm(bool is3d, int seed);
+int batch_blocks_per_sm(bool is3d, int seed, bool open);
 template <class Cfg>
 cudaError_t launch_null(const PopView<Cfg>& V, int y_lo, int y_hi, const typename Cfg::prim* ez0, double B0,
                         double* scratch, int64_t scratch_doubles, double* out, cudaStream_t s);

@@ -77,6 +77,7 @@ struct StepArgs {
     int nx, ny, nz;
     int64_t stride;  // elements between consecutive planes
     int periodic[3];
+    int open_mask;  // bit a: axis a has an open (or driven) face
     int flags;
     Phys<real> k;
     HalfScale hs;

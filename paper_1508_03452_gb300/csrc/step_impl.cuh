@@ -232,7 +232,7 @@ struct StepMinBlocks {
 // cells outside the grid return at once, except in the learned-seed variant,
 // whose warp-wide MMA needs all 32 lanes: there they work on a clamped cell
 // and store nothing.
-template <class Cfg, bool IS3D, int SEED>
+template <class Cfg, bool IS3D, int SEED, bool OPEN>
 __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, const int z, const int tid,
                                           unsigned char* smem_raw)
 {
@@ -248,8 +248,25 @@ __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, 
         x = x < A.nx ? x : A.nx - 1;
         y = y < A.ny ? y : A.ny - 1;
     }
-    const Off o = make_off<IS3D>(x, y, z, A.nx, A.ny, A.nz, A.periodic);
-    const int64_t c = x + (int64_t)A.nx * (y + (int64_t)A.ny * z);
+    // Open faces (Sec. IV: the boundary cells copy their interior neighbour): a
+    // cell on an open face takes the update of the cell clamped into
+    // [1, n - 2] along every open axis, so the copy happens in this pass and
+    // lands in the ordinary coalesced stores. `c` is the cell whose update is
+    // computed (loads), `co` the cell written.
+    // The open-face code is compiled into the variant for runs with an open or
+    // driven face, and (as a run-time branch) into the learned-seed variant,
+    // whose registers are allocated better with it (15 % in a same-box A/B).
+    constexpr bool kOpenCode = OPEN || SEED == SEED_MLP;
+    int xs = x, ys = y, zs = z;
+    if (kOpenCode && A.open_mask) {
+        if ((A.open_mask & 1) && A.nx >= 3) xs = min(max(x, 1), A.nx - 2);
+        if ((A.open_mask & 2) && A.ny >= 3) ys = min(max(y, 1), A.ny - 2);
+        if ((A.open_mask & 4) && A.nz >= 3) zs = min(max(z, 1), A.nz - 2);
+    }
+    const Off o = make_off<IS3D>(xs, ys, zs, A.nx, A.ny, A.nz, A.periodic);
+    const int64_t c = xs + (int64_t)A.nx * (ys + (int64_t)A.ny * zs);
+    // offset of the written cell from the computed one (0 away from open faces)
+    const int dco = kOpenCode ? (x - xs) + A.nx * ((y - ys) + A.ny * (z - zs)) : 0;
     const Phys<R>& k = A.k;
 
     // 1. streaming of f and g (with their moments) and of h (with its moments)
@@ -368,7 +385,7 @@ __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, 
 
     if (!active) return;  // (only reached by clamped lanes of the learned-seed variant)
     if (kCanDump && A.dump != nullptr && ok) {
-        float* d = A.dump + c * (MLP_IN + MLP_OUT);
+        float* d = A.dump + (c + dco) * (MLP_IN + MLP_OUT);
         for (int j = 0; j < MLP_IN; ++j) d[j] = feat[j];
         for (int a = 0; a < 3; ++a) d[MLP_IN + a] = (float)beta[a];
         d[MLP_IN + 3] = (float)((nw.eps) / (k.eps_r + T[0][0]) - R(1));
@@ -380,21 +397,22 @@ __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, 
     for (int a = 0; a < 3; ++a) dE[a] = nw.E[a] - k.Er[a];
     EqCell<R> q;
     eq_cell(nw, n_dev, eps_dev, dE, dB, k, q);
-    CollideFG<0, Cfg>::run(A, c, sp, nth, q);
+    CollideFG<0, Cfg>::run(A, c + dco, sp, nth, q);
     const bool em_coll = (A.flags & FLAG_NO_EM_COLLISION) == 0;
     // h_c - h_ref = 2 h^eq(E - Er, B - Br, J) - (h - h_ref)  (Eq. Maxwell-eq is linear)
-    CollideH<0, Cfg>::run(A, c, sp, nth, dE, dB, J, em_coll);
-    A.hout[24 * A.stride + c] = (typename Cfg::hpop)(em_coll ? R(2) * nw.rho - sp[62 * nth] : sp[62 * nth]);
+    const int64_t co = c + dco;
+    CollideH<0, Cfg>::run(A, co, sp, nth, dE, dB, J, em_coll);
+    A.hout[24 * A.stride + co] = (typename Cfg::hpop)(em_coll ? R(2) * nw.rho - sp[62 * nth] : sp[62 * nth]);
 
-    A.pout[P_N * A.stride + c] = (typename Cfg::prim)nw.n;
-    A.pout[P_EPS * A.stride + c] = (typename Cfg::prim)nw.eps;
+    A.pout[P_N * A.stride + co] = (typename Cfg::prim)nw.n;
+    A.pout[P_EPS * A.stride + co] = (typename Cfg::prim)nw.eps;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        A.pout[(P_U + a) * A.stride + c] = (typename Cfg::prim)nw.u[a];
-        A.pout[(P_E + a) * A.stride + c] = (typename Cfg::prim)nw.E[a];
-        A.pout[(P_B + a) * A.stride + c] = (typename Cfg::prim)nw.B[a];
+        A.pout[(P_U + a) * A.stride + co] = (typename Cfg::prim)nw.u[a];
+        A.pout[(P_E + a) * A.stride + co] = (typename Cfg::prim)nw.E[a];
+        A.pout[(P_B + a) * A.stride + co] = (typename Cfg::prim)nw.B[a];
     }
-    A.pout[P_RHO * A.stride + c] = (typename Cfg::prim)nw.rho;
+    A.pout[P_RHO * A.stride + co] = (typename Cfg::prim)nw.rho;
 
     // recovery counters, aggregated per warp
     const unsigned mask = __activemask();
@@ -420,12 +438,13 @@ __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, 
 }
 
 // one run: a 2-D grid of blocks over (x, y) and z
-template <class Cfg, bool IS3D, int SEED>
+template <class Cfg, bool IS3D, int SEED, bool OPEN>
 __global__ void __launch_bounds__(kStepThreads, StepMinBlocks<Cfg, SEED>::value) step_kernel(const StepArgs<Cfg> A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    step_cell<Cfg, IS3D, SEED>(A, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y,
-                               blockIdx.z, threadIdx.x + threadIdx.y * blockDim.x, smem_raw);
+    step_cell<Cfg, IS3D, SEED, OPEN>(A, blockIdx.x * blockDim.x + threadIdx.x,
+                                     blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z,
+                                     threadIdx.x + threadIdx.y * blockDim.x, smem_raw);
 }
 
 template <class Cfg>
@@ -450,7 +469,7 @@ __host__ __device__ constexpr size_t batch_args_bytes()
 // (persistent when the grid is one wave of resident blocks). A block copies
 // the arguments of a tile's run from device memory into shared memory when
 // the run changes from its previous tile.
-template <class Cfg, bool IS3D, int SEED>
+template <class Cfg, bool IS3D, int SEED, bool OPEN>
 __global__ void __launch_bounds__(kStepThreads, StepMinBlocks<Cfg, SEED>::value)
     step_batch_kernel(const unsigned char* __restrict__ args, const int4* __restrict__ tiles, int ntiles, int bx)
 {
@@ -470,7 +489,7 @@ __global__ void __launch_bounds__(kStepThreads, StepMinBlocks<Cfg, SEED>::value)
             run = td.x;
         }
         __syncwarp();  // every lane starts a tile together (the learned seed's MMA)
-        step_cell<Cfg, IS3D, SEED>(*sA, td.y + tx, td.z + ty, td.w, tid, smem_raw);
+        step_cell<Cfg, IS3D, SEED, OPEN>(*sA, td.y + tx, td.z + ty, td.w, tid, smem_raw);
     }
 }
 
@@ -486,100 +505,125 @@ size_t batch_smem_bytes(int seed)
     return step_cell_smem<Cfg>(seed) + batch_args_bytes<Cfg>();
 }
 
+// Calls f.template run<IS3D, SEED, OPEN>() for the kernel variant of a run:
+// 2-D / 3-D, recovery seed, periodic only / with an open or driven face.
+template <class F>
+cudaError_t dispatch_variant(bool is3d, int seed, bool open, F&& f)
+{
+#define LB_VARIANT(D, S, O) \
+    if (is3d == D && seed == S && open == O) return f.template run<D, S, O>();
+    LB_VARIANT(false, SEED_PREV, false)
+    LB_VARIANT(false, SEED_PREV, true)
+    LB_VARIANT(false, SEED_COLD, false)
+    LB_VARIANT(false, SEED_COLD, true)
+    LB_VARIANT(false, SEED_MLP, false)
+    LB_VARIANT(false, SEED_MLP, true)
+    LB_VARIANT(true, SEED_PREV, false)
+    LB_VARIANT(true, SEED_PREV, true)
+    LB_VARIANT(true, SEED_COLD, false)
+    LB_VARIANT(true, SEED_COLD, true)
+    LB_VARIANT(true, SEED_MLP, false)
+    LB_VARIANT(true, SEED_MLP, true)
+#undef LB_VARIANT
+    return cudaErrorInvalidValue;
+}
+
+template <class Cfg>
+struct SetSmemAttr {
+    template <bool D, int S, bool O>
+    cudaError_t run()
+    {
+        const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        cudaError_t e = cudaFuncSetAttribute(step_kernel<Cfg, D, S, O>, a, (int)step_smem_bytes<Cfg>(S));
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(step_batch_kernel<Cfg, D, S, O>, a, (int)batch_smem_bytes<Cfg>(S));
+        return e;
+    }
+};
+
 template <class Cfg>
 cudaError_t configure_step_kernels()
 {
     static bool configured = false;  // one attribute call per instantiation
     if (configured) return cudaSuccess;
-    const int b = (int)step_smem_bytes<Cfg>(SEED_PREV), m = (int)step_smem_bytes<Cfg>(SEED_MLP);
-    const int bb = (int)batch_smem_bytes<Cfg>(SEED_PREV), bm = (int)batch_smem_bytes<Cfg>(SEED_MLP);
-    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<Cfg, true, SEED_PREV>, a, b);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<Cfg, false, SEED_PREV>, a, b);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<Cfg, true, SEED_COLD>, a, b);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<Cfg, false, SEED_COLD>, a, b);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<Cfg, true, SEED_MLP>, a, m);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_kernel<Cfg, false, SEED_MLP>, a, m);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_batch_kernel<Cfg, true, SEED_PREV>, a, bb);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_batch_kernel<Cfg, false, SEED_PREV>, a, bb);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_batch_kernel<Cfg, true, SEED_COLD>, a, bb);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_batch_kernel<Cfg, false, SEED_COLD>, a, bb);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_batch_kernel<Cfg, true, SEED_MLP>, a, bm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(step_batch_kernel<Cfg, false, SEED_MLP>, a, bm);
-    if (e == cudaSuccess) configured = true;
-    return e;
+    for (int d = 0; d < 2; ++d)
+        for (int seed = 0; seed < 3; ++seed)
+            for (int o = 0; o < 2; ++o) {
+                const cudaError_t e = dispatch_variant(d == 1, seed, o == 1, SetSmemAttr<Cfg>{});
+                if (e != cudaSuccess) return e;
+            }
+    configured = true;
+    return cudaSuccess;
 }
+
+template <class Cfg>
+struct BatchOccupancy {
+    int* nb;
+    template <bool D, int S, bool O>
+    cudaError_t run()
+    {
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, step_batch_kernel<Cfg, D, S, O>, kStepThreads,
+                                                             batch_smem_bytes<Cfg>(S));
+    }
+};
 
 // resident blocks per SM of the batched kernel (for a one-wave persistent grid)
 template <class Cfg>
-int batch_blocks_per_sm(bool is3d, int seed)
+int batch_blocks_per_sm(bool is3d, int seed, bool open)
 {
-    cudaError_t e = configure_step_kernels<Cfg>();
-    if (e != cudaSuccess) return 0;
+    if (configure_step_kernels<Cfg>() != cudaSuccess) return 0;
     int nb = 0;
-    const size_t smem = batch_smem_bytes<Cfg>(seed);
-    if (seed == SEED_MLP)
-        e = is3d ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_batch_kernel<Cfg, true, SEED_MLP>, kStepThreads, smem)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_batch_kernel<Cfg, false, SEED_MLP>, kStepThreads, smem);
-    else if (seed == SEED_COLD)
-        e = is3d ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_batch_kernel<Cfg, true, SEED_COLD>, kStepThreads, smem)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_batch_kernel<Cfg, false, SEED_COLD>, kStepThreads, smem);
-    else
-        e = is3d ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_batch_kernel<Cfg, true, SEED_PREV>, kStepThreads, smem)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_batch_kernel<Cfg, false, SEED_PREV>, kStepThreads, smem);
-    return e == cudaSuccess ? nb : 0;
+    return dispatch_variant(is3d, seed, open, BatchOccupancy<Cfg>{&nb}) == cudaSuccess ? nb : 0;
 }
 
 template <class Cfg>
+struct LaunchBatch {
+    const unsigned char* args;
+    const int4* tiles;
+    int ntiles, bx, grid;
+    cudaStream_t stream;
+    template <bool D, int S, bool O>
+    cudaError_t run()
+    {
+        step_batch_kernel<Cfg, D, S, O><<<grid, kStepThreads, batch_smem_bytes<Cfg>(S), stream>>>(args, tiles, ntiles, bx);
+        return cudaGetLastError();
+    }
+};
+
+template <class Cfg>
 cudaError_t launch_step_batch(const unsigned char* d_args, const int4* d_tiles, int ntiles, int bx, int grid,
-                              bool is3d, int seed, cudaStream_t stream)
+                              bool is3d, int seed, bool open, cudaStream_t stream)
 {
     if (ntiles <= 0) return cudaSuccess;
     if (bx != 32 && bx != 64 && bx != 128) return cudaErrorInvalidValue;
-    cudaError_t e = configure_step_kernels<Cfg>();
+    const cudaError_t e = configure_step_kernels<Cfg>();
     if (e != cudaSuccess) return e;
-    const size_t smem = batch_smem_bytes<Cfg>(seed);
     const int g = grid > 0 && grid < ntiles ? grid : ntiles;
-    if (seed == SEED_MLP) {
-        if (is3d) step_batch_kernel<Cfg, true, SEED_MLP><<<g, kStepThreads, smem, stream>>>(d_args, d_tiles, ntiles, bx);
-        else step_batch_kernel<Cfg, false, SEED_MLP><<<g, kStepThreads, smem, stream>>>(d_args, d_tiles, ntiles, bx);
-    } else if (seed == SEED_COLD) {
-        if (is3d) step_batch_kernel<Cfg, true, SEED_COLD><<<g, kStepThreads, smem, stream>>>(d_args, d_tiles, ntiles, bx);
-        else step_batch_kernel<Cfg, false, SEED_COLD><<<g, kStepThreads, smem, stream>>>(d_args, d_tiles, ntiles, bx);
-    } else {
-        if (is3d) step_batch_kernel<Cfg, true, SEED_PREV><<<g, kStepThreads, smem, stream>>>(d_args, d_tiles, ntiles, bx);
-        else step_batch_kernel<Cfg, false, SEED_PREV><<<g, kStepThreads, smem, stream>>>(d_args, d_tiles, ntiles, bx);
-    }
-    return cudaGetLastError();
+    return dispatch_variant(is3d, seed, open, LaunchBatch<Cfg>{d_args, d_tiles, ntiles, bx, g, stream});
 }
+
+template <class Cfg>
+struct LaunchRun {
+    const StepArgs<Cfg>* A;
+    dim3 grid, block;
+    cudaStream_t stream;
+    template <bool D, int S, bool O>
+    cudaError_t run()
+    {
+        step_kernel<Cfg, D, S, O><<<grid, block, step_smem_bytes<Cfg>(S), stream>>>(*A);
+        return cudaGetLastError();
+    }
+};
 
 template <class Cfg>
 cudaError_t launch_step(const StepArgs<Cfg>& A, cudaStream_t stream)
 {
     const int bx = A.nx >= LB_STEP_BX ? LB_STEP_BX : (A.nx >= 64 ? 64 : 32);
     const int by = kStepThreads / bx;
-    const size_t smem_base = step_smem_bytes<Cfg>(SEED_PREV), smem_mlp = step_smem_bytes<Cfg>(SEED_MLP);
     const cudaError_t ce = configure_step_kernels<Cfg>();
     if (ce != cudaSuccess) return ce;
-    dim3 block(bx, by, 1);
-    dim3 grid((A.nx + bx - 1) / bx, (A.ny + by - 1) / by, A.nz);
-    const bool d3 = A.nz > 1;
-    switch (A.seed) {
-        case SEED_MLP:
-            if (d3) step_kernel<Cfg, true, SEED_MLP><<<grid, block, smem_mlp, stream>>>(A);
-            else step_kernel<Cfg, false, SEED_MLP><<<grid, block, smem_mlp, stream>>>(A);
-            break;
-        case SEED_COLD:
-            if (d3) step_kernel<Cfg, true, SEED_COLD><<<grid, block, smem_base, stream>>>(A);
-            else step_kernel<Cfg, false, SEED_COLD><<<grid, block, smem_base, stream>>>(A);
-            break;
-        default:
-            if (d3) step_kernel<Cfg, true, SEED_PREV><<<grid, block, smem_base, stream>>>(A);
-            else step_kernel<Cfg, false, SEED_PREV><<<grid, block, smem_base, stream>>>(A);
-            break;
-    }
-    return cudaGetLastError();
+    const dim3 block(bx, by, 1);
+    const dim3 grid((A.nx + bx - 1) / bx, (A.ny + by - 1) / by, A.nz);
+    return dispatch_variant(A.nz > 1, A.seed, A.open_mask != 0, LaunchRun<Cfg>{&A, grid, block, stream});
 }
 
 }  // namespace lb
