@@ -36,6 +36,7 @@ struct RunState {
     int periodic[3] = {1, 1, 1};
     float* d_samples = nullptr;  // caller-owned training-sample buffer (or NULL)
     void* d_ez0 = nullptr;       // E^z of the initial state (primitive type, N), for the reconnection rate
+    double* d_drive = nullptr;   // drive velocity per (x, y) column (driven runs)
 };
 
 constexpr size_t kStatsBytes = lb::kNumStats * sizeof(unsigned long long);  // totals (checkpoint)
@@ -396,7 +397,7 @@ int issue_step(lbrmhd_handle h, const lbrmhd_schedule& sc, int in, cudaStream_t 
     for (const auto& r : h->runs)
         if (has_open(r))
             LB_CK(lb::launch_boundaries<Cfg>(view<Cfg>(r, out), make_phys<R>(r.p, r.ref, runref(r)), r.p.bc,
-                                             r.p.drive_layers, r.p.drive_u0, s));
+                                             r.p.drive_layers, r.d_drive, s));
     return LBRMHD_OK;
 }
 
@@ -440,7 +441,7 @@ int issue_steps(lbrmhd_handle h, const lbrmhd_schedule& sc, int in, int64_t n, c
             LB_CK(lb::launch_step<Cfg>(make_args<Cfg>(h, r, cin), st));
             if (has_open(r))
                 LB_CK(lb::launch_boundaries<Cfg>(view<Cfg>(r, 1 - cin), make_phys<R>(r.p, r.ref, runref(r)), r.p.bc,
-                                                 r.p.drive_layers, r.p.drive_u0, st));
+                                                 r.p.drive_layers, r.d_drive, st));
         }
     }
     for (int i = 0; i < S; ++i) {
@@ -839,6 +840,10 @@ int lbrmhd_create(const lbrmhd_params* params, int n_runs, lbrmhd_handle* out)
             }
         }
         ok = ok && cudaMalloc(&s.d_ez0, s.N * qb) == cudaSuccess;
+        if (ok && s.p.bc[4] == LBRMHD_DRIVEN) {
+            ok = cudaMalloc(&s.d_drive, 2 * sizeof(double) * s.p.nx * s.p.ny) == cudaSuccess;
+            ok = ok && lb::launch_drive_profile(s.p.nx, s.p.ny, s.p.drive_u0, s.d_drive, nullptr) == cudaSuccess;
+        }
         ok = ok && cudaMalloc(&s.d_stats, kStatsAlloc) == cudaSuccess;
         if (ok) cudaMemset(s.d_stats, 0, kStatsAlloc);
         max_blocks = std::max<int64_t>(max_blocks, (s.N + lb::kDiagThreads - 1) / lb::kDiagThreads);
@@ -875,6 +880,7 @@ int lbrmhd_destroy(lbrmhd_handle h)
         }
         if (r.d_stats) cudaFree(r.d_stats);
         if (r.d_ez0) cudaFree(r.d_ez0);
+        if (r.d_drive) cudaFree(r.d_drive);
     }
     if (h->d_scratch) cudaFree(h->d_scratch);
     if (h->d_io) cudaFree(h->d_io);

@@ -291,23 +291,33 @@ __global__ void bfix_kernel(PopView<Cfg> V, Phys<typename Cfg::real> k, int a, i
 // equilibrium of their own n, eps, B, rho_c with the two-vortex drive velocity
 // (max |u| = u0) and E = -u x B
 // ---------------------------------------------------------------------------
+// the two-vortex drive velocity of column (x, y), (u_x, u_y) with max |u| = u0:
+// tabulated once per run (it does not change in time)
+__global__ void drive_profile_kernel(int nx, int ny, double u0, double* uv)
+{
+    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (m >= (int64_t)nx * ny) return;
+    const int x = (int)(m % nx), y = (int)(m / nx);
+    const double X = -3.0 + (x + 0.5) * 6.0 / nx;
+    const double Y = -3.0 + (y + 0.5) * 6.0 / ny;
+    const double xs = X < 0.0 ? X : X - 3.0;
+    const double pi = 3.14159265358979323846;
+    uv[2 * m] = u0 * sin(pi * xs / 3.0) * cos(pi * Y / 6.0);
+    uv[2 * m + 1] = u0 * cos(pi * xs / 3.0) * sin(pi * Y / 6.0);
+}
+
 template <class Cfg>
-__global__ void drive_kernel(PopView<Cfg> V, Phys<typename Cfg::real> k, int layers, double u0)
+__global__ void drive_kernel(PopView<Cfg> V, Phys<typename Cfg::real> k, int layers, const double* __restrict__ uv)
 {
     using R = typename Cfg::real;
     const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t plane = (int64_t)V.nx * V.ny;
     if (m >= plane * layers) return;
-    const int x = (int)(m % V.nx), y = (int)((m / V.nx) % V.ny);
-    const int64_t c = m;
-    const double X = -3.0 + (x + 0.5) * 6.0 / V.nx;
-    const double Y = -3.0 + (y + 0.5) * 6.0 / V.ny;
-    const double xs = X < 0.0 ? X : X - 3.0;
-    const double pi = 3.14159265358979323846;
+    const int64_t c = m, col = m % plane;
     Prim<R> s;
     load_prim<Cfg>(V.prim, V.stride, c, s);
-    s.u[0] = (R)(u0 * sin(pi * xs / 3.0) * cos(pi * Y / 6.0));
-    s.u[1] = (R)(u0 * cos(pi * xs / 3.0) * sin(pi * Y / 6.0));
+    s.u[0] = (R)uv[2 * col];
+    s.u[1] = (R)uv[2 * col + 1];
     s.u[2] = R(0);
     s.E[0] = -(s.u[1] * s.B[2] - s.u[2] * s.B[1]);
     s.E[1] = -(s.u[2] * s.B[0] - s.u[0] * s.B[2]);
@@ -534,9 +544,15 @@ cudaError_t launch_means(const InitInputs& in, int64_t N, double* partial, doubl
     return cudaGetLastError();
 }
 
+cudaError_t launch_drive_profile(int nx, int ny, double u0, double* uv, cudaStream_t s)
+{
+    drive_profile_kernel<<<blocks_for((int64_t)nx * ny, 256), 256, 0, s>>>(nx, ny, u0, uv);
+    return cudaGetLastError();
+}
+
 template <class Cfg>
 cudaError_t launch_boundaries(const PopView<Cfg>& V, const Phys<typename Cfg::real>& k, const int* bc, int layers,
-                              double u0, cudaStream_t s)
+                              const double* drive_uv, cudaStream_t s)
 {
     const int n[3] = {V.nx, V.ny, V.nz};
     // (the copy of the interior neighbour into the open faces is done by the
@@ -551,9 +567,9 @@ cudaError_t launch_boundaries(const PopView<Cfg>& V, const Phys<typename Cfg::re
             if (hi) bfix_kernel<Cfg><<<blocks_for(m, 128), 128, 0, s>>>(V, k, a, 1, 1);
         }
     }
-    if (bc[4] == 2 && layers > 0) {
+    if (bc[4] == 2 && layers > 0 && drive_uv) {
         const int nl = layers < V.nz ? layers : V.nz;
-        drive_kernel<Cfg><<<blocks_for((int64_t)V.nx * V.ny * nl, 128), 128, 0, s>>>(V, k, nl, u0);
+        drive_kernel<Cfg><<<blocks_for((int64_t)V.nx * V.ny * nl, 128), 128, 0, s>>>(V, k, nl, drive_uv);
     }
     return cudaGetLastError();
 }
@@ -604,7 +620,7 @@ cudaError_t launch_null(const PopView<Cfg>& V, int y_lo, int y_hi, const typenam
     template cudaError_t launch_init<CFG>(const PopView<CFG>&, const InitInputs&, const Phys<double>&, int*,      \
                                           cudaStream_t);                                                           \
     template cudaError_t launch_boundaries<CFG>(const PopView<CFG>&, const Phys<CFG::real>&, const int*, int,      \
-                                                double, cudaStream_t);                                             \
+                                                const double*, cudaStream_t);                                      \
     template cudaError_t launch_moments<CFG>(const PopView<CFG>&, const Phys<double>&, double*, cudaStream_t);     \
     template cudaError_t launch_populations<CFG>(const PopView<CFG>&, const RefPops&, double*, double*, double*,  \
                                                  cudaStream_t);                                                    \

@@ -85,7 +85,9 @@ cudaError_t launch_init(const PopView<Cfg>& V, const InitInputs& in, const Phys<
 cudaError_t launch_means(const InitInputs& in, int64_t N, double* partial, double* out, cudaStream_t s);
 template <class Cfg>
 cudaError_t launch_boundaries(const PopView<Cfg>& V, const Phys<typename Cfg::real>& k, const int* bc, int layers,
-                              double u0, cudaStream_t s);
+                              const double* drive_uv, cudaStream_t s);
+// the drive velocity of every (x, y) column (2 float64 each) for a driven run
+cudaError_t launch_drive_profile(int nx, int ny, double u0, double* uv, cudaStream_t s);
 template <class Cfg>
 cudaError_t launch_moments(const PopView<Cfg>& V, const Phys<double>& k, double* out, cudaStream_t s);
 template <class Cfg>
