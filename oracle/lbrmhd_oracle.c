@@ -65,6 +65,23 @@
  *       number-density lattice weights w'_i; nu = sqrt(27), i.e. c_t = c_0.
  *   R23 after the E solve, J is taken from Eq. Ex_force (equal to Eq. Ohm at
  *       the solution, and well conditioned at large sigma).
+ *   R24 the E, B in the eigen-solve's tensor T - eps0 F F: the coupling
+ *       subsection takes the fields of the previous time step. Taken
+ *       literally (one pass), the collision that follows re-inserts the EM
+ *       momentum of the new fields into T^{mu nu} without the fluid paying
+ *       for it, so the EM inertia drops out: the Alfven speed comes out as
+ *       B0 c / sqrt(eps + p) instead of B0 c / sqrt(eps + p + B0^2), 9.6 %
+ *       fast in the paper's own Alfven test (v_A = 0.40785), whose pulse then
+ *       misses the analytic solution by 35 % at t = 1. Reading: the previous
+ *       step's E is the starting point of a fixed-point iteration in which the
+ *       tensor is formed with the E that Ohm's law gives for the recovered
+ *       velocity (and the B of the streamed h), until that E reproduces
+ *       itself; the collision at the new time level then conserves
+ *       T^{mu nu}. Each update is relaxed by 1 / (1 + r), r = B^2 k/(1+k) /
+ *       (w gamma^2) the EM-to-fluid inertia ratio (k of Eq. Ohm's implicit
+ *       solve), which makes it exact for the linearised ideal problem and
+ *       keeps it convergent when B^2 > eps + p. The literal one-pass reading
+ *       is the ORC_ONE_PASS_RECOVERY test switch.
  *
  * Units: mu_0 = 1, eps_0 = 1/(mu_0 c^2); dt = dx / (sqrt(2) c) (Sec. III,
  * time-step synchronisation).
@@ -419,17 +436,47 @@ int orc_recover_cell(const orc_params* P, const orc_lattice* L, const double* f,
     const double* up = prim_prev + ORC_U;
     const double gp = 1.0 / sqrt(1.0 - dot3(up, up) / (c * c));
     const double seed[4] = {gp, gp * up[0] / c, gp * up[1] / c, gp * up[2] / c};
-    double U[4], lambda;
-    int it = orc_landau(P, T, prim_prev + ORC_E, prim_prev + ORC_B, seed, U, &lambda);
-    if (it < 0) return -1;
-    const double* Eo = prim_prev + ORC_E;
-    const double* Bo = prim_prev + ORC_B;
-    /* eigenvalue = eps + (eps0/2)(c^2 B^2 - E^2), E and B of the previous step */
+    double U[4], lambda, u[3], E[3], J[3];
+    /* Ec, Bc: the fields of the tensor T - eps0 F F (R13, R24) */
+    double Ec[3], Bc[3];
+    for (int a = 0; a < 3; ++a) {
+        Ec[a] = prim_prev[ORC_E + a];
+        Bc[a] = (P->flags & ORC_ONE_PASS_RECOVERY) ? prim_prev[ORC_B + a] : B[a];
+    }
+    double sd[4] = {seed[0], seed[1], seed[2], seed[3]};
+    int it = 0;
+    /* the inner solve leaves relative noise ~ power_tol in E: the outer test
+     * asks for 100 x that, and a residual that stops decreasing near it is at
+     * its round-off floor */
+    const double tol = 100.0 * (P->power_tol > 0 ? P->power_tol : 1e-14);
+    double d_prev = INFINITY;
+    for (int outer = 0;; ++outer) {
+        if (outer == 64) return -1; /* the fields did not settle */
+        const int i1 = orc_landau(P, T, Ec, Bc, sd, U, &lambda);
+        if (i1 < 0) return -1;
+        it += i1;
+        for (int a = 0; a < 3; ++a) u[a] = c * U[a + 1] / U[0];
+        orc_ohm_solve(P, Ep, u, B, rho_c, E);
+        if (P->flags & ORC_ONE_PASS_RECOVERY) break;
+        double d = 0.0;
+        for (int a = 0; a < 3; ++a) d += (E[a] - Ec[a]) * (E[a] - Ec[a]);
+        const double scale = sqrt(dot3(E, E)) + 1e-6 * c * sqrt(dot3(B, B)) + 1e-300;
+        if (sqrt(d) <= tol * scale || (d >= d_prev && sqrt(d) <= 1e3 * tol * scale)) break;
+        d_prev = d;
+        /* relaxed update of the tensor's E (R24) */
+        const double epsk = lambda - 0.5 * eps0_of(P) * (c * c * dot3(Bc, Bc) - dot3(Ec, Ec));
+        const double nk = N[0] / U[0];
+        const double w = epsk + (P->gamma_ad - 1.0) * (epsk - nk * c * c);
+        const double kk = 0.5 * orc_dt(P) * c * c * P->sigma * U[0];
+        const double r = dot3(B, B) * (kk / (1.0 + kk)) / (w * U[0] * U[0]);
+        for (int a = 0; a < 3; ++a) Ec[a] += (E[a] - Ec[a]) / (1.0 + r);
+        for (int a = 0; a < 4; ++a) sd[a] = U[a];
+    }
+    const double* Eo = Ec;
+    const double* Bo = Bc;
+    /* eigenvalue = eps + (eps0/2)(c^2 B^2 - E^2), E and B of the tensor */
     const double eps = lambda - 0.5 * eps0_of(P) * (c * c * dot3(Bo, Bo) - dot3(Eo, Eo));
     const double n = N[0] / U[0]; /* R15; both in units with U^0 = gamma */
-    double u[3] = {c * U[1] / U[0], c * U[2] / U[0], c * U[3] / U[0]};
-    double E[3], J[3];
-    orc_ohm_solve(P, Ep, u, B, rho_c, E);
     /* R23: J at the solution of Eq. Ex_force, J = (E' - E) / ((dt/2) mu0 c^2),
      * which equals Eq. Ohm there; Eq. Ohm evaluated directly loses
      * log10(sigma |u x B| / |J|) digits at large sigma. */

@@ -34,6 +34,7 @@ extern "C" {
 #define ORC_FIRST_ORDER 2     /* limiter phi = 0: first-order upwind streaming */
 #define ORC_IMPLICIT_AS_PRINTED 4 /* collision term implicit in f(t+dt) towards f^eq(t) */
 #define ORC_PRINTED_FEQ 8     /* delta_{i0} term and nu^2/5 sign of Eq. Dis_fun_EM exactly as printed */
+#define ORC_ONE_PASS_RECOVERY 16 /* eigen-solve once, with E and B of the previous step (R24 taken literally) */
 
 /* primitive layout of one cell (field-major planes in the simulation) */
 #define ORC_N 0
@@ -57,7 +58,8 @@ typedef struct orc_params {
     double nu;            /* temperature parameter; <= 0 selects sqrt(27) */
     double drive_u0;      /* peak drive speed of the driven layers */
     int32_t drive_layers; /* number of driven z-layers above the -z face */
-    int32_t flags;        /* ORC_NO_EM_COLLISION | ORC_FIRST_ORDER | ORC_IMPLICIT_AS_PRINTED | ORC_PRINTED_FEQ */
+    int32_t flags;        /* ORC_NO_EM_COLLISION | ORC_FIRST_ORDER | ORC_IMPLICIT_AS_PRINTED | ORC_PRINTED_FEQ |
+                             ORC_ONE_PASS_RECOVERY */
     int32_t threads;      /* OpenMP threads (0: runtime default) */
     int32_t max_power_iters;
     double power_tol;

@@ -205,3 +205,23 @@ def mlp_init_params(seed: int = 0) -> np.ndarray:
         parts.append(r.normal(0.0, scale * math.sqrt(2.0 / fan_in), size=fan_out * fan_in))
         parts.append(np.zeros(fan_out))
     return np.concatenate(parts).astype(np.float32)
+
+
+def alfven_paper(ncell=400, *, B0=1.0, By=0.1, eta_A=0.118591, vA=0.40785, n0=1.0, p0=1.0, x0=-0.8,
+                 x1=0.0) -> Fields:
+    """The paper's nonlinear Alfven-wave test (Sec. IV, Alfven-wave subsection):
+    x in [-1, 1] with `ncell` cells, n = p = 1, B = (B0, By, B^z), and inside
+    x0 < x < x1 the pulse B^z = eta_A B0 sin(2 pi (3 s^2 - 2 s^3)), s = (x - x0)
+    / (x1 - x0), with u^z = -(v_A / B0) B^z (zero outside). dx = 2 / ncell."""
+    dx = 2.0 / ncell
+    x = -1.0 + (np.arange(ncell) + 0.5) * dx
+    s = (x - x0) / (x1 - x0)
+    inside = (x > x0) & (x < x1)
+    Bz = np.where(inside, eta_A * B0 * np.sin(2.0 * math.pi * (3.0 * s * s - 2.0 * s ** 3)), 0.0)
+    u = np.zeros((3, ncell))
+    u[2] = -(vA / B0) * Bz
+    B = np.zeros((3, ncell))
+    B[0], B[1], B[2] = B0, By, Bz
+    return Fields(ncell, 1, 1, np.full(ncell, n0), np.full(ncell, p0), u, B,
+                  meta={"workload": "alfven_paper", "dx": dx, "x": x, "vA": vA, "x0": x0, "x1": x1,
+                        "eta_A": eta_A, "B0": B0})

@@ -212,3 +212,52 @@ def test_driven_layers_hold_the_drive():
                 d = O.drive_velocity(P, x, y)
                 assert abs(ux[z, y, x] - d[0]) < 1e-15 and abs(uy[z, y, x] - d[1]) < 1e-15
     assert np.sqrt(ux[0] ** 2 + uy[0] ** 2).max() <= 0.05 + 1e-15
+
+
+def _alfven_pulse_error(t_end, flags=0):
+    """The paper's nonlinear Alfven test (Sec. IV, Alfven-wave subsection): 400
+    cells on [-1, 1], n = p = 1, B = (1, 0.1, B^z), the pulse of amplitude
+    eta_A B0 on (-0.8, 0), sigma = 1e5, open faces; relative L2 distance of
+    B^z at t_end to the initial pulse shifted by the printed v_A = 0.40785."""
+    g = json.load(open(os.path.join(GOLDEN, "alfven_speed.json")))
+    F = W.alfven_paper(400, B0=g["B0"], eta_A=g["eta_A"], vA=g["v_A"])
+    x, dx = F.meta["x"], F.meta["dx"]
+    s, P = _sim(F, sigma=1e5, dx=dx, bc=(OPEN, OPEN, PER, PER, PER, PER), flags=flags)
+    steps = int(round(t_end / O.dt(P)))
+    s.step(steps)
+    t = steps * O.dt(P)
+    xs = (x - g["v_A"] * t - F.meta["x0"]) / (F.meta["x1"] - F.meta["x0"])
+    exact = np.where((xs > 0) & (xs < 1), g["eta_A"] * g["B0"] * np.sin(2 * np.pi * (3 * xs ** 2 - 2 * xs ** 3)), 0.0)
+    assert s.stats()["recover_fail"] == 0
+    return np.linalg.norm(s.moments()[11] - exact) / np.linalg.norm(exact)
+
+
+def test_paper_alfven_pulse_travels_at_printed_speed():
+    """The paper's ideal-MHD Alfven pulse lands on the analytic solution (the
+    initial pulse shifted by v_A = 0.40785) at t = 1 and t = 1.5."""
+    assert _alfven_pulse_error(1.0) < 0.05
+    assert _alfven_pulse_error(1.5) < 0.06
+
+
+def test_one_pass_recovery_misses_the_em_inertia():
+    """Reading R24: with the eigen-solve done once with the previous step's
+    fields, the EM momentum drops out of the inertia. The linear Alfven wave at
+    B0 = 1 (eps + p = 5) then travels at B0 / sqrt(eps + p) = 0.447 instead of
+    B0 / sqrt(eps + p + B0^2) = 0.408; the self-consistent solve gets 0.408,
+    and the paper's pulse misses by a third."""
+    def speed(flags):
+        nx, B0 = 64, 1.0
+        F = W.alfven_wave(nx, 1, 1, B0=B0)
+        s, P = _sim(F, sigma=1e6, flags=flags)
+        vA, k = F.meta["vA"], 2 * np.pi / nx
+        nsteps = int(round(0.25 * nx / (vA * O.dt(P))))
+        mode = lambda a: np.fft.fft(a)[1]
+        m0 = s.moments()
+        s.step(nsteps)
+        m = s.moments()
+        R0 = mode(m0[11]) - (B0 / vA) * mode(m0[5])
+        R = mode(m[11]) - (B0 / vA) * mode(m[5])
+        return -np.angle(R / R0) / k / (nsteps * O.dt(P))
+    assert abs(speed(0) / (1.0 / math.sqrt(6.0)) - 1) < 0.01
+    assert abs(speed(O.ONE_PASS_RECOVERY) / (1.0 / math.sqrt(5.0)) - 1) < 0.01
+    assert _alfven_pulse_error(1.0, flags=O.ONE_PASS_RECOVERY) > 0.25
