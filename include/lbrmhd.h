@@ -74,6 +74,9 @@ extern "C" {
 /* switches (flags) */
 #define LBRMHD_FLAG_NO_EM_COLLISION 1 /* h is streamed without collision: h(x + v dt, t + dt) = h(x, t) */
 #define LBRMHD_FLAG_UNSHIFTED_POWER 2 /* recovery by the plain power method (no spectral shift) */
+#define LBRMHD_FLAG_ONE_PASS_RECOVERY 4 /* one eigen-solve with the previous step's E, B (the coupling
+                                          subsection taken literally: loses the EM inertia, see the
+                                          self-consistent recovery in lbrmhd_step) */
 
 /* rows of lbrmhd_get_moments output (each row N values) */
 #define LBRMHD_NMOMENTS 16 /* n, p, eps, u(3), E(3), B(3), rho_c, J(3) */
@@ -131,7 +134,11 @@ int lbrmhd_init_fields_device(lbrmhd_handle h, int run, const double* n, const d
                               const double* B, const double* E);
 
 /* Advances every run by nsteps time steps (asynchronous on the handle's
- * stream). Recovery failures are counted per run (lbrmhd_get_stats) and the
+ * stream). The primitive recovery is self-consistent: the eigen-solve of the
+ * coupling subsection (Sec. III) starts from the previous step's E and is
+ * repeated with the E that Ohm's law gives for the recovered velocity (and
+ * the streamed B) until that E reproduces itself, so that the collision
+ * conserves T^{mu nu} and the EM momentum keeps its inertia. Recovery failures are counted per run (lbrmhd_get_stats) and the
  * affected cells keep their previous primitives. Errors: STATE (a run was
  * never initialised), BAD_ARG (nsteps < 0), CUDA. */
 int lbrmhd_step(lbrmhd_handle h, int64_t nsteps);

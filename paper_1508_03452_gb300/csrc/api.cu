@@ -602,7 +602,8 @@ std::string check_params(const lbrmhd_params& p)
     if (p.precision < LBRMHD_FP64 || p.precision > LBRMHD_FP16_DEV) return "unknown precision";
     if (p.recovery != LBRMHD_RECOVERY_PLAIN && p.recovery != LBRMHD_RECOVERY_MLP && p.recovery != LBRMHD_RECOVERY_COLD)
         return "unknown recovery mode";
-    if (p.flags & ~(LBRMHD_FLAG_NO_EM_COLLISION | LBRMHD_FLAG_UNSHIFTED_POWER)) return "unknown flag";
+    if (p.flags & ~(LBRMHD_FLAG_NO_EM_COLLISION | LBRMHD_FLAG_UNSHIFTED_POWER | LBRMHD_FLAG_ONE_PASS_RECOVERY))
+        return "unknown flag";
     for (int f = 0; f < 6; ++f) {
         if (p.bc[f] < 0 || p.bc[f] > 2) return "unknown boundary kind";
         if (p.bc[f] == LBRMHD_DRIVEN && f != 4) return "DRIVEN is only allowed on the -z face";

@@ -328,19 +328,19 @@ __device__ __forceinline__ void ohm_current(const R* E, const R* u, const R* B, 
 
 // ---------------------------------------------------------------------------
 // Landau eigen-solve (coupling subsection): largest eigenpair of
-// A = [T - eps0 F F(E_old, B_old)] eta by a power iteration, shifted by
-// p_old - s_old (which pushes the spacelike eigenvalues to ~0) unless
-// `shifted` is false (the paper's plain power method), started from the
-// velocity `seed` (beta). T holds the moments with eps_r taken out of T^00
-// (the reference rest state's other entries included); the returned lambda is
-// the eigenvalue minus eps_r. Returns the iteration count, or -1 if it failed.
+// A = [T - eps0 F F(E, B)] eta by a power iteration, shifted by p_old - s
+// (s = eps0 (c^2 B^2 - E^2) / 2; the shift pushes the spacelike eigenvalues
+// to ~0) unless `shifted` is false (the paper's plain power method), started
+// from the velocity `seed` (beta); convergence is accepted from iteration
+// `min_it` on. T holds the moments with eps_r taken out of T^00 (the
+// reference rest state's other entries included); the returned lambda is the
+// eigenvalue minus eps_r, s_old the s of (E, B). Returns the iteration count,
+// or -1 if it failed.
 // ---------------------------------------------------------------------------
 template <class R>
-__device__ __forceinline__ int landau(const R T[4][4], const Prim<R>& old, const Phys<R>& k, R beta[3], R& lambda,
-                                      R& s_old, const R* seed, bool shifted)
+__device__ __forceinline__ int landau(const R T[4][4], const R* E, const R* B, R p_old, const Phys<R>& k, R beta[3],
+                                      R& lambda, R& s_old, const R* seed, bool shifted, int min_it)
 {
-    const R* E = old.E;
-    const R* B = old.B;
     const R E2 = E[0] * E[0] + E[1] * E[1] + E[2] * E[2];
     const R B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
     const R ExB[3] = {E[1] * B[2] - E[2] * B[1], E[2] * B[0] - E[0] * B[2], E[0] * B[1] - E[1] * B[0]};
@@ -359,7 +359,6 @@ __device__ __forceinline__ int landau(const R T[4][4], const Prim<R>& old, const
         }
     }
     s_old = R(0.5) * k.eps0 * (k.c2 * B2 - E2);
-    const R p_old = k.gm1 * (old.eps - old.n * k.c2);
     const R shift = shifted ? p_old - s_old : R(0);
     const R a00_full = k.eps_r + shift;  // eps_r restored in the first row only
     R v1 = seed[0], v2 = seed[1], v3 = seed[2];
@@ -375,7 +374,7 @@ __device__ __forceinline__ int landau(const R T[4][4], const Prim<R>& old, const
         const R d2 = sq(n1 - v1) + sq(n2 - v2) + sq(n3 - v3);
         const R b2 = n1 * n1 + n2 * n2 + n3 * n3;
         v1 = n1; v2 = n2; v3 = n3;
-        if (it >= 2 && (d2 <= k.tol * k.tol * b2 || d2 == R(0))) {
+        if (it >= min_it && (d2 <= k.tol * k.tol * b2 || d2 == R(0))) {
             done = true;
             break;
         }

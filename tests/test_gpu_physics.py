@@ -59,3 +59,50 @@ def test_alfven_phase_speed_on_gpu(precision):
     R = mode(m[11]) - (B0 / vA) * mode(m[5])
     err = -np.angle(R / R0) / k / (nsteps * dt) / vA - 1.0
     assert abs(err) < 0.03, err
+
+
+@pytest.mark.parametrize("precision", [L.FP64, L.FP32])
+def test_paper_alfven_pulse_on_gpu(precision):
+    """The paper's nonlinear ideal-MHD Alfven pulse (400 cells on [-1, 1],
+    B = (1, 0.1, B^z), sigma = 1e5, open faces) lands within 5 % (L2) of the
+    initial pulse shifted by the printed v_A = 0.40785 at t = 1."""
+    g = json.load(open(os.path.join(GOLDEN, "alfven_speed.json")))
+    F = W.alfven_paper(400, B0=g["B0"], eta_A=g["eta_A"], vA=g["v_A"])
+    x, dx = F.meta["x"], F.meta["dx"]
+    s = L.Solver(L.make_params(400, 1, 1, sigma=1e5, dx=dx, bc=OPEN_X, precision=precision))
+    s.init_fields(0, F.n, F.p, F.u, F.B)
+    dt = dx / math.sqrt(2.0)
+    steps = int(round(1.0 / dt))
+    s.step(steps)
+    t = steps * dt
+    Bz = s.moments()[11]
+    st = s.stats()
+    s.close()
+    xs = (x - g["v_A"] * t - F.meta["x0"]) / (F.meta["x1"] - F.meta["x0"])
+    exact = np.where((xs > 0) & (xs < 1), g["eta_A"] * g["B0"] * np.sin(2 * np.pi * (3 * xs ** 2 - 2 * xs ** 3)), 0.0)
+    assert st["recover_fail"] == 0
+    assert np.linalg.norm(Bz - exact) / np.linalg.norm(exact) < 0.05
+
+
+def test_relativistic_alfven_speed_on_gpu():
+    """Strong field (B0 = 1, eps + p = 5): the linear Alfven wave travels at
+    B0 / sqrt(eps + p + B0^2) = 0.408, the EM momentum keeping its inertia; the
+    one-pass recovery travels at B0 / sqrt(eps + p) = 0.447."""
+    def speed(flags):
+        nx, B0 = 64, 1.0
+        F = W.alfven_wave(nx, 1, 1, B0=B0)
+        vA, k = F.meta["vA"], 2 * np.pi / nx
+        s = L.Solver(L.make_params(nx, 1, 1, sigma=1e6, precision=L.FP64, flags=flags))
+        s.init_fields(0, F.n, F.p, F.u, F.B)
+        dt = 1.0 / math.sqrt(2.0)
+        nsteps = int(round(0.25 * nx / (vA * dt)))
+        mode = lambda a: np.fft.fft(a)[1]
+        m0 = s.moments()
+        s.step(nsteps)
+        m = s.moments()
+        s.close()
+        R0 = mode(m0[11]) - (B0 / vA) * mode(m0[5])
+        R = mode(m[11]) - (B0 / vA) * mode(m[5])
+        return -np.angle(R / R0) / k / (nsteps * dt)
+    assert abs(speed(0) * math.sqrt(6.0) - 1) < 0.01
+    assert abs(speed(L.FLAG_ONE_PASS_RECOVERY) * math.sqrt(5.0) - 1) < 0.01
