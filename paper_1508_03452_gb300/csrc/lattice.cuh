@@ -97,6 +97,14 @@ struct Prim {
 template <class R>
 __device__ __forceinline__ R sq(R a) { return a * a; }
 
+__device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
+
+// 1/x where a few ulp do not matter (a relaxation factor, a spectral shift):
+// the hardware reciprocal approximation in float32, the division in float64
+__device__ __forceinline__ float rcp_approx(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double rcp_approx(double x) { return 1.0 / x; }
+
 // ---------------------------------------------------------------------------
 // equilibria in deviation form (restated from Eq. Dis_fun_EM with the
 // readings of the delta_{i0} term, the sign of the nu^2/5 term, the
@@ -292,28 +300,31 @@ __device__ __forceinline__ void em_moments(const R* h, const Phys<R>& k, R* Ep, 
 }
 
 // ---------------------------------------------------------------------------
-// Ohm-coupled E solve (Eqs. Ohm and Ex_force, closed form) and J
+// Ohm-coupled E solve (Eqs. Ohm and Ex_force, closed form)
 //   [(1+k) I - (k/c^2) u u^T] E = E' - k u x B - (dt/2) c^2 rho u,  k = (dt/2) c^2 sigma g
 //   E = a/(1+k) - k/(1+k) u x B + k/(1+k) (u.a) u / (c^2 (1 + k/g^2)),  a = E' - (dt/2) c^2 rho u
-// J is taken from Eq. Ex_force, J = (E' - E) / ((dt/2) mu0 c^2), which equals
-// Eq. Ohm at the solution and stays accurate at large sigma in float32.
+// The caller takes J from Eq. Ex_force, J = (E' - E) / ((dt/2) mu0 c^2),
+// which equals Eq. Ohm at the solution and stays accurate at large sigma in
+// float32.
 // ---------------------------------------------------------------------------
+// With ig = 1/g: 1 + k/g^2 = 1 + (dt/2) c^2 sigma ig, and one reciprocal of
+// D = (1 + k)(1 + k/g^2) gives both 1/(1+k) and the u u^T coefficient.
 template <class R>
-__device__ __forceinline__ void ohm_solve(const R* Ep, const R* u, const R* B, R rho, R g2, const Phys<R>& k, R* E,
-                                          R* J)
+__device__ __forceinline__ void ohm_solve(const R* Ep, const R* u, const R* B, R rho, R g, R ig, const Phys<R>& k,
+                                          R* E)
 {
-    const R kk = k.half_dt_c2 * k.sigma * sqrt(g2);
-    const R inv1k = R(1) / (R(1) + kk);
+    const R hs = k.half_dt_c2 * k.sigma;
+    const R kk = hs * g;
+    const R kg = R(1) + hs * ig;  // 1 + k/g^2
+    const R inv = R(1) / ((R(1) + kk) * kg);
+    const R inv1k = kg * inv;
     const R kfrac = kk * inv1k;
     R a[3];
     for (int c = 0; c < 3; ++c) a[c] = Ep[c] - k.half_dt_c2 * rho * u[c];
     const R ua = u[0] * a[0] + u[1] * a[1] + u[2] * a[2];
-    const R s = kfrac * ua / (k.c2 * (R(1) + kk / g2));
+    const R s = kk * ua * inv * (k.inv_c * k.inv_c);
     const R uxB[3] = {u[1] * B[2] - u[2] * B[1], u[2] * B[0] - u[0] * B[2], u[0] * B[1] - u[1] * B[0]};
-    for (int c = 0; c < 3; ++c) {
-        E[c] = a[c] * inv1k - kfrac * uxB[c] + s * u[c];
-        J[c] = (Ep[c] - E[c]) * k.inv_half_dt_c2;
-    }
+    for (int c = 0; c < 3; ++c) E[c] = a[c] * inv1k - kfrac * uxB[c] + s * u[c];
 }
 
 // J from Eq. Ohm for stored primitives (initial state, outputs, driven cells)
@@ -328,7 +339,8 @@ __device__ __forceinline__ void ohm_current(const R* E, const R* u, const R* B, 
 
 // ---------------------------------------------------------------------------
 // Landau eigen-solve (coupling subsection): largest eigenpair of
-// A = [T - eps0 F F(E, B)] eta by a power iteration, shifted by p_old - s
+// A = [T - eps0 F F(E, B)] eta (T and B given by landau_b) by a power
+// iteration, shifted by p_old - s
 // (s = eps0 (c^2 B^2 - E^2) / 2; the shift pushes the spacelike eigenvalues
 // to ~0) unless `shifted` is false (the paper's plain power method), started
 // from the velocity `seed` (beta); convergence is accepted from iteration
@@ -338,38 +350,57 @@ __device__ __forceinline__ void ohm_current(const R* E, const R* u, const R* B, 
 // or -1 if it failed.
 // ---------------------------------------------------------------------------
 template <class R>
-__device__ __forceinline__ int landau(const R T[4][4], const R* E, const R* B, R p_old, const Phys<R>& k, R beta[3],
+struct LandauB {
+    R t00, t0[3], tab[3][3];  // T with the magnetic stresses eps0 c^2 (d_ab B^2 - B_a B_b) taken out
+    R B[3], sB;               // B and eps0 c^2 B^2 / 2
+};
+
+// The part of the Landau matrix that does not depend on E (for fixed B).
+// T[0][0] holds T^00 - eps_r: A[0][0] and lambda are deviations from eps_r.
+template <class R>
+__device__ __forceinline__ void landau_b(const R T[4][4], const R* B, const Phys<R>& k, LandauB<R>& L)
+{
+    const R B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+    L.t00 = T[0][0];
+    for (int a = 0; a < 3; ++a) {
+        L.B[a] = B[a];
+        L.t0[a] = T[0][a + 1];
+        for (int b = 0; b < 3; ++b)
+            L.tab[a][b] = T[a + 1][b + 1] - k.eps0 * k.c2 * ((a == b ? B2 : R(0)) - B[a] * B[b]);
+    }
+    L.sB = R(0.5) * k.eps0 * k.c2 * B2;
+}
+
+template <class R>
+__device__ __forceinline__ int landau(const LandauB<R>& L, const R* E, R p_old, const Phys<R>& k, R beta[3],
                                       R& lambda, R& s_old, const R* seed, bool shifted, int min_it)
 {
+    const R* B = L.B;
     const R E2 = E[0] * E[0] + E[1] * E[1] + E[2] * E[2];
-    const R B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
     const R ExB[3] = {E[1] * B[2] - E[2] * B[1], E[2] * B[0] - E[0] * B[2], E[0] * B[1] - E[1] * B[0]};
     // S = eps0 F^{mu rho} F_rho^nu: S00 = eps0 E^2, S0a = eps0 c (E x B)_a,
-    // Sab = eps0 [-E_a E_b + c^2 (d_ab B^2 - B_a B_b)]
-    // T[0][0] holds T^00 - eps_r: A[0][0] and lambda are deviations from eps_r
+    // Sab = eps0 [-E_a E_b + c^2 (d_ab B^2 - B_a B_b)]; A = (T - S) eta
     R A[4][4];
-    A[0][0] = T[0][0] - k.eps0 * E2;
+    A[0][0] = L.t00 - k.eps0 * E2;
     for (int a = 0; a < 3; ++a) {
-        const R m0a = T[0][a + 1] - k.eps0 * k.c * ExB[a];
+        const R m0a = L.t0[a] - k.eps0 * k.c * ExB[a];
         A[0][a + 1] = -m0a;
         A[a + 1][0] = m0a;
-        for (int b = 0; b < 3; ++b) {
-            const R sab = k.eps0 * (-E[a] * E[b] + k.c2 * ((a == b ? B2 : R(0)) - B[a] * B[b]));
-            A[a + 1][b + 1] = -(T[a + 1][b + 1] - sab);
-        }
+        for (int b = 0; b < 3; ++b) A[a + 1][b + 1] = -(L.tab[a][b] + k.eps0 * E[a] * E[b]);
     }
-    s_old = R(0.5) * k.eps0 * (k.c2 * B2 - E2);
+    s_old = L.sB - R(0.5) * k.eps0 * E2;
     const R shift = shifted ? p_old - s_old : R(0);
     const R a00_full = k.eps_r + shift;  // eps_r restored in the first row only
     R v1 = seed[0], v2 = seed[1], v3 = seed[2];
     int it = 0;
     bool done = false;
+#pragma unroll 1
     for (it = 1; it <= k.maxit; ++it) {
         const R w0 = A[0][0] + A[0][1] * v1 + A[0][2] * v2 + A[0][3] * v3 + a00_full;
         const R w1 = A[1][0] + (A[1][1] + shift) * v1 + A[1][2] * v2 + A[1][3] * v3;
         const R w2 = A[2][0] + A[2][1] * v1 + (A[2][2] + shift) * v2 + A[2][3] * v3;
         const R w3 = A[3][0] + A[3][1] * v1 + A[3][2] * v2 + (A[3][3] + shift) * v3;
-        const R iw = R(1) / w0;
+        const R iw = rcp_approx(w0);  // a scale error is undone by the next iteration
         const R n1 = w1 * iw, n2 = w2 * iw, n3 = w3 * iw;
         const R d2 = sq(n1 - v1) + sq(n2 - v2) + sq(n3 - v3);
         const R b2 = n1 * n1 + n2 * n2 + n3 * n3;

@@ -368,52 +368,68 @@ __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, 
     R p_shift = k.gm1 * (old.eps - old.n * k.c2);
     const R tol_o = k.tol * (sizeof(R) == 8 ? R(100) : R(10));
     const R Bn2 = Bn[0] * Bn[0] + Bn[1] * Bn[1] + Bn[2] * Bn[2];
-    R beta[3] = {seed[0], seed[1], seed[2]}, lambda, s_old, b2 = R(0), g2 = R(1), g = R(1);
+    R beta[3] = {seed[0], seed[1], seed[2]}, lambda, s_old, b2 = R(0), g2 = R(1), g = R(1), ig = R(1);
+    LandauB<R> LB;
+    landau_b(T, Bc, k, LB);
     Prim<R> nw;
     R J[3], n_dev, eps_dev;
     int it = 0;
     bool ok = true;
     R d_prev = R(1e30);
+#pragma unroll 1
     for (int outer = 0;; ++outer) {
         const R sd[3] = {beta[0], beta[1], beta[2]};
-        // a re-solve starts from the converged velocity of the previous field
-        // estimate and may stop after one iteration
+        // each solve starts from the latest velocity and may stop after one
+        // iteration (the last solve's own test then confirms the eigenvector);
+        // a single solve with the previous fields iterates at least twice
         const int i1 =
-            outer < 64 ? landau(T, Ec, Bc, p_shift, k, beta, lambda, s_old, sd, shifted, outer == 0 ? 2 : 1) : -1;
+            outer < 64 ? landau(LB, Ec, p_shift, k, beta, lambda, s_old, sd, shifted, one_pass ? 2 : 1) : -1;
         if (i1 <= 0) {  // the eigen-solve failed, or the fields did not settle
             ok = false;
             break;
         }
         it += i1;
         b2 = beta[0] * beta[0] + beta[1] * beta[1] + beta[2] * beta[2];
-        g2 = R(1) / (R(1) - b2);
-        g = sqrt(g2);
+        g = rsqrt_r(R(1) - b2);
+        g2 = g * g;
+        ig = (R(1) - b2) * g;
 #pragma unroll
         for (int a = 0; a < 3; ++a) nw.u[a] = k.c * beta[a];
-        ohm_solve(Ep, nw.u, Bn, rho, g2, k, nw.E, J);
+        ohm_solve(Ep, nw.u, Bn, rho, g, ig, k, nw.E);
         if (one_pass) break;
-        R d = R(0), e2 = R(0);
+        R d = R(0), e2 = R(0), dB = R(0);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             d += (nw.E[a] - Ec[a]) * (nw.E[a] - Ec[a]);
             e2 += nw.E[a] * nw.E[a];
+            dB += (nw.E[a] - Ec[a]) * Bn[a];
         }
-        // the inner solve leaves relative noise ~ tol in E: a residual that
-        // stops decreasing near the outer bound is at its round-off floor
-        const R scale = sqrt(e2) + R(1e-6) * k.c * sqrt(Bn2);
-        if (sqrt(d) <= tol_o * scale || (d >= d_prev && sqrt(d) <= R(1e3) * tol_o * scale)) break;
+        // E is judged against the motional field scale |E| + c |B| |beta|: a
+        // mismatch below it moves the fluid part of T by less than the outer
+        // tolerance times the EM momentum it could carry. A residual that
+        // stops decreasing near the bound is at its round-off floor (the
+        // inner solve leaves noise ~ tol).
+        const R bound = tol_o * tol_o * (e2 + k.c2 * Bn2 * (b2 + R(1e-12)));
+        if (d <= bound || (d >= d_prev && d <= R(1e6) * bound)) break;
         d_prev = d;
-        // relaxation 1 / (1 + r), r = B^2 k/(1+k) / (w gamma^2): the EM-to-fluid inertia ratio
+        // Relaxed update: the part of E across B feeds back through the EM
+        // momentum eps0 E x B with gain -r, r = B^2 k/(1+k) / (w gamma^2) (the
+        // EM-to-fluid inertia ratio), and takes 1/(1+r) of the step; the part
+        // along B does not feed back and takes all of it. Only the rate of
+        // convergence depends on these factors.
         const R ed = lambda - s_old;  // eps - eps_r
-        const R w = k.eps_r + k.p_r + ed + k.gm1 * ed;
+        const R W = (k.eps_r + k.p_r + ed + k.gm1 * ed) * g2;
         const R kk = k.half_dt_c2 * k.sigma * g;
-        const R r = Bn2 * (kk / (R(1) + kk)) / (w * g2);
-        const R th = R(1) / (R(1) + r);
+        const R q = kk * rcp_approx((R(1) + kk) * W);  // r / B^2
+        const R th = rcp_approx(R(1) + Bn2 * q);
+        const R par = th * q * dB;                      // (1 - th) (dE.B) / B^2
 #pragma unroll
-        for (int a = 0; a < 3; ++a) Ec[a] += th * (nw.E[a] - Ec[a]);
-        const R nd = (dN0 - k.n_r * (g2 * b2 / (g + R(1)))) / g;  // n - n_r
+        for (int a = 0; a < 3; ++a) Ec[a] += th * (nw.E[a] - Ec[a]) + par * Bn[a];
+        const R nd = (dN0 - k.n_r * (g2 * b2 * rcp_approx(g + R(1)))) * ig;  // n - n_r
         p_shift = k.p_r + k.gm1 * (ed - nd * k.c2);
     }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) J[a] = (Ep[a] - nw.E[a]) * k.inv_half_dt_c2;
     if (ok) {
         eps_dev = lambda - s_old;
         // n = N^0 / U^0: n - n_r = (dN0 - n_r (g - 1)) / g, g - 1 = g^2 b^2 / (g + 1)
