@@ -19,7 +19,9 @@ Kelvin-Helmholtz runs): its MLUPS and eigen-solve iterations per cell beside
 the plain path's, and both float32 arms' errors against the float64 GPU build;
 and, under "batched_sweep", the 64-run uneven-grid Kelvin-Helmholtz sweep in
 one handle: one launch per run per step against the autotuned schedule
-replayed from CUDA graphs.
+replayed from CUDA graphs; and, under "flux_rope_3d", the driven 3-D flux rope
+(256^3, open faces, the lowest layers driven) with the plain and the learned
+seed.
 
 Prints one JSON line (rank 0).
 """
@@ -295,7 +297,7 @@ def learned_seed_leg(args, stream, plain_moments, plain_iters, steps_total):
     ref.step(steps_total)
     m64 = ref.moments(0)
     ref.close()
-    return {
+    return P, {
         "value": len(SIGMAS) * N * args.steps / (ms * 1e-3) / 1e6, "unit": UNIT,
         "iters_per_cell": sum(s["iter_total"] for s in stats) / (len(SIGMAS) * N * steps_total),
         "iters_p99": hist_quantile(hist, 0.99),
@@ -355,6 +357,50 @@ def batched_sweep_leg(args, stream, steps=10):
         "per_run_one_stream_mlups": cells * steps / (ms_plain * 1e-3) / 1e6,
         "schedule": sched.as_dict(), "autotune_ms_per_step": tune_ms, "recover_fail": fails,
     }
+
+
+def flux_rope_case(n, prec, recovery):
+    from paper_1508_03452_gb300 import lbrmhd as L
+    from paper_1508_03452_gb300 import workloads as W
+
+    F = W.flux_rope(n, n, n)
+    bc = (L.OPEN,) * 4 + (L.DRIVEN, L.OPEN)  # open faces, driven bottom (z = 0)
+    P = L.make_params(n, n, n, bc=bc, sigma=500.0, drive_u0=0.05, drive_layers=W.drive_layers_for(n),
+                      precision=prec, recovery=recovery)
+    return F, P
+
+
+def flux_rope_leg(args, stream, weights, n=256, steps=10):
+    """The driven 3-D flux rope (the paper's stellar-flare set-up, sigma = 500,
+    open faces, the lowest layers driven at 0.05 c) on an n^3 lattice: plain
+    and learned seed (the network of the learned-seed leg), 3 warm-up and
+    `steps` timed steps each, one run per handle."""
+    import torch
+
+    from paper_1508_03452_gb300 import lbrmhd as L
+
+    prec = {"fp32": L.FP32, "fp16": L.FP16_DEV, "fp64": L.FP64}[args.precision]
+    out = {"workload": f"flux_rope_{n}^3_sigma_500_open_driven", "grid": [n, n, n], "steps": steps}
+    for name, rec in (("plain", L.RECOVERY_PLAIN), ("learned_seed", L.RECOVERY_MLP)):
+        if rec == L.RECOVERY_MLP and weights is None:
+            continue
+        F, P = flux_rope_case(n, prec, rec)
+        s = L.Solver(P, stream=stream)
+        if rec == L.RECOVERY_MLP:
+            s.set_mlp_weights(weights)
+        s.init_fields(0, F.n, F.p, F.u, F.B)
+        s.step(3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = s.stats()
+        s.close()
+        out[name] = {"value": n ** 3 * steps / (e0.elapsed_time(e1) * 1e-3) / 1e6, "unit": UNIT,
+                     "iters_per_cell": st["iter_total"] / (n ** 3 * (steps + 3)), "failures": st["recover_fail"]}
+    return out
 
 
 def run_gpu(args, world, rank, local):
@@ -457,10 +503,13 @@ def run_gpu(args, world, rank, local):
                          "iters_max": max(s["iter_max"] for s in stats),
                          "failures": sum(s["recover_fail"] for s in stats)},
         }
+        weights = None
         if plain_moments is not None:
-            line["learned_seed"] = learned_seed_leg(args, stream, plain_moments, plain_iters, steps_total)
+            weights, line["learned_seed"] = learned_seed_leg(args, stream, plain_moments, plain_iters, steps_total)
         if not args.no_sweep:
             line["batched_sweep"] = batched_sweep_leg(args, stream)
+        if not args.no_3d:
+            line["flux_rope_3d"] = flux_rope_leg(args, stream, weights)
         clocks = clk.summary()
         if clocks:
             line["clocks"] = clocks
@@ -474,17 +523,21 @@ def run_gpu(args, world, rank, local):
 
 def run_profile_case(args):
     """Small profiling case (no timing): one 1024 x 1024 current-sheet run
-    (sigma = 100) in the chosen precision, init + `--steps` steps."""
+    (sigma = 100), or with --profile-3d N the driven N^3 flux rope, in the
+    chosen precision, init + `--steps` steps."""
     import torch
 
     from paper_1508_03452_gb300 import lbrmhd as L
     from paper_1508_03452_gb300 import workloads as W
 
     prec = {"fp32": L.FP32, "fp16": L.FP16_DEV, "fp64": L.FP64}[args.precision]
-    F = W.current_sheet(NX, NY, 1, delta=8.0)
     rec = L.RECOVERY_MLP if args.profile_learned else L.RECOVERY_PLAIN
-    s = L.Solver(L.make_params(NX, NY, 1, sigma=100.0, precision=prec, recovery=rec),
-                 stream=torch.cuda.current_stream())
+    if args.profile_3d:
+        F, P = flux_rope_case(args.profile_3d, prec, rec)
+    else:
+        F = W.current_sheet(NX, NY, 1, delta=8.0)
+        P = L.make_params(NX, NY, 1, sigma=100.0, precision=prec, recovery=rec)
+    s = L.Solver(P, stream=torch.cuda.current_stream())
     if args.profile_learned:  # untrained weights: the inference cost, not the seed quality
         s.set_mlp_weights(torch.tensor(W.mlp_init_params(1), device="cuda"))
     s.init_fields(0, F.n, F.p, F.u, F.B)
@@ -503,9 +556,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned-seed", action="store_true", help="skip the learned-seed comparison leg")
     ap.add_argument("--no-sweep", action="store_true", help="skip the 64-run batched sweep leg")
+    ap.add_argument("--no-3d", action="store_true", help="skip the 3-D flux-rope leg")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--profile-case", action="store_true", help="untimed 1024^2 single-run case for ncu captures")
     ap.add_argument("--profile-learned", action="store_true", help="--profile-case with the learned-seed kernel")
+    ap.add_argument("--profile-3d", type=int, default=0, metavar="N", help="--profile-case on the driven N^3 flux rope")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if args.profile_case:
