@@ -82,6 +82,34 @@
  *       solve), which makes it exact for the linearised ideal problem and
  *       keeps it convergent when B^2 > eps + p. The literal one-pass reading
  *       is the ORC_ONE_PASS_RECOVERY test switch.
+ *   R25 the photospheric body force of the flare set-up (Sec. IV, stellar
+ *       flare: F = F0 (sin(pi xs / 3) cos(pi y / 6), cos(pi xs / 3) sin(pi y / 6), 0),
+ *       xs = x on x < 0 and x - 3 on x >= 0, in the lowest drive_layers
+ *       z-layers). The paper gives no forcing
+ *       scheme. Reading: a force density F adds c F dt to T^{0a} and its
+ *       work F.u dt (u of the previous step) to T^00 in every step, put into
+ *       the streamed f before the recovery: the rest population takes
+ *       F.u dt / (p_0^0)^2, a moving one c dt (F . p_i) / S with
+ *       S = sum_j p_j^0 (p_j^x)^2 (the lattice is isotropic to that order), so
+ *       the populations' added moments are exactly those two and nothing else.
+ *   R26 the force acts only while the largest |u| of the state at the start
+ *       of the step is below drive_vmax (the paper's 0.3 c cut-off).
+ *   R27 the iterative E, J initialisation of the flare set-up (Sec. IV): from
+ *       the initial state (E = -u x B), repeat one step without the force and
+ *       then hold the fluid and B at their initial values: n, p, u and B of
+ *       every cell are reset, f and g go back to their equilibria, and the
+ *       Maxwell populations keep their state but for the B they carry, which
+ *       is moved back to the initial B through the populations whose b
+ *       carries it (h_k += (B0 - B).b_k / 8: sum b b^T = 8 I, sum e b^T = 0,
+ *       sum b = 0, so E' and rho_c do not move); E and rho_c evolve, J
+ *       follows Eq. Ohm. Cells on an open face are left as the face copy
+ *       made them (R19: the state of their interior neighbour). The scheme's
+ *       tau_h = 1/2 leaves a small mode that
+ *       flips sign every step, so the test compares E with its value two
+ *       steps before: until max |E_k - E_{k-2}| <= tol max |E_k|. Resetting
+ *       h to its equilibrium instead would drop the non-equilibrium part that
+ *       the tau_h = 1/2 scheme needs: the steady current then comes out
+ *       twice curl B.
  *
  * Units: mu_0 = 1, eps_0 = 1/(mu_0 c^2); dt = dx / (sqrt(2) c) (Sec. III,
  * time-step synchronisation).
@@ -597,6 +625,7 @@ struct orc_sim {
     orc_params P;
     orc_lattice L;
     int64_t N;
+    int force_on; /* R26: the body force acts in the current step */
     double *f, *g, *h, *prim;       /* state at t: f[19][N], g[19][N], h[25][N], prim[ORC_NPRIM][N] */
     double *f2, *g2, *h2, *prim2;   /* state at t + dt */
     double *fc, *gc, *hc;           /* post-collision populations at t */
@@ -727,6 +756,81 @@ int orc_init(orc_sim* s, const double* n, const double* p, const double* u, cons
     return 0;
 }
 
+/* R27: initial state whose E (and with it rho_c and J) has relaxed under the
+ * scheme with n, p, u, B held at their initial values. Returns the number of
+ * steps taken (>= 1), or -1 on a bad input; *residual = max |E_k - E_{k-2}| /
+ * max |E_k| of the last step k (E_{-1} = E_0, the initial E; 0 when E stays
+ * 0). The run then starts from step 0 with zero counters. */
+int orc_init_relaxed(orc_sim* s, const double* n, const double* p, const double* u, const double* B, int max_iters,
+                     double tol, double* residual)
+{
+    const orc_params* P = &s->P;
+    const orc_lattice* L = &s->L;
+    const int64_t N = s->N;
+    const double c = P->c;
+    if (orc_init(s, n, p, u, B, NULL) != 0) return -1;
+    double* E_m1 = (double*)malloc(3 * N * sizeof(double)); /* E_{k-1} */
+    double* E_m2 = (double*)malloc(3 * N * sizeof(double)); /* E_{k-2} */
+    if (!E_m1 || !E_m2) {
+        free(E_m1); free(E_m2);
+        return -1;
+    }
+    memcpy(E_m1, s->prim + (int64_t)ORC_E * N, 3 * N * sizeof(double));
+    memcpy(E_m2, E_m1, 3 * N * sizeof(double));
+    const double f0 = s->P.drive_f0;
+    s->P.drive_f0 = 0.0; /* no force while the fields relax */
+    int k = 0;
+    double res = 0.0;
+    while (k < (max_iters > 0 ? max_iters : 1)) {
+        ++k;
+        orc_step(s, 1);
+        double dmax = 0.0, emax = 0.0;
+        for (int64_t id = 0; id < N; ++id) {
+            double pr[ORC_NPRIM], fe[19], ge[19], dB[3], d2 = 0.0, e2 = 0.0;
+            gather_cell(s->prim, ORC_NPRIM, N, id, pr);
+            const int q[3] = {(int)(id % P->nx), (int)((id / P->nx) % P->ny), (int)(id / ((int64_t)P->nx * P->ny))};
+            const int nn[3] = {P->nx, P->ny, P->nz};
+            int face = 0; /* open-face cells keep the copy of their interior neighbour (R19) */
+            for (int a = 0; a < 3; ++a)
+                if (nn[a] >= 3 && ((q[a] == 0 && P->bc[2 * a] != ORC_PERIODIC) ||
+                                   (q[a] == nn[a] - 1 && P->bc[2 * a + 1] != ORC_PERIODIC)))
+                    face = 1;
+            for (int a = 0; a < 3; ++a) {
+                const double d = pr[ORC_E + a] - E_m2[a * N + id];
+                d2 += d * d;
+                e2 += pr[ORC_E + a] * pr[ORC_E + a];
+                E_m2[a * N + id] = E_m1[a * N + id];
+                E_m1[a * N + id] = pr[ORC_E + a];
+                dB[a] = B[a * N + id] - pr[ORC_B + a];
+            }
+            if (d2 > dmax) dmax = d2;
+            if (e2 > emax) emax = e2;
+            if (face) continue;
+            for (int k2 = 0; k2 < 24; ++k2) s->h[(int64_t)k2 * N + id] += dot3(dB, L->b[k2]) / 8.0;
+            pr[ORC_N] = n[id];
+            pr[ORC_EPS] = n[id] * c * c + p[id] / (P->gamma_ad - 1.0);
+            for (int a = 0; a < 3; ++a) {
+                pr[ORC_U + a] = u[a * N + id];
+                pr[ORC_B + a] = B[a * N + id];
+            }
+            orc_ohm_current(P, pr + ORC_E, pr + ORC_U, pr + ORC_B, pr[ORC_RHOC], pr + ORC_J);
+            scatter_cell(s->prim, ORC_NPRIM, N, id, pr);
+            orc_feq(P, L, pr[ORC_N], pr[ORC_EPS], pr + ORC_U, pr + ORC_E, pr + ORC_B, fe);
+            orc_geq(P, L, pr[ORC_N], pr + ORC_U, ge);
+            scatter_cell(s->f, 19, N, id, fe);
+            scatter_cell(s->g, 19, N, id, ge);
+        }
+        res = emax > 0.0 ? sqrt(dmax / emax) : (dmax > 0.0 ? INFINITY : 0.0);
+        if (res <= tol) break;
+    }
+    s->P.drive_f0 = f0;
+    s->iter_total = s->iter_max = s->recover_fail = 0;
+    s->steps = 0;
+    free(E_m1); free(E_m2);
+    if (residual) *residual = res;
+    return k;
+}
+
 /* Collision of one cell at time t (R6-R8 and Eq. LB_Maxwell with tau_h = 1/2):
  *   f_c = f - K_i (f - f^eq(t)),  g_c = g - (dt/tau)(g - g^eq(t)),
  *   h_c = h - 2 (h - h^eq(t)) = 2 h^eq - h  (h_0 included, h_0^eq = rho_c).
@@ -785,6 +889,12 @@ static int stream_recover_local(const orc_sim* s, int x, int y, int z, const dou
     hn[24] = hc[24 * N + id];
 
     gather_cell(s->prim, ORC_NPRIM, N, id, pr);
+    if (s->force_on && z < P->drive_layers) { /* R25 */
+        double F[3], df[19];
+        orc_drive_force(P, x, y, F);
+        orc_force_populations(P, L, F, pr + ORC_U, df);
+        for (int i = 0; i < 19; ++i) fn[i] += df[i];
+    }
     const int it = orc_recover_cell(P, L, fn, gn, hn, pr, pn);
     /* on failure keep the previous primitives; the failure is counted */
     if (it < 0) memcpy(pn, pr, sizeof(pr));
@@ -935,16 +1045,56 @@ static void normal_b_fix(orc_sim* s)
     }
 }
 
-/* R21: the drive pattern (the paper's two co-rotating photospheric vortices),
- * on x, y in [-3, 3] mapped onto the grid, scaled to max |u| = u0. */
-void orc_drive_velocity(const orc_params* P, int x, int y, double* u)
+/* The paper's two co-rotating photospheric vortices (Sec. IV, stellar flare)
+ * with amplitude amp, on x, y in [-3, 3] mapped onto the grid: x* = x on the
+ * half x < 0 and x - 3 on the other. */
+static void two_vortex(const orc_params* P, int x, int y, double amp, double* v)
 {
     const double X = -3.0 + (x + 0.5) * 6.0 / P->nx;
     const double Y = -3.0 + (y + 0.5) * 6.0 / P->ny;
     const double xs = (X < 0.0) ? X : X - 3.0;
-    u[0] = P->drive_u0 * sin(M_PI * xs / 3.0) * cos(M_PI * Y / 6.0);
-    u[1] = P->drive_u0 * cos(M_PI * xs / 3.0) * sin(M_PI * Y / 6.0);
-    u[2] = 0.0;
+    v[0] = amp * sin(M_PI * xs / 3.0) * cos(M_PI * Y / 6.0);
+    v[1] = amp * cos(M_PI * xs / 3.0) * sin(M_PI * Y / 6.0);
+    v[2] = 0.0;
+}
+
+/* R21: the drive velocity, max |u| = drive_u0. */
+void orc_drive_velocity(const orc_params* P, int x, int y, double* u) { two_vortex(P, x, y, P->drive_u0, u); }
+
+/* R25: the body force density of column (x, y), amplitude drive_f0. */
+void orc_drive_force(const orc_params* P, int x, int y, double* F) { two_vortex(P, x, y, P->drive_f0, F); }
+
+/* R25: the change of the 19 streamed f of one cell under the force density F
+ * for one step, u the velocity of the previous step:
+ *   sum_i p^0 p^a df_i = c F^a dt,  sum_i p^0 p^0 df_i = F.u dt,
+ *   sum_i p^a p^b df_i = 0. */
+void orc_force_populations(const orc_params* P, const orc_lattice* L, const double* F, const double* u, double* df)
+{
+    const double dt = orc_dt(P), c = P->c;
+    double S = 0.0;
+    for (int i = 0; i < 19; ++i) S += L->p[i][0] * L->p[i][1] * L->p[i][1];
+    for (int i = 0; i < 19; ++i) {
+        double Fp = 0.0;
+        for (int a = 0; a < 3; ++a) Fp += F[a] * L->p[i][a + 1];
+        df[i] = c * dt * Fp / S;
+    }
+    df[0] += dot3(F, u) * dt / (L->p[0][0] * L->p[0][0]);
+}
+
+/* R26: whether the force acts in the step that starts from s->prim. */
+int orc_force_on(const orc_sim* s)
+{
+    const orc_params* P = &s->P;
+    if (P->drive_f0 == 0.0 || P->drive_layers <= 0) return 0;
+    if (!(P->drive_vmax > 0.0)) return 1;
+    const int64_t N = s->N;
+    double m = 0.0;
+    for (int64_t id = 0; id < N; ++id) {
+        double u2 = 0.0;
+        for (int a = 0; a < 3; ++a) u2 += s->prim[(ORC_U + a) * N + id] * s->prim[(ORC_U + a) * N + id];
+        if (u2 > m) m = u2;
+    }
+    return m < P->drive_vmax * P->drive_vmax;
 }
 
 static void drive_layers(orc_sim* s)
@@ -980,6 +1130,7 @@ int orc_step(orc_sim* s, int64_t nsteps)
     int64_t fails = 0;
     for (int64_t t = 0; t < nsteps; ++t) {
         int64_t it_sum = 0, it_max = s->iter_max;
+        s->force_on = orc_force_on(s);
         collide_all(s);
 #pragma omp parallel for collapse(2) schedule(static) reduction(+ : fails, it_sum) reduction(max : it_max)
         for (int z = 0; z < P->nz; ++z)
@@ -1055,6 +1206,7 @@ int orc_update_cells(orc_sim* s, const int64_t* cells, int64_t ncells, double* f
 {
     const orc_params* P = &s->P;
     const int64_t N = s->N;
+    s->force_on = orc_force_on(s);
     collide_all(s);
     double* fo = (double*)calloc(19 * N, sizeof(double));
     double* go = (double*)calloc(19 * N, sizeof(double));
@@ -1091,6 +1243,7 @@ int orc_update_cells_from(orc_sim* s, const double* fc, const double* gc, const 
     memcpy(s->gc, gc, 19 * N * sizeof(double));
     memcpy(s->hc, hc, 25 * N * sizeof(double));
     memcpy(s->prim, prim, ORC_NPRIM * N * sizeof(double));
+    s->force_on = orc_force_on(s);
     int rc = 0;
     for (int64_t m = 0; m < ncells; ++m) {
         const int64_t id = cells[m];

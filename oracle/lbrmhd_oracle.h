@@ -63,6 +63,8 @@ typedef struct orc_params {
     int32_t threads;      /* OpenMP threads (0: runtime default) */
     int32_t max_power_iters;
     double power_tol;
+    double drive_f0;      /* R25: amplitude of the photospheric body force (0: none) */
+    double drive_vmax;    /* R26: the force acts while max |u| < drive_vmax (<= 0: always) */
 } orc_params;
 
 typedef struct orc_lattice {
@@ -101,11 +103,16 @@ int orc_recover_cell(const orc_params* P, const orc_lattice* L, const double* f,
                      const double* h, const double* prim_prev, double* prim_out);
 void orc_stream_population(const orc_params* P, int i, const double* fi, double* out);
 void orc_drive_velocity(const orc_params* P, int x, int y, double* u);
+void orc_drive_force(const orc_params* P, int x, int y, double* F);
+void orc_force_populations(const orc_params* P, const orc_lattice* L, const double* F, const double* u, double* df);
 
 orc_sim* orc_create(const orc_params* P);
 void orc_destroy(orc_sim* s);
 int orc_init(orc_sim* s, const double* n, const double* p, const double* u, const double* B, const double* E);
 int orc_step(orc_sim* s, int64_t nsteps);
+int orc_force_on(const orc_sim* s);
+int orc_init_relaxed(orc_sim* s, const double* n, const double* p, const double* u, const double* B, int max_iters,
+                     double tol, double* residual);
 void orc_get_moments(const orc_sim* s, double* out);
 void orc_get_state(const orc_sim* s, double* f, double* g, double* h, double* prim);
 void orc_set_state(orc_sim* s, const double* f, const double* g, const double* h, const double* prim);

@@ -33,6 +33,7 @@ class Params(C.Structure):
         ("alpha", C.c_double), ("c", C.c_double), ("dx", C.c_double), ("nu", C.c_double),
         ("drive_u0", C.c_double), ("drive_layers", C.c_int32), ("flags", C.c_int32),
         ("threads", C.c_int32), ("max_power_iters", C.c_int32), ("power_tol", C.c_double),
+        ("drive_f0", C.c_double), ("drive_vmax", C.c_double),
     ]
 
 
@@ -106,6 +107,12 @@ def lib():
             L.orc_recover_cell.argtypes = [P, C.POINTER(Lattice), dp, dp, dp, dp, dp]
             L.orc_stream_population.argtypes = [P, C.c_int, dp, dp]
             L.orc_drive_velocity.argtypes = [P, C.c_int, C.c_int, dp]
+            L.orc_drive_force.argtypes = [P, C.c_int, C.c_int, dp]
+            L.orc_force_populations.argtypes = [P, C.POINTER(Lattice), dp, dp, dp]
+            L.orc_force_on.restype = C.c_int
+            L.orc_force_on.argtypes = [C.c_void_p]
+            L.orc_init_relaxed.restype = C.c_int
+            L.orc_init_relaxed.argtypes = [C.c_void_p, dp, dp, dp, dp, C.c_int, C.c_double, dp]
             _lib = L
     return _lib
 
@@ -120,7 +127,7 @@ def _f64(a) -> np.ndarray:
 
 def make_params(nx=1, ny=1, nz=1, *, bc=(PERIODIC,) * 6, tau=1.0, sigma=100.0, gamma_ad=4.0 / 3.0, alpha=0.1,
                 c=1.0, dx=1.0, nu=0.0, drive_u0=0.0, drive_layers=0, flags=0, threads=1,
-                max_power_iters=1000, power_tol=1e-14) -> Params:
+                max_power_iters=1000, power_tol=1e-14, drive_f0=0.0, drive_vmax=0.0) -> Params:
     P = Params()
     P.nx, P.ny, P.nz = nx, ny, nz
     for k in range(6):
@@ -128,6 +135,7 @@ def make_params(nx=1, ny=1, nz=1, *, bc=(PERIODIC,) * 6, tau=1.0, sigma=100.0, g
     P.tau, P.sigma, P.gamma_ad, P.alpha, P.c, P.dx, P.nu = tau, sigma, gamma_ad, alpha, c, dx, nu
     P.drive_u0, P.drive_layers, P.flags, P.threads = drive_u0, drive_layers, flags, threads
     P.max_power_iters, P.power_tol = max_power_iters, power_tol
+    P.drive_f0, P.drive_vmax = drive_f0, drive_vmax
     return P
 
 
@@ -236,6 +244,21 @@ def drive_velocity(P, x, y) -> np.ndarray:
     return out
 
 
+def drive_force(P, x, y) -> np.ndarray:
+    out = np.zeros(3)
+    lib().orc_drive_force(C.byref(P), int(x), int(y), _dp(out))
+    return out
+
+
+def force_populations(P, F, u) -> np.ndarray:
+    """R25: the change of a cell's 19 streamed f under force density F for one
+    step (u: the previous step's velocity)."""
+    F, u = _f64(F).reshape(3), _f64(u).reshape(3)
+    out = np.zeros(19)
+    lib().orc_force_populations(C.byref(P), C.byref(_lat(P)), _dp(F), _dp(u), _dp(out))
+    return out
+
+
 class Sim:
     """Owning wrapper of one oracle simulation (arrays x-fastest, field-major)."""
 
@@ -260,6 +283,23 @@ class Sim:
         rc = lib().orc_init(self._h, _dp(n), _dp(p), _dp(u), _dp(B), None if Ep is None else _dp(Ep))
         if rc != 0:
             raise ValueError("oracle init failed (superluminal velocity?)")
+
+    def init_relaxed(self, n, p, u, B, max_iters=200, tol=1e-12):
+        """R27: initial state with E (rho_c, J) relaxed under the scheme at
+        fixed n, p, u, B; returns (steps taken, final residual)."""
+        N = self.N
+        n = _f64(n).reshape(N); p = _f64(p).reshape(N)
+        u = _f64(u).reshape(3 * N); B = _f64(B).reshape(3 * N)
+        res = C.c_double(0.0)
+        k = lib().orc_init_relaxed(self._h, _dp(n), _dp(p), _dp(u), _dp(B), int(max_iters), float(tol),
+                                   C.byref(res))
+        if k < 0:
+            raise ValueError("oracle init failed (superluminal velocity?)")
+        return k, res.value
+
+    def force_on(self) -> bool:
+        """R26: whether the body force acts in the next step."""
+        return bool(lib().orc_force_on(self._h))
 
     def step(self, nsteps: int) -> int:
         return lib().orc_step(self._h, int(nsteps))
