@@ -102,6 +102,13 @@ typedef struct lbrmhd_params {
     int32_t flags;          /* LBRMHD_FLAG_* */
     int32_t max_iters;      /* recovery iteration cap (0: 64) */
     double tol;             /* recovery tolerance (0: 1e-14 for FP64, 1e-6 otherwise) */
+    double drive_f0;        /* photospheric body force of the flare set-up (Sec. IV): amplitude F0 of the
+                               two-vortex force density F = F0 (sin(pi xs/3) cos(pi y/6), cos(pi xs/3) sin(pi y/6), 0)
+                               on x, y in [-3, 3] (xs = x on x < 0, x - 3 on x >= 0), applied in the lowest
+                               drive_layers z-layers; it adds c F dt to T^{0a} and F.u dt to T^00 of the streamed
+                               fluid populations each step. 0: no force. Not with LBRMHD_DRIVEN. */
+    double drive_vmax;      /* the force acts while the largest |u| of the state is below drive_vmax
+                               (the paper's 0.3 c); <= 0: always */
 } lbrmhd_params;
 
 typedef struct lbrmhd_state_s* lbrmhd_handle;
@@ -132,6 +139,22 @@ int lbrmhd_init_fields(lbrmhd_handle h, int run, const double* n, const double* 
 /* As lbrmhd_init_fields with device arrays (float64, same layout). */
 int lbrmhd_init_fields_device(lbrmhd_handle h, int run, const double* n, const double* p, const double* u,
                               const double* B, const double* E);
+
+/* Initial state of one run whose E, J have relaxed under the scheme (the
+ * iterative initialisation of the flare set-up, Sec. IV): from the state of
+ * lbrmhd_init_fields(n, p, u, B, E = NULL), repeat one step of this run (no
+ * body force) in which, after the recovery and before the boundary pass,
+ * every cell is held at the given n, p, u, B: f and g at their equilibria,
+ * the B carried by h moved back to B (h_k += (B0 - B).b_k / 8; E' and rho_c
+ * unchanged), J from Eq. Ohm; E and rho_c evolve. Stops when max |E_k - E_{k-2}| <= tol max |E_k| (k: the step
+ * count; E_{-1} = the initial E) or after max_iters steps. Writes the steps
+ * taken to *iters and that ratio of the last step to *residual (either may be
+ * NULL); the run then starts at step 0 with zero counters. Host arrays as in
+ * lbrmhd_init_fields; synchronises the stream once per step. Other runs of the
+ * handle are untouched. Errors: BAD_ARG (as lbrmhd_init_fields, max_iters < 1,
+ * tol < 0, a run with LBRMHD_DRIVEN), OOM, CUDA. */
+int lbrmhd_init_fields_relaxed(lbrmhd_handle h, int run, const double* n, const double* p, const double* u,
+                               const double* B, int max_iters, double tol, int* iters, double* residual);
 
 /* Advances every run by nsteps time steps (asynchronous on the handle's
  * stream). The primitive recovery is self-consistent: the eigen-solve of the

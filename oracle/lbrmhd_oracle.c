@@ -95,15 +95,16 @@
  *   R26 the force acts only while the largest |u| of the state at the start
  *       of the step is below drive_vmax (the paper's 0.3 c cut-off).
  *   R27 the iterative E, J initialisation of the flare set-up (Sec. IV): from
- *       the initial state (E = -u x B), repeat one step without the force and
- *       then hold the fluid and B at their initial values: n, p, u and B of
- *       every cell are reset, f and g go back to their equilibria, and the
- *       Maxwell populations keep their state but for the B they carry, which
- *       is moved back to the initial B through the populations whose b
- *       carries it (h_k += (B0 - B).b_k / 8: sum b b^T = 8 I, sum e b^T = 0,
- *       sum b = 0, so E' and rho_c do not move); E and rho_c evolve, J
- *       follows Eq. Ohm. Cells on an open face are left as the face copy
- *       made them (R19: the state of their interior neighbour). The scheme's
+ *       the initial state (E = -u x B), repeat one step without the force in
+ *       which, after the recovery and before the boundary pass, the fluid and
+ *       B are held at their initial values: n, p, u and B of every cell are
+ *       reset, f and g go back to their equilibria, and the Maxwell
+ *       populations keep their state but for the B they carry, which is moved
+ *       back to the initial B through the populations whose b carries it
+ *       (h_k += (B0 - B).b_k / 8: sum b b^T = 8 I, sum e b^T = 0, sum b = 0,
+ *       so E' and rho_c do not move); E and rho_c evolve, J follows Eq. Ohm.
+ *       The open faces then copy their (held) interior neighbours and the
+ *       normal-B fix follows, as in every step. The scheme's
  *       tau_h = 1/2 leaves a small mode that
  *       flips sign every step, so the test compares E with its value two
  *       steps before: until max |E_k - E_{k-2}| <= tol max |E_k|. Resetting
@@ -756,11 +757,16 @@ int orc_init(orc_sim* s, const double* n, const double* p, const double* u, cons
     return 0;
 }
 
+static int64_t step_interior(orc_sim* s);
+static void open_boundaries(orc_sim* s);
+static void normal_b_fix(orc_sim* s);
+
 /* R27: initial state whose E (and with it rho_c and J) has relaxed under the
  * scheme with n, p, u, B held at their initial values. Returns the number of
- * steps taken (>= 1), or -1 on a bad input; *residual = max |E_k - E_{k-2}| /
- * max |E_k| of the last step k (E_{-1} = E_0, the initial E; 0 when E stays
- * 0). The run then starts from step 0 with zero counters. */
+ * steps taken (>= 1), or -1 on a bad input (or a DRIVEN run); *residual =
+ * max |E_k - E_{k-2}| / max |E_k| of the last step k (E_{-1} = E_0, the
+ * initial E; 0 when E stays 0). The run then starts from step 0 with zero
+ * counters. */
 int orc_init_relaxed(orc_sim* s, const double* n, const double* p, const double* u, const double* B, int max_iters,
                      double tol, double* residual)
 {
@@ -768,7 +774,11 @@ int orc_init_relaxed(orc_sim* s, const double* n, const double* p, const double*
     const orc_lattice* L = &s->L;
     const int64_t N = s->N;
     const double c = P->c;
+    if (P->bc[4] == ORC_DRIVEN) return -1;
     if (orc_init(s, n, p, u, B, NULL) != 0) return -1;
+#ifdef _OPENMP
+    if (P->threads > 0) omp_set_num_threads(P->threads);
+#endif
     double* E_m1 = (double*)malloc(3 * N * sizeof(double)); /* E_{k-1} */
     double* E_m2 = (double*)malloc(3 * N * sizeof(double)); /* E_{k-2} */
     if (!E_m1 || !E_m2) {
@@ -783,30 +793,12 @@ int orc_init_relaxed(orc_sim* s, const double* n, const double* p, const double*
     double res = 0.0;
     while (k < (max_iters > 0 ? max_iters : 1)) {
         ++k;
-        orc_step(s, 1);
-        double dmax = 0.0, emax = 0.0;
+        step_interior(s);
         for (int64_t id = 0; id < N; ++id) {
-            double pr[ORC_NPRIM], fe[19], ge[19], dB[3], d2 = 0.0, e2 = 0.0;
+            double pr[ORC_NPRIM], fe[19], ge[19], dB[3];
             gather_cell(s->prim, ORC_NPRIM, N, id, pr);
-            const int q[3] = {(int)(id % P->nx), (int)((id / P->nx) % P->ny), (int)(id / ((int64_t)P->nx * P->ny))};
-            const int nn[3] = {P->nx, P->ny, P->nz};
-            int face = 0; /* open-face cells keep the copy of their interior neighbour (R19) */
-            for (int a = 0; a < 3; ++a)
-                if (nn[a] >= 3 && ((q[a] == 0 && P->bc[2 * a] != ORC_PERIODIC) ||
-                                   (q[a] == nn[a] - 1 && P->bc[2 * a + 1] != ORC_PERIODIC)))
-                    face = 1;
-            for (int a = 0; a < 3; ++a) {
-                const double d = pr[ORC_E + a] - E_m2[a * N + id];
-                d2 += d * d;
-                e2 += pr[ORC_E + a] * pr[ORC_E + a];
-                E_m2[a * N + id] = E_m1[a * N + id];
-                E_m1[a * N + id] = pr[ORC_E + a];
-                dB[a] = B[a * N + id] - pr[ORC_B + a];
-            }
-            if (d2 > dmax) dmax = d2;
-            if (e2 > emax) emax = e2;
-            if (face) continue;
-            for (int k2 = 0; k2 < 24; ++k2) s->h[(int64_t)k2 * N + id] += dot3(dB, L->b[k2]) / 8.0;
+            for (int a = 0; a < 3; ++a) dB[a] = B[a * N + id] - pr[ORC_B + a];
+            for (int q = 0; q < 24; ++q) s->h[(int64_t)q * N + id] += dot3(dB, L->b[q]) / 8.0;
             pr[ORC_N] = n[id];
             pr[ORC_EPS] = n[id] * c * c + p[id] / (P->gamma_ad - 1.0);
             for (int a = 0; a < 3; ++a) {
@@ -819,6 +811,22 @@ int orc_init_relaxed(orc_sim* s, const double* n, const double* p, const double*
             orc_geq(P, L, pr[ORC_N], pr + ORC_U, ge);
             scatter_cell(s->f, 19, N, id, fe);
             scatter_cell(s->g, 19, N, id, ge);
+        }
+        open_boundaries(s);
+        normal_b_fix(s);
+        double dmax = 0.0, emax = 0.0;
+        for (int64_t id = 0; id < N; ++id) {
+            double d2 = 0.0, e2 = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                const double E = s->prim[(ORC_E + a) * N + id];
+                const double d = E - E_m2[a * N + id];
+                d2 += d * d;
+                e2 += E * E;
+                E_m2[a * N + id] = E_m1[a * N + id];
+                E_m1[a * N + id] = E;
+            }
+            if (d2 > dmax) dmax = d2;
+            if (e2 > emax) emax = e2;
         }
         res = emax > 0.0 ? sqrt(dmax / emax) : (dmax > 0.0 ? INFINITY : 0.0);
         if (res <= tol) break;
@@ -1121,14 +1129,12 @@ static void drive_layers(orc_sim* s)
             }
 }
 
-int orc_step(orc_sim* s, int64_t nsteps)
+/* One step up to (without) the boundary pass; returns the failed cells. */
+static int64_t step_interior(orc_sim* s)
 {
     const orc_params* P = &s->P;
-#ifdef _OPENMP
-    if (P->threads > 0) omp_set_num_threads(P->threads);
-#endif
     int64_t fails = 0;
-    for (int64_t t = 0; t < nsteps; ++t) {
+    {
         int64_t it_sum = 0, it_max = s->iter_max;
         s->force_on = orc_force_on(s);
         collide_all(s);
@@ -1149,14 +1155,27 @@ int orc_step(orc_sim* s, int64_t nsteps)
         tmp = s->g; s->g = s->g2; s->g2 = tmp;
         tmp = s->h; s->h = s->h2; s->h2 = tmp;
         tmp = s->prim; s->prim = s->prim2; s->prim2 = tmp;
-        open_boundaries(s);
-        normal_b_fix(s);
-        drive_layers(s);
         s->iter_total += it_sum;
         s->iter_max = it_max;
         s->steps += 1;
     }
     s->recover_fail += fails;
+    return fails;
+}
+
+int orc_step(orc_sim* s, int64_t nsteps)
+{
+    const orc_params* P = &s->P;
+#ifdef _OPENMP
+    if (P->threads > 0) omp_set_num_threads(P->threads);
+#endif
+    int64_t fails = 0;
+    for (int64_t t = 0; t < nsteps; ++t) {
+        fails += step_interior(s);
+        open_boundaries(s);
+        normal_b_fix(s);
+        drive_layers(s);
+    }
     return fails ? -1 : 0;
 }
 

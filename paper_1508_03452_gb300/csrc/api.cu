@@ -36,7 +36,8 @@ struct RunState {
     int periodic[3] = {1, 1, 1};
     float* d_samples = nullptr;  // caller-owned training-sample buffer (or NULL)
     void* d_ez0 = nullptr;       // E^z of the initial state (primitive type, N), for the reconnection rate
-    double* d_drive = nullptr;   // drive velocity per (x, y) column (driven runs)
+    double* d_drive = nullptr;   // drive velocity (driven runs) or body force (forced runs) per (x, y) column
+    double* d_umax = nullptr;    // forced runs with a cut-off: max |u|^2 of the state, running max of the next
 };
 
 constexpr size_t kStatsBytes = lb::kNumStats * sizeof(unsigned long long);  // totals (checkpoint)
@@ -259,6 +260,13 @@ bool has_open(const RunState& r)
     return r.p.bc[0] || r.p.bc[1] || r.p.bc[2] || r.p.bc[3] || r.p.bc[4] || r.p.bc[5];
 }
 
+bool forced(const RunState& r) { return r.p.drive_f0 != 0.0 && r.p.drive_layers > 0; }
+bool capped(const RunState& r) { return forced(r) && r.p.drive_vmax > 0.0; }
+
+// runs stepped by the kernel variant with the open-face code (which also
+// holds the body force)
+bool open_variant(const RunState& r) { return has_open(r) || forced(r); }
+
 // kernel arguments of one run reading input buffer `in`
 template <class Cfg>
 lb::StepArgs<Cfg> make_args(lbrmhd_handle h, const RunState& r, int in)
@@ -289,6 +297,17 @@ lb::StepArgs<Cfg> make_args(lbrmhd_handle h, const RunState& r, int in)
     A.mlp = h->d_mlp;
     A.dump = r.d_samples;
     A.seed = run_seed(r);
+    if (forced(r)) {
+        const double dt = r.p.dx / (std::sqrt(2.0) * r.p.c);
+        A.open_mask |= lb::OPEN_EXTRA;
+        A.fdrive = r.d_drive;
+        A.force_layers = std::min(r.p.drive_layers, r.p.nz);
+        A.vmax2 = capped(r) ? r.p.drive_vmax * r.p.drive_vmax : 0.0;
+        A.umax_in = r.d_umax;
+        A.umax_out = capped(r) ? r.d_umax + 1 : nullptr;
+        A.force_cdt = (R)(r.p.c * dt / (10.0 * lb::kQ));
+        A.force_dt = (R)dt;
+    }
     return A;
 }
 
@@ -308,7 +327,7 @@ int build_tiles(lbrmhd_handle h, const lbrmhd_schedule& sc)
             std::vector<std::vector<int4>> per;
             for (int ri = 0; ri < (int)h->runs.size(); ++ri) {
                 const RunState& r = h->runs[ri];
-                if ((r.p.nz > 1) != (is3d == 1) || run_seed(r) != seed || has_open(r) != (open == 1)) continue;
+                if ((r.p.nz > 1) != (is3d == 1) || run_seed(r) != seed || open_variant(r) != (open == 1)) continue;
                 std::vector<int4> t;
                 for (int z = 0; z < r.p.nz; ++z)
                     for (int y0 = 0; y0 < r.p.ny; y0 += by)
@@ -394,10 +413,12 @@ int issue_step(lbrmhd_handle h, const lbrmhd_schedule& sc, int in, cudaStream_t 
     } else {
         for (const auto& r : h->runs) LB_CK(lb::launch_step<Cfg>(make_args<Cfg>(h, r, in), s));
     }
-    for (const auto& r : h->runs)
+    for (const auto& r : h->runs) {
         if (has_open(r))
             LB_CK(lb::launch_boundaries<Cfg>(view<Cfg>(r, out), make_phys<R>(r.p, r.ref, runref(r)), r.p.bc,
                                              r.p.drive_layers, r.d_drive, s));
+        if (capped(r)) LB_CK(lb::launch_umax_roll(r.d_umax, s));
+    }
     return LBRMHD_OK;
 }
 
@@ -442,6 +463,7 @@ int issue_steps(lbrmhd_handle h, const lbrmhd_schedule& sc, int in, int64_t n, c
             if (has_open(r))
                 LB_CK(lb::launch_boundaries<Cfg>(view<Cfg>(r, 1 - cin), make_phys<R>(r.p, r.ref, runref(r)), r.p.bc,
                                                  r.p.drive_layers, r.d_drive, st));
+            if (capped(r)) LB_CK(lb::launch_umax_roll(r.d_umax, st));
         }
     }
     for (int i = 0; i < S; ++i) {
@@ -556,6 +578,7 @@ int init_run(lbrmhd_handle h, RunState& r, const lb::InitInputs& in)
     const size_t qb = sizeof(typename Cfg::prim);
     LB_CK(cudaMemcpyAsync(r.d_ez0, (const char*)r.prim[r.cur] + (size_t)(lb::P_E + 2) * r.stride * qb, r.N * qb,
                           cudaMemcpyDeviceToDevice, h->stream));
+    if (capped(r)) LB_CK(lb::launch_umax_state<Cfg>(view<Cfg>(r, r.cur), r.d_umax, h->stream));
     r.initialized = true;
     runs_changed(h);
     r.steps = 0;
@@ -612,6 +635,11 @@ std::string check_params(const lbrmhd_params& p)
         if ((p.bc[2 * a] == LBRMHD_PERIODIC) != (p.bc[2 * a + 1] == LBRMHD_PERIODIC))
             return "an axis must be periodic on both faces or on neither";
     if (p.bc[4] == LBRMHD_DRIVEN && p.drive_layers < 0) return "drive_layers must be >= 0";
+    if (!std::isfinite(p.drive_f0) || !std::isfinite(p.drive_vmax)) return "drive_f0 and drive_vmax must be finite";
+    if (p.drive_f0 != 0.0) {
+        if (p.drive_layers < 1) return "a body force needs drive_layers >= 1";
+        if (p.bc[4] == LBRMHD_DRIVEN) return "a body force replaces the DRIVEN face: use OPEN or PERIODIC on -z";
+    }
     return "";
 }
 
@@ -692,7 +720,7 @@ std::string batch_signature(lbrmhd_handle h)
     std::ostringstream o;
     o << "p" << h->precision;
     for (const auto& r : h->runs)
-        o << "_" << r.p.nx << "x" << r.p.ny << "x" << r.p.nz << "s" << run_seed(r) << (has_open(r) ? "o" : "");
+        o << "_" << r.p.nx << "x" << r.p.ny << "x" << r.p.nz << "s" << run_seed(r) << (open_variant(r) ? "o" : "");
     return o.str();
 }
 
@@ -793,6 +821,84 @@ int autotune(lbrmhd_handle h, int trials, lbrmhd_schedule* best_out, double* bes
 
 }  // namespace
 
+namespace {
+
+// the cut-off's maximum |u|^2 taken from the current state of a run
+int refresh_umax(lbrmhd_handle h, RunState& r)
+{
+    if (!capped(r)) return LBRMHD_OK;
+    switch (h->precision) {
+        case LBRMHD_FP64: LB_CK(lb::launch_umax_state<lb::CfgF64>(view<lb::CfgF64>(r, r.cur), r.d_umax, h->stream)); break;
+        case LBRMHD_FP32: LB_CK(lb::launch_umax_state<lb::CfgF32>(view<lb::CfgF32>(r, r.cur), r.d_umax, h->stream)); break;
+        default: LB_CK(lb::launch_umax_state<lb::CfgF16>(view<lb::CfgF16>(r, r.cur), r.d_umax, h->stream));
+    }
+    return LBRMHD_OK;
+}
+
+// The relaxed initialisation after init_common(host inputs): the inputs n, p,
+// u (3), B (3) are in h->d_io, the layout the step kernel's relaxation reads.
+template <class Cfg>
+int relax_run(lbrmhd_handle h, RunState& r, int max_iters, double tol, int* iters, double* residual)
+{
+    using R = typename Cfg::real;
+    const int64_t N = r.N;
+    const int start = r.cur;
+    double* e = nullptr;  // E_{k-1}, E_{k-2}
+    if (cudaMalloc(&e, 6 * N * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, LBRMHD_ERR_OOM, "relaxation history allocation failed");
+    }
+    int k = 0;
+    double res = 0.0;
+    cudaError_t ce = lb::launch_relax_history<Cfg>(view<Cfg>(r, r.cur), e, h->stream);
+    while (ce == cudaSuccess && k < max_iters) {
+        ++k;
+        ce = cudaMemsetAsync(h->d_small, 0, 2 * sizeof(double), h->stream);
+        lb::StepArgs<Cfg> A = make_args<Cfg>(h, r, r.cur);
+        A.force_layers = 0;  // no body force while the fields relax
+        A.umax_out = nullptr;
+        A.open_mask |= lb::OPEN_EXTRA;
+        A.relax_in = h->d_io;
+        A.relax_e = e;
+        A.relax_red = h->d_small;
+        if (ce == cudaSuccess) ce = lb::launch_step<Cfg>(A, h->stream);
+        if (ce == cudaSuccess && has_open(r))
+            ce = lb::launch_boundaries<Cfg>(view<Cfg>(r, 1 - r.cur), make_phys<R>(r.p, r.ref, runref(r)), r.p.bc,
+                                            r.p.drive_layers, r.d_drive, h->stream);
+        r.cur ^= 1;
+        double red[2] = {0.0, 0.0};
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(red, h->d_small, sizeof(red), cudaMemcpyDeviceToHost, h->stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+        res = red[1] > 0.0 ? std::sqrt(red[0] / red[1]) : (red[0] > 0.0 ? INFINITY : 0.0);
+        if (res <= tol) break;
+    }
+    cudaFree(e);
+    if (ce != cudaSuccess) return fail(h, LBRMHD_ERR_CUDA, std::string("relaxed initialisation: ") + cudaGetErrorString(ce));
+    // every run of a handle steps from the same buffer parity
+    if (r.cur != start) {
+        const size_t pb = pop_bytes(h->precision), hb = hp_bytes(h->precision);
+        LB_CK(cudaMemcpyAsync(r.pops[start], r.pops[r.cur], 38 * r.stride * pb, cudaMemcpyDeviceToDevice, h->stream));
+        LB_CK(cudaMemcpyAsync(r.h[start], r.h[r.cur], 25 * r.stride * hb, cudaMemcpyDeviceToDevice, h->stream));
+        LB_CK(cudaMemcpyAsync(r.prim[start], r.prim[r.cur], lb::NPRIM * r.stride * hb, cudaMemcpyDeviceToDevice,
+                              h->stream));
+        r.cur = start;
+    }
+    // a fresh start: counters, step count, E^z_0, the cut-off's maximum
+    const size_t qb = sizeof(typename Cfg::prim);
+    LB_CK(cudaMemsetAsync(r.d_stats, 0, kStatsAlloc, h->stream));
+    LB_CK(cudaMemcpyAsync(r.d_ez0, (const char*)r.prim[r.cur] + (size_t)(lb::P_E + 2) * r.stride * qb, r.N * qb,
+                          cudaMemcpyDeviceToDevice, h->stream));
+    if (capped(r)) LB_CK(lb::launch_umax_state<Cfg>(view<Cfg>(r, r.cur), r.d_umax, h->stream));
+    LB_CK(cudaStreamSynchronize(h->stream));
+    r.steps = 0;
+    runs_changed(h);
+    if (iters) *iters = k;
+    if (residual) *residual = res;
+    return LBRMHD_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int lbrmhd_create(const lbrmhd_params* params, int n_runs, lbrmhd_handle* out)
@@ -841,9 +947,15 @@ int lbrmhd_create(const lbrmhd_params* params, int n_runs, lbrmhd_handle* out)
             }
         }
         ok = ok && cudaMalloc(&s.d_ez0, s.N * qb) == cudaSuccess;
-        if (ok && s.p.bc[4] == LBRMHD_DRIVEN) {
+        if (ok && (s.p.bc[4] == LBRMHD_DRIVEN || forced(s))) {
+            // the two-vortex pattern: velocity of the driven layers, or the force density
+            const double amp = forced(s) ? s.p.drive_f0 : s.p.drive_u0;
             ok = cudaMalloc(&s.d_drive, 2 * sizeof(double) * s.p.nx * s.p.ny) == cudaSuccess;
-            ok = ok && lb::launch_drive_profile(s.p.nx, s.p.ny, s.p.drive_u0, s.d_drive, nullptr) == cudaSuccess;
+            ok = ok && lb::launch_drive_profile(s.p.nx, s.p.ny, amp, s.d_drive, nullptr) == cudaSuccess;
+        }
+        if (ok && capped(s)) {
+            ok = cudaMalloc(&s.d_umax, 2 * sizeof(double)) == cudaSuccess;
+            if (ok) cudaMemset(s.d_umax, 0, 2 * sizeof(double));
         }
         ok = ok && cudaMalloc(&s.d_stats, kStatsAlloc) == cudaSuccess;
         if (ok) cudaMemset(s.d_stats, 0, kStatsAlloc);
@@ -882,6 +994,7 @@ int lbrmhd_destroy(lbrmhd_handle h)
         if (r.d_stats) cudaFree(r.d_stats);
         if (r.d_ez0) cudaFree(r.d_ez0);
         if (r.d_drive) cudaFree(r.d_drive);
+        if (r.d_umax) cudaFree(r.d_umax);
     }
     if (h->d_scratch) cudaFree(h->d_scratch);
     if (h->d_io) cudaFree(h->d_io);
@@ -912,6 +1025,22 @@ int lbrmhd_init_fields(lbrmhd_handle h, int run, const double* n, const double* 
                        const double* E)
 {
     return init_common(h, run, n, p, u, B, E, false);
+}
+
+int lbrmhd_init_fields_relaxed(lbrmhd_handle h, int run, const double* n, const double* p, const double* u,
+                               const double* B, int max_iters, double tol, int* iters, double* residual)
+{
+    if (bad_run(h, run)) return h ? fail(h, LBRMHD_ERR_BAD_ARG, "run out of range") : LBRMHD_ERR_BAD_ARG;
+    if (max_iters < 1 || !(tol >= 0)) return fail(h, LBRMHD_ERR_BAD_ARG, "max_iters must be >= 1 and tol >= 0");
+    RunState& r = h->runs[run];
+    if (r.p.bc[4] == LBRMHD_DRIVEN) return fail(h, LBRMHD_ERR_BAD_ARG, "relaxed initialisation of a DRIVEN run");
+    int rc = init_common(h, run, n, p, u, B, nullptr, false);
+    if (rc) return rc;
+    switch (h->precision) {
+        case LBRMHD_FP64: return relax_run<lb::CfgF64>(h, r, max_iters, tol, iters, residual);
+        case LBRMHD_FP32: return relax_run<lb::CfgF32>(h, r, max_iters, tol, iters, residual);
+        default: return relax_run<lb::CfgF16>(h, r, max_iters, tol, iters, residual);
+    }
 }
 
 int lbrmhd_init_fields_device(lbrmhd_handle h, int run, const double* n, const double* p, const double* u,
@@ -1164,6 +1293,8 @@ int lbrmhd_set_state(lbrmhd_handle h, const void* host_buf, size_t bytes)
                                   h->stream));
         LB_CK(cudaMemcpyAsync(r.d_ez0, o, r.N * hb, cudaMemcpyHostToDevice, h->stream));
         o += r.N * hb;
+        const int rc2 = refresh_umax(h, r);
+        if (rc2) return rc2;
         r.initialized = true;
         runs_changed(h);
     }

@@ -616,6 +616,72 @@ cudaError_t launch_null(const PopView<Cfg>& V, int y_lo, int y_hi, const typenam
     return cudaGetLastError();
 }
 
+// max |u|^2 of a state into out[0] (float64 bits, atomicMax; out[0] zeroed
+// before), out[1] (the running maximum of the next step) zeroed
+template <class Cfg>
+__global__ void umax_state_kernel(PopView<Cfg> V, double* out)
+{
+    const int64_t N = (int64_t)V.nx * V.ny * V.nz;
+    double m = 0.0;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
+        double u2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            const double u = (double)V.prim[(P_U + a) * V.stride + c];
+            u2 += u * u;
+        }
+        m = fmax(m, u2);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x % 32 == 0) atomicMax(reinterpret_cast<unsigned long long*>(out), (unsigned long long)__double_as_longlong(m));
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[1] = 0.0;
+}
+
+// after a step: the running maximum becomes the input state's, and restarts
+__global__ void umax_roll_kernel(double* u)
+{
+    u[0] = u[1];
+    u[1] = 0.0;
+}
+
+// E of a state into both history planes E_{k-1}, E_{k-2} (3 N float64 each)
+template <class Cfg>
+__global__ void relax_history_kernel(PopView<Cfg> V, double* e)
+{
+    const int64_t N = (int64_t)V.nx * V.ny * V.nz;
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    for (int a = 0; a < 3; ++a) {
+        const double E = (double)V.prim[(P_E + a) * V.stride + c];
+        e[a * N + c] = E;
+        e[(3 + a) * N + c] = E;
+    }
+}
+
+template <class Cfg>
+cudaError_t launch_umax_state(const PopView<Cfg>& V, double* out, cudaStream_t s)
+{
+    const int64_t N = (int64_t)V.nx * V.ny * V.nz;
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    const int64_t nb = blocks_for(N, 256);
+    umax_state_kernel<Cfg><<<(unsigned)(nb < 1216 ? nb : 1216), 256, 0, s>>>(V, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_umax_roll(double* u, cudaStream_t s)
+{
+    umax_roll_kernel<<<1, 1, 0, s>>>(u);
+    return cudaGetLastError();
+}
+
+template <class Cfg>
+cudaError_t launch_relax_history(const PopView<Cfg>& V, double* e, cudaStream_t s)
+{
+    const int64_t N = (int64_t)V.nx * V.ny * V.nz;
+    relax_history_kernel<Cfg><<<blocks_for(N, 256), 256, 0, s>>>(V, e);
+    return cudaGetLastError();
+}
+
 #define LB_INSTANTIATE(CFG)                                                                                        \
     template cudaError_t launch_init<CFG>(const PopView<CFG>&, const InitInputs&, const Phys<double>&, int*,      \
                                           cudaStream_t);                                                           \
@@ -627,7 +693,9 @@ cudaError_t launch_null(const PopView<Cfg>& V, int y_lo, int y_hi, const typenam
     template cudaError_t launch_diag<CFG>(const PopView<CFG>&, const Phys<double>&, const RefState&, double*,      \
                                           int64_t, double*, cudaStream_t);                                         \
     template cudaError_t launch_null<CFG>(const PopView<CFG>&, int, int, const CFG::prim*, double, double*,       \
-                                          int64_t, double*, cudaStream_t);
+                                          int64_t, double*, cudaStream_t);                                         \
+    template cudaError_t launch_umax_state<CFG>(const PopView<CFG>&, double*, cudaStream_t);                      \
+    template cudaError_t launch_relax_history<CFG>(const PopView<CFG>&, double*, cudaStream_t);
 
 LB_INSTANTIATE(CfgF64)
 LB_INSTANTIATE(CfgF32)

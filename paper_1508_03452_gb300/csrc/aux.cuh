@@ -90,6 +90,14 @@ cudaError_t launch_boundaries(const PopView<Cfg>& V, const Phys<typename Cfg::re
 cudaError_t launch_drive_profile(int nx, int ny, double u0, double* uv, cudaStream_t s);
 template <class Cfg>
 cudaError_t launch_moments(const PopView<Cfg>& V, const Phys<double>& k, double* out, cudaStream_t s);
+// max |u|^2 of a state into out[0], out[1] = 0 (body-force cut-off)
+template <class Cfg>
+cudaError_t launch_umax_state(const PopView<Cfg>& V, double* out, cudaStream_t s);
+// after a step of a run with a cut-off: u[0] = u[1], u[1] = 0
+cudaError_t launch_umax_roll(double* u, cudaStream_t s);
+// E of a state into the two history planes of the relaxed initialisation
+template <class Cfg>
+cudaError_t launch_relax_history(const PopView<Cfg>& V, double* e, cudaStream_t s);
 template <class Cfg>
 cudaError_t launch_populations(const PopView<Cfg>& V, const RefPops& ref, double* f, double* g, double* h,
                                cudaStream_t s);

@@ -86,7 +86,25 @@ struct StepArgs {
     const unsigned char* mlp;   // device inference blob of the learned seed (SEED_MLP)
     float* dump;                // optional: per cell 20 features + 4 targets of the learned seed
     int seed;                   // SEED_PREV | SEED_MLP | SEED_COLD
+    // photospheric body force (open-variant code): the pattern F of each (x, y)
+    // column (2 float64, amplitude F0), applied in z < force_layers while the
+    // input state's max |u|^2 (*umax_in) is below vmax2 (vmax2 <= 0: always);
+    // force_cdt = c dt / (10 q) and force_dt = dt put it into the populations
+    const double* fdrive;
+    int force_layers;
+    double vmax2;
+    const double* umax_in;  // max |u|^2 of the input state (forced runs with a cut-off)
+    double* umax_out;       // running max |u|^2 of the output state (float64 bits, atomicMax)
+    real force_cdt, force_dt;
+    // relaxed initialisation (open-variant code): the initial n, p, u (3), B (3)
+    // planes (8 N float64) the fluid and B are held at, E_{k-1}, E_{k-2} (6 N
+    // float64) and the running max |E - E_{k-2}|^2, max |E|^2 (2 float64 bits)
+    const double* relax_in;
+    double* relax_e;
+    double* relax_red;
 };
+// open_mask bit for runs that need the open-variant code without an open face
+constexpr int OPEN_EXTRA = 8;
 
 // population load / store in the configured format
 template <class Cfg>

@@ -227,6 +227,80 @@ struct StepMinBlocks {
                                                                 : LB_STEP_MIN_BLOCKS;
 };
 
+// Photospheric body force (reading R25) on the streamed f of one cell: the
+// rest population takes F.u dt, a moving one c dt (F . chat_i) / (10 q)
+// (p_i = (1, q chat_i), sum_i chat_i^a chat_i^b = 10 delta_ab), so the added
+// moments are T^00 += F.u dt and T^0a += c dt F^a, nothing else.
+template <int I, class Cfg>
+struct AddForce {
+    using R = typename Cfg::real;
+    static __device__ __forceinline__ void run(R* sp, int nth, const R (&F)[3], R s, R w)
+    {
+        constexpr int cx = c19(I, 0), cy = c19(I, 1), cz = c19(I, 2);
+        if constexpr (cx == 0 && cy == 0 && cz == 0)
+            sp[I * nth] += w;
+        else
+            sp[I * nth] += s * (R(cx) * F[0] + R(cy) * F[1] + R(cz) * F[2]);
+        AddForce<I + 1, Cfg>::run(sp, nth, F, s, w);
+    }
+};
+template <class Cfg>
+struct AddForce<19, Cfg> {
+    using R = typename Cfg::real;
+    static __device__ __forceinline__ void run(R*, int, const R (&)[3], R, R) {}
+};
+
+// Relaxed initialisation (reading R27): f and g of the cell at the
+// equilibrium of its (reset) primitives, so that the collision returns it.
+template <int I, class Cfg>
+struct SetEqFG {
+    using R = typename Cfg::real;
+    static __device__ __forceinline__ void run(R* sp, int nth, const EqCell<R>& q)
+    {
+        sp[I * nth] = feq_dev<I>(q);
+        sp[(19 + I) * nth] = geq_dev<I>(q);
+        SetEqFG<I + 1, Cfg>::run(sp, nth, q);
+    }
+};
+template <class Cfg>
+struct SetEqFG<19, Cfg> {
+    using R = typename Cfg::real;
+    static __device__ __forceinline__ void run(R*, int, const EqCell<R>&) {}
+};
+
+// Relaxed initialisation: move the B carried by the streamed h by dB through
+// the populations whose b carries it, h_k += (dB . b_k) / 8 (sum b b^T = 8 I,
+// sum e b^T = 0, sum b = 0: E' and rho_c do not move).
+template <int K, class Cfg>
+struct ShiftHB {
+    using R = typename Cfg::real;
+    static __device__ __forceinline__ void run(R* sp, int nth, const R (&dB)[3])
+    {
+        constexpr int p = K / 8, j = K % 2, se = j == 0 ? 1 : -1;
+        sp[(38 + K) * nth] += R(-se * plane_orient(p)) * R(0.125) * dB[plane_normal(p)];
+        ShiftHB<K + 1, Cfg>::run(sp, nth, dB);
+    }
+};
+template <class Cfg>
+struct ShiftHB<24, Cfg> {
+    using R = typename Cfg::real;
+    static __device__ __forceinline__ void run(R*, int, const R (&)[3]) {}
+};
+
+// warp-wide maximum of a non-negative float64, folded into *dst (atomicMax on
+// the bit pattern, which orders non-negative doubles)
+__device__ __forceinline__ void warp_max_into(double v, double* dst)
+{
+    const unsigned mask = __activemask();
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(mask, b, o);
+        b = t > b ? t : b;
+    }
+    if ((threadIdx.x + blockDim.x * threadIdx.y) % 32 == (unsigned)(__ffs(mask) - 1))
+        atomicMax(reinterpret_cast<unsigned long long*>(dst), b);
+}
+
 // One cell update (x, y, z) of one run; `tid` is the thread's index in its
 // block of kStepThreads threads (its rows of the shared-memory buffers). Threads of
 // cells outside the grid return at once, except in the learned-seed variant,
@@ -290,6 +364,17 @@ __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, 
         old.B[a] = (R)A.pin[(P_B + a) * A.stride + c];
     }
     old.rho = R(0);
+    if constexpr (kOpenCode) {
+        if (zs < A.force_layers && (A.vmax2 <= 0.0 || *A.umax_in < A.vmax2)) {
+            const double* fd = A.fdrive + 2 * (xs + (int64_t)A.nx * ys);
+            const R F[3] = {(R)fd[0], (R)fd[1], R(0)};
+            const R w = (F[0] * old.u[0] + F[1] * old.u[1]) * A.force_dt;
+            AddForce<0, Cfg>::run(sp, nth, F, A.force_cdt, w);
+            Tm[0] += w;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) Tm[a + 1] += R(10) * A.force_cdt * F[a];
+        }
+    }
 
     // 2. moments (reference state added back): rest state (eps_r, p_r) and the
     // reference EM terms k.Tem
@@ -457,6 +542,49 @@ __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, 
         for (int a = 0; a < 3; ++a) d[MLP_IN + a] = (float)beta[a];
         d[MLP_IN + 3] = (float)((nw.eps) / (k.eps_r + T[0][0]) - R(1));
     }
+    bool relax_eq = false;
+    if constexpr (kOpenCode) {
+        if (A.umax_out)
+            warp_max_into((double)(nw.u[0] * nw.u[0] + nw.u[1] * nw.u[1] + nw.u[2] * nw.u[2]), A.umax_out);
+        if (A.relax_in) {
+            // relaxed initialisation (reading R27): track E of every written
+            // cell, then hold the cell at the initial n, p, u, B before the
+            // collision (the boundary pass follows)
+            const int64_t NN = (int64_t)A.nx * A.ny * A.nz, cw = c + dco;
+            double d2 = 0.0, e2 = 0.0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const double E = (double)nw.E[a];
+                const double em2 = A.relax_e[(3 + a) * NN + cw];
+                d2 += (E - em2) * (E - em2);
+                e2 += E * E;
+                A.relax_e[(3 + a) * NN + cw] = A.relax_e[a * NN + cw];
+                A.relax_e[a * NN + cw] = E;
+            }
+            warp_max_into(d2, A.relax_red);
+            warp_max_into(e2, A.relax_red + 1);
+            {  // (an open-face cell is held at the fields of its interior source, whose update it is)
+                const double* in = A.relax_in;
+                const double n0 = in[c], p0 = in[NN + c];
+                nw.n = (R)n0;
+                nw.eps = (R)(n0 * (double)k.c2 + p0 / (double)k.gm1);
+                n_dev = (R)(n0 - (double)k.n_r);
+                eps_dev = (R)((n0 - (double)k.n_r) * (double)k.c2 + (p0 - (double)k.p_r) / (double)k.gm1);
+                R dBs[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    nw.u[a] = (R)in[(2 + a) * NN + c];
+                    const double B0 = in[(5 + a) * NN + c];
+                    dBs[a] = (R)(B0 - (double)nw.B[a]);
+                    nw.B[a] = (R)B0;
+                    dB[a] = (R)(B0 - (double)k.Br[a]);
+                }
+                ShiftHB<0, Cfg>::run(sp, nth, dBs);
+                ohm_current(nw.E, nw.u, nw.B, nw.rho, k, J);
+                relax_eq = true;
+            }
+        }
+    }
 
     // 4. collisions at the new time level and stores
     R dE[3];
@@ -464,6 +592,7 @@ __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, 
     for (int a = 0; a < 3; ++a) dE[a] = nw.E[a] - k.Er[a];
     EqCell<R> q;
     eq_cell(nw, n_dev, eps_dev, dE, dB, k, q);
+    if (kOpenCode && relax_eq) SetEqFG<0, Cfg>::run(sp, nth, q);
     CollideFG<0, Cfg>::run(A, c + dco, sp, nth, q);
     const bool em_coll = (A.flags & FLAG_NO_EM_COLLISION) == 0;
     // h_c - h_ref = 2 h^eq(E - Er, B - Br, J) - (h - h_ref)  (Eq. Maxwell-eq is linear)

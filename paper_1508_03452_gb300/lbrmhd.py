@@ -34,6 +34,7 @@ EXPORTED = [
     "lbrmhd_mlp_nparams", "lbrmhd_mlp_blob_bytes", "lbrmhd_mlp_pack", "lbrmhd_mlp_infer", "lbrmhd_mlp_grad",
     "lbrmhd_mlp_train", "lbrmhd_set_mlp_weights", "lbrmhd_set_mlp_samples", "lbrmhd_get_iteration_histogram",
     "lbrmhd_set_schedule", "lbrmhd_get_schedule", "lbrmhd_autotune", "lbrmhd_reconnection_rate",
+    "lbrmhd_init_fields_relaxed",
 ]
 
 
@@ -44,7 +45,7 @@ class Params(C.Structure):
         ("tau", C.c_double), ("sigma", C.c_double), ("gamma_ad", C.c_double), ("alpha", C.c_double),
         ("c", C.c_double), ("dx", C.c_double), ("drive_u0", C.c_double),
         ("drive_layers", C.c_int32), ("precision", C.c_int32), ("recovery", C.c_int32), ("flags", C.c_int32),
-        ("max_iters", C.c_int32), ("tol", C.c_double),
+        ("max_iters", C.c_int32), ("tol", C.c_double), ("drive_f0", C.c_double), ("drive_vmax", C.c_double),
     ]
 
 
@@ -62,7 +63,7 @@ def make_schedule(kind=SCHED_BATCH, bx=128, waves=0, order=0, streams=1, graph_s
 
 def make_params(nx, ny=1, nz=1, *, bc=(PERIODIC,) * 6, tau=1.0, sigma=100.0, gamma_ad=4.0 / 3.0, alpha=0.1, c=1.0,
                 dx=1.0, drive_u0=0.0, drive_layers=0, precision=FP32, recovery=RECOVERY_PLAIN, flags=0, max_iters=0,
-                tol=0.0) -> Params:
+                tol=0.0, drive_f0=0.0, drive_vmax=0.0) -> Params:
     P = Params()
     P.nx, P.ny, P.nz = int(nx), int(ny), int(nz)
     for k in range(6):
@@ -70,6 +71,7 @@ def make_params(nx, ny=1, nz=1, *, bc=(PERIODIC,) * 6, tau=1.0, sigma=100.0, gam
     P.tau, P.sigma, P.gamma_ad, P.alpha, P.c, P.dx = tau, sigma, gamma_ad, alpha, c, dx
     P.drive_u0, P.drive_layers = drive_u0, int(drive_layers)
     P.precision, P.recovery, P.flags, P.max_iters, P.tol = int(precision), int(recovery), int(flags), int(max_iters), tol
+    P.drive_f0, P.drive_vmax = drive_f0, drive_vmax
     return P
 
 
@@ -104,6 +106,8 @@ def load(build_if_missing: bool = True):
         L.lbrmhd_destroy.argtypes = [vp]
         L.lbrmhd_set_stream.argtypes = [vp, vp]
         L.lbrmhd_init_fields.argtypes = [vp, C.c_int, dp, dp, dp, dp, dp]
+        L.lbrmhd_init_fields_relaxed.argtypes = [vp, C.c_int, dp, dp, dp, dp, C.c_int, C.c_double,
+                                                 C.POINTER(C.c_int), dp]
         L.lbrmhd_init_fields_device.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp]
         L.lbrmhd_step.argtypes = [vp, i64]
         L.lbrmhd_get_moments.argtypes = [vp, C.c_int, dp]
@@ -282,6 +286,16 @@ class Solver:
         Ep = None if E is None else _f64(E, 3 * N)
         self._check(self._L.lbrmhd_init_fields(self._h, run, _dp(n), _dp(p), _dp(u), _dp(B),
                                                None if Ep is None else _dp(Ep)))
+
+    def init_fields_relaxed(self, run, n, p, u, B, max_iters=200, tol=1e-6):
+        """Initial state whose E, J have relaxed with n, p, u, B held (the
+        flare set-up's iterative initialisation); returns (steps, residual)."""
+        N = self.cells[run]
+        n, p, u, B = _f64(n, N), _f64(p, N), _f64(u, 3 * N), _f64(B, 3 * N)
+        its, res = C.c_int(0), C.c_double(0.0)
+        self._check(self._L.lbrmhd_init_fields_relaxed(self._h, run, _dp(n), _dp(p), _dp(u), _dp(B), int(max_iters),
+                                                       float(tol), C.byref(its), C.byref(res)))
+        return its.value, res.value
 
     def init_fields_device(self, run, n, p, u, B, E=None):
         """Device float64 arrays: torch tensors (contiguous, cuda) or integer pointers."""
