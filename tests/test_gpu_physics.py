@@ -18,25 +18,57 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 OPEN_X = (L.OPEN, L.OPEN, L.PERIODIC, L.PERIODIC, L.PERIODIC, L.PERIODIC)
 
 
-@pytest.mark.parametrize("precision", [L.FP64, L.FP32])
-def test_paper_current_sheet_matches_erf_on_gpu(precision):
-    """100 cells on [-1.5, 1.5], sigma = 100, p = 50, open faces, from the erf
-    profile at t = 1 to t = 9: within 1 % of the exact self-similar solution."""
+def _gpu_sheet(N, sigma, precision, *, t_end=None, steps=None):
     g = json.load(open(os.path.join(GOLDEN, "current_sheet_convergence.json")))
-    F = W.current_sheet_paper(100, sigma=g["sigma"], t0=g["t_start"], B0=g["B0"], p0=g["p"], n0=g["n"])
+    F = W.current_sheet_paper(N, sigma=sigma, t0=g["t_start"], B0=g["B0"], p0=g["p"], n0=g["n"])
     dx = F.meta["dx"]
-    s = L.Solver(L.make_params(F.nx, 1, 1, sigma=g["sigma"], dx=dx, bc=OPEN_X, precision=precision))
+    s = L.Solver(L.make_params(F.nx, 1, 1, sigma=sigma, dx=dx, bc=OPEN_X, precision=precision))
     s.init_fields(0, F.n, F.p, F.u, F.B)
     dt = dx / math.sqrt(2.0)
-    steps = int(round((g["t_end"] - g["t_start"]) / dt))
+    if steps is None:
+        steps = int(round((t_end - g["t_start"]) / dt))
     s.step(steps)
-    t = g["t_start"] + steps * dt
+    return F, s, g["t_start"] + steps * dt, dt
+
+
+@pytest.mark.parametrize("sigma", [50.0, 100.0])
+@pytest.mark.parametrize("precision", [L.FP64, L.FP32])
+def test_paper_current_sheet_matches_erf_on_gpu(precision, sigma):
+    """100 cells on [-1.5, 1.5], p = 50, open faces, from the erf profile at
+    t = 1 to t = 9 (Sec. IV, the paper's sigma = 50 and 100): within 1 % of
+    the exact self-similar solution."""
+    F, s, t, _ = _gpu_sheet(100, sigma, precision, t_end=9.0)
     By = s.moments()[10]
     st = s.stats()
     s.close()
-    exact = np.array([math.erf(0.5 * math.sqrt(g["sigma"] / t) * v) for v in F.meta["x"]])
+    exact = np.array([math.erf(0.5 * math.sqrt(sigma / t) * v) for v in F.meta["x"]])
     assert st["recover_fail"] == 0
     assert np.linalg.norm(By - exact) / np.linalg.norm(exact) < 0.01
+
+
+def test_paper_convergence_slope_on_gpu():
+    """The paper's convergence study on the GPU (float64): RMS difference of
+    the sigma = 100 sheet at t = 9 on 25, 50, 100 cells against a 200-cell run
+    (averaged onto the coarse cells, linear in time between two steps); slope
+    within 0.25 of the printed -1.9668."""
+    g = json.load(open(os.path.join(GOLDEN, "current_sheet_convergence.json")))
+    Ns, errs = (25, 50, 100), []
+    for N in Ns:
+        _, s, t, _ = _gpu_sheet(N, g["sigma"], L.FP64, t_end=g["t_end"])
+        By = s.moments()[10]
+        s.close()
+        _, r, _, dtr = _gpu_sheet(g["reference_cells"], g["sigma"], L.FP64, steps=0)
+        k = int(math.floor((t - g["t_start"]) / dtr))
+        r.step(k)
+        a = r.moments()[10]
+        r.step(1)
+        b = r.moments()[10]
+        r.close()
+        w = (t - g["t_start"] - k * dtr) / dtr
+        ref = ((1 - w) * a + w * b).reshape(N, -1).mean(axis=1)
+        errs.append(math.sqrt(np.mean((By - ref) ** 2)))
+    slope = np.polyfit(np.log(Ns), np.log(errs), 1)[0]
+    assert abs(slope - g["slope"]) < 0.25, (slope, errs)
 
 
 @pytest.mark.parametrize("precision", [L.FP64, L.FP32])
