@@ -166,13 +166,10 @@ class ClockSampler:
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline_sample(seconds: float = 12.0, threads: int | None = None):
-    """The oracle as it stands on the host cores: the sigma = 100 current sheet,
-    full 1024-wide rows, a strip of 32 rows (periodic), stepped for ~`seconds`."""
+def _oracle_strip_mlups(seconds: float, threads: int):
     import oracle as O
     from paper_1508_03452_gb300 import workloads as W
 
-    threads = threads or os.cpu_count() or 1
     ny = 32
     F = W.current_sheet(NX, ny, 1, delta=8.0)
     s = O.Sim(O.make_params(NX, ny, 1, sigma=100.0, threads=threads))
@@ -186,9 +183,20 @@ def cpu_baseline_sample(seconds: float = 12.0, threads: int | None = None):
         if time.perf_counter() - t0 >= seconds:
             break
     el = time.perf_counter() - t0
-    return {"value": NX * ny * steps / el / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"current sheet sigma=100, {NX}x{ny} periodic strip of the 1024x1024 workload, {steps} steps, "
-                      f"{el:.1f} s, FP64 C oracle with OpenMP"}
+    return NX * ny * steps / el / 1e6, steps, el
+
+
+def cpu_baseline_sample(seconds: float = 12.0, threads: int | None = None):
+    """The oracle as it stands on the host cores: the sigma = 100 current sheet,
+    full 1024-wide rows, a strip of 32 rows (periodic), stepped for ~`seconds`
+    on all cores, and for a quarter of that on one thread."""
+    threads = threads or os.cpu_count() or 1
+    v, steps, el = _oracle_strip_mlups(seconds, threads)
+    v1, steps1, el1 = _oracle_strip_mlups(seconds / 4, 1)
+    return {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"current sheet sigma=100, {NX}x32 periodic strip of the 1024x1024 workload, {steps} steps, "
+                      f"{el:.1f} s, FP64 C oracle with OpenMP",
+            "single_thread": {"value": v1, "unit": UNIT, "steps": steps1, "seconds": el1}}
 
 
 def run_reference(args, world, rank):
@@ -275,34 +283,47 @@ def learned_seed_leg(args, stream, plain_moments, plain_iters, steps_total):
 
     F = W.current_sheet(NX, NY, 1, delta=8.0)
     N = NX * NY
-    solver = L.Solver([L.make_params(NX, NY, 1, sigma=sg, precision=prec, recovery=L.RECOVERY_MLP) for sg in SIGMAS],
-                      stream=stream)
-    solver.set_mlp_weights(P)
-    for r in range(len(SIGMAS)):
-        solver.init_fields(r, F.n, F.p, F.u, F.B)
-    solver.step(args.warmup)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    solver.step(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    stats = [solver.stats(r) for r in range(len(SIGMAS))]
-    hist = sum(solver.iteration_histogram(r) for r in range(len(SIGMAS)))
-    m_mlp = solver.moments(1)
-    solver.close()
+
+    def learned_run(precision):
+        solver = L.Solver([L.make_params(NX, NY, 1, sigma=sg, precision=precision, recovery=L.RECOVERY_MLP)
+                           for sg in SIGMAS], stream=stream)
+        solver.set_mlp_weights(P)
+        for r in range(len(SIGMAS)):
+            solver.init_fields(r, F.n, F.p, F.u, F.B)
+        solver.step(args.warmup)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solver.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        stats = [solver.stats(r) for r in range(len(SIGMAS))]
+        hist = sum(solver.iteration_histogram(r) for r in range(len(SIGMAS)))
+        m = solver.moments(1)
+        solver.close()
+        return ms, stats, hist, m
+
+    ms, stats, hist, m_mlp = learned_run(prec)
+    # mixed precision + learned seed: float16-deviation storage of f, g
+    ms_mx, stats_mx, hist_mx, m_mx = learned_run(L.FP16_DEV)
     ref = L.Solver(L.make_params(NX, NY, 1, sigma=SIGMAS[1], precision=L.FP64), stream=stream)
     ref.init_fields(0, F.n, F.p, F.u, F.B)
     ref.step(steps_total)
     m64 = ref.moments(0)
     ref.close()
+    cells = len(SIGMAS) * N
     return P, {
-        "value": len(SIGMAS) * N * args.steps / (ms * 1e-3) / 1e6, "unit": UNIT,
-        "iters_per_cell": sum(s["iter_total"] for s in stats) / (len(SIGMAS) * N * steps_total),
+        "value": cells * args.steps / (ms * 1e-3) / 1e6, "unit": UNIT,
+        "iters_per_cell": sum(s["iter_total"] for s in stats) / (cells * steps_total),
         "iters_p99": hist_quantile(hist, 0.99),
         "plain_iters_per_cell": plain_iters,
         "failures": sum(s["recover_fail"] for s in stats),
+        "mixed_fp16dev": {"value": cells * args.steps / (ms_mx * 1e-3) / 1e6, "unit": UNIT,
+                          "iters_per_cell": sum(s["iter_total"] for s in stats_mx) / (cells * steps_total),
+                          "iters_p99": hist_quantile(hist_mx, 0.99),
+                          "failures": sum(s["recover_fail"] for s in stats_mx),
+                          "err_vs_fp64": rel_errors(m_mx, m64)},
         "err_vs_fp64": rel_errors(m_mlp, m64), "plain_err_vs_fp64": rel_errors(plain_moments, m64),
         "error_run": f"sigma={SIGMAS[1]}, {steps_total} steps, relative L2 per field against the float64 GPU build",
         "train": {"samples": int(data.shape[0]), "adam_steps": train_steps, "batch": 1024,
