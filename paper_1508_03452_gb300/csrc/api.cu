@@ -585,6 +585,18 @@ int init_run(lbrmhd_handle h, RunState& r, const lb::InitInputs& in)
     return LBRMHD_OK;
 }
 
+// the cut-off's maximum |u|^2 taken from the current state of a run
+int refresh_umax(lbrmhd_handle h, RunState& r)
+{
+    if (!capped(r)) return LBRMHD_OK;
+    switch (h->precision) {
+        case LBRMHD_FP64: LB_CK(lb::launch_umax_state<lb::CfgF64>(view<lb::CfgF64>(r, r.cur), r.d_umax, h->stream)); break;
+        case LBRMHD_FP32: LB_CK(lb::launch_umax_state<lb::CfgF32>(view<lb::CfgF32>(r, r.cur), r.d_umax, h->stream)); break;
+        default: LB_CK(lb::launch_umax_state<lb::CfgF16>(view<lb::CfgF16>(r, r.cur), r.d_umax, h->stream));
+    }
+    return LBRMHD_OK;
+}
+
 int init_common(lbrmhd_handle h, int run, const double* n, const double* p, const double* u, const double* B,
                 const double* E, bool device_inputs)
 {
@@ -802,6 +814,8 @@ int autotune(lbrmhd_handle h, int trials, lbrmhd_schedule* best_out, double* bes
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         for (size_t i = 0; i < h->runs.size() && !rc; ++i) rc = write_stats(h, h->runs[i], saved[i].data());
+        // the dry steps rolled the body-force cut-off's maximum: take it from the state again
+        for (size_t i = 0; i < h->runs.size() && !rc; ++i) rc = refresh_umax(h, h->runs[i]);
         if (rc) return rc;
         if (cache && *cache) {
             std::ofstream f(cache, std::ios::app);
@@ -822,18 +836,6 @@ int autotune(lbrmhd_handle h, int trials, lbrmhd_schedule* best_out, double* bes
 }  // namespace
 
 namespace {
-
-// the cut-off's maximum |u|^2 taken from the current state of a run
-int refresh_umax(lbrmhd_handle h, RunState& r)
-{
-    if (!capped(r)) return LBRMHD_OK;
-    switch (h->precision) {
-        case LBRMHD_FP64: LB_CK(lb::launch_umax_state<lb::CfgF64>(view<lb::CfgF64>(r, r.cur), r.d_umax, h->stream)); break;
-        case LBRMHD_FP32: LB_CK(lb::launch_umax_state<lb::CfgF32>(view<lb::CfgF32>(r, r.cur), r.d_umax, h->stream)); break;
-        default: LB_CK(lb::launch_umax_state<lb::CfgF16>(view<lb::CfgF16>(r, r.cur), r.d_umax, h->stream));
-    }
-    return LBRMHD_OK;
-}
 
 // The relaxed initialisation after init_common(host inputs): the inputs n, p,
 // u (3), B (3) are in h->d_io, the layout the step kernel's relaxation reads.
@@ -857,6 +859,7 @@ int relax_run(lbrmhd_handle h, RunState& r, int max_iters, double tol, int* iter
         lb::StepArgs<Cfg> A = make_args<Cfg>(h, r, r.cur);
         A.force_layers = 0;  // no body force while the fields relax
         A.umax_out = nullptr;
+        A.seed = lb::SEED_PREV;  // the plain open-face variant (the seed does not change the converged state)
         A.open_mask |= lb::OPEN_EXTRA;
         A.relax_in = h->d_io;
         A.relax_e = e;

@@ -193,3 +193,41 @@ def test_force_parameters_are_checked():
     with pytest.raises(L.LbrmhdError):
         s.init_fields_relaxed(0, np.ones(N), np.ones(N), np.zeros((3, N)), np.zeros((3, N)))
     s.close()
+
+
+def test_autotune_keeps_the_cut_off_state(tmp_path, monkeypatch):
+    """The autotuner's dry steps leave a forced run with a cut-off where it
+    was: continuing after tuning equals a run that was never tuned (float64,
+    where every schedule is bit-identical)."""
+    monkeypatch.setenv("LBRMHD_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    F, kw = _flare()
+    kw["drive_vmax"] = 1.5e-3
+    P = L.make_params(F.nx, F.ny, F.nz, bc=OPEN6, precision=L.FP64, **kw)
+    a, b = L.Solver([P, P]), L.Solver([P, P])
+    for s in (a, b):
+        for r in range(2):
+            s.init_fields(r, F.n, F.p, F.u, F.B)
+        s.step(2)
+    a.autotune(trials=1)
+    a.step(8)
+    b.step(8)
+    for r in range(2):
+        assert np.array_equal(a.moments(r), b.moments(r))
+    a.close()
+    b.close()
+
+
+def test_relaxed_init_of_a_learned_seed_run_needs_no_weights():
+    """The relaxation steps use the previous-step seed, so a learned-seed run
+    can be relaxed before its network is set (float64 parity with the oracle)."""
+    nx, ny = 32, 4
+    N = nx * ny
+    B = np.zeros((3, N))
+    B[2] = 0.05 * np.sin(2 * np.pi * (np.arange(N) % nx) / nx)
+    args = (np.ones(N), np.ones(N), np.zeros((3, N)), B)
+    ref = O.Sim(O.make_params(nx, ny, 1, sigma=10.0, threads=8))
+    ref.init_relaxed(*args, max_iters=6, tol=0.0)
+    s = L.Solver(L.make_params(nx, ny, 1, sigma=10.0, precision=L.FP64, recovery=L.RECOVERY_MLP))
+    assert s.init_fields_relaxed(0, *args, max_iters=6, tol=0.0)[0] == 6
+    assert_parity(rel_errors(s.moments(), ref.moments()), TOL[L.FP64])
+    s.close()
