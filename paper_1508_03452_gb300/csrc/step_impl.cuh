@@ -167,6 +167,32 @@ struct PullH<24, IS3D, Cfg> {
                                                R&) {}
 };
 
+// (f_i^eq, g_i^eq) deviations of population I as one float32 pair: the
+// per-direction parts of Eq. Dis_fun_EM and Eq. Hupp share their structure
+// (even + s_a odd_a + s_b odd_b + s_a s_b cross), so they are formed with pair
+// instructions (the same terms as feq_dev / geq_dev, summed in pairs)
+template <int I>
+__device__ __forceinline__ float2 eq_pair(const EqCell<float>& q)
+{
+    constexpr int a = ax1(I), b = ax2(I);
+    float2 v;
+    if constexpr (a < 0) {
+        v = make_float2(q.f_rest, q.g_base);
+    } else if constexpr (b < 0) {
+        constexpr float sa = (float)c19(I, a);
+        v = __ffma2_rn(make_float2(sa, sa), make_float2(q.f_odd[a], q.g_lin[a]),
+                       make_float2(q.f_even_ax[a], q.g_base + q.g_sq[a]));
+    } else {
+        constexpr int m = a + b - 1;
+        constexpr float sa = (float)c19(I, a), sb = (float)c19(I, b), sab = sa * sb;
+        v = __ffma2_rn(make_float2(sab, sab), make_float2(q.f_cross[m], q.g_x[m]),
+                       make_float2(q.f_even_dg[m], q.g_base + q.g_sq[a] + q.g_sq[b]));
+        v = __ffma2_rn(make_float2(sa, sa), make_float2(q.f_odd[a], q.g_lin[a]), v);
+        v = __ffma2_rn(make_float2(sb, sb), make_float2(q.f_odd[b], q.g_lin[b]), v);
+    }
+    return __fmul2_rn(make_float2((float)w19(I), (float)wg19(I)), v);
+}
+
 template <int I, class Cfg>
 struct CollideFG {
     using R = typename Cfg::real;
@@ -175,8 +201,20 @@ struct CollideFG {
     {
         const R fd = sp[I * nth], gd = sp[(19 + I) * nth];
         const R K = k_aw<I>(q);
-        const R fo = fd - K * (fd - feq_dev<I>(q));
-        const R go = gd - A.k.inv_tau * (gd - geq_dev<I>(q));
+        R fo, go;
+        if constexpr (sizeof(R) == 4) {
+            // f and g of one direction relax in lock-step: the float32 pair
+            // instructions do both (fd - K (fd - feq), gd - (dt/tau)(gd - geq))
+            const float2 eq = eq_pair<I>(q);
+            const float2 d = make_float2(fd, gd);
+            const float2 t = __fadd2_rn(d, make_float2(-eq.x, -eq.y));
+            const float2 o = __ffma2_rn(make_float2(-K, -A.k.inv_tau), t, d);
+            fo = o.x;
+            go = o.y;
+        } else {
+            fo = fd - K * (fd - feq_dev<I>(q));
+            go = gd - A.k.inv_tau * (gd - geq_dev<I>(q));
+        }
         st_pop<Cfg>(A.fout + (int64_t)I * A.stride + c, fo, A.hs.finv[I]);
         st_pop<Cfg>(A.gout + (int64_t)I * A.stride + c, go, A.hs.ginv[I]);
         CollideFG<I + 1, Cfg>::run(A, c, sp, nth, q);
