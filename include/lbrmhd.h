@@ -49,9 +49,11 @@ extern "C" {
 #define LBRMHD_ERR_BAD_ARG (-1)      /* invalid argument or parameter */
 #define LBRMHD_ERR_OOM (-2)          /* device or host allocation failed */
 #define LBRMHD_ERR_CUDA (-3)         /* a CUDA runtime call failed */
-#define LBRMHD_ERR_NONCONVERGED (-4) /* a recovery did not converge (cells keep their previous state) */
+#define LBRMHD_ERR_NONCONVERGED (-4) /* reserved: lbrmhd_step is asynchronous, so a recovery that does not
+                                        converge is not returned but counted per run (lbrmhd_get_stats,
+                                        recover_fail) and its cells keep their previous primitives */
 #define LBRMHD_ERR_NONFINITE (-5)    /* a NaN or Inf was found by the diagnostics */
-#define LBRMHD_ERR_TIMEOUT (-6)      /* a device-side wait gave up */
+#define LBRMHD_ERR_TIMEOUT (-6)      /* reserved: no kernel of the library waits on another */
 #define LBRMHD_ERR_STATE (-7)        /* call out of order (e.g. step before init_fields) */
 
 /* boundary kinds, per face -x,+x,-y,+y,-z,+z */
