@@ -42,8 +42,8 @@
  *   R11 bulk-viscosity term: alpha (c dt/dx) sum_a [f(x+e_a) - 2 f + f(x-e_a)],
  *       i != 0. Coefficient: parity UNPINNED.
  *   R12 one rest EM population h_0 (25 EM populations per cell).
- *   R13 both the subtraction before the eigen-solve and the eigenvalue shift use
- *       E, B of the previous step; "F^{mu rho} F^nu_rho" is the first term of
+ *   R13 the subtraction before the eigen-solve starts from E, B of the previous
+ *       step (then R24 iterates E); "F^{mu rho} F^nu_rho" is the first term of
  *       T_EM with the index placement that gives T^00_EM = eps0 (E^2+c^2B^2)/2.
  *   R14 power method until the change of the spatial part of U is at most
  *       1e-14 of its size (or zero), seeded with the previous U.
