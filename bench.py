@@ -97,6 +97,29 @@ def profiled_traffic(precision: str):
     return float(m_b.group(1))
 
 
+def profiled_instructions(precision: str):
+    """Warp instructions per cell of the step kernel from the committed ncu
+    summary, if it was taken on the current kernel sources."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    m_sha = re.search(r"kernel_sources_sha:\s*([0-9a-f]+)", text)
+    m_i = re.search(rf"warp_instructions_per_cell_{precision}:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_i or m_sha.group(1) != kernel_sha():
+        return None
+    return float(m_i.group(1))
+
+
+def issue_ceiling(instr_per_cell, sms: int, sm_mhz: float):
+    """Cell updates per second, in millions, if every scheduler issued every
+    cycle: one thread per cell, so a warp instruction serves 32 cells; four
+    schedulers per SM."""
+    if not instr_per_cell or not sms or not sm_mhz:
+        return None
+    return sms * 4 * sm_mhz * 1e6 * 32 / instr_per_cell / 1e6
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -570,6 +593,13 @@ def run_gpu(args, world, rank, local):
         clocks = clk.summary()
         if clocks:
             line["clocks"] = clocks
+        ipc = profiled_instructions(args.precision)
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        ceil = issue_ceiling(ipc, sms, (clocks or {}).get("sm_max_mhz") or (peaks or {}).get("sm_max_mhz"))
+        if ceil:
+            # the kernel is issue-bound: its instruction count at full issue against the achieved rate
+            line["issue_roofline"] = {"warp_instructions_per_cell": ipc, "sms": sms, "ceiling_mlups": ceil,
+                                      "frac": value / ceil, "source": "ncu instruction count in the profile summary"}
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline_sample(args.cpu_seconds)
         print(json.dumps(line), flush=True)

@@ -61,3 +61,15 @@ def test_reference_arm_runs_on_rank_zero_only():
     with redirect_stdout(buf):
         bench.run_reference(Args(), 2, 1)
     assert buf.getvalue() == ""
+
+
+def test_issue_ceiling_counts_schedulers_and_lanes():
+    """152 SMs x 4 schedulers x 2070 MHz, 32 cells per warp instruction: at
+    3322 warp instructions per cell the full-issue rate is 12,123 MLUPS; the
+    committed profile's count is used only while the kernel sources match."""
+    import bench
+
+    assert bench.issue_ceiling(3322, 152, 2070.0) == pytest.approx(152 * 4 * 2070e6 * 32 / 3322 / 1e6)
+    assert bench.issue_ceiling(None, 152, 2070.0) is None and bench.issue_ceiling(3322, 0, 2070.0) is None
+    ipc = bench.profiled_instructions("fp32")
+    assert ipc is None or ipc > 1000
