@@ -94,6 +94,14 @@
  *       the populations' added moments are exactly those two and nothing else.
  *   R26 the force acts only while the largest |u| of the state at the start
  *       of the step is below drive_vmax (the paper's 0.3 c cut-off).
+ *   R28 (an option, ORC_GAUSS_CHARGE; the default is the paper's): the charge
+ *       in Ohm's convection current rho_c u (Eq. Ohm) taken from Gauss's law
+ *       (Eq. Gauss_E), eps0 div E of the previous step's E by central
+ *       differences (clamped at open faces), instead of the moment
+ *       rho_c = sum h (Eq. Cal_rhoc), which stays the charge of the Maxwell
+ *       populations. The two agree for the physical fields; the moment also
+ *       carries a grid-scale mode that tau_h = 1/2 does not damp and that any
+ *       flow amplifies through the convection current.
  *   R27 the iterative E, J initialisation of the flare set-up (Sec. IV): from
  *       the initial state (E = -u x B), repeat one step without the force in
  *       which, after the recovery and before the boundary pass, the fluid and
@@ -459,9 +467,18 @@ int orc_landau(const orc_params* P, const double* T16, const double* E_prev, con
 int orc_recover_cell(const orc_params* P, const orc_lattice* L, const double* f, const double* g,
                      const double* h, const double* prim_prev, double* prim_out)
 {
+    return orc_recover_cell_rho(P, L, f, g, h, prim_prev, NAN, prim_out);
+}
+
+/* As orc_recover_cell, with rho_ohm (unless NaN) as the charge of Ohm's
+ * convection current (R28). */
+int orc_recover_cell_rho(const orc_params* P, const orc_lattice* L, const double* f, const double* g,
+                         const double* h, const double* prim_prev, double rho_ohm, double* prim_out)
+{
     const double c = P->c;
     double T[16], N[4], Ep[3], B[3], rho_c;
     orc_moments(L, f, g, h, T, N, Ep, B, &rho_c);
+    const double rho_j = isnan(rho_ohm) ? rho_c : rho_ohm;
     const double* up = prim_prev + ORC_U;
     const double gp = 1.0 / sqrt(1.0 - dot3(up, up) / (c * c));
     const double seed[4] = {gp, gp * up[0] / c, gp * up[1] / c, gp * up[2] / c};
@@ -485,7 +502,7 @@ int orc_recover_cell(const orc_params* P, const orc_lattice* L, const double* f,
         if (i1 < 0) return -1;
         it += i1;
         for (int a = 0; a < 3; ++a) u[a] = c * U[a + 1] / U[0];
-        orc_ohm_solve(P, Ep, u, B, rho_c, E);
+        orc_ohm_solve(P, Ep, u, B, rho_j, E);
         if (P->flags & ORC_ONE_PASS_RECOVERY) break;
         double d = 0.0;
         for (int a = 0; a < 3; ++a) d += (E[a] - Ec[a]) * (E[a] - Ec[a]);
@@ -897,13 +914,24 @@ static int stream_recover_local(const orc_sim* s, int x, int y, int z, const dou
     hn[24] = hc[24 * N + id];
 
     gather_cell(s->prim, ORC_NPRIM, N, id, pr);
+    double rho_ohm = NAN;
+    if (P->flags & ORC_GAUSS_CHARGE) { /* R28: eps0 div E of the previous step */
+        double div = 0.0;
+        const int n[3] = {P->nx, P->ny, P->nz};
+        for (int a = 0; a < 3; ++a) {
+            if (n[a] == 1) continue;
+            div += (s->prim[(ORC_E + a) * N + nb_index(P, x, y, z, a, 1)] -
+                    s->prim[(ORC_E + a) * N + nb_index(P, x, y, z, a, -1)]) / (2.0 * P->dx);
+        }
+        rho_ohm = eps0_of(P) * div;
+    }
     if (s->force_on && z < P->drive_layers) { /* R25 */
         double F[3], df[19];
         orc_drive_force(P, x, y, F);
         orc_force_populations(P, L, F, pr + ORC_U, df);
         for (int i = 0; i < 19; ++i) fn[i] += df[i];
     }
-    const int it = orc_recover_cell(P, L, fn, gn, hn, pr, pn);
+    const int it = orc_recover_cell_rho(P, L, fn, gn, hn, pr, rho_ohm, pn);
     /* on failure keep the previous primitives; the failure is counted */
     if (it < 0) memcpy(pn, pr, sizeof(pr));
     return it;

@@ -35,6 +35,7 @@ extern "C" {
 #define ORC_IMPLICIT_AS_PRINTED 4 /* collision term implicit in f(t+dt) towards f^eq(t) */
 #define ORC_PRINTED_FEQ 8     /* delta_{i0} term and nu^2/5 sign of Eq. Dis_fun_EM exactly as printed */
 #define ORC_ONE_PASS_RECOVERY 16 /* eigen-solve once, with E and B of the previous step (R24 taken literally) */
+#define ORC_GAUSS_CHARGE 32   /* R28 (option): Ohm's convection current with the charge eps0 div E (Eq. Gauss_E) */
 
 /* primitive layout of one cell (field-major planes in the simulation) */
 #define ORC_N 0
@@ -101,6 +102,8 @@ int orc_landau(const orc_params* P, const double* T16, const double* E_prev, con
                const double* U_seed, double* U_out, double* lambda_out);
 int orc_recover_cell(const orc_params* P, const orc_lattice* L, const double* f, const double* g,
                      const double* h, const double* prim_prev, double* prim_out);
+int orc_recover_cell_rho(const orc_params* P, const orc_lattice* L, const double* f, const double* g,
+                         const double* h, const double* prim_prev, double rho_ohm, double* prim_out);
 void orc_stream_population(const orc_params* P, int i, const double* fi, double* out);
 void orc_drive_velocity(const orc_params* P, int x, int y, double* u);
 void orc_drive_force(const orc_params* P, int x, int y, double* F);

@@ -18,7 +18,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "liblbrmhd_oracle.so")
 
 PERIODIC, OPEN, DRIVEN = 0, 1, 2
-NO_EM_COLLISION, FIRST_ORDER, IMPLICIT_AS_PRINTED, PRINTED_FEQ, ONE_PASS_RECOVERY = 1, 2, 4, 8, 16
+NO_EM_COLLISION, FIRST_ORDER, IMPLICIT_AS_PRINTED, PRINTED_FEQ, ONE_PASS_RECOVERY, GAUSS_CHARGE = 1, 2, 4, 8, 16, 32
 # primitive layout (per cell)
 N_, EPS_, U_, E_, B_, RHOC_, J_, NPRIM = 0, 1, 2, 5, 8, 11, 12, 15
 # get_moments output rows

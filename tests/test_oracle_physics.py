@@ -261,3 +261,19 @@ def test_one_pass_recovery_misses_the_em_inertia():
     assert abs(speed(0) / (1.0 / math.sqrt(6.0)) - 1) < 0.01
     assert abs(speed(O.ONE_PASS_RECOVERY) / (1.0 / math.sqrt(5.0)) - 1) < 0.01
     assert _alfven_pulse_error(1.0, flags=O.ONE_PASS_RECOVERY) > 0.25
+
+
+def test_paper_current_sheet_with_gauss_charge():
+    """Reading R28 (option) leaves the paper's resistive test unchanged: the
+    100-cell sigma = 100 sheet lands on the erf solution at t = 9 within 1 %."""
+    g = json.load(open(os.path.join(GOLDEN, "current_sheet_convergence.json")))
+    F = W.current_sheet_paper(100, sigma=g["sigma"], t0=g["t_start"], B0=g["B0"], p0=g["p"], n0=g["n"])
+    s, P = _sim(F, sigma=g["sigma"], dx=F.meta["dx"], bc=(OPEN, OPEN, PER, PER, PER, PER), threads=1,
+                flags=O.GAUSS_CHARGE)
+    dt = O.dt(P)
+    steps = int(round((g["t_end"] - g["t_start"]) / dt))
+    s.step(steps)
+    t = g["t_start"] + steps * dt
+    exact = np.array([math.erf(0.5 * math.sqrt(100.0 / t) * v) for v in F.meta["x"]])
+    By = s.moments()[10]
+    assert np.linalg.norm(By - exact) / np.linalg.norm(exact) < 0.01
