@@ -79,6 +79,11 @@ extern "C" {
 #define LBRMHD_FLAG_ONE_PASS_RECOVERY 4 /* one eigen-solve with the previous step's E, B (the coupling
                                           subsection taken literally: loses the EM inertia, see the
                                           self-consistent recovery in lbrmhd_step) */
+#define LBRMHD_FLAG_GAUSS_CHARGE 8 /* an option beyond the paper: the charge of Ohm's convection current rho_c u
+                                      (Eq. Ohm) from Gauss's law, eps0 div E of the previous step's E by central
+                                      differences (Eq. Gauss_E), instead of the Maxwell moment sum h (Eq.
+                                      Cal_rhoc), which carries a grid-scale mode that any flow amplifies; with
+                                      alpha <= 0.02 it keeps flowing magnetised plasma stable */
 
 /* rows of lbrmhd_get_moments output (each row N values) */
 #define LBRMHD_NMOMENTS 16 /* n, p, eps, u(3), E(3), B(3), rho_c, J(3) */

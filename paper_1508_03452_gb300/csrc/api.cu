@@ -637,7 +637,8 @@ std::string check_params(const lbrmhd_params& p)
     if (p.precision < LBRMHD_FP64 || p.precision > LBRMHD_FP16_DEV) return "unknown precision";
     if (p.recovery != LBRMHD_RECOVERY_PLAIN && p.recovery != LBRMHD_RECOVERY_MLP && p.recovery != LBRMHD_RECOVERY_COLD)
         return "unknown recovery mode";
-    if (p.flags & ~(LBRMHD_FLAG_NO_EM_COLLISION | LBRMHD_FLAG_UNSHIFTED_POWER | LBRMHD_FLAG_ONE_PASS_RECOVERY))
+    if (p.flags & ~(LBRMHD_FLAG_NO_EM_COLLISION | LBRMHD_FLAG_UNSHIFTED_POWER | LBRMHD_FLAG_ONE_PASS_RECOVERY |
+                    LBRMHD_FLAG_GAUSS_CHARGE))
         return "unknown flag";
     for (int f = 0; f < 6; ++f) {
         if (p.bc[f] < 0 || p.bc[f] > 2) return "unknown boundary kind";

@@ -53,6 +53,7 @@ constexpr int kStepThreads = 128;  // threads (cells) per block of the step kern
 constexpr int FLAG_NO_EM_COLLISION = 1;
 constexpr int FLAG_UNSHIFTED_POWER = 2;
 constexpr int FLAG_ONE_PASS_RECOVERY = 4;
+constexpr int FLAG_GAUSS_CHARGE = 8;  // Ohm's convection current with eps0 div E of the previous step
 enum { SEED_PREV = 0, SEED_MLP = 1, SEED_COLD = 2 };
 
 // Population scale for float16 relative deviations: stored value =

@@ -485,6 +485,20 @@ __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, 
     // recovered velocity and the streamed B, until that E reproduces itself;
     // the collision below then conserves T^{mu nu}, and the EM momentum keeps
     // its inertia. FLAG_ONE_PASS_RECOVERY: one solve with the previous E, B.
+    // the charge of Ohm's convection current: the moment rho_c = sum h (Eq.
+    // Cal_rhoc), or with FLAG_GAUSS_CHARGE eps0 div E of the previous step's
+    // E by central differences (Eq. Gauss_E), which carries no grid-scale
+    // mode for a flow to amplify
+    R rho_j = rho;
+    if (A.flags & FLAG_GAUSS_CHARGE) {
+        R div = R(0);
+        if (A.nx > 1) div += (R)A.pin[P_E * A.stride + c + o.x[3]] - (R)A.pin[P_E * A.stride + c + o.x[1]];
+        if (A.ny > 1)
+            div += (R)A.pin[(P_E + 1) * A.stride + c + o.y[3]] - (R)A.pin[(P_E + 1) * A.stride + c + o.y[1]];
+        if (IS3D && A.nz > 1)
+            div += (R)A.pin[(P_E + 2) * A.stride + c + o.z[3]] - (R)A.pin[(P_E + 2) * A.stride + c + o.z[1]];
+        rho_j = k.eps0 * div / (R(2) * k.dx);
+    }
     const bool one_pass = (A.flags & FLAG_ONE_PASS_RECOVERY) != 0;
     const bool shifted = (A.flags & FLAG_UNSHIFTED_POWER) == 0;
     R Ec[3], Bc[3];
@@ -523,7 +537,7 @@ __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, 
         ig = (R(1) - b2) * g;
 #pragma unroll
         for (int a = 0; a < 3; ++a) nw.u[a] = k.c * beta[a];
-        ohm_solve(Ep, nw.u, Bn, rho, g, ig, k, nw.E);
+        ohm_solve(Ep, nw.u, Bn, rho_j, g, ig, k, nw.E);
         if (one_pass) break;
         R d = R(0), e2 = R(0), dB = R(0);
 #pragma unroll

@@ -19,7 +19,7 @@ ERR_BAD_ARG, ERR_OOM, ERR_CUDA, ERR_NONCONVERGED, ERR_NONFINITE, ERR_TIMEOUT, ER
 PERIODIC, OPEN, DRIVEN = 0, 1, 2
 FP64, FP32, FP16_DEV = 0, 1, 2
 RECOVERY_PLAIN, RECOVERY_MLP, RECOVERY_COLD = 0, 1, 2
-FLAG_NO_EM_COLLISION, FLAG_UNSHIFTED_POWER, FLAG_ONE_PASS_RECOVERY = 1, 2, 4
+FLAG_NO_EM_COLLISION, FLAG_UNSHIFTED_POWER, FLAG_ONE_PASS_RECOVERY, FLAG_GAUSS_CHARGE = 1, 2, 4, 8
 MLP_NPARAM, MLP_NFEAT, MLP_ROW = 9924, 20, 24
 SCHED_PER_RUN, SCHED_BATCH = 0, 1
 NMOMENTS, NDIAG, NTABLE, NHIST = 16, 10, 311, 17
