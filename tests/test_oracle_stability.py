@@ -127,3 +127,18 @@ def test_gauss_charge_and_small_viscosity_keep_a_flowing_plasma():
         out[flags] = (s.stats()["recover_fail"], np.abs(s.moments()[4]).max())
     assert out[0][0] > 0
     assert out[O.GAUSS_CHARGE][0] == 0 and out[O.GAUSS_CHARGE][1] < 1e-6, out
+
+
+def test_gauss_charge_and_small_viscosity_carry_a_kelvin_helmholtz_run():
+    """Kelvin-Helmholtz shear layers (V = 0.2c, density ratio 3, B0 = 0.1,
+    sigma = 1e3, 64^2): with the moment charge the run fails within 500 steps
+    even at alpha = 0.02; with the Gauss-law charge (R28) and alpha = 0.02 it
+    runs 1000 steps with every cell recovered."""
+    F = W.kelvin_helmholtz(64, 64, 1, V=0.2, ratio=3.0, B0=0.1, a=2.0, noise=1e-3, seed=3)
+    fails = {}
+    for flags, steps in ((0, 500), (O.GAUSS_CHARGE, 1000)):
+        s = O.Sim(O.make_params(64, 64, 1, sigma=1e3, alpha=0.02, threads=8, flags=flags))
+        s.init(F.n, F.p, F.u, F.B)
+        s.step(steps)
+        fails[flags] = s.stats()["recover_fail"]
+    assert fails[0] > 0 and fails[O.GAUSS_CHARGE] == 0, fails
