@@ -142,3 +142,22 @@ def test_gauss_charge_and_small_viscosity_carry_a_kelvin_helmholtz_run():
         s.step(steps)
         fails[flags] = s.stats()["recover_fail"]
     assert fails[0] > 0 and fails[O.GAUSS_CHARGE] == 0, fails
+
+
+def test_fluid_scheme_velocity_limit():
+    """Without any field the fluid scheme itself bounds the flow speed: a
+    uniform 0.4c flow (seeded noise, 32^2, alpha = 0.02) runs 500 steps, a
+    0.5c flow fails within 100 (the paper notes instability at high
+    velocity, Sec. V)."""
+    nx = ny = 32
+    N = nx * ny
+    rng = np.random.default_rng(1)
+    fails = {}
+    for V, steps in ((0.4, 500), (0.5, 100)):
+        u = np.zeros((3, N))
+        u[0] = V + 1e-4 * rng.uniform(-1, 1, N)
+        s = O.Sim(O.make_params(nx, ny, 1, sigma=100.0, alpha=0.02, threads=8))
+        s.init(np.ones(N), np.ones(N), u, np.zeros((3, N)))
+        s.step(steps)
+        fails[V] = s.stats()["recover_fail"]
+    assert fails[0.4] == 0 and fails[0.5] > 0, fails
