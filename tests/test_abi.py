@@ -73,6 +73,29 @@ def test_bad_parameters_are_rejected():
     with pytest.raises(L.LbrmhdError) as e:
         L.Solver(L.make_params(8, 4, 4, bc=(L.OPEN, L.PERIODIC, 0, 0, 0, 0)))
     assert e.value.code == L.ERR_BAD_ARG
+    # the photospheric body force: needs forced layers, replaces the DRIVEN
+    # face, finite values; unknown flags are refused
+    for kw in (dict(drive_f0=0.05, drive_layers=0), dict(drive_f0=0.05, drive_layers=2,
+                                                       bc=(L.OPEN,) * 4 + (L.DRIVEN, L.OPEN)),
+               dict(drive_f0=float("nan"), drive_layers=2), dict(drive_vmax=float("inf")), dict(flags=16)):
+        with pytest.raises(L.LbrmhdError) as e:
+            L.Solver(L.make_params(8, 8, 8, **kw))
+        assert e.value.code == L.ERR_BAD_ARG, kw
+
+
+def test_valid_options_pass_validation():
+    """Valid force and Gauss-charge parameters pass the parameter check: with
+    no GPU the creation then fails on the device, not on the arguments."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    for kw in (dict(drive_f0=0.05, drive_layers=2, drive_vmax=0.75, bc=(L.OPEN,) * 6),
+               dict(flags=L.FLAG_GAUSS_CHARGE | L.FLAG_ONE_PASS_RECOVERY)):
+        with pytest.raises(L.LbrmhdError) as e:
+            L.Solver(L.make_params(8, 8, 8, **kw))
+        assert e.value.code == L.ERR_CUDA, kw
+    lib = L.load()
+    assert lib.lbrmhd_init_fields_relaxed(None, 0, None, None, None, None, 10, 1e-6, None, None) == L.ERR_BAD_ARG
 
 
 def test_no_cpu_fallback_without_gpu():
