@@ -75,11 +75,22 @@ def whole_job_mlups(world: int, cells_per_rank: int, steps: int, seconds: float)
     return world * cells_per_rank * steps / seconds / 1e6
 
 
+def code_only(src: str) -> str:
+    """C++/CUDA source without its comments, trailing blanks and empty lines:
+    what the compiler sees (the sources hold no string literal with a comment
+    marker)."""
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    lines = (re.sub(r"//.*", "", line).rstrip() for line in src.splitlines())
+    return "\n".join(line for line in lines if line)
+
+
 def kernel_sha() -> str:
+    """Identity of the step kernel's code (comments excluded), which the
+    committed ncu summary records beside the counters it took."""
     h = hashlib.sha256()
     for name in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1508_03452_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_1508_03452_gb300", "csrc", name)) as f:
+            h.update(code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

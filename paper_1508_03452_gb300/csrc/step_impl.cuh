@@ -7,9 +7,12 @@
 //      D3Q13 hop of Eq. LB_Maxwell;
 //   2. moments T^{mu nu}, N^mu (reference rest state added back), E', B,
 //      rho_c (Eqs. Cal_E, Cal_B, Cal_rhoc);
-//   3. Landau eigen-solve with the previous E, B (coupling subsection),
-//      n = N^0 / U^0, the Ohm-coupled E solve and J (Eqs. Ohm, Ex_force), the
-//      EOS (Eq. EOS);
+//   3. recovery (coupling subsection): the Landau eigen-solve of T - eps0 F F
+//      iterated with the Ohm-coupled E solve until the tensor's E reproduces
+//      itself (starting from the previous step's E and the streamed B), then
+//      n = N^0 / U^0, J (Eq. Ex_force) and the EOS (Eq. EOS); optionally the
+//      body force of the flare set-up before it and the relaxed
+//      initialisation's reset after it (open-face variant);
 //   4. collision at the new time level: Anderson-Witting for f towards Eq.
 //      Dis_fun_EM, BGK for g towards Eq. Hupp, tau_h = 1/2 for h
 //      (h -> 2 h^eq - h) towards Eq. Maxwell-eq; store populations and

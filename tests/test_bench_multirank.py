@@ -73,3 +73,15 @@ def test_issue_ceiling_counts_schedulers_and_lanes():
     assert bench.issue_ceiling(None, 152, 2070.0) is None and bench.issue_ceiling(3322, 0, 2070.0) is None
     ipc = bench.profiled_instructions("fp32")
     assert ipc is None or ipc > 1000
+
+
+def test_kernel_hash_ignores_comments():
+    """The code identity that ties an ncu summary to the kernel sources does
+    not move when only a comment or a blank line changes, and does when code
+    does."""
+    import bench
+
+    a = "int f(int x) {\n    return x + 1;  // one more\n}\n"
+    b = "/* a note */\nint f(int x) {\n\n    return x + 1;\n}  // end\n"
+    c = "int f(int x) {\n    return x + 2;\n}\n"
+    assert bench.code_only(a) == bench.code_only(b) != bench.code_only(c)
