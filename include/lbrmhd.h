@@ -213,9 +213,9 @@ int lbrmhd_get_diagnostics(lbrmhd_handle h, int run, double* out);
  * Limits and rules:
  *   - runs of at most 16,777,216 cells (256^3); larger runs are rejected with
  *     LBRMHD_ERR_BAD_ARG and a message naming the limit.
- *   - The first call on a device looks up the device address of the static
- *     array (once per device, with that device current); make that first call
- *     before any stream capture.
+ *   - lbrmhd_create looks up the device address of the static array, with the
+ *     handle's device current, and keeps it in the handle; this call itself
+ *     makes no lookup and no allocation.
  *   - Every call shares the one array, which keeps the previous call's
  *     contents; each call writes every entry it later reads, so no clearing is
  *     needed. Calls whose work overlaps on the GPU (other streams, other

@@ -40,7 +40,9 @@
  *       Sweby flux-limited upwind face values with the minmod limiter,
  *       dimensionally unsplit. Parity with the 2013 flux: UNPINNED.
  *   R11 bulk-viscosity term: alpha (c dt/dx) sum_a [f(x+e_a) - 2 f + f(x-e_a)],
- *       i != 0. Coefficient: parity UNPINNED.
+ *       i != 0. The printed coefficient is garbled; pinned by the term's share
+ *       of the damping of a momentum mode in one step, 4 alpha (c dt/dx)
+ *       sin^2(k dx/2) with dx/dt = sqrt(2) c.
  *   R12 one rest EM population h_0 (25 EM populations per cell).
  *   R13 the subtraction before the eigen-solve starts from E, B of the previous
  *       step (then R24 iterates E); "F^{mu rho} F^nu_rho" is the first term of

@@ -5,7 +5,6 @@
 #include <cstdlib>
 #include <cstring>
 #include <fstream>
-#include <mutex>
 #include <sstream>
 #include <string>
 #include <vector>
@@ -60,6 +59,7 @@ struct lbrmhd_state_s {
     size_t io_bytes = 0;
     double* d_small = nullptr;  // 32 float64
     int* d_flag = nullptr;
+    double* d_noalloc = nullptr;  // device address of g_noalloc_partials in this handle's context
     unsigned char* d_mlp = nullptr;  // packed network of the learned seed
     bool mlp_set = false;
     // launch schedule (lbrmhd_set_schedule / lbrmhd_autotune)
@@ -670,25 +670,20 @@ static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxBlocks * l
 
 // The host-side name g_noalloc_partials is only a stand-in for the device
 // array, not its address; a kernel handed it would fault or, on systems where
-// the GPU can reach host memory, silently use the wrong memory. The device
-// address is looked up once per device, with that device current, and cached.
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mutex;
-double* g_noalloc_ptr[kMaxDevices] = {};
-
-int noalloc_scratch(lbrmhd_handle h, double** out)
+// the GPU can reach host memory, silently use the wrong memory. lbrmhd_create
+// looks the device address up with the handle's device current and keeps it
+// in the handle, so the address always belongs to the context the handle's
+// kernels run in (nothing is cached across handles or contexts).
+int lookup_noalloc_scratch(double** out)
 {
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (h->device < 0 || h->device >= kMaxDevices) return fail(h, LBRMHD_ERR_BAD_ARG, "device id out of range");
-    if (!g_noalloc_ptr[h->device]) {
-        double* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_noalloc_partials);
-        if (e != cudaSuccess || !p)
-            return fail(h, LBRMHD_ERR_CUDA, std::string("cudaGetSymbolAddress(g_noalloc_partials): ") +
-                                                cudaGetErrorString(e));
-        g_noalloc_ptr[h->device] = p;
+    double* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_noalloc_partials);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        *out = nullptr;
+        return LBRMHD_ERR_CUDA;
     }
-    *out = g_noalloc_ptr[h->device];
+    *out = p;
     return LBRMHD_OK;
 }
 
@@ -981,6 +976,11 @@ int lbrmhd_create(const lbrmhd_params* params, int n_runs, lbrmhd_handle* out)
         lbrmhd_destroy(h);
         return LBRMHD_ERR_CUDA;
     }
+    if (lookup_noalloc_scratch(&h->d_noalloc) != LBRMHD_OK) {
+        g_create_error = "cudaGetSymbolAddress of the static diagnostics scratch failed";
+        lbrmhd_destroy(h);
+        return LBRMHD_ERR_CUDA;
+    }
     *out = h;
     return LBRMHD_OK;
 }
@@ -1164,15 +1164,13 @@ int lbrmhd_get_diagnostics_noalloc(lbrmhd_handle h, int run, double* d_out)
 {
     if (bad_run(h, run) || !d_out) return h ? fail(h, LBRMHD_ERR_BAD_ARG, "bad run or NULL output") : LBRMHD_ERR_BAD_ARG;
     RunState& r = h->runs[run];
-    if (!r.initialized) return fail(h, LBRMHD_ERR_STATE, "run not initialised");
     if (r.N > kNoAllocMaxCells)
         return fail(h, LBRMHD_ERR_BAD_ARG,
                     "lbrmhd_get_diagnostics_noalloc: run has " + std::to_string(r.N) + " cells, above the limit of " +
                         std::to_string(kNoAllocMaxCells) + " of its static scratch; use lbrmhd_get_diagnostics");
+    if (!r.initialized) return fail(h, LBRMHD_ERR_STATE, "run not initialised");
     LB_CK(cudaSetDevice(h->device));
-    double* partial = nullptr;
-    const int rc = noalloc_scratch(h, &partial);
-    if (rc) return rc;
+    double* partial = h->d_noalloc;
     const lb::Phys<double> k = make_phys<double>(r.p, r.ref, runref(r));
     switch (h->precision) {
         case LBRMHD_FP64:

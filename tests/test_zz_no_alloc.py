@@ -5,9 +5,11 @@ that must not pay the device-wide synchronisation cudaMalloc / cudaFree may
 imply). It keeps its partial sums in a static device array of the library and
 writes to a caller-owned device buffer.
 
-The test calls it through the C ABI, twice in a row on changing states (the
-second call runs over the array the first one left behind), and checks each
-result against lbrmhd_get_diagnostics. The file is named to be collected last.
+The tests call it through the C ABI and check each result against
+lbrmhd_get_diagnostics: twice in a row on changing states (the second call
+runs over the array the first one left behind), in every storage precision,
+and a large run followed by a small one (the small call must not pick up the
+large call's leftover partial sums). The file is named to be collected last.
 """
 import ctypes as C
 
@@ -20,7 +22,20 @@ from paper_1508_03452_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("precision", [L.FP64, L.FP32])
+def _noalloc(lib, s, d_out, stream):
+    rc = lib.lbrmhd_get_diagnostics_noalloc(s._h, 0, C.c_void_p(d_out.data_ptr()))
+    assert rc == L.OK, lib.lbrmhd_last_error(s._h)
+    stream.synchronize()
+    return d_out.cpu().numpy()
+
+
+def _check(got, want, ncells):
+    scale = np.maximum(np.abs(want), 1e-300)
+    assert np.all(np.abs(got - want) <= 1e-12 * scale + 1e-15), (got, want)
+    assert got[9] == ncells and got[8] == 0
+
+
+@pytest.mark.parametrize("precision", [L.FP64, L.FP32, L.FP16_DEV])
 def test_noalloc_diagnostics_match_allocating_call(precision):
     torch = pytest.importorskip("torch")
     F = W.kelvin_helmholtz(96, 80, 1, V=0.1, ratio=3.0, B0=0.1, a=2.0, noise=1e-2, seed=21)
@@ -31,22 +46,31 @@ def test_noalloc_diagnostics_match_allocating_call(precision):
     d_out = torch.full((L.NDIAG,), float("nan"), dtype=torch.float64, device="cuda")
     for steps in (3, 7):
         s.step(steps)
-        rc = lib.lbrmhd_get_diagnostics_noalloc(s._h, 0, C.c_void_p(d_out.data_ptr()))
-        assert rc == L.OK, lib.lbrmhd_last_error(s._h)
-        stream.synchronize()
-        got = d_out.cpu().numpy()
-        want = s.diagnostics()
-        scale = np.maximum(np.abs(want), 1e-300)
-        assert np.all(np.abs(got - want) <= 1e-12 * scale + 1e-15), (got, want)
-        assert got[9] == F.N and got[8] == 0
+        _check(_noalloc(lib, s, d_out, stream), s.diagnostics(), F.N)
     s.close()
 
 
+def test_noalloc_large_run_then_small_run():
+    """A 512 x 512 run fills 2048 blocks of partial sums; a 40 x 24 run after it
+    uses 8 and must read only its own."""
+    torch = pytest.importorskip("torch")
+    stream = torch.cuda.current_stream()
+    lib = L.load()
+    d_out = torch.full((L.NDIAG,), float("nan"), dtype=torch.float64, device="cuda")
+    for nx, ny in ((512, 512), (40, 24)):
+        F = W.current_sheet(nx, ny, 1, delta=8.0)
+        s = L.Solver(L.make_params(nx, ny, 1, sigma=100.0, precision=L.FP32), stream=stream)
+        s.init_fields(0, F.n, F.p, F.u, F.B)
+        s.step(2)
+        _check(_noalloc(lib, s, d_out, stream), s.diagnostics(), F.N)
+        s.close()
+
+
 def test_noalloc_rejects_runs_above_its_limit():
+    """The size check comes first: a run above the limit is rejected without
+    being initialised."""
     torch = pytest.importorskip("torch")
     s = L.Solver(L.make_params(4096, 4097, 1, precision=L.FP16_DEV))
-    N = s.cells[0]
-    s.init_fields(0, np.ones(N), np.ones(N), np.zeros(3 * N), np.zeros(3 * N))
     lib = L.load()
     d_out = torch.zeros(L.NDIAG, dtype=torch.float64, device="cuda")
     rc = lib.lbrmhd_get_diagnostics_noalloc(s._h, 0, C.c_void_p(d_out.data_ptr()))
