@@ -49,11 +49,13 @@ extern "C" {
 #define LBRMHD_ERR_BAD_ARG (-1)      /* invalid argument or parameter */
 #define LBRMHD_ERR_OOM (-2)          /* device or host allocation failed */
 #define LBRMHD_ERR_CUDA (-3)         /* a CUDA runtime call failed */
-#define LBRMHD_ERR_NONCONVERGED (-4) /* reserved: lbrmhd_step is asynchronous, so a recovery that does not
-                                        converge is not returned but counted per run (lbrmhd_get_stats,
-                                        recover_fail) and its cells keep their previous primitives */
+#define LBRMHD_ERR_NONCONVERGED (-4) /* recoveries failed to converge: lbrmhd_step is asynchronous, so the
+                                        failures are counted per run (lbrmhd_get_stats, recover_fail), their
+                                        cells keep their previous primitives, and lbrmhd_get_status returns
+                                        this code */
 #define LBRMHD_ERR_NONFINITE (-5)    /* a NaN or Inf was found by the diagnostics */
-#define LBRMHD_ERR_TIMEOUT (-6)      /* reserved: no kernel of the library waits on another */
+#define LBRMHD_ERR_TIMEOUT (-6)      /* a kernel's bounded wait for its own tile copies ran out (the block
+                                        skipped its update); returned by lbrmhd_get_status */
 #define LBRMHD_ERR_STATE (-7)        /* call out of order (e.g. step before init_fields) */
 
 /* boundary kinds, per face -x,+x,-y,+y,-z,+z */
@@ -84,6 +86,13 @@ extern "C" {
                                       differences (Eq. Gauss_E), instead of the Maxwell moment sum h (Eq.
                                       Cal_rhoc), which carries a grid-scale mode that any flow amplifies; with
                                       alpha <= 0.02 it keeps flowing magnetised plasma stable */
+#define LBRMHD_FLAG_NO_TMA_TILES 16 /* 2-D periodic runs stored in float32 / float16 normally step by the TMA
+                                       tile kernel (tensor-map copies of each tile and its halo through shared
+                                       memory); this flag keeps them on the per-cell kernel, which loads every
+                                       stencil value from global memory. Both compute the same update. */
+#define LBRMHD_FLAG_FIRST_ORDER_FLUX 32 /* a study option, not the paper's scheme: the fluid face fluxes without
+                                           the minmod-limited correction (Sec. III streaming, reading of h_i^a),
+                                           i.e. plain first-order upwind, as the limiter gives at a discontinuity */
 
 /* rows of lbrmhd_get_moments output (each row N values) */
 #define LBRMHD_NMOMENTS 16 /* n, p, eps, u(3), E(3), B(3), rho_c, J(3) */
@@ -243,6 +252,17 @@ int lbrmhd_reconnection_rate(lbrmhd_handle h, int run, int y_lo, int y_hi, doubl
 /* Counters of one run: [0] steps taken, [1] recovery failures, [2] sum of
  * recovery iterations, [3] maximum recovery iterations. Host output. */
 int lbrmhd_get_stats(lbrmhd_handle h, int run, int64_t* out4);
+
+/* Health of the whole handle, for a caller that steps asynchronously and
+ * checks now and then. Synchronises the handle's stream. out3 (host, may be
+ * NULL): [0] status bits raised by the step kernels since lbrmhd_create (1: a
+ * TMA tile copy did not arrive within its wait limit, and that tile's update
+ * was skipped), [1] recovery failures summed over every run since its
+ * initialisation, [2] number of runs that step by the TMA tile kernel.
+ * Returns LBRMHD_ERR_TIMEOUT if status bit 1 is set, else
+ * LBRMHD_ERR_NONCONVERGED if any recovery failed, else LBRMHD_OK; errors:
+ * BAD_ARG (NULL handle), CUDA. */
+int lbrmhd_get_status(lbrmhd_handle h, int64_t* out3);
 
 /* Histogram of recovery iteration counts of one run since its
  * initialisation, LBRMHD_NHIST int64 host values: out[k] (k < LBRMHD_NHIST -

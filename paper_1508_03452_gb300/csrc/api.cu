@@ -37,6 +37,8 @@ struct RunState {
     void* d_ez0 = nullptr;       // E^z of the initial state (primitive type, N), for the reconnection rate
     double* d_drive = nullptr;   // drive velocity (driven runs) or body force (forced runs) per (x, y) column
     double* d_umax = nullptr;    // forced runs with a cut-off: max |u|^2 of the state, running max of the next
+    // tensor maps of the TMA tile kernel for input buffer 0 and 1 (empty: the run takes the per-cell kernel)
+    std::vector<lb::TileMaps> tmaps;
 };
 
 constexpr size_t kStatsBytes = lb::kNumStats * sizeof(unsigned long long);  // totals (checkpoint)
@@ -60,6 +62,7 @@ struct lbrmhd_state_s {
     double* d_small = nullptr;  // 32 float64
     int* d_flag = nullptr;
     double* d_noalloc = nullptr;  // device address of g_noalloc_partials in this handle's context
+    int* d_status = nullptr;      // lb::STATUS_* bits raised by the step kernels
     unsigned char* d_mlp = nullptr;  // packed network of the learned seed
     bool mlp_set = false;
     // launch schedule (lbrmhd_set_schedule / lbrmhd_autotune)
@@ -129,7 +132,8 @@ lb::Phys<R> make_phys(const lbrmhd_params& p, const lb::RefState& ref, const Run
     k.inv_half_dt_c2 = (R)(1.0 / (0.5 * dt * p.c * p.c));
     k.gm1 = (R)(p.gamma_ad - 1.0);
     k.C = (R)C;
-    k.kappa = (R)(0.5 * (1.0 - C));
+    // LBRMHD_FLAG_FIRST_ORDER_FLUX: the limiter's correction term off, i.e. plain first-order upwind
+    k.kappa = (p.flags & LBRMHD_FLAG_FIRST_ORDER_FLUX) ? (R)0 : (R)(0.5 * (1.0 - C));
     k.kvisc = (R)(p.alpha * p.c * dt / p.dx);
     k.n_r = (R)ref.n_r;
     k.eps_r = (R)ref.eps_r;
@@ -267,6 +271,87 @@ bool capped(const RunState& r) { return forced(r) && r.p.drive_vmax > 0.0; }
 // holds the body force)
 bool open_variant(const RunState& r) { return has_open(r) || forced(r); }
 
+// ---------------------------------------------------------------------------
+// Tensor maps of the TMA tile kernel (2-D runs with periodic faces, float32 or
+// float16 storage, rows a whole number of 16-byte units long)
+// ---------------------------------------------------------------------------
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled()
+{
+    static const EncodeTiledFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return (EncodeTiledFn) nullptr;
+        }
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+// whether a run's layout admits the tile kernel (the flags are checked at launch)
+bool tile_layout_ok(const lbrmhd_params& p, bool open_var)
+{
+    if (p.precision == LBRMHD_FP64 || p.nz != 1 || open_var) return false;
+    const int px = lb::tile_halo_x((int)pop_bytes(p.precision));
+    return p.nx % px == 0 && p.nx >= lb::kTileW + 2 * px && p.ny >= lb::kTileH + 2 * lb::kTileHaloY;
+}
+
+// encodes one map of `rank` dims over `base` (x, y, then planes of `plane`
+// bytes, then groups of `group` bytes); false if the driver rejects it
+bool encode_map(CUtensorMap* m, CUtensorMapDataType dt, int elem, void* base, int rank, const RunState& r,
+                int planes, int groups, const cuuint32_t* box)
+{
+    const EncodeTiledFn enc = encode_tiled();
+    if (!enc) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)r.p.nx, (cuuint64_t)r.p.ny, (cuuint64_t)planes, (cuuint64_t)groups};
+    const cuuint64_t strides[3] = {(cuuint64_t)r.p.nx * elem, (cuuint64_t)r.stride * elem,
+                                   (cuuint64_t)r.stride * elem * planes};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return enc(m, dt, (cuuint32_t)rank, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// the maps of both input buffers of a run (left empty where the tile kernel does not apply)
+void make_tile_maps(RunState& r)
+{
+    r.tmaps.clear();
+    if (!tile_layout_ok(r.p, open_variant(r))) return;
+    const int pb = (int)pop_bytes(r.p.precision);
+    const int px = lb::tile_halo_x(pb), pxh = lb::tile_halo_x(4);
+    const CUtensorMapDataType pdt = pb == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const CUtensorMapDataType fdt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const cuuint32_t bh = lb::kTileH + 2 * lb::kTileHaloY;
+    const cuuint32_t box_fg[4] = {(cuuint32_t)(lb::kTileW + 2 * px), bh, 2, 2};
+    const cuuint32_t box_h[3] = {(cuuint32_t)(lb::kTileW + 2 * pxh), bh, 4};
+    const cuuint32_t box_p[3] = {lb::kTileW, lb::kTileH, (cuuint32_t)lb::NPRIM};
+    const cuuint32_t box_fo[3] = {lb::kTileW, lb::kTileH, 38};
+    const cuuint32_t box_ho[3] = {lb::kTileW, lb::kTileH, 25};
+    std::vector<lb::TileMaps> maps(2);
+    bool ok = true;
+    for (int in = 0; in < 2 && ok; ++in) {
+        const int out = 1 - in;
+        lb::TileMaps& m = maps[in];
+        ok = ok && encode_map(&m.fg_in, pdt, pb, r.pops[in], 4, r, 19, 2, box_fg);
+        ok = ok && encode_map(&m.h_in, fdt, 4, r.h[in], 3, r, 25, 1, box_h);
+        ok = ok && encode_map(&m.p_in, fdt, 4, r.prim[in], 3, r, lb::NPRIM, 1, box_p);
+        ok = ok && encode_map(&m.fg_out, pdt, pb, r.pops[out], 3, r, 38, 1, box_fo);
+        ok = ok && encode_map(&m.h_out, fdt, 4, r.h[out], 3, r, 25, 1, box_ho);
+        ok = ok && encode_map(&m.p_out, fdt, 4, r.prim[out], 3, r, lb::NPRIM, 1, box_p);
+    }
+    if (ok) r.tmaps = std::move(maps);
+}
+
+const lb::TileMaps* tile_maps(const RunState& r, int in) { return r.tmaps.empty() ? nullptr : &r.tmaps[in]; }
+
+
 // kernel arguments of one run reading input buffer `in`
 template <class Cfg>
 lb::StepArgs<Cfg> make_args(lbrmhd_handle h, const RunState& r, int in)
@@ -297,6 +382,7 @@ lb::StepArgs<Cfg> make_args(lbrmhd_handle h, const RunState& r, int in)
     A.mlp = h->d_mlp;
     A.dump = r.d_samples;
     A.seed = run_seed(r);
+    A.status = h->d_status;
     if (forced(r)) {
         const double dt = r.p.dx / (std::sqrt(2.0) * r.p.c);
         A.open_mask |= lb::OPEN_EXTRA;
@@ -411,7 +497,7 @@ int issue_step(lbrmhd_handle h, const lbrmhd_schedule& sc, int in, cudaStream_t 
                                              s));
         }
     } else {
-        for (const auto& r : h->runs) LB_CK(lb::launch_step<Cfg>(make_args<Cfg>(h, r, in), s));
+        for (const auto& r : h->runs) LB_CK(lb::launch_step<Cfg>(make_args<Cfg>(h, r, in), s, tile_maps(r, in)));
     }
     for (const auto& r : h->runs) {
         if (has_open(r))
@@ -459,7 +545,7 @@ int issue_steps(lbrmhd_handle h, const lbrmhd_schedule& sc, int in, int64_t n, c
         for (size_t ri = 0; ri < h->runs.size(); ++ri) {
             const RunState& r = h->runs[ri];
             cudaStream_t st = h->aux[ri % S];
-            LB_CK(lb::launch_step<Cfg>(make_args<Cfg>(h, r, cin), st));
+            LB_CK(lb::launch_step<Cfg>(make_args<Cfg>(h, r, cin), st, tile_maps(r, cin)));
             if (has_open(r))
                 LB_CK(lb::launch_boundaries<Cfg>(view<Cfg>(r, 1 - cin), make_phys<R>(r.p, r.ref, runref(r)), r.p.bc,
                                                  r.p.drive_layers, r.d_drive, st));
@@ -638,7 +724,7 @@ std::string check_params(const lbrmhd_params& p)
     if (p.recovery != LBRMHD_RECOVERY_PLAIN && p.recovery != LBRMHD_RECOVERY_MLP && p.recovery != LBRMHD_RECOVERY_COLD)
         return "unknown recovery mode";
     if (p.flags & ~(LBRMHD_FLAG_NO_EM_COLLISION | LBRMHD_FLAG_UNSHIFTED_POWER | LBRMHD_FLAG_ONE_PASS_RECOVERY |
-                    LBRMHD_FLAG_GAUSS_CHARGE))
+                    LBRMHD_FLAG_GAUSS_CHARGE | LBRMHD_FLAG_NO_TMA_TILES | LBRMHD_FLAG_FIRST_ORDER_FLUX))
         return "unknown flag";
     for (int f = 0; f < 6; ++f) {
         if (p.bc[f] < 0 || p.bc[f] > 2) return "unknown boundary kind";
@@ -860,7 +946,7 @@ int relax_run(lbrmhd_handle h, RunState& r, int max_iters, double tol, int* iter
         A.relax_in = h->d_io;
         A.relax_e = e;
         A.relax_red = h->d_small;
-        if (ce == cudaSuccess) ce = lb::launch_step<Cfg>(A, h->stream);
+        if (ce == cudaSuccess) ce = lb::launch_step<Cfg>(A, h->stream, nullptr);
         if (ce == cudaSuccess && has_open(r))
             ce = lb::launch_boundaries<Cfg>(view<Cfg>(r, 1 - r.cur), make_phys<R>(r.p, r.ref, runref(r)), r.p.bc,
                                             r.p.drive_layers, r.d_drive, h->stream);
@@ -965,6 +1051,8 @@ int lbrmhd_create(const lbrmhd_params* params, int n_runs, lbrmhd_handle* out)
     h->scratch_blocks = max_blocks;
     ok = ok && cudaMalloc(&h->d_small, 32 * sizeof(double)) == cudaSuccess;
     ok = ok && cudaMalloc(&h->d_flag, sizeof(int)) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->d_status, sizeof(int)) == cudaSuccess;
+    if (ok) cudaMemset(h->d_status, 0, sizeof(int));
     if (!ok) {
         cudaGetLastError();
         lbrmhd_destroy(h);
@@ -976,6 +1064,7 @@ int lbrmhd_create(const lbrmhd_params* params, int n_runs, lbrmhd_handle* out)
         lbrmhd_destroy(h);
         return LBRMHD_ERR_CUDA;
     }
+    for (auto& r : h->runs) make_tile_maps(r);
     if (lookup_noalloc_scratch(&h->d_noalloc) != LBRMHD_OK) {
         g_create_error = "cudaGetSymbolAddress of the static diagnostics scratch failed";
         lbrmhd_destroy(h);
@@ -1004,6 +1093,7 @@ int lbrmhd_destroy(lbrmhd_handle h)
     if (h->d_io) cudaFree(h->d_io);
     if (h->d_small) cudaFree(h->d_small);
     if (h->d_flag) cudaFree(h->d_flag);
+    if (h->d_status) cudaFree(h->d_status);
     if (h->d_mlp) cudaFree(h->d_mlp);
     drop_graphs(h);
     if (h->d_args) cudaFree(h->d_args);
@@ -1186,6 +1276,31 @@ int lbrmhd_get_diagnostics_noalloc(lbrmhd_handle h, int run, double* d_out)
                                               h->stream));
             break;
     }
+    return LBRMHD_OK;
+}
+
+int lbrmhd_get_status(lbrmhd_handle h, int64_t* out3)
+{
+    if (!h) return LBRMHD_ERR_BAD_ARG;
+    LB_CK(cudaSetDevice(h->device));
+    int status = 0;
+    LB_CK(cudaMemcpyAsync(&status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    LB_CK(cudaStreamSynchronize(h->stream));
+    int64_t fails = 0, tiled = 0;
+    for (const auto& r : h->runs) {
+        unsigned long long s[lb::kNumStats];
+        const int rc = read_stats(h, r, s);
+        if (rc) return rc;
+        fails += (int64_t)s[0];
+        tiled += !r.tmaps.empty() && (r.p.flags & (LBRMHD_FLAG_GAUSS_CHARGE | LBRMHD_FLAG_NO_TMA_TILES)) == 0 ? 1 : 0;
+    }
+    if (out3) {
+        out3[0] = status;
+        out3[1] = fails;
+        out3[2] = tiled;
+    }
+    if (status & lb::STATUS_TMA_TIMEOUT) return fail(h, LBRMHD_ERR_TIMEOUT, "a TMA tile copy did not arrive in time");
+    if (fails > 0) return fail(h, LBRMHD_ERR_NONCONVERGED, std::to_string(fails) + " recoveries did not converge");
     return LBRMHD_OK;
 }
 

@@ -54,6 +54,7 @@ constexpr int FLAG_NO_EM_COLLISION = 1;
 constexpr int FLAG_UNSHIFTED_POWER = 2;
 constexpr int FLAG_ONE_PASS_RECOVERY = 4;
 constexpr int FLAG_GAUSS_CHARGE = 8;  // Ohm's convection current with eps0 div E of the previous step
+constexpr int FLAG_NO_TMA_TILES = 16;  // per-cell global loads even where the TMA tile path applies
 enum { SEED_PREV = 0, SEED_MLP = 1, SEED_COLD = 2 };
 
 // Population scale for float16 relative deviations: stored value =
@@ -103,7 +104,11 @@ struct StepArgs {
     const double* relax_in;
     double* relax_e;
     double* relax_red;
+    // status word of the handle: kernels OR in STATUS_* bits (device int)
+    int* status;
 };
+// status bits a step kernel can raise
+constexpr int STATUS_TMA_TIMEOUT = 1;  // a tile's copy did not arrive within the wait limit
 // open_mask bit for runs that need the open-variant code without an open face
 constexpr int OPEN_EXTRA = 8;
 

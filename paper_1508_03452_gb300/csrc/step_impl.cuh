@@ -20,6 +20,7 @@
 #pragma once
 #include "common.cuh"
 #include "mlp.cuh"
+#include "tma.cuh"
 
 namespace lb {
 
@@ -196,11 +197,14 @@ __device__ __forceinline__ float2 eq_pair(const EqCell<float>& q)
     return __fmul2_rn(make_float2((float)w19(I), (float)wg19(I)), v);
 }
 
-template <int I, class Cfg>
+// TILE: the post-collision values go to the block's shared-memory output
+// tile `ofg` (f then g, one row of nth cells per population) instead of
+// global memory
+template <int I, class Cfg, bool TILE>
 struct CollideFG {
     using R = typename Cfg::real;
     static __device__ __forceinline__ void run(const StepArgs<Cfg>& A, int64_t c, const R* sp, int nth,
-                                               const EqCell<R>& q)
+                                               const EqCell<R>& q, typename Cfg::pop* ofg)
     {
         const R fd = sp[I * nth], gd = sp[(19 + I) * nth];
         const R K = k_aw<I>(q);
@@ -218,33 +222,44 @@ struct CollideFG {
             fo = fd - K * (fd - feq_dev<I>(q));
             go = gd - A.k.inv_tau * (gd - geq_dev<I>(q));
         }
-        st_pop<Cfg>(A.fout + (int64_t)I * A.stride + c, fo, A.hs.finv[I]);
-        st_pop<Cfg>(A.gout + (int64_t)I * A.stride + c, go, A.hs.ginv[I]);
-        CollideFG<I + 1, Cfg>::run(A, c, sp, nth, q);
+        if constexpr (TILE) {
+            st_pop<Cfg>(ofg + I * nth, fo, A.hs.finv[I]);
+            st_pop<Cfg>(ofg + (19 + I) * nth, go, A.hs.ginv[I]);
+        } else {
+            st_pop<Cfg>(A.fout + (int64_t)I * A.stride + c, fo, A.hs.finv[I]);
+            st_pop<Cfg>(A.gout + (int64_t)I * A.stride + c, go, A.hs.ginv[I]);
+        }
+        CollideFG<I + 1, Cfg, TILE>::run(A, c, sp, nth, q, ofg);
     }
 };
-template <class Cfg>
-struct CollideFG<19, Cfg> {
+template <class Cfg, bool TILE>
+struct CollideFG<19, Cfg, TILE> {
     using R = typename Cfg::real;
-    static __device__ __forceinline__ void run(const StepArgs<Cfg>&, int64_t, const R*, int, const EqCell<R>&) {}
+    static __device__ __forceinline__ void run(const StepArgs<Cfg>&, int64_t, const R*, int, const EqCell<R>&,
+                                               typename Cfg::pop*) {}
 };
 
-template <int K, class Cfg>
+// TILE: the post-collision h replaces the streamed value in its slot (the
+// slots then form the block's h output tile)
+template <int K, class Cfg, bool TILE>
 struct CollideH {
     using R = typename Cfg::real;
-    static __device__ __forceinline__ void run(const StepArgs<Cfg>& A, int64_t c, const R* sp, int nth, const R* E,
+    static __device__ __forceinline__ void run(const StepArgs<Cfg>& A, int64_t c, R* sp, int nth, const R* E,
                                                const R* B, const R* J, bool em_coll)
     {
         const R hv = sp[(38 + K) * nth];
         const R v = em_coll ? R(2) * heq13<K>(E, B, J, A.k) - hv : hv;
-        A.hout[(int64_t)K * A.stride + c] = (typename Cfg::hpop)v;
-        CollideH<K + 1, Cfg>::run(A, c, sp, nth, E, B, J, em_coll);
+        if constexpr (TILE)
+            sp[(38 + K) * nth] = v;
+        else
+            A.hout[(int64_t)K * A.stride + c] = (typename Cfg::hpop)v;
+        CollideH<K + 1, Cfg, TILE>::run(A, c, sp, nth, E, B, J, em_coll);
     }
 };
-template <class Cfg>
-struct CollideH<24, Cfg> {
+template <class Cfg, bool TILE>
+struct CollideH<24, Cfg, TILE> {
     using R = typename Cfg::real;
-    static __device__ __forceinline__ void run(const StepArgs<Cfg>&, int64_t, const R*, int, const R*, const R*,
+    static __device__ __forceinline__ void run(const StepArgs<Cfg>&, int64_t, R*, int, const R*, const R*,
                                                const R*, bool) {}
 };
 
@@ -347,14 +362,245 @@ __device__ __forceinline__ void warp_max_into(double v, double* dst)
         atomicMax(reinterpret_cast<unsigned long long*>(dst), b);
 }
 
+// ---------------------------------------------------------------------------
+// TMA tile path (2-D runs with periodic faces, float32 / float16 storage).
+// A block updates a tile of kTileW x kTileH cells (one thread per cell, thread
+// tid = tx + kTileW ty). Its inputs arrive by tensor-map copies into shared
+// memory: the f, g planes of two directions at a time, then the h planes four
+// at a time, each as a box of the tile plus a halo of 2 rows and one 16-byte
+// unit of columns on either side (the minmod stencil reaches 2 cells along
+// each axis, the Maxwell hop 1 cell diagonally), through a ring of
+// kRingStages buffers refilled as the block consumes them; the primitives of
+// the tile come in one box. The stencil then reads shared memory at
+// compile-time offsets. The post-collision populations and primitives are
+// collected in shared memory and written back by three tensor-map stores.
+// Tiles whose halo would leave the grid (within 2 rows or one unit of columns
+// of an edge) take the per-cell path with its periodic wrap.
+// ---------------------------------------------------------------------------
+static_assert(kTileW * kTileH == kStepThreads, "one thread per tile cell");
+constexpr int kRingStages = 3;
+constexpr int kFgStages = 10;                     // directions (0,1), (2,3), ..., (18, -)
+constexpr int kHStages = 7;                       // h planes 0-3, 4-7, ..., 24
+constexpr int kTileStages = kFgStages + kHStages;  // 17
+
+template <class Cfg>
+struct TileGeo {
+    using pop = typename Cfg::pop;
+    static constexpr int PX = tile_halo_x((int)sizeof(pop));  // f, g column halo: one 16-byte unit
+    static constexpr int PXH = tile_halo_x(4);                // h column halo (float)
+    static constexpr int BWF = kTileW + 2 * PX;       // f, g box width
+    static constexpr int BWH = kTileW + 2 * PXH;      // h box width
+    static constexpr int BH = kTileH + 2 * kTileHaloY;  // box height
+    static constexpr int FG_PLANE = BWF * BH;         // elements per f or g plane in a stage
+    static constexpr int H_PLANE = BWH * BH;
+    static constexpr unsigned FG_STAGE_BYTES = 4u * FG_PLANE * sizeof(pop);
+    static constexpr unsigned H_STAGE_BYTES = 4u * H_PLANE * sizeof(float);
+    static constexpr unsigned STAGE_BYTES =
+        ((FG_STAGE_BYTES > H_STAGE_BYTES ? FG_STAGE_BYTES : H_STAGE_BYTES) + 127u) / 128u * 128u;
+    static constexpr unsigned PRIM_BYTES = (unsigned)NPRIM * kStepThreads * sizeof(float);
+};
+
+// The block's view of its tile buffers (shared memory) and maps.
+template <class Cfg>
+struct TileCtx {
+    unsigned char* ring;  // kRingStages x STAGE_BYTES
+    float* pbuf;          // [NPRIM][kStepThreads]: input primitives, then the output ones
+    typename Cfg::pop* ofg;  // [38][kStepThreads] output f, g (float32: the slots; float16: the idle ring)
+    uint64_t* bar;        // kRingStages ring barriers, then the primitives' barrier
+    int* abort;           // set when a wait ran out: the whole block then stops
+    const TileMaps* M;
+    int x0, y0;
+};
+
+// issue the copy of stage j into its ring buffer (one thread)
+template <class Cfg>
+__device__ __forceinline__ void tile_issue(const TileCtx<Cfg>& t, int j)
+{
+    using G = TileGeo<Cfg>;
+    const int s = j % kRingStages;
+    unsigned char* dst = t.ring + (size_t)s * G::STAGE_BYTES;
+    if (j < kFgStages) {
+        mbar_arrive_expect_tx(&t.bar[s], G::FG_STAGE_BYTES);
+        tma_load_4d(dst, &t.M->fg_in, t.x0 - G::PX, t.y0 - 2, 2 * j, 0, &t.bar[s]);
+    } else {
+        mbar_arrive_expect_tx(&t.bar[s], G::H_STAGE_BYTES);
+        tma_load_3d(dst, &t.M->h_in, t.x0 - G::PXH, t.y0 - 2, 4 * (j - kFgStages), &t.bar[s]);
+    }
+}
+
+// One streamed fluid population from its shared-memory tile plane; p points
+// at this cell, neighbours at compile-time offsets (dx + BWF dy). The same
+// operations in the same order as stream_pop (2-D).
+template <int I, bool VISC, class Cfg>
+__device__ __forceinline__ typename Cfg::real stream_tile(const typename Cfg::pop* p, const Phys<typename Cfg::real>& k,
+                                                          float scale)
+{
+    using R = typename Cfg::real;
+    constexpr int BW = TileGeo<Cfg>::BWF;
+    auto ld = [](const typename Cfg::pop* q) -> R {
+        if constexpr (Cfg::kHalf)
+            return __half2float(*q) * 1.0f;
+        else
+            return *q;
+    };
+    constexpr int s[2] = {c19(I, 0), c19(I, 1)};
+    const R v0 = ld(p);
+    R flux = R(0), lap = R(0);
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const int st = a == 0 ? 1 : BW;
+        const int sa = s[a];
+        if (sa != 0) {
+            const R um2 = ld(p - 2 * sa * st);
+            const R um1 = ld(p - sa * st);
+            const R up1 = ld(p + sa * st);
+            flux += flux_diff(um2, um1, v0, up1, k.kappa);
+            if (VISC) lap += (um1 + up1) - R(2) * v0;
+        } else if (VISC) {
+            lap += (ld(p - st) + ld(p + st)) - R(2) * v0;
+        }
+    }
+    R out = v0 - k.C * flux;
+    if (VISC && I != 0) out += k.kvisc * lap;
+    if constexpr (Cfg::kHalf) out *= scale;
+    return out;
+}
+
+// moments of one streamed (f, g) pair of direction I, as in StreamAll
+template <int I, class R>
+__device__ __forceinline__ void fg_moments(R f, R g, R (&Tm)[10], R& Nm, R (&Na)[3])
+{
+    constexpr int cx = c19(I, 0), cy = c19(I, 1), cz = c19(I, 2);
+    Tm[0] += f;
+    if (cx) Tm[1] += R(cx) * f;
+    if (cy) Tm[2] += R(cy) * f;
+    if (cz) Tm[3] += R(cz) * f;
+    if (cx) Tm[4] += f;
+    if (cy) Tm[5] += f;
+    if (cz) Tm[6] += f;
+    if (cx * cy) Tm[7] += R(cx * cy) * f;
+    if (cx * cz) Tm[8] += R(cx * cz) * f;
+    if (cy * cz) Tm[9] += R(cy * cz) * f;
+    Nm += g;
+    if (cx) Na[0] += R(cx) * g;
+    if (cy) Na[1] += R(cy) * g;
+    if (cz) Na[2] += R(cz) * g;
+}
+
+// moments of one pulled h of moving population K, as in PullH
+template <int K, class R>
+__device__ __forceinline__ void h_moments(R hv, R (&dEp)[3], R (&bn)[3], R& rho)
+{
+    constexpr int p = K / 8, i = (K % 8) / 2, j = K % 2, ie = (i + 3) % 4;
+    rho += hv;
+    constexpr int se = j == 0 ? 1 : -1;
+    dEp[plane_a1(p)] += R(se * hop_s1(ie)) * hv;
+    dEp[plane_a2(p)] += R(se * hop_s2(ie)) * hv;
+    bn[plane_normal(p)] += R(-se * plane_orient(p)) * hv;
+}
+
+template <int I, class Cfg>
+__device__ __forceinline__ void tile_fg_dir(const typename Cfg::pop* b, int center, int d, const StepArgs<Cfg>& A,
+                                            typename Cfg::real* sp, int nth, typename Cfg::real (&Tm)[10],
+                                            typename Cfg::real& Nm, typename Cfg::real (&Na)[3])
+{
+    using R = typename Cfg::real;
+    using G = TileGeo<Cfg>;
+    if constexpr (I < 19) {
+        const R f = stream_tile<I, true, Cfg>(b + d * G::FG_PLANE + center, A.k, A.hs.f[I]);
+        const R g = stream_tile<I, false, Cfg>(b + (2 + d) * G::FG_PLANE + center, A.k, A.hs.g[I]);
+        sp[I * nth] = f;
+        sp[(19 + I) * nth] = g;
+        fg_moments<I>(f, g, Tm, Nm, Na);
+    }
+}
+
+template <int K, class Cfg>
+__device__ __forceinline__ void tile_h_plane(const float* b, int center, int d, typename Cfg::real* sp, int nth,
+                                             typename Cfg::real (&dEp)[3], typename Cfg::real (&bn)[3],
+                                             typename Cfg::real& rho)
+{
+    using R = typename Cfg::real;
+    using G = TileGeo<Cfg>;
+    if constexpr (K < 24) {
+        const R hv = (R)b[d * G::H_PLANE + center - hop13(K, 1) * G::BWH - hop13(K, 0)];
+        sp[(38 + K) * nth] = hv;
+        h_moments<K>(hv, dEp, bn, rho);
+    } else if constexpr (K == 24) {
+        const R hv = (R)b[d * G::H_PLANE + center];
+        sp[62 * nth] = hv;
+        rho += hv;
+    }
+}
+
+// Stage J of the ring: wait for its copy, stream its planes, release the
+// buffer and refill it with stage J + kRingStages. Returns false (for every
+// thread of the block) if a copy did not arrive in time.
+template <int J, class Cfg>
+struct TileStages {
+    using R = typename Cfg::real;
+    static __device__ __forceinline__ bool run(const TileCtx<Cfg>& t, const StepArgs<Cfg>& A, int tid, R* sp, int nth,
+                                               R (&Tm)[10], R& Nm, R (&Na)[3], R (&dEp)[3], R (&bn)[3], R& rho)
+    {
+        using G = TileGeo<Cfg>;
+        constexpr int s = J % kRingStages;
+        const unsigned char* buf = t.ring + (size_t)s * G::STAGE_BYTES;
+        const int tx = tid % kTileW, ty = tid / kTileW;
+        bool arrived = mbar_wait_bounded(&t.bar[s], (uint32_t)((J / kRingStages) & 1));
+        if constexpr (J == kTileStages - 1) arrived = arrived && mbar_wait_bounded(&t.bar[kRingStages], 0u);
+        if (!arrived) *reinterpret_cast<volatile int*>(t.abort) = 1;
+        if (arrived) {
+            if constexpr (J < kFgStages) {
+                const auto* b = reinterpret_cast<const typename Cfg::pop*>(buf);
+                const int center = (ty + 2) * G::BWF + tx + G::PX;
+                tile_fg_dir<2 * J, Cfg>(b, center, 0, A, sp, nth, Tm, Nm, Na);
+                tile_fg_dir<2 * J + 1, Cfg>(b, center, 1, A, sp, nth, Tm, Nm, Na);
+            } else {
+                const float* b = reinterpret_cast<const float*>(buf);
+                const int center = (ty + 2) * G::BWH + tx + G::PXH;
+                constexpr int K0 = 4 * (J - kFgStages);
+                tile_h_plane<K0, Cfg>(b, center, 0, sp, nth, dEp, bn, rho);
+                tile_h_plane<K0 + 1, Cfg>(b, center, 1, sp, nth, dEp, bn, rho);
+                tile_h_plane<K0 + 2, Cfg>(b, center, 2, sp, nth, dEp, bn, rho);
+                tile_h_plane<K0 + 3, Cfg>(b, center, 3, sp, nth, dEp, bn, rho);
+            }
+        }
+        __syncthreads();  // every thread is done with buffer s (and has seen any abort)
+        if (*reinterpret_cast<volatile int*>(t.abort)) {
+            // let the copies already issued land before the block gives up its
+            // shared memory (each wait again bounded)
+            if (tid == 0) {
+                for (int j = J; j < J + kRingStages && j < kTileStages; ++j)
+                    mbar_wait_bounded(&t.bar[j % kRingStages], (uint32_t)((j / kRingStages) & 1));
+                mbar_wait_bounded(&t.bar[kRingStages], 0u);
+            }
+            return false;
+        }
+        if (tid == 0 && J + kRingStages < kTileStages) tile_issue<Cfg>(t, J + kRingStages);
+        return TileStages<J + 1, Cfg>::run(t, A, tid, sp, nth, Tm, Nm, Na, dEp, bn, rho);
+    }
+};
+template <class Cfg>
+struct TileStages<kTileStages, Cfg> {
+    using R = typename Cfg::real;
+    static __device__ __forceinline__ bool run(const TileCtx<Cfg>&, const StepArgs<Cfg>&, int, R*, int, R (&)[10], R&,
+                                               R (&)[3], R (&)[3], R (&)[3], R&)
+    {
+        return true;
+    }
+};
+
 // One cell update (x, y, z) of one run; `tid` is the thread's index in its
 // block of kStepThreads threads (its rows of the shared-memory buffers). Threads of
 // cells outside the grid return at once, except in the learned-seed variant,
 // whose warp-wide MMA needs all 32 lanes: there they work on a clamped cell
 // and store nothing.
-template <class Cfg, bool IS3D, int SEED, bool OPEN>
+// TILE: a cell of an interior tile of the TMA tile path (2-D, periodic,
+// every cell active): its inputs come from the block's ring and primitive
+// buffers (tc), its outputs go to the block's shared-memory output tiles.
+template <class Cfg, bool IS3D, int SEED, bool OPEN, bool TILE = false>
 __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, const int z, const int tid,
-                                          unsigned char* smem_raw)
+                                          unsigned char* smem_raw, const TileCtx<Cfg>* tc = nullptr)
 {
     constexpr int nth = kStepThreads;  // a compile-time stride of the shared-memory slots
     using R = typename Cfg::real;
@@ -392,22 +638,33 @@ __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, 
     // 1. streaming of f and g (with their moments) and of h (with its moments)
     R Tm[10] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
     R Nm = R(0), Na[3] = {R(0), R(0), R(0)};
-    StreamAll<0, IS3D, Cfg>::run(A, o, c, sp, nth, Tm, Nm, Na);
     R dEp[3] = {R(0), R(0), R(0)}, bn[3] = {R(0), R(0), R(0)}, rho = R(0);
-    PullH<0, IS3D, Cfg>::run(A, o, c, sp, nth, dEp, bn, rho);
-    const R h24 = (R)A.hin[24 * A.stride + c];
-    sp[62 * nth] = h24;
-    rho += h24;
+    if constexpr (TILE) {
+        if (!TileStages<0, Cfg>::run(*tc, A, tid, sp, nth, Tm, Nm, Na, dEp, bn, rho)) return;
+    } else {
+        StreamAll<0, IS3D, Cfg>::run(A, o, c, sp, nth, Tm, Nm, Na);
+        PullH<0, IS3D, Cfg>::run(A, o, c, sp, nth, dEp, bn, rho);
+        const R h24 = (R)A.hin[24 * A.stride + c];
+        sp[62 * nth] = h24;
+        rho += h24;
+    }
+    // previous primitives (the tile path's box has arrived with the last stage)
+    auto ldp = [&](int P) -> R {
+        if constexpr (TILE)
+            return (R)tc->pbuf[P * nth + tid];
+        else
+            return (R)A.pin[P * A.stride + c];
+    };
 
     // previous primitives used by the recovery
     Prim<R> old;
-    old.n = (R)A.pin[P_N * A.stride + c];
-    old.eps = (R)A.pin[P_EPS * A.stride + c];
+    old.n = ldp(P_N);
+    old.eps = ldp(P_EPS);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        old.u[a] = (R)A.pin[(P_U + a) * A.stride + c];
-        old.E[a] = (R)A.pin[(P_E + a) * A.stride + c];
-        old.B[a] = (R)A.pin[(P_B + a) * A.stride + c];
+        old.u[a] = ldp(P_U + a);
+        old.E[a] = ldp(P_E + a);
+        old.B[a] = ldp(P_B + a);
     }
     old.rho = R(0);
     if constexpr (kOpenCode) {
@@ -493,7 +750,7 @@ __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, 
     // E by central differences (Eq. Gauss_E), which carries no grid-scale
     // mode for a flow to amplify
     R rho_j = rho;
-    if (A.flags & FLAG_GAUSS_CHARGE) {
+    if (!TILE && (A.flags & FLAG_GAUSS_CHARGE)) {
         R div = R(0);
         if (A.nx > 1) div += (R)A.pin[P_E * A.stride + c + o.x[3]] - (R)A.pin[P_E * A.stride + c + o.x[1]];
         if (A.ny > 1)
@@ -590,7 +847,7 @@ __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, 
     } else {
         // keep the previous primitives (the failure is counted)
         nw = old;
-        nw.rho = (R)A.pin[P_RHO * A.stride + c];
+        nw.rho = ldp(P_RHO);
         n_dev = nw.n - k.n_r;
         eps_dev = nw.eps - k.eps_r;
 #pragma unroll
@@ -656,22 +913,31 @@ __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, 
     EqCell<R> q;
     eq_cell(nw, n_dev, eps_dev, dE, dB, k, q);
     if (kOpenCode && relax_eq) SetEqFG<0, Cfg>::run(sp, nth, q);
-    CollideFG<0, Cfg>::run(A, c + dco, sp, nth, q);
+    CollideFG<0, Cfg, TILE>::run(A, c + dco, sp, nth, q, TILE ? tc->ofg + tid : nullptr);
     const bool em_coll = (A.flags & FLAG_NO_EM_COLLISION) == 0;
     // h_c - h_ref = 2 h^eq(E - Er, B - Br, J) - (h - h_ref)  (Eq. Maxwell-eq is linear)
     const int64_t co = c + dco;
-    CollideH<0, Cfg>::run(A, co, sp, nth, dE, dB, J, em_coll);
-    A.hout[24 * A.stride + co] = (typename Cfg::hpop)(em_coll ? R(2) * nw.rho - sp[62 * nth] : sp[62 * nth]);
-
-    A.pout[P_N * A.stride + co] = (typename Cfg::prim)nw.n;
-    A.pout[P_EPS * A.stride + co] = (typename Cfg::prim)nw.eps;
+    CollideH<0, Cfg, TILE>::run(A, co, sp, nth, dE, dB, J, em_coll);
+    const R h24o = em_coll ? R(2) * nw.rho - sp[62 * nth] : sp[62 * nth];
+    if constexpr (TILE)
+        sp[62 * nth] = h24o;
+    else
+        A.hout[24 * A.stride + co] = (typename Cfg::hpop)h24o;
+    auto stp = [&](int P, R v) {
+        if constexpr (TILE)
+            tc->pbuf[P * nth + tid] = (float)v;
+        else
+            A.pout[P * A.stride + co] = (typename Cfg::prim)v;
+    };
+    stp(P_N, nw.n);
+    stp(P_EPS, nw.eps);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        A.pout[(P_U + a) * A.stride + co] = (typename Cfg::prim)nw.u[a];
-        A.pout[(P_E + a) * A.stride + co] = (typename Cfg::prim)nw.E[a];
-        A.pout[(P_B + a) * A.stride + co] = (typename Cfg::prim)nw.B[a];
+        stp(P_U + a, nw.u[a]);
+        stp(P_E + a, nw.E[a]);
+        stp(P_B + a, nw.B[a]);
     }
-    A.pout[P_RHO * A.stride + co] = (typename Cfg::prim)nw.rho;
+    stp(P_RHO, nw.rho);
 
     // recovery counters, aggregated per warp
     const unsigned mask = __activemask();
@@ -712,6 +978,83 @@ __host__ __device__ constexpr size_t step_cell_smem(int seed)
     return seed == SEED_MLP ? (size_t)kStepSlots * sizeof(typename Cfg::real) * kStepThreads +
                                   (size_t)(MLP_ACT_BYTES_PER_CELL + 8 * sizeof(float)) * kStepThreads
                             : (size_t)kStepSlots * sizeof(typename Cfg::real) * kStepThreads;
+}
+
+// the tile path applies to storage formats whose h and primitives are float
+template <class Cfg>
+constexpr bool kTileCapable = sizeof(typename Cfg::hpop) == 4 && sizeof(typename Cfg::prim) == 4 &&
+                              sizeof(typename Cfg::real) == 4;
+
+__host__ __device__ constexpr size_t align128(size_t b) { return (b + 127) / 128 * 128; }
+
+// shared memory of the tile kernel: the per-cell slots (and learned-seed
+// buffers), the ring, the primitive tile, barriers
+template <class Cfg>
+__host__ __device__ constexpr size_t tile_smem_bytes(int seed)
+{
+    return align128(step_cell_smem<Cfg>(seed)) + (size_t)kRingStages * TileGeo<Cfg>::STAGE_BYTES +
+           TileGeo<Cfg>::PRIM_BYTES + 128;
+}
+
+// One run of a 2-D periodic grid in tiles of kTileW x kTileH cells: interior
+// tiles by TMA copies through shared memory, edge tiles cell by cell.
+template <class Cfg, int SEED>
+__global__ void __launch_bounds__(kStepThreads, StepMinBlocks<Cfg, SEED>::value)
+    step_tile_kernel(const __grid_constant__ StepArgs<Cfg> A, const __grid_constant__ TileMaps M)
+{
+    using G = TileGeo<Cfg>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * kTileW, y0 = blockIdx.y * kTileH;
+    const bool interior = x0 >= G::PX && x0 + kTileW + G::PX <= A.nx && y0 >= 2 && y0 + kTileH + 2 <= A.ny;
+    if (!interior) {  // block-uniform
+        step_cell<Cfg, false, SEED, false>(A, x0 + tid % kTileW, y0 + tid / kTileW, 0, tid, smem_raw);
+        return;
+    }
+    size_t off = align128(step_cell_smem<Cfg>(SEED));
+    TileCtx<Cfg> t;
+    t.ring = smem_raw + off;
+    off += (size_t)kRingStages * G::STAGE_BYTES;
+    t.pbuf = reinterpret_cast<float*>(smem_raw + off);
+    off += G::PRIM_BYTES;
+    // the output f, g tile: float32 overwrites the streamed values in their
+    // slots; float16 uses the ring, idle once the last stage is consumed
+    static_assert(!Cfg::kHalf || 38u * kStepThreads * sizeof(typename Cfg::pop) <= kRingStages * G::STAGE_BYTES,
+                  "ring too small for the float16 output tile");
+    if constexpr (Cfg::kHalf)
+        t.ofg = reinterpret_cast<typename Cfg::pop*>(t.ring);
+    else
+        t.ofg = reinterpret_cast<typename Cfg::pop*>(smem_raw);
+    t.bar = reinterpret_cast<uint64_t*>(smem_raw + off);
+    t.abort = reinterpret_cast<int*>(t.bar + kRingStages + 1);
+    t.M = &M;
+    t.x0 = x0;
+    t.y0 = y0;
+    if (tid == 0) {
+        for (int i = 0; i <= kRingStages; ++i) mbar_init(&t.bar[i], 1u);
+        *t.abort = 0;
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        mbar_arrive_expect_tx(&t.bar[kRingStages], G::PRIM_BYTES);
+        tma_load_3d(t.pbuf, &M.p_in, x0, y0, 0, &t.bar[kRingStages]);
+        for (int j = 0; j < kRingStages; ++j) tile_issue<Cfg>(t, j);
+    }
+    step_cell<Cfg, false, SEED, false, true>(A, x0 + tid % kTileW, y0 + tid / kTileW, 0, tid, smem_raw, &t);
+    if (*reinterpret_cast<volatile int*>(t.abort)) {  // every thread returned from the same stage
+        if (tid == 0) atomicOr(A.status, STATUS_TMA_TIMEOUT);
+        return;
+    }
+    fence_proxy_async_smem();  // the output tiles written by every thread, before the copies read them
+    __syncthreads();
+    if (tid == 0) {
+        tma_store_3d(&M.fg_out, t.ofg, x0, y0, 0);
+        tma_store_3d(&M.h_out, reinterpret_cast<const float*>(smem_raw) + 38 * kStepThreads, x0, y0, 0);
+        tma_store_3d(&M.p_out, t.pbuf, x0, y0, 0);
+        tma_store_commit();
+        tma_store_wait_read();  // the block's shared memory stays until the stores have read it
+    }
 }
 
 // the batched kernel keeps the arguments of its current run in shared memory,
@@ -810,8 +1153,25 @@ cudaError_t configure_step_kernels()
                 const cudaError_t e = dispatch_variant(d == 1, seed, o == 1, SetSmemAttr<Cfg>{});
                 if (e != cudaSuccess) return e;
             }
+    if constexpr (kTileCapable<Cfg>) {
+        const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        cudaError_t e = cudaFuncSetAttribute(step_tile_kernel<Cfg, SEED_PREV>, a, (int)tile_smem_bytes<Cfg>(SEED_PREV));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(step_tile_kernel<Cfg, SEED_COLD>, a, (int)tile_smem_bytes<Cfg>(SEED_COLD));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(step_tile_kernel<Cfg, SEED_MLP>, a, (int)tile_smem_bytes<Cfg>(SEED_MLP));
+        if (e != cudaSuccess) return e;
+    }
     configured = true;
     return cudaSuccess;
+}
+
+// whether a run's step takes the TMA tile kernel (given its tensor maps)
+template <class Cfg>
+bool tile_path(const StepArgs<Cfg>& A, const TileMaps* maps)
+{
+    return kTileCapable<Cfg> && maps != nullptr && A.nz == 1 && A.open_mask == 0 &&
+           (A.flags & (FLAG_GAUSS_CHARGE | FLAG_NO_TMA_TILES)) == 0;
 }
 
 template <class Cfg>
@@ -874,8 +1234,23 @@ struct LaunchRun {
 };
 
 template <class Cfg>
-cudaError_t launch_step(const StepArgs<Cfg>& A, cudaStream_t stream)
+cudaError_t launch_step(const StepArgs<Cfg>& A, cudaStream_t stream, const TileMaps* maps)
 {
+    if constexpr (kTileCapable<Cfg>) {
+        if (tile_path(A, maps)) {
+            const cudaError_t ce = configure_step_kernels<Cfg>();
+            if (ce != cudaSuccess) return ce;
+            const dim3 grid((A.nx + kTileW - 1) / kTileW, (A.ny + kTileH - 1) / kTileH, 1);
+            const size_t sm = tile_smem_bytes<Cfg>(A.seed);
+            if (A.seed == SEED_MLP)
+                step_tile_kernel<Cfg, SEED_MLP><<<grid, kStepThreads, sm, stream>>>(A, *maps);
+            else if (A.seed == SEED_COLD)
+                step_tile_kernel<Cfg, SEED_COLD><<<grid, kStepThreads, sm, stream>>>(A, *maps);
+            else
+                step_tile_kernel<Cfg, SEED_PREV><<<grid, kStepThreads, sm, stream>>>(A, *maps);
+            return cudaGetLastError();
+        }
+    }
     const int bx = A.nx >= LB_STEP_BX ? LB_STEP_BX : (A.nx >= 64 ? 64 : 32);
     const int by = kStepThreads / bx;
     const cudaError_t ce = configure_step_kernels<Cfg>();

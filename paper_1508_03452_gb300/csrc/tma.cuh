@@ -1,0 +1,135 @@
+// tma.cuh -- the Blackwell data-movement primitives the tiled step kernel uses:
+// mbarriers in shared memory, tensor-map (TMA) tile loads completed on an
+// mbarrier, tensor-map tile stores from shared memory, and the proxy fences
+// between them. Inline PTX (sm_90 and later; compiled for sm_103a).
+//
+// Every wait is bounded: a wait that has not seen its phase complete within
+// kTmaWaitNs of global time returns false instead of spinning on, so a lost
+// copy surfaces as an error status rather than a hung GPU.
+#pragma once
+
+#include <cuda.h>  // CUtensorMap (an opaque 128-byte descriptor)
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lb {
+
+constexpr unsigned long long kTmaWaitNs = 500ull * 1000ull * 1000ull;  // 0.5 s
+
+// Tile of the tiled step: kTileW x kTileH cells, one thread per cell; the
+// input boxes reach kTileHaloY rows above and below and one 16-byte unit of
+// columns on either side (tile_halo_x elements of `bytes` bytes).
+constexpr int kTileW = 32, kTileH = 4, kTileHaloY = 2;
+__host__ __device__ constexpr int tile_halo_x(int bytes) { return 16 / bytes; }
+
+// Tensor maps of one run of the tiled step for one input buffer (the other
+// buffer is the output). Boxes: fg_in (kTileW + 2 halo, kTileH + 4, 2, 2),
+// h_in (kTileW + 8, kTileH + 4, 4), p_in (kTileW, kTileH, 12); the outputs
+// (kTileW, kTileH, 38 | 25 | 12).
+struct TileMaps {  // (aligned as CUtensorMap)
+    CUtensorMap fg_in;   // (x, y, direction 0..18, f | g) of the input f, g planes
+    CUtensorMap h_in;    // (x, y, k 0..24) input h
+    CUtensorMap p_in;    // (x, y, primitive 0..11) input primitives
+    CUtensorMap fg_out;  // (x, y, plane 0..37) output f then g
+    CUtensorMap h_out;   // (x, y, k) output h
+    CUtensorMap p_out;   // (x, y, primitive) output primitives
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// makes the initialised barriers visible to the asynchronous (TMA) proxy
+__device__ __forceinline__ void mbar_init_fence()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// waits for the phase of parity `parity` of *bar; false after kTmaWaitNs
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > kTmaWaitNs) return false;
+    return true;
+}
+
+// 3-D / 4-D tile loads into shared memory, completing on *bar (byte count)
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// 3-D tile store from shared memory (bulk-group completion)
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, const void* src, int c0, int c1, int c2)
+{
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_store_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+// the committed stores have finished reading shared memory
+__device__ __forceinline__ void tma_store_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+
+// orders this thread's generic-proxy shared-memory writes before later
+// asynchronous-proxy (TMA) accesses to them
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* map)
+{
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+}  // namespace lb

@@ -20,6 +20,7 @@ PERIODIC, OPEN, DRIVEN = 0, 1, 2
 FP64, FP32, FP16_DEV = 0, 1, 2
 RECOVERY_PLAIN, RECOVERY_MLP, RECOVERY_COLD = 0, 1, 2
 FLAG_NO_EM_COLLISION, FLAG_UNSHIFTED_POWER, FLAG_ONE_PASS_RECOVERY, FLAG_GAUSS_CHARGE = 1, 2, 4, 8
+FLAG_NO_TMA_TILES, FLAG_FIRST_ORDER_FLUX = 16, 32
 MLP_NPARAM, MLP_NFEAT, MLP_ROW = 9924, 20, 24
 SCHED_PER_RUN, SCHED_BATCH = 0, 1
 NMOMENTS, NDIAG, NTABLE, NHIST = 16, 10, 311, 17
@@ -34,7 +35,7 @@ EXPORTED = [
     "lbrmhd_mlp_nparams", "lbrmhd_mlp_blob_bytes", "lbrmhd_mlp_pack", "lbrmhd_mlp_infer", "lbrmhd_mlp_grad",
     "lbrmhd_mlp_train", "lbrmhd_set_mlp_weights", "lbrmhd_set_mlp_samples", "lbrmhd_get_iteration_histogram",
     "lbrmhd_set_schedule", "lbrmhd_get_schedule", "lbrmhd_autotune", "lbrmhd_reconnection_rate",
-    "lbrmhd_init_fields_relaxed",
+    "lbrmhd_init_fields_relaxed", "lbrmhd_get_status",
 ]
 
 
@@ -116,6 +117,7 @@ def load(build_if_missing: bool = True):
         L.lbrmhd_get_diagnostics.argtypes = [vp, C.c_int, dp]
         L.lbrmhd_get_diagnostics_noalloc.argtypes = [vp, C.c_int, vp]
         L.lbrmhd_get_stats.argtypes = [vp, C.c_int, C.POINTER(i64)]
+        L.lbrmhd_get_status.argtypes = [vp, C.POINTER(i64)]
         L.lbrmhd_state_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
         L.lbrmhd_get_state.argtypes = [vp, vp, C.c_size_t]
         L.lbrmhd_set_state.argtypes = [vp, vp, C.c_size_t]
@@ -331,6 +333,16 @@ class Solver:
         out = (C.c_int64 * 4)()
         self._check(self._L.lbrmhd_get_stats(self._h, run, out))
         return {"steps": out[0], "recover_fail": out[1], "iter_total": out[2], "iter_max": out[3]}
+
+    def status(self) -> dict:
+        """Health of the handle (synchronises): status bits of the step kernels,
+        recovery failures over all runs, runs on the TMA tile kernel, and the
+        call's return code (OK, ERR_NONCONVERGED or ERR_TIMEOUT)."""
+        out = (C.c_int64 * 3)()
+        rc = self._L.lbrmhd_get_status(self._h, out)
+        if rc not in (OK, ERR_NONCONVERGED, ERR_TIMEOUT):
+            self._check(rc)
+        return {"bits": out[0], "recover_fail": out[1], "tiled_runs": out[2], "rc": rc}
 
     def iteration_histogram(self, run=0) -> np.ndarray:
         """Recovery iteration counts since init: [k] = cell updates converged in

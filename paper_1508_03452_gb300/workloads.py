@@ -225,3 +225,29 @@ def alfven_paper(ncell=400, *, B0=1.0, By=0.1, eta_A=0.118591, vA=0.40785, n0=1.
     return Fields(ncell, 1, 1, np.full(ncell, n0), np.full(ncell, p0), u, B,
                   meta={"workload": "alfven_paper", "dx": dx, "x": x, "vA": vA, "x0": x0, "x1": x1,
                         "eta_A": eta_A, "B0": B0})
+
+
+def kelvin_helmholtz_paper(ncell=512, *, U0=0.6, dn=1.8, c=2.5, B0=0.06, n0=1.0, p0=1.0, u_pert=0.01,
+                           k=2.0 * math.pi) -> Fields:
+    """The paper's Kelvin-Helmholtz-driven reconnection set-up (Sec. IV,
+    Kelvin-Helmholtz-driven reconnection): [-0.5, 0.5]^2 in ncell^2 cells
+    (dx = 1 / ncell, to be run with dx/dt = 2.5 sqrt 2, i.e. c = 2.5, periodic
+    in x and open in y), one shear layer at y = 0 of width a = dx:
+    u_x = (U0 c / 2) tanh(y / a), n = n0 + (dn / 2) tanh(y / a), p = p0,
+    B_x = B0 tanh(y / a), B_y = B_z = 0, and the single-mode perturbation
+    u_y = u_pert sin(k x) exp(-y^2 / b^2), b = 10 dx. U0 is given in units of
+    c; u_pert in the velocity unit of the run. E is left to the solver (ideal
+    Ohm's law, as the paper's initial field)."""
+    dx = 1.0 / ncell
+    xc = -0.5 + (np.arange(ncell) + 0.5) * dx
+    X, Y = np.meshgrid(xc, xc, indexing="xy")  # X[j, i] = x_i, Y[j, i] = y_j: x-fastest after reshape
+    x, y = X.reshape(-1), Y.reshape(-1)
+    N = ncell * ncell
+    a, b = dx, 10.0 * dx
+    t = np.tanh(y / a)
+    u = np.zeros((3, N)); B = np.zeros((3, N))
+    u[0] = 0.5 * U0 * c * t
+    u[1] = u_pert * np.sin(k * x) * np.exp(-(y * y) / (b * b))
+    B[0] = B0 * t
+    return Fields(ncell, ncell, 1, n0 + 0.5 * dn * t, np.full(N, p0), u, B,
+                  meta={"workload": "kh_paper", "dx": dx, "c": c, "U0": U0, "dn": dn, "B0": B0, "x": xc, "y": xc})

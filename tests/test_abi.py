@@ -77,7 +77,7 @@ def test_bad_parameters_are_rejected():
     # face, finite values; unknown flags are refused
     for kw in (dict(drive_f0=0.05, drive_layers=0), dict(drive_f0=0.05, drive_layers=2,
                                                        bc=(L.OPEN,) * 4 + (L.DRIVEN, L.OPEN)),
-               dict(drive_f0=float("nan"), drive_layers=2), dict(drive_vmax=float("inf")), dict(flags=16)):
+               dict(drive_f0=float("nan"), drive_layers=2), dict(drive_vmax=float("inf")), dict(flags=64)):
         with pytest.raises(L.LbrmhdError) as e:
             L.Solver(L.make_params(8, 8, 8, **kw))
         assert e.value.code == L.ERR_BAD_ARG, kw
