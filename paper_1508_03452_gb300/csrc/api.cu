@@ -63,6 +63,7 @@ struct lbrmhd_state_s {
     int* d_flag = nullptr;
     double* d_noalloc = nullptr;  // device address of g_noalloc_partials in this handle's context
     int* d_status = nullptr;      // lb::STATUS_* bits raised by the step kernels
+    unsigned int* d_barrier = nullptr;  // arrival counter of the persistent launch's grid barrier
     unsigned char* d_mlp = nullptr;  // packed network of the learned seed
     bool mlp_set = false;
     // launch schedule (lbrmhd_set_schedule / lbrmhd_autotune)
@@ -470,7 +471,7 @@ int upload_args(lbrmhd_handle h)
 template <class Cfg>
 int prepare_batch(lbrmhd_handle h, const lbrmhd_schedule& sc)
 {
-    if (sc.kind != LBRMHD_SCHED_BATCH) return LBRMHD_OK;
+    if (sc.kind != LBRMHD_SCHED_BATCH && sc.kind != LBRMHD_SCHED_PERSISTENT) return LBRMHD_OK;
     int rc = LBRMHD_OK;
     if (h->tiles_dirty) rc = build_tiles(h, sc);
     if (!rc && h->args_dirty) rc = upload_args<Cfg>(h);
@@ -522,12 +523,53 @@ int ensure_aux(lbrmhd_handle h, int n)
     return LBRMHD_OK;
 }
 
+// whether the handle's runs admit the persistent launch: every run periodic
+// and unforced (no boundary or cut-off pass between steps) and all of one
+// kernel variant
+std::string persistent_unsupported(lbrmhd_handle h)
+{
+    for (const auto& r : h->runs)
+        if (open_variant(r) || capped(r)) return "the persistent schedule needs periodic, unforced runs";
+    for (const auto& r : h->runs)
+        if ((r.p.nz > 1) != (h->runs[0].p.nz > 1) || run_seed(r) != run_seed(h->runs[0]))
+            return "the persistent schedule needs runs of one kernel variant (all 2-D or all 3-D, one seed)";
+    return "";
+}
+
+constexpr unsigned long long kBarrierWaitNs = 1000ull * 1000ull * 1000ull;  // 1 s
+
+// n steps of every run in one cooperative launch (tiles and arguments prepared)
+template <class Cfg>
+int issue_persistent(lbrmhd_handle h, const lbrmhd_schedule& sc, int in, int64_t n, cudaStream_t s)
+{
+    const std::string m = persistent_unsupported(h);
+    if (!m.empty()) return fail(h, LBRMHD_ERR_BAD_ARG, m);
+    if (h->groups.size() != 1) return fail(h, LBRMHD_ERR_STATE, "persistent launch needs one tile group");
+    const auto& g = h->groups[0];
+    int dev_sms = 0;
+    LB_CK(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, h->device));
+    const int per_sm = lb::persistent_blocks_per_sm<Cfg>(g.is3d, g.seed, g.open);
+    if (per_sm < 1) return fail(h, LBRMHD_ERR_CUDA, "persistent kernel does not fit on an SM");
+    const int grid = std::min(per_sm * dev_sms, g.count);
+    const size_t parity_bytes = h->runs.size() * lb::batch_args_stride<Cfg>();
+    for (int64_t done = 0; done < n;) {
+        const int k = (int)std::min<int64_t>(n - done, 1 << 20);
+        LB_CK(cudaMemsetAsync(h->d_barrier, 0, sizeof(unsigned int), s));
+        LB_CK(lb::launch_step_persistent<Cfg>((const unsigned char*)h->d_args, parity_bytes, (int)((in + done) & 1),
+                                              h->d_tiles + g.first, g.count, sc.bx, k, grid, g.is3d, g.seed, g.open,
+                                              h->d_barrier, h->d_status, kBarrierWaitNs, s));
+        done += k;
+    }
+    return LBRMHD_OK;
+}
+
 // n steps of every run from input buffer `in`, issued after and completed
 // before the work of stream `s` (host state untouched, as issue_step)
 template <class Cfg>
 int issue_steps(lbrmhd_handle h, const lbrmhd_schedule& sc, int in, int64_t n, cudaStream_t s)
 {
     using R = typename Cfg::real;
+    if (sc.kind == LBRMHD_SCHED_PERSISTENT) return issue_persistent<Cfg>(h, sc, in, n, s);
     const int S = sc.kind == LBRMHD_SCHED_PER_RUN ? std::min<int>(sc.streams, (int)h->runs.size()) : 1;
     if (S <= 1) {
         for (int64_t t = 0; t < n; ++t) {
@@ -798,7 +840,8 @@ int write_stats(lbrmhd_handle h, const RunState& r, const unsigned long long* to
 
 std::string check_schedule(const lbrmhd_schedule& s)
 {
-    if (s.kind != LBRMHD_SCHED_PER_RUN && s.kind != LBRMHD_SCHED_BATCH) return "unknown schedule kind";
+    if (s.kind != LBRMHD_SCHED_PER_RUN && s.kind != LBRMHD_SCHED_BATCH && s.kind != LBRMHD_SCHED_PERSISTENT)
+        return "unknown schedule kind";
     if (s.bx != 32 && s.bx != 64 && s.bx != 128) return "tile width must be 32, 64 or 128";
     if (s.waves < 0 || s.waves > 8) return "waves must be in 0..8";
     if (s.order != 0 && s.order != 1) return "order must be 0 or 1";
@@ -862,6 +905,10 @@ int autotune(lbrmhd_handle h, int trials, lbrmhd_schedule* best_out, double* bes
             for (int waves : {0, 1})
                 for (int order : {0, 1})
                     if (nr > 1 || order == 0) cand.push_back({LBRMHD_SCHED_BATCH, bx, waves, order, 1, 0});
+        if (persistent_unsupported(h).empty())
+            for (int bx : {128, 64, 32})
+                for (int order : {0, 1})
+                    if (nr > 1 || order == 0) cand.push_back({LBRMHD_SCHED_PERSISTENT, bx, 1, order, 1, 0});
         // the counters are restored afterwards: dry steps only write the
         // scratch (output) buffers
         std::vector<std::vector<unsigned long long>> saved(h->runs.size(),
@@ -1053,6 +1100,7 @@ int lbrmhd_create(const lbrmhd_params* params, int n_runs, lbrmhd_handle* out)
     ok = ok && cudaMalloc(&h->d_flag, sizeof(int)) == cudaSuccess;
     ok = ok && cudaMalloc(&h->d_status, sizeof(int)) == cudaSuccess;
     if (ok) cudaMemset(h->d_status, 0, sizeof(int));
+    ok = ok && cudaMalloc(&h->d_barrier, 2 * sizeof(unsigned int)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         lbrmhd_destroy(h);
@@ -1094,6 +1142,7 @@ int lbrmhd_destroy(lbrmhd_handle h)
     if (h->d_small) cudaFree(h->d_small);
     if (h->d_flag) cudaFree(h->d_flag);
     if (h->d_status) cudaFree(h->d_status);
+    if (h->d_barrier) cudaFree(h->d_barrier);
     if (h->d_mlp) cudaFree(h->d_mlp);
     drop_graphs(h);
     if (h->d_args) cudaFree(h->d_args);

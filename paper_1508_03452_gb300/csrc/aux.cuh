@@ -74,6 +74,19 @@ cudaError_t launch_step_batch(const unsigned char* d_args, const int4* d_tiles, 
                               bool is3d, int seed, bool open, cudaStream_t stream);
 template <class Cfg>
 int batch_blocks_per_sm(bool is3d, int seed, bool open);
+// nsteps steps of every run of one kernel variant in one cooperative launch
+// (grid-wide barrier between steps; *counter zero on entry)
+template <class Cfg>
+cudaError_t launch_step_persistent(const unsigned char* d_args, size_t parity_bytes, int in0, const int4* d_tiles,
+                                   int ntiles, int bx, int nsteps, int grid, bool is3d, int seed, bool open,
+                                   unsigned int* counter, int* status, unsigned long long wait_ns,
+                                   cudaStream_t stream);
+template <class Cfg>
+int persistent_blocks_per_sm(bool is3d, int seed, bool open);
+// a cooperative grid of `blocks` blocks meeting at a grid barrier that never
+// completes when `unreachable` (the bounded wait's self-test)
+cudaError_t launch_barrier_selftest(int blocks, unsigned int* counter, int* status, int unreachable,
+                                    unsigned long long wait_ns, cudaStream_t stream);
 template <class Cfg>
 cudaError_t launch_null(const PopView<Cfg>& V, int y_lo, int y_hi, const typename Cfg::prim* ez0, double B0,
                         double* scratch, int64_t scratch_doubles, double* out, cudaStream_t s);

@@ -108,7 +108,8 @@ struct StepArgs {
     int* status;
 };
 // status bits a step kernel can raise
-constexpr int STATUS_TMA_TIMEOUT = 1;  // a tile's copy did not arrive within the wait limit
+constexpr int STATUS_TMA_TIMEOUT = 1;      // a tile's copy did not arrive within the wait limit
+constexpr int STATUS_BARRIER_TIMEOUT = 2;  // a persistent launch's grid barrier gave up waiting
 // open_mask bit for runs that need the open-variant code without an open face
 constexpr int OPEN_EXTRA = 8;
 

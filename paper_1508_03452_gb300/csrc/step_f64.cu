@@ -6,4 +6,8 @@ template cudaError_t launch_step<CfgF64>(const StepArgs<CfgF64>&, cudaStream_t, 
 template cudaError_t launch_step_batch<CfgF64>(const unsigned char*, const int4*, int, int, int, bool, int, bool,
                                                   cudaStream_t);
 template int batch_blocks_per_sm<CfgF64>(bool, int, bool);
+template cudaError_t launch_step_persistent<CfgF64>(const unsigned char*, size_t, int, const int4*, int, int, int, int,
+                                                     bool, int, bool, unsigned int*, int*, unsigned long long,
+                                                     cudaStream_t);
+template int persistent_blocks_per_sm<CfgF64>(bool, int, bool);
 }  // namespace lb

@@ -1095,6 +1095,76 @@ __global__ void __launch_bounds__(kStepThreads, StepMinBlocks<Cfg, SEED>::value)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Persistent multi-step launch: one cooperative grid (every block resident)
+// walks the tile list of all runs for `nsteps` steps, with a grid-wide
+// barrier between steps (step t + 1 of a cell reads its neighbours' step t).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Every block arrives on *counter and waits until it reaches `target`; the
+// wait gives up after wait_ns of global time (status bit, false for every
+// thread of the block). All blocks of the grid must be resident (cooperative
+// launch) for the barrier to complete.
+__device__ __forceinline__ bool grid_barrier(unsigned int* counter, unsigned int target, int* status,
+                                             unsigned long long wait_ns)
+{
+    __syncthreads();
+    int ok = 1;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(counter, 1u);
+        const unsigned long long t0 = global_ns();
+        while (ld_acquire_u32(counter) < target) {
+            if (global_ns() - t0 > wait_ns) {
+                atomicOr(status, STATUS_BARRIER_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(100);
+        }
+        __threadfence();
+    }
+    return __syncthreads_and(ok) != 0;
+}
+
+template <class Cfg, bool IS3D, int SEED, bool OPEN>
+__global__ void __launch_bounds__(kStepThreads, StepMinBlocks<Cfg, SEED>::value)
+    step_persistent_kernel(const unsigned char* __restrict__ args, size_t parity_bytes, int in0,
+                           const int4* __restrict__ tiles, int ntiles, int bx, int nsteps, unsigned int* counter,
+                           int* status, unsigned long long wait_ns)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    StepArgs<Cfg>* sA = reinterpret_cast<StepArgs<Cfg>*>(smem_raw + step_cell_smem<Cfg>(SEED));
+    const int tid = threadIdx.x;
+    const int tx = tid % bx, ty = tid / bx;
+    for (int t = 0; t < nsteps; ++t) {
+        // argument records of the runs for this step's input buffer
+        const unsigned char* a = args + (size_t)((in0 + t) & 1) * parity_bytes;
+        int run = -1;
+        for (int i = blockIdx.x; i < ntiles; i += gridDim.x) {
+            const int4 td = __ldg(tiles + i);
+            if (td.x != run) {
+                __syncthreads();
+                const int4* src = reinterpret_cast<const int4*>(a + (size_t)td.x * batch_args_bytes<Cfg>());
+                int4* dst = reinterpret_cast<int4*>(sA);
+                for (int j = tid; j < (int)(batch_args_bytes<Cfg>() / 16); j += kStepThreads) dst[j] = __ldg(src + j);
+                __syncthreads();
+                run = td.x;
+            }
+            __syncwarp();
+            step_cell<Cfg, IS3D, SEED, OPEN>(*sA, td.y + tx, td.z + ty, td.w, tid, smem_raw);
+        }
+        if (t + 1 < nsteps && !grid_barrier(counter, (unsigned int)(t + 1) * gridDim.x, status, wait_ns)) return;
+        __syncthreads();  // the block's args copy is rewritten by the next step's first tile
+    }
+}
+
 template <class Cfg>
 size_t step_smem_bytes(int seed)
 {
@@ -1218,6 +1288,76 @@ cudaError_t launch_step_batch(const unsigned char* d_args, const int4* d_tiles, 
     if (e != cudaSuccess) return e;
     const int g = grid > 0 && grid < ntiles ? grid : ntiles;
     return dispatch_variant(is3d, seed, open, LaunchBatch<Cfg>{d_args, d_tiles, ntiles, bx, g, stream});
+}
+
+template <class Cfg>
+struct PersistentOccupancy {
+    int* nb;
+    template <bool D, int S, bool O>
+    cudaError_t run()
+    {
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, step_persistent_kernel<Cfg, D, S, O>,
+                                                             kStepThreads, batch_smem_bytes<Cfg>(S));
+    }
+};
+
+template <class Cfg>
+struct LaunchPersistent {
+    const unsigned char* args;
+    size_t parity_bytes;
+    int in0;
+    const int4* tiles;
+    int ntiles, bx, nsteps, grid;
+    unsigned int* counter;
+    int* status;
+    unsigned long long wait_ns;
+    cudaStream_t stream;
+    template <bool D, int S, bool O>
+    cudaError_t run()
+    {
+        cudaError_t e = cudaFuncSetAttribute(step_persistent_kernel<Cfg, D, S, O>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem_bytes<Cfg>(S));
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(kStepThreads);
+        cfg.dynamicSmemBytes = batch_smem_bytes<Cfg>(S);
+        cfg.stream = stream;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, step_persistent_kernel<Cfg, D, S, O>, args, parity_bytes, in0, tiles, ntiles,
+                                  bx, nsteps, counter, status, wait_ns);
+    }
+};
+
+// resident blocks per SM of the persistent kernel (its grid is this times the SM count)
+template <class Cfg>
+int persistent_blocks_per_sm(bool is3d, int seed, bool open)
+{
+    if (configure_step_kernels<Cfg>() != cudaSuccess) return 0;
+    int nb = 0;
+    const cudaError_t e = dispatch_variant(is3d, seed, open, PersistentOccupancy<Cfg>{&nb});
+    return e == cudaSuccess ? nb : 0;
+}
+
+// nsteps steps of every run of one kernel variant in one cooperative launch;
+// *counter must be 0 on entry (the caller clears it on the stream)
+template <class Cfg>
+cudaError_t launch_step_persistent(const unsigned char* d_args, size_t parity_bytes, int in0, const int4* d_tiles,
+                                   int ntiles, int bx, int nsteps, int grid, bool is3d, int seed, bool open,
+                                   unsigned int* counter, int* status, unsigned long long wait_ns,
+                                   cudaStream_t stream)
+{
+    if (ntiles <= 0 || nsteps <= 0) return cudaSuccess;
+    if (bx != 32 && bx != 64 && bx != 128) return cudaErrorInvalidValue;
+    const cudaError_t e = configure_step_kernels<Cfg>();
+    if (e != cudaSuccess) return e;
+    return dispatch_variant(is3d, seed, open,
+                            LaunchPersistent<Cfg>{d_args, parity_bytes, in0, d_tiles, ntiles, bx, nsteps, grid,
+                                                  counter, status, wait_ns, stream});
 }
 
 template <class Cfg>
