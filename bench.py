@@ -46,8 +46,8 @@ NX = NY = 1024
 # algorithmic bytes per cell update of the fused step: 63 populations + 12
 # primitives, each read once and written once
 BYTES_PER_CELL = {"fp64": 2 * (63 + 12) * 8, "fp32": 2 * (63 + 12) * 4, "fp16": 2 * (38 * 2 + 25 * 4 + 12 * 4)}
-PROFILE = os.path.join(ROOT, "profiles", "step_kernel_current_sheet_1024.md")
-KERNEL_SOURCES = ["step_impl.cuh", "lattice.cuh", "common.cuh", "mlp.cuh"]
+PROFILE = os.path.join(ROOT, "profiles", "step_tile_kernel_current_sheet_1024.md")
+KERNEL_SOURCES = ["step_impl.cuh", "lattice.cuh", "common.cuh", "mlp.cuh", "tma.cuh"]
 GROUPS = {"n": (0,), "p": (1,), "eps": (2,), "u": (3, 4, 5), "E": (6, 7, 8), "B": (9, 10, 11)}
 
 
@@ -370,9 +370,11 @@ def batched_sweep_leg(args, stream, steps=10):
     """The batched sweep: 64 independent Kelvin-Helmholtz runs of uneven square
     grids (sides 256..1024 step 128, sigma log-uniform [10, 1e4], V in [0.1,
     0.5] c, density ratio {1, 3, 10}; seeded) in one handle, timed with one
-    launch per run per step on one stream, then with the autotuned schedule
-    replayed from CUDA graphs. Short horizon: sheared magnetised flows are
-    unstable in the scheme within a few hundred steps."""
+    launch per run per step on one stream, with the autotuned schedule
+    replayed from CUDA graphs, and with the persistent schedule (all steps in
+    one cooperative launch). The runs take the Gauss-law charge and alpha =
+    0.02, the options under which the scheme carries flowing magnetised
+    plasma furthest; the leg is marked invalid if any recovery failed in it."""
     import torch
 
     from paper_1508_03452_gb300 import lbrmhd as L
@@ -380,8 +382,8 @@ def batched_sweep_leg(args, stream, steps=10):
 
     prec = {"fp32": L.FP32, "fp16": L.FP16_DEV, "fp64": L.FP64}[args.precision]
     specs = W.kh_sweep(64)
-    solver = L.Solver([L.make_params(sp.nx, sp.ny, 1, sigma=sp.sigma, precision=prec) for sp in specs],
-                      stream=stream)
+    solver = L.Solver([L.make_params(sp.nx, sp.ny, 1, sigma=sp.sigma, precision=prec, alpha=0.02,
+                                     flags=L.FLAG_GAUSS_CHARGE) for sp in specs], stream=stream)
     for r, sp in enumerate(specs):
         F = W.kelvin_helmholtz(sp.nx, sp.ny, 1, V=sp.V, ratio=sp.ratio, B0=0.1, noise=1e-3, seed=sp.seed)
         solver.init_fields(r, F.n, F.p, F.u, F.B)
@@ -404,14 +406,57 @@ def batched_sweep_leg(args, stream, steps=10):
     solver.set_schedule(sched)
     solver.step(graph_steps)  # captures the graphs
     ms_tuned = timed(steps)
+    solver.set_schedule(L.make_schedule(L.SCHED_PERSISTENT, 128, 1, 0, 1, 0))
+    ms_persist = timed(steps)
+    status = solver.status()
     fails = sum(solver.stats(r)["recover_fail"] for r in range(len(specs)))
     solver.close()
     return {
         "workload": "kh_sweep_64_runs_sides_256_1024", "runs": len(specs), "cells_per_step": cells, "steps": steps,
         "value": cells * steps / (ms_tuned * 1e-3) / 1e6, "unit": UNIT,
         "per_run_one_stream_mlups": cells * steps / (ms_plain * 1e-3) / 1e6,
+        "persistent_mlups": cells * steps / (ms_persist * 1e-3) / 1e6,
         "schedule": sched.as_dict(), "autotune_ms_per_step": tune_ms, "recover_fail": fails,
+        "status_bits": status["bits"], "valid": fails == 0 and status["bits"] == 0,
+        "options": "Gauss-law charge (LBRMHD_FLAG_GAUSS_CHARGE), alpha = 0.02",
     }
+
+
+def kh_2048_leg(args, stream, steps=10):
+    """Config 3: Kelvin-Helmholtz shear layers on a 2048^2 periodic lattice
+    (V = 0.3 c, density ratio 10, B0 = 0.1, sigma = 1e3, seeded noise 1e-3),
+    float32 against float16-deviation storage (float32 arithmetic), each timed
+    over `steps` steps after 3 warm-up steps, with both errors against a
+    float64 GPU run of the same 13 steps."""
+    import torch
+
+    from paper_1508_03452_gb300 import lbrmhd as L
+    from paper_1508_03452_gb300 import workloads as W
+
+    n = 2048
+    F = W.kelvin_helmholtz(n, n, 1, V=0.3, ratio=10.0, B0=0.1, a=2.0, noise=1e-3, seed=3)
+    out = {"workload": "kh_2048x2048_V0.3_ratio10_sigma1e3", "grid": [n, n, 1], "steps": steps}
+    moms = {}
+    for name, prec in (("fp32", L.FP32), ("fp16_dev", L.FP16_DEV), ("fp64", L.FP64)):
+        s = L.Solver(L.make_params(n, n, 1, sigma=1e3, precision=prec), stream=stream)
+        s.init_fields(0, F.n, F.p, F.u, F.B)
+        s.step(3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = s.stats()
+        moms[name] = s.moments()
+        tiled = s.status()["tiled_runs"]
+        s.close()
+        out[name] = {"value": n * n * steps / (e0.elapsed_time(e1) * 1e-3) / 1e6, "unit": UNIT,
+                     "iters_per_cell": st["iter_total"] / (n * n * (steps + 3)), "failures": st["recover_fail"],
+                     "tile_kernel": bool(tiled)}
+    for name in ("fp32", "fp16_dev"):
+        out[name]["err_vs_fp64"] = rel_errors(moms[name], moms["fp64"])
+    return out
 
 
 def flux_rope_case(n, prec, recovery):
@@ -543,6 +588,8 @@ def run_gpu(args, world, rank, local):
     plain_iters = sum(s["iter_total"] for s in stats) / (len(SIGMAS) * N * steps_total)
     plain_hist = sum(solver.iteration_histogram(r) for r in range(len(SIGMAS)))
     plain_moments = solver.moments(1) if (rank == 0 and not args.no_learned_seed) else None
+    status = solver.status()
+    kernel_name = "lb::step_tile_kernel" if status["tiled_runs"] == len(SIGMAS) else "lb::step_kernel"
     launches = args.steps * len(SIGMAS)
     value = whole_job_mlups(world, cells, args.steps, ms * 1e-3)
     # roofline of the dominant (only) kernel of the timed region: the fused step
@@ -585,7 +632,7 @@ def run_gpu(args, world, rank, local):
                        "parallelism": f"replicas{world}" if world > 1 else "single"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "lb::step_kernel", "bytes_per_cell": bpc,
+                         "kernel": kernel_name, "bytes_per_cell": bpc,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
                     "d2h_bytes_per_step": d2h / args.steps},
@@ -599,6 +646,8 @@ def run_gpu(args, world, rank, local):
             weights, line["learned_seed"] = learned_seed_leg(args, stream, plain_moments, plain_iters, steps_total)
         if not args.no_sweep:
             line["batched_sweep"] = batched_sweep_leg(args, stream)
+        if not args.no_kh2048:
+            line["kh_2048"] = kh_2048_leg(args, stream)
         if not args.no_3d:
             line["flux_rope_3d"] = flux_rope_leg(args, stream, weights)
         clocks = clk.summary()
@@ -655,6 +704,7 @@ def main():
     ap.add_argument("--no-learned-seed", action="store_true", help="skip the learned-seed comparison leg")
     ap.add_argument("--no-sweep", action="store_true", help="skip the 64-run batched sweep leg")
     ap.add_argument("--no-3d", action="store_true", help="skip the 3-D flux-rope leg")
+    ap.add_argument("--no-kh2048", action="store_true", help="skip the 2048^2 Kelvin-Helmholtz leg")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--profile-case", action="store_true", help="untimed 1024^2 single-run case for ncu captures")
     ap.add_argument("--profile-learned", action="store_true", help="--profile-case with the learned-seed kernel")

@@ -86,10 +86,14 @@ extern "C" {
                                       differences (Eq. Gauss_E), instead of the Maxwell moment sum h (Eq.
                                       Cal_rhoc), which carries a grid-scale mode that any flow amplifies; with
                                       alpha <= 0.02 it keeps flowing magnetised plasma stable */
-#define LBRMHD_FLAG_NO_TMA_TILES 16 /* 2-D periodic runs stored in float32 / float16 normally step by the TMA
-                                       tile kernel (tensor-map copies of each tile and its halo through shared
-                                       memory); this flag keeps them on the per-cell kernel, which loads every
-                                       stencil value from global memory. Both compute the same update. */
+#define LBRMHD_FLAG_TMA_TILES 16 /* 2-D periodic runs stored in float32 / float16 step by the TMA tile
+                                    kernel: persistent blocks stream 32 x 8-cell tiles whose populations and
+                                    halo arrive by tensor-map copies through a ring of shared-memory buffers,
+                                    stencil reads from shared memory, outputs by tensor-map stores, plus a
+                                    per-cell launch over the edge tiles. The same update as the default
+                                    per-cell kernel (to float rounding); measured slower on GB300 (the
+                                    block-wide waits per ring stage cost more than the loads they replace), so
+                                    it is an option, not the default. Ignored with LBRMHD_FLAG_GAUSS_CHARGE. */
 #define LBRMHD_FLAG_FIRST_ORDER_FLUX 32 /* a study option, not the paper's scheme: the fluid face fluxes without
                                            the minmod-limited correction (Sec. III streaming, reading of h_i^a),
                                            i.e. plain first-order upwind, as the limiter gives at a discontinuity */
@@ -257,9 +261,11 @@ int lbrmhd_get_stats(lbrmhd_handle h, int run, int64_t* out4);
  * checks now and then. Synchronises the handle's stream. out3 (host, may be
  * NULL): [0] status bits raised by the step kernels since lbrmhd_create (1: a
  * TMA tile copy did not arrive within its wait limit, and that tile's update
- * was skipped), [1] recovery failures summed over every run since its
- * initialisation, [2] number of runs that step by the TMA tile kernel.
- * Returns LBRMHD_ERR_TIMEOUT if status bit 1 is set, else
+ * was skipped; 2: a persistent launch's grid barrier gave up waiting, and the
+ * launch's remaining steps were skipped), [1] recovery failures summed over every run since its
+ * initialisation, [2] number of runs that step by the TMA tile kernel
+ * (LBRMHD_FLAG_TMA_TILES).
+ * Returns LBRMHD_ERR_TIMEOUT if a status bit is set, else
  * LBRMHD_ERR_NONCONVERGED if any recovery failed, else LBRMHD_OK; errors:
  * BAD_ARG (NULL handle), CUDA. */
 int lbrmhd_get_status(lbrmhd_handle h, int64_t* out3);
@@ -297,9 +303,15 @@ int lbrmhd_lattice_tables(double* out, size_t n);
 #define LBRMHD_SCHED_PER_RUN 0 /* one launch per run per step (a grid over the run's cells) */
 #define LBRMHD_SCHED_BATCH 1   /* one launch per step over the tiles of every run (per kernel variant:
                                   2-D / 3-D runs, recovery seed) */
+#define LBRMHD_SCHED_PERSISTENT 2 /* one cooperative launch for all the steps of an lbrmhd_step call (or of
+                                     each captured graph): every block resident, walking the tiles of every
+                                     run, a grid-wide barrier between steps whose wait gives up after 1 s
+                                     (status bit 2, LBRMHD_ERR_TIMEOUT from lbrmhd_get_status); for runs
+                                     that are all periodic, unforced and of one kernel variant (BAD_ARG
+                                     from lbrmhd_step otherwise). bx and order as for BATCH. */
 
 typedef struct lbrmhd_schedule {
-    int32_t kind;        /* LBRMHD_SCHED_PER_RUN | LBRMHD_SCHED_BATCH */
+    int32_t kind;        /* LBRMHD_SCHED_PER_RUN | LBRMHD_SCHED_BATCH | LBRMHD_SCHED_PERSISTENT */
     int32_t bx;          /* BATCH: tile width 32 | 64 | 128 (a tile is bx x 128 / bx cells) */
     int32_t waves;       /* BATCH: 0 = one block per tile; w > 0 = persistent grid of w waves of
                             resident blocks, each block walking the tile list */
@@ -317,9 +329,10 @@ typedef struct lbrmhd_schedule {
 int lbrmhd_set_schedule(lbrmhd_handle h, const lbrmhd_schedule* sched);
 int lbrmhd_get_schedule(lbrmhd_handle h, lbrmhd_schedule* sched);
 
-/* Autotuner: times PER_RUN on 1, 4 and up to 16 streams and every BATCH
- * combination of bx {128, 64, 32}, waves {0, 1}, order {0, 1} on the
- * handle's current state with `trials` dry
+/* Autotuner: times PER_RUN on 1, 4 and up to 16 streams, every BATCH
+ * combination of bx {128, 64, 32}, waves {0, 1}, order {0, 1}, and (where the
+ * runs admit it) PERSISTENT with bx {128, 64, 32}, order {0, 1}, one step per
+ * launch, on the handle's current state with `trials` dry
  * steps each (steps whose output buffers are discarded: the state, the step
  * counters and the recovery counters are left as they were; attached sample
  * buffers are written), sets the fastest (keeping graph_steps) and returns
@@ -330,6 +343,16 @@ int lbrmhd_get_schedule(lbrmhd_handle h, lbrmhd_schedule* sched);
  * (trials outside 1..100), STATE (a run not initialised, a learned-seed run
  * without weights), CUDA. */
 int lbrmhd_autotune(lbrmhd_handle h, int trials, lbrmhd_schedule* best, double* best_ms);
+
+/* Self-test of the bounded wait of the persistent schedule's grid barrier:
+ * a cooperative grid of a few blocks meets at the same barrier code; with
+ * `unreachable` != 0 it waits for one arrival more than the grid has, which
+ * never comes, and every block must give up after wait_seconds (0 < w <= 10)
+ * and raise the status bit. Runs on a scratch counter and status word of the
+ * handle (the handle's own status is left alone). Returns LBRMHD_ERR_TIMEOUT
+ * if the wait ran out, LBRMHD_OK if the barrier completed; errors: BAD_ARG,
+ * CUDA. Synchronises the handle's stream. */
+int lbrmhd_barrier_selftest(lbrmhd_handle h, int unreachable, double wait_seconds);
 
 /* ------------------------------------------------------------------------
  * Learned recovery seed. The paper has no counterpart: it fixes the

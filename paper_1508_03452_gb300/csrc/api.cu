@@ -39,6 +39,8 @@ struct RunState {
     double* d_umax = nullptr;    // forced runs with a cut-off: max |u|^2 of the state, running max of the next
     // tensor maps of the TMA tile kernel for input buffer 0 and 1 (empty: the run takes the per-cell kernel)
     std::vector<lb::TileMaps> tmaps;
+    int4* d_edge = nullptr;  // the run's edge tiles (32 x 4 cells) for the per-cell launch beside the tile kernel
+    int nedge = 0;
 };
 
 constexpr size_t kStatsBytes = lb::kNumStats * sizeof(unsigned long long);  // totals (checkpoint)
@@ -63,6 +65,7 @@ struct lbrmhd_state_s {
     int* d_flag = nullptr;
     double* d_noalloc = nullptr;  // device address of g_noalloc_partials in this handle's context
     int* d_status = nullptr;      // lb::STATUS_* bits raised by the step kernels
+    int sms = 1;                  // multiprocessors of the device
     unsigned int* d_barrier = nullptr;  // arrival counter of the persistent launch's grid barrier
     unsigned char* d_mlp = nullptr;  // packed network of the learned seed
     bool mlp_set = false;
@@ -321,7 +324,7 @@ bool encode_map(CUtensorMap* m, CUtensorMapDataType dt, int elem, void* base, in
 }
 
 // the maps of both input buffers of a run (left empty where the tile kernel does not apply)
-void make_tile_maps(RunState& r)
+void make_tile_maps(RunState& r, int run_index)
 {
     r.tmaps.clear();
     if (!tile_layout_ok(r.p, open_variant(r))) return;
@@ -347,10 +350,27 @@ void make_tile_maps(RunState& r)
         ok = ok && encode_map(&m.h_out, fdt, 4, r.h[out], 3, r, 25, 1, box_ho);
         ok = ok && encode_map(&m.p_out, fdt, 4, r.prim[out], 3, r, lb::NPRIM, 1, box_p);
     }
-    if (ok) r.tmaps = std::move(maps);
+    if (!ok) return;
+    // the 32 x 4 tiles outside the rectangle of interior tiles, as (run, x0, y0, 0)
+    const lb::TileRange tr = lb::interior_tiles(r.p.nx, r.p.ny, px);
+    const int ix0 = tr.x0 * lb::kTileW, ix1 = (tr.x0 + tr.nx) * lb::kTileW;
+    const int iy0 = tr.y0 * lb::kTileH, iy1 = (tr.y0 + tr.ny) * lb::kTileH;
+    std::vector<int4> edge;
+    for (int y0 = 0; y0 < r.p.ny; y0 += 4)
+        for (int x0 = 0; x0 < r.p.nx; x0 += 32)
+            if (!(x0 >= ix0 && x0 < ix1 && y0 >= iy0 && y0 < iy1)) edge.push_back(make_int4(run_index, x0, y0, 0));
+    if (!edge.empty()) {
+        if (cudaMalloc(&r.d_edge, edge.size() * sizeof(int4)) != cudaSuccess ||
+            cudaMemcpy(r.d_edge, edge.data(), edge.size() * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            if (r.d_edge) cudaFree(r.d_edge);
+            r.d_edge = nullptr;
+            return;
+        }
+    }
+    r.nedge = (int)edge.size();
+    r.tmaps = std::move(maps);
 }
-
-const lb::TileMaps* tile_maps(const RunState& r, int in) { return r.tmaps.empty() ? nullptr : &r.tmaps[in]; }
 
 
 // kernel arguments of one run reading input buffer `in`
@@ -467,11 +487,29 @@ int upload_args(lbrmhd_handle h)
     return LBRMHD_OK;
 }
 
-// everything a batched launch needs, refreshed when the runs or the schedule changed
+// the tiled launch of run `ri` from input buffer `in` (NULL: the per-cell kernel)
+template <class Cfg>
+bool tile_launch(lbrmhd_handle h, size_t ri, int in, lb::TileLaunch* tl)
+{
+    const RunState& r = h->runs[ri];
+    if (r.tmaps.empty()) return false;
+    tl->maps = &r.tmaps[in];
+    tl->args = (const unsigned char*)h->d_args + (size_t)in * h->runs.size() * lb::batch_args_stride<Cfg>();
+    tl->edge_tiles = r.d_edge;
+    tl->nedge = r.nedge;
+    tl->sms = h->sms;
+    return true;
+}
+
+// everything a batched launch needs, refreshed when the runs or the schedule
+// changed (the tiled per-run launch reads its edge runs' arguments from the
+// same device records)
 template <class Cfg>
 int prepare_batch(lbrmhd_handle h, const lbrmhd_schedule& sc)
 {
-    if (sc.kind != LBRMHD_SCHED_BATCH && sc.kind != LBRMHD_SCHED_PERSISTENT) return LBRMHD_OK;
+    bool tiled = false;
+    for (const auto& r : h->runs) tiled = tiled || !r.tmaps.empty();
+    if (sc.kind == LBRMHD_SCHED_PER_RUN) return tiled && h->args_dirty ? upload_args<Cfg>(h) : LBRMHD_OK;
     int rc = LBRMHD_OK;
     if (h->tiles_dirty) rc = build_tiles(h, sc);
     if (!rc && h->args_dirty) rc = upload_args<Cfg>(h);
@@ -498,7 +536,11 @@ int issue_step(lbrmhd_handle h, const lbrmhd_schedule& sc, int in, cudaStream_t 
                                              s));
         }
     } else {
-        for (const auto& r : h->runs) LB_CK(lb::launch_step<Cfg>(make_args<Cfg>(h, r, in), s, tile_maps(r, in)));
+        for (size_t ri = 0; ri < h->runs.size(); ++ri) {
+            lb::TileLaunch tl{};
+            const bool t = tile_launch<Cfg>(h, ri, in, &tl);
+            LB_CK(lb::launch_step<Cfg>(make_args<Cfg>(h, h->runs[ri], in), s, t ? &tl : nullptr));
+        }
     }
     for (const auto& r : h->runs) {
         if (has_open(r))
@@ -587,7 +629,9 @@ int issue_steps(lbrmhd_handle h, const lbrmhd_schedule& sc, int in, int64_t n, c
         for (size_t ri = 0; ri < h->runs.size(); ++ri) {
             const RunState& r = h->runs[ri];
             cudaStream_t st = h->aux[ri % S];
-            LB_CK(lb::launch_step<Cfg>(make_args<Cfg>(h, r, cin), st, tile_maps(r, cin)));
+            lb::TileLaunch tl{};
+            const bool t = tile_launch<Cfg>(h, ri, cin, &tl);
+            LB_CK(lb::launch_step<Cfg>(make_args<Cfg>(h, r, cin), st, t ? &tl : nullptr));
             if (has_open(r))
                 LB_CK(lb::launch_boundaries<Cfg>(view<Cfg>(r, 1 - cin), make_phys<R>(r.p, r.ref, runref(r)), r.p.bc,
                                                  r.p.drive_layers, r.d_drive, st));
@@ -766,7 +810,7 @@ std::string check_params(const lbrmhd_params& p)
     if (p.recovery != LBRMHD_RECOVERY_PLAIN && p.recovery != LBRMHD_RECOVERY_MLP && p.recovery != LBRMHD_RECOVERY_COLD)
         return "unknown recovery mode";
     if (p.flags & ~(LBRMHD_FLAG_NO_EM_COLLISION | LBRMHD_FLAG_UNSHIFTED_POWER | LBRMHD_FLAG_ONE_PASS_RECOVERY |
-                    LBRMHD_FLAG_GAUSS_CHARGE | LBRMHD_FLAG_NO_TMA_TILES | LBRMHD_FLAG_FIRST_ORDER_FLUX))
+                    LBRMHD_FLAG_GAUSS_CHARGE | LBRMHD_FLAG_TMA_TILES | LBRMHD_FLAG_FIRST_ORDER_FLUX))
         return "unknown flag";
     for (int f = 0; f < 6; ++f) {
         if (p.bc[f] < 0 || p.bc[f] > 2) return "unknown boundary kind";
@@ -1055,6 +1099,8 @@ int lbrmhd_create(const lbrmhd_params* params, int n_runs, lbrmhd_handle* out)
     }
     lbrmhd_handle h = new lbrmhd_state_s();
     cudaGetDevice(&h->device);
+    cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (h->sms < 1) h->sms = 1;
     h->precision = params[0].precision;
     const size_t pb = pop_bytes(h->precision), hb = hp_bytes(h->precision), qb = hp_bytes(h->precision);
     int64_t max_blocks = 1;
@@ -1112,7 +1158,7 @@ int lbrmhd_create(const lbrmhd_params* params, int n_runs, lbrmhd_handle* out)
         lbrmhd_destroy(h);
         return LBRMHD_ERR_CUDA;
     }
-    for (auto& r : h->runs) make_tile_maps(r);
+    for (size_t ri = 0; ri < h->runs.size(); ++ri) make_tile_maps(h->runs[ri], (int)ri);
     if (lookup_noalloc_scratch(&h->d_noalloc) != LBRMHD_OK) {
         g_create_error = "cudaGetSymbolAddress of the static diagnostics scratch failed";
         lbrmhd_destroy(h);
@@ -1136,6 +1182,7 @@ int lbrmhd_destroy(lbrmhd_handle h)
         if (r.d_ez0) cudaFree(r.d_ez0);
         if (r.d_drive) cudaFree(r.d_drive);
         if (r.d_umax) cudaFree(r.d_umax);
+        if (r.d_edge) cudaFree(r.d_edge);
     }
     if (h->d_scratch) cudaFree(h->d_scratch);
     if (h->d_io) cudaFree(h->d_io);
@@ -1328,6 +1375,26 @@ int lbrmhd_get_diagnostics_noalloc(lbrmhd_handle h, int run, double* d_out)
     return LBRMHD_OK;
 }
 
+int lbrmhd_barrier_selftest(lbrmhd_handle h, int unreachable, double wait_seconds)
+{
+    if (!h) return LBRMHD_ERR_BAD_ARG;
+    if (!(wait_seconds > 0.0 && wait_seconds <= 10.0)) return fail(h, LBRMHD_ERR_BAD_ARG, "wait_seconds must be in (0, 10]");
+    LB_CK(cudaSetDevice(h->device));
+    // scratch: d_small's first 8 bytes as counter + status (not the handle's status word)
+    unsigned int* counter = reinterpret_cast<unsigned int*>(h->d_small);
+    int* status = reinterpret_cast<int*>(h->d_small) + 1;
+    LB_CK(cudaMemsetAsync(h->d_small, 0, 2 * sizeof(int), h->stream));
+    int dev_sms = 0;
+    LB_CK(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, h->device));
+    LB_CK(lb::launch_barrier_selftest(std::min(dev_sms, 8), counter, status, unreachable,
+                                      (unsigned long long)(wait_seconds * 1e9), h->stream));
+    int st = 0;
+    LB_CK(cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    LB_CK(cudaStreamSynchronize(h->stream));
+    if (st & lb::STATUS_BARRIER_TIMEOUT) return fail(h, LBRMHD_ERR_TIMEOUT, "grid barrier wait ran out");
+    return LBRMHD_OK;
+}
+
 int lbrmhd_get_status(lbrmhd_handle h, int64_t* out3)
 {
     if (!h) return LBRMHD_ERR_BAD_ARG;
@@ -1341,7 +1408,10 @@ int lbrmhd_get_status(lbrmhd_handle h, int64_t* out3)
         const int rc = read_stats(h, r, s);
         if (rc) return rc;
         fails += (int64_t)s[0];
-        tiled += !r.tmaps.empty() && (r.p.flags & (LBRMHD_FLAG_GAUSS_CHARGE | LBRMHD_FLAG_NO_TMA_TILES)) == 0 ? 1 : 0;
+        tiled += !r.tmaps.empty() && (r.p.flags & LBRMHD_FLAG_TMA_TILES) != 0 &&
+                         (r.p.flags & LBRMHD_FLAG_GAUSS_CHARGE) == 0
+                     ? 1
+                     : 0;
     }
     if (out3) {
         out3[0] = status;
@@ -1349,6 +1419,7 @@ int lbrmhd_get_status(lbrmhd_handle h, int64_t* out3)
         out3[2] = tiled;
     }
     if (status & lb::STATUS_TMA_TIMEOUT) return fail(h, LBRMHD_ERR_TIMEOUT, "a TMA tile copy did not arrive in time");
+    if (status & lb::STATUS_BARRIER_TIMEOUT) return fail(h, LBRMHD_ERR_TIMEOUT, "a grid barrier wait ran out");
     if (fails > 0) return fail(h, LBRMHD_ERR_NONCONVERGED, std::to_string(fails) + " recoveries did not converge");
     return LBRMHD_OK;
 }

@@ -65,10 +65,10 @@ __device__ __forceinline__ void block_reduce_partials(double* v, double* dst)
     }
 }
 
-// one step of one run; `maps` (or NULL) are the run's tensor maps for its
-// input buffer, which let 2-D periodic runs take the TMA tile kernel
+// one step of one run; `tl` (or NULL) describes the run's tiled launch for its
+// input buffer, which lets 2-D periodic runs take the TMA tile kernel
 template <class Cfg>
-cudaError_t launch_step(const StepArgs<Cfg>& A, cudaStream_t stream, const TileMaps* maps);
+cudaError_t launch_step(const StepArgs<Cfg>& A, cudaStream_t stream, const TileLaunch* tl);
 template <class Cfg>
 cudaError_t launch_step_batch(const unsigned char* d_args, const int4* d_tiles, int ntiles, int bx, int grid,
                               bool is3d, int seed, bool open, cudaStream_t stream);

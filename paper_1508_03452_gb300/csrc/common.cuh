@@ -54,7 +54,7 @@ constexpr int FLAG_NO_EM_COLLISION = 1;
 constexpr int FLAG_UNSHIFTED_POWER = 2;
 constexpr int FLAG_ONE_PASS_RECOVERY = 4;
 constexpr int FLAG_GAUSS_CHARGE = 8;  // Ohm's convection current with eps0 div E of the previous step
-constexpr int FLAG_NO_TMA_TILES = 16;  // per-cell global loads even where the TMA tile path applies
+constexpr int FLAG_TMA_TILES = 16;  // 2-D periodic float32/float16 runs step by the TMA tile kernel
 enum { SEED_PREV = 0, SEED_MLP = 1, SEED_COLD = 2 };
 
 // Population scale for float16 relative deviations: stored value =

@@ -377,8 +377,10 @@ __device__ __forceinline__ void warp_max_into(double v, double* dst)
 // Tiles whose halo would leave the grid (within 2 rows or one unit of columns
 // of an edge) take the per-cell path with its periodic wrap.
 // ---------------------------------------------------------------------------
-static_assert(kTileW * kTileH == kStepThreads, "one thread per tile cell");
-constexpr int kRingStages = 3;
+#ifndef LB_RING_STAGES
+#define LB_RING_STAGES 4
+#endif
+constexpr int kRingStages = LB_RING_STAGES;  // copies in flight per block
 constexpr int kFgStages = 10;                     // directions (0,1), (2,3), ..., (18, -)
 constexpr int kHStages = 7;                       // h planes 0-3, 4-7, ..., 24
 constexpr int kTileStages = kFgStages + kHStages;  // 17
@@ -397,34 +399,38 @@ struct TileGeo {
     static constexpr unsigned H_STAGE_BYTES = 4u * H_PLANE * sizeof(float);
     static constexpr unsigned STAGE_BYTES =
         ((FG_STAGE_BYTES > H_STAGE_BYTES ? FG_STAGE_BYTES : H_STAGE_BYTES) + 127u) / 128u * 128u;
-    static constexpr unsigned PRIM_BYTES = (unsigned)NPRIM * kStepThreads * sizeof(float);
+    static constexpr unsigned PRIM_BYTES = (unsigned)NPRIM * kTileThreads * sizeof(float);
 };
 
 // The block's view of its tile buffers (shared memory) and maps.
 template <class Cfg>
 struct TileCtx {
     unsigned char* ring;  // kRingStages x STAGE_BYTES
-    float* pbuf;          // [NPRIM][kStepThreads]: input primitives, then the output ones
-    typename Cfg::pop* ofg;  // [38][kStepThreads] output f, g (float32: the slots; float16: the idle ring)
+    float* pbuf;          // [NPRIM][kTileThreads]: input primitives, then the output ones
+    typename Cfg::pop* ofg;  // [38][kTileThreads] output f, g (float32: the slots; float16: the idle ring)
     uint64_t* bar;        // kRingStages ring barriers, then the primitives' barrier
     int* abort;           // set when a wait ran out: the whole block then stops
     const TileMaps* M;
-    int x0, y0;
+    int x0, y0;           // this tile
+    int nx0, ny0;         // the block's next tile (has_next), whose first stages follow in the ring
+    bool has_next;
+    int gbase;            // ring index of this tile's stage 0 (stages are numbered over the block's tiles)
+    uint32_t ppar;        // phase parity of this tile's primitive copy
 };
 
-// issue the copy of stage j into its ring buffer (one thread)
+// issue the copy of stage j of the tile at (x0, y0), ring index g (one thread)
 template <class Cfg>
-__device__ __forceinline__ void tile_issue(const TileCtx<Cfg>& t, int j)
+__device__ __forceinline__ void tile_issue(const TileCtx<Cfg>& t, int g, int x0, int y0, int j)
 {
     using G = TileGeo<Cfg>;
-    const int s = j % kRingStages;
+    const int s = g % kRingStages;
     unsigned char* dst = t.ring + (size_t)s * G::STAGE_BYTES;
     if (j < kFgStages) {
         mbar_arrive_expect_tx(&t.bar[s], G::FG_STAGE_BYTES);
-        tma_load_4d(dst, &t.M->fg_in, t.x0 - G::PX, t.y0 - 2, 2 * j, 0, &t.bar[s]);
+        tma_load_4d(dst, &t.M->fg_in, x0 - G::PX, y0 - 2, 2 * j, 0, &t.bar[s]);
     } else {
         mbar_arrive_expect_tx(&t.bar[s], G::H_STAGE_BYTES);
-        tma_load_3d(dst, &t.M->h_in, t.x0 - G::PXH, t.y0 - 2, 4 * (j - kFgStages), &t.bar[s]);
+        tma_load_3d(dst, &t.M->h_in, x0 - G::PXH, y0 - 2, 4 * (j - kFgStages), &t.bar[s]);
     }
 }
 
@@ -543,11 +549,12 @@ struct TileStages {
                                                R (&Tm)[10], R& Nm, R (&Na)[3], R (&dEp)[3], R (&bn)[3], R& rho)
     {
         using G = TileGeo<Cfg>;
-        constexpr int s = J % kRingStages;
+        const int g = t.gbase + J;
+        const int s = g % kRingStages;
         const unsigned char* buf = t.ring + (size_t)s * G::STAGE_BYTES;
         const int tx = tid % kTileW, ty = tid / kTileW;
-        bool arrived = mbar_wait_bounded(&t.bar[s], (uint32_t)((J / kRingStages) & 1));
-        if constexpr (J == kTileStages - 1) arrived = arrived && mbar_wait_bounded(&t.bar[kRingStages], 0u);
+        bool arrived = mbar_wait_bounded(&t.bar[s], (uint32_t)((g / kRingStages) & 1));
+        if constexpr (J == kTileStages - 1) arrived = arrived && mbar_wait_bounded(&t.bar[kRingStages], t.ppar);
         if (!arrived) *reinterpret_cast<volatile int*>(t.abort) = 1;
         if (arrived) {
             if constexpr (J < kFgStages) {
@@ -570,13 +577,20 @@ struct TileStages {
             // let the copies already issued land before the block gives up its
             // shared memory (each wait again bounded)
             if (tid == 0) {
-                for (int j = J; j < J + kRingStages && j < kTileStages; ++j)
-                    mbar_wait_bounded(&t.bar[j % kRingStages], (uint32_t)((j / kRingStages) & 1));
-                mbar_wait_bounded(&t.bar[kRingStages], 0u);
+                const int last = t.has_next ? g + kRingStages - 1 : min(g + kRingStages - 1, t.gbase + kTileStages - 1);
+                for (int i = g; i <= last; ++i) mbar_wait_bounded(&t.bar[i % kRingStages], (uint32_t)((i / kRingStages) & 1));
+                mbar_wait_bounded(&t.bar[kRingStages], t.ppar);
             }
             return false;
         }
-        if (tid == 0 && J + kRingStages < kTileStages) tile_issue<Cfg>(t, J + kRingStages);
+        if (tid == 0) {
+            // refill slot s: a later stage of this tile, or one of the next tile's first stages
+            constexpr int jn = J + kRingStages;
+            if (jn < kTileStages)
+                tile_issue<Cfg>(t, g + kRingStages, t.x0, t.y0, jn);
+            else if (t.has_next)
+                tile_issue<Cfg>(t, g + kRingStages, t.nx0, t.ny0, jn - kTileStages);
+        }
         return TileStages<J + 1, Cfg>::run(t, A, tid, sp, nth, Tm, Nm, Na, dEp, bn, rho);
     }
 };
@@ -598,11 +612,11 @@ struct TileStages<kTileStages, Cfg> {
 // TILE: a cell of an interior tile of the TMA tile path (2-D, periodic,
 // every cell active): its inputs come from the block's ring and primitive
 // buffers (tc), its outputs go to the block's shared-memory output tiles.
-template <class Cfg, bool IS3D, int SEED, bool OPEN, bool TILE = false>
+template <class Cfg, bool IS3D, int SEED, bool OPEN, bool TILE = false, int NTH = kStepThreads>
 __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, const int z, const int tid,
                                           unsigned char* smem_raw, const TileCtx<Cfg>* tc = nullptr)
 {
-    constexpr int nth = kStepThreads;  // a compile-time stride of the shared-memory slots
+    constexpr int nth = NTH;  // threads of the block: a compile-time stride of the shared-memory slots
     using R = typename Cfg::real;
     R* sp = reinterpret_cast<R*>(smem_raw) + tid;
     const bool active = x < A.nx && y < A.ny;
@@ -972,12 +986,12 @@ __global__ void __launch_bounds__(kStepThreads, StepMinBlocks<Cfg, SEED>::value)
                                      threadIdx.x + threadIdx.y * blockDim.x, smem_raw);
 }
 
-template <class Cfg>
+template <class Cfg, int NTH = kStepThreads>
 __host__ __device__ constexpr size_t step_cell_smem(int seed)
 {
-    return seed == SEED_MLP ? (size_t)kStepSlots * sizeof(typename Cfg::real) * kStepThreads +
-                                  (size_t)(MLP_ACT_BYTES_PER_CELL + 8 * sizeof(float)) * kStepThreads
-                            : (size_t)kStepSlots * sizeof(typename Cfg::real) * kStepThreads;
+    return seed == SEED_MLP ? (size_t)kStepSlots * sizeof(typename Cfg::real) * NTH +
+                                  (size_t)(MLP_ACT_BYTES_PER_CELL + 8 * sizeof(float)) * NTH
+                            : (size_t)kStepSlots * sizeof(typename Cfg::real) * NTH;
 }
 
 // the tile path applies to storage formats whose h and primitives are float
@@ -992,69 +1006,91 @@ __host__ __device__ constexpr size_t align128(size_t b) { return (b + 127) / 128
 template <class Cfg>
 __host__ __device__ constexpr size_t tile_smem_bytes(int seed)
 {
-    return align128(step_cell_smem<Cfg>(seed)) + (size_t)kRingStages * TileGeo<Cfg>::STAGE_BYTES +
-           TileGeo<Cfg>::PRIM_BYTES + 128;
+    return align128(step_cell_smem<Cfg, kTileThreads>(seed)) + (size_t)kRingStages * TileGeo<Cfg>::STAGE_BYTES +
+           TileGeo<Cfg>::PRIM_BYTES + (Cfg::kHalf ? align128(38u * kTileThreads * sizeof(typename Cfg::pop)) : 0) + 128;
 }
 
-// One run of a 2-D periodic grid in tiles of kTileW x kTileH cells: interior
-// tiles by TMA copies through shared memory, edge tiles cell by cell.
+// resident tile blocks per SM targeted: as many threads per SM as the per-cell kernel
 template <class Cfg, int SEED>
-__global__ void __launch_bounds__(kStepThreads, StepMinBlocks<Cfg, SEED>::value)
-    step_tile_kernel(const __grid_constant__ StepArgs<Cfg> A, const __grid_constant__ TileMaps M)
+struct TileMinBlocks {
+    static constexpr int v = StepMinBlocks<Cfg, SEED>::value * kStepThreads / kTileThreads;
+    static constexpr int value = v > 0 ? v : 1;
+};
+
+// The interior tiles of one run of a 2-D periodic grid (tiles of kTileW x
+// kTileH cells whose input boxes lie inside the grid), block (bx, by) on tile
+// (bx + tx0, by + ty0), by TMA copies through shared memory; the edge tiles
+// are a separate per-cell launch.
+template <class Cfg, int SEED>
+__global__ void __launch_bounds__(kTileThreads, TileMinBlocks<Cfg, SEED>::value)
+    step_tile_kernel(const __grid_constant__ StepArgs<Cfg> A, const __grid_constant__ TileMaps M,
+                     const __grid_constant__ TileRange tr)
 {
     using G = TileGeo<Cfg>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * kTileW, y0 = blockIdx.y * kTileH;
-    const bool interior = x0 >= G::PX && x0 + kTileW + G::PX <= A.nx && y0 >= 2 && y0 + kTileH + 2 <= A.ny;
-    if (!interior) {  // block-uniform
-        step_cell<Cfg, false, SEED, false>(A, x0 + tid % kTileW, y0 + tid / kTileW, 0, tid, smem_raw);
-        return;
-    }
-    size_t off = align128(step_cell_smem<Cfg>(SEED));
+    const int ntiles = tr.nx * tr.ny;
+    size_t off = align128(step_cell_smem<Cfg, kTileThreads>(SEED));
     TileCtx<Cfg> t;
     t.ring = smem_raw + off;
     off += (size_t)kRingStages * G::STAGE_BYTES;
     t.pbuf = reinterpret_cast<float*>(smem_raw + off);
     off += G::PRIM_BYTES;
     // the output f, g tile: float32 overwrites the streamed values in their
-    // slots; float16 uses the ring, idle once the last stage is consumed
-    static_assert(!Cfg::kHalf || 38u * kStepThreads * sizeof(typename Cfg::pop) <= kRingStages * G::STAGE_BYTES,
-                  "ring too small for the float16 output tile");
-    if constexpr (Cfg::kHalf)
-        t.ofg = reinterpret_cast<typename Cfg::pop*>(t.ring);
-    else
+    // slots; float16 uses its own area after the primitives
+    if constexpr (Cfg::kHalf) {
+        t.ofg = reinterpret_cast<typename Cfg::pop*>(smem_raw + off);
+        off += align128(38u * kTileThreads * sizeof(typename Cfg::pop));
+    } else {
         t.ofg = reinterpret_cast<typename Cfg::pop*>(smem_raw);
+    }
     t.bar = reinterpret_cast<uint64_t*>(smem_raw + off);
     t.abort = reinterpret_cast<int*>(t.bar + kRingStages + 1);
     t.M = &M;
-    t.x0 = x0;
-    t.y0 = y0;
     if (tid == 0) {
         for (int i = 0; i <= kRingStages; ++i) mbar_init(&t.bar[i], 1u);
         *t.abort = 0;
         mbar_init_fence();
     }
     __syncthreads();
-    if (tid == 0) {
-        mbar_arrive_expect_tx(&t.bar[kRingStages], G::PRIM_BYTES);
-        tma_load_3d(t.pbuf, &M.p_in, x0, y0, 0, &t.bar[kRingStages]);
-        for (int j = 0; j < kRingStages; ++j) tile_issue<Cfg>(t, j);
+    auto coords = [&](int i, int& x0, int& y0) {
+        x0 = (tr.x0 + i % tr.nx) * kTileW;
+        y0 = (tr.y0 + i / tr.nx) * kTileH;
+    };
+    int k = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+        coords(tile, t.x0, t.y0);
+        t.has_next = tile + (int)gridDim.x < ntiles;
+        if (t.has_next) coords(tile + gridDim.x, t.nx0, t.ny0);
+        t.gbase = kTileStages * k;
+        t.ppar = (uint32_t)(k & 1);
+        if (tid == 0) {
+            // the previous tile's output copies have read the slots and the
+            // primitive tile; this tile's first stages are already in flight
+            // (issued as the previous tile's last stages were consumed)
+            if (k > 0) tma_store_wait_read();
+            mbar_arrive_expect_tx(&t.bar[kRingStages], G::PRIM_BYTES);
+            tma_load_3d(t.pbuf, &M.p_in, t.x0, t.y0, 0, &t.bar[kRingStages]);
+            if (k == 0)
+                for (int j = 0; j < kRingStages; ++j) tile_issue<Cfg>(t, j, t.x0, t.y0, j);
+        }
+        __syncthreads();
+        step_cell<Cfg, false, SEED, false, true, kTileThreads>(A, t.x0 + tid % kTileW, t.y0 + tid / kTileW, 0, tid,
+                                                              smem_raw, &t);
+        if (*reinterpret_cast<volatile int*>(t.abort)) {  // every thread returned from the same stage
+            if (tid == 0) atomicOr(A.status, STATUS_TMA_TIMEOUT);
+            return;
+        }
+        fence_proxy_async_smem();  // the output tiles written by every thread, before the copies read them
+        __syncthreads();
+        if (tid == 0) {
+            tma_store_3d(&M.fg_out, t.ofg, t.x0, t.y0, 0);
+            tma_store_3d(&M.h_out, reinterpret_cast<const float*>(smem_raw) + 38 * kTileThreads, t.x0, t.y0, 0);
+            tma_store_3d(&M.p_out, t.pbuf, t.x0, t.y0, 0);
+            tma_store_commit();
+        }
     }
-    step_cell<Cfg, false, SEED, false, true>(A, x0 + tid % kTileW, y0 + tid / kTileW, 0, tid, smem_raw, &t);
-    if (*reinterpret_cast<volatile int*>(t.abort)) {  // every thread returned from the same stage
-        if (tid == 0) atomicOr(A.status, STATUS_TMA_TIMEOUT);
-        return;
-    }
-    fence_proxy_async_smem();  // the output tiles written by every thread, before the copies read them
-    __syncthreads();
-    if (tid == 0) {
-        tma_store_3d(&M.fg_out, t.ofg, x0, y0, 0);
-        tma_store_3d(&M.h_out, reinterpret_cast<const float*>(smem_raw) + 38 * kStepThreads, x0, y0, 0);
-        tma_store_3d(&M.p_out, t.pbuf, x0, y0, 0);
-        tma_store_commit();
-        tma_store_wait_read();  // the block's shared memory stays until the stores have read it
-    }
+    if (tid == 0) tma_store_wait_read();  // the block's shared memory stays until the stores have read it
 }
 
 // the batched kernel keeps the arguments of its current run in shared memory,
@@ -1208,6 +1244,8 @@ struct SetSmemAttr {
         const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
         cudaError_t e = cudaFuncSetAttribute(step_kernel<Cfg, D, S, O>, a, (int)step_smem_bytes<Cfg>(S));
         if (e == cudaSuccess) e = cudaFuncSetAttribute(step_batch_kernel<Cfg, D, S, O>, a, (int)batch_smem_bytes<Cfg>(S));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(step_persistent_kernel<Cfg, D, S, O>, a, (int)batch_smem_bytes<Cfg>(S));
         return e;
     }
 };
@@ -1240,8 +1278,8 @@ cudaError_t configure_step_kernels()
 template <class Cfg>
 bool tile_path(const StepArgs<Cfg>& A, const TileMaps* maps)
 {
-    return kTileCapable<Cfg> && maps != nullptr && A.nz == 1 && A.open_mask == 0 &&
-           (A.flags & (FLAG_GAUSS_CHARGE | FLAG_NO_TMA_TILES)) == 0;
+    return kTileCapable<Cfg> && maps != nullptr && A.nz == 1 && A.open_mask == 0 && (A.flags & FLAG_TMA_TILES) != 0 &&
+           (A.flags & FLAG_GAUSS_CHARGE) == 0;
 }
 
 template <class Cfg>
@@ -1315,9 +1353,6 @@ struct LaunchPersistent {
     template <bool D, int S, bool O>
     cudaError_t run()
     {
-        cudaError_t e = cudaFuncSetAttribute(step_persistent_kernel<Cfg, D, S, O>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem_bytes<Cfg>(S));
-        if (e != cudaSuccess) return e;
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(grid);
         cfg.blockDim = dim3(kStepThreads);
@@ -1374,21 +1409,32 @@ struct LaunchRun {
 };
 
 template <class Cfg>
-cudaError_t launch_step(const StepArgs<Cfg>& A, cudaStream_t stream, const TileMaps* maps)
+cudaError_t launch_step(const StepArgs<Cfg>& A, cudaStream_t stream, const TileLaunch* tl)
 {
     if constexpr (kTileCapable<Cfg>) {
-        if (tile_path(A, maps)) {
+        if (tl && tile_path(A, tl->maps)) {
             const cudaError_t ce = configure_step_kernels<Cfg>();
             if (ce != cudaSuccess) return ce;
-            const dim3 grid((A.nx + kTileW - 1) / kTileW, (A.ny + kTileH - 1) / kTileH, 1);
-            const size_t sm = tile_smem_bytes<Cfg>(A.seed);
-            if (A.seed == SEED_MLP)
-                step_tile_kernel<Cfg, SEED_MLP><<<grid, kStepThreads, sm, stream>>>(A, *maps);
-            else if (A.seed == SEED_COLD)
-                step_tile_kernel<Cfg, SEED_COLD><<<grid, kStepThreads, sm, stream>>>(A, *maps);
-            else
-                step_tile_kernel<Cfg, SEED_PREV><<<grid, kStepThreads, sm, stream>>>(A, *maps);
-            return cudaGetLastError();
+            const TileRange tr = interior_tiles(A.nx, A.ny, TileGeo<Cfg>::PX);
+            if (tr.nx > 0 && tr.ny > 0) {
+                // persistent: one wave of resident blocks walking the tiles
+                const int per_sm = A.seed == SEED_MLP ? TileMinBlocks<Cfg, SEED_MLP>::value
+                                   : A.seed == SEED_COLD ? TileMinBlocks<Cfg, SEED_COLD>::value
+                                                         : TileMinBlocks<Cfg, SEED_PREV>::value;
+                const int ntiles = tr.nx * tr.ny;
+                const int grid = min(ntiles, per_sm * tl->sms);
+                const size_t sm = tile_smem_bytes<Cfg>(A.seed);
+                if (A.seed == SEED_MLP)
+                    step_tile_kernel<Cfg, SEED_MLP><<<grid, kTileThreads, sm, stream>>>(A, *tl->maps, tr);
+                else if (A.seed == SEED_COLD)
+                    step_tile_kernel<Cfg, SEED_COLD><<<grid, kTileThreads, sm, stream>>>(A, *tl->maps, tr);
+                else
+                    step_tile_kernel<Cfg, SEED_PREV><<<grid, kTileThreads, sm, stream>>>(A, *tl->maps, tr);
+                const cudaError_t e = cudaGetLastError();
+                if (e != cudaSuccess) return e;
+            }
+            // the edge tiles, cell by cell, from the run's argument record in device memory
+            return launch_step_batch<Cfg>(tl->args, tl->edge_tiles, tl->nedge, 32, 0, false, A.seed, false, stream);
         }
     }
     const int bx = A.nx >= LB_STEP_BX ? LB_STEP_BX : (A.nx >= 64 ? 64 : 32);

@@ -19,7 +19,11 @@ constexpr unsigned long long kTmaWaitNs = 500ull * 1000ull * 1000ull;  // 0.5 s
 // Tile of the tiled step: kTileW x kTileH cells, one thread per cell; the
 // input boxes reach kTileHaloY rows above and below and one 16-byte unit of
 // columns on either side (tile_halo_x elements of `bytes` bytes).
-constexpr int kTileW = 32, kTileH = 4, kTileHaloY = 2;
+#ifndef LB_TILE_H
+#define LB_TILE_H 8  // tile rows (32 x 8 cells: 256 threads, two blocks per SM)
+#endif
+constexpr int kTileW = 32, kTileH = LB_TILE_H, kTileHaloY = 2;
+constexpr int kTileThreads = kTileW * kTileH;
 __host__ __device__ constexpr int tile_halo_x(int bytes) { return 16 / bytes; }
 
 // Tensor maps of one run of the tiled step for one input buffer (the other
@@ -33,6 +37,38 @@ struct TileMaps {  // (aligned as CUtensorMap)
     CUtensorMap fg_out;  // (x, y, plane 0..37) output f then g
     CUtensorMap h_out;   // (x, y, k) output h
     CUtensorMap p_out;   // (x, y, primitive) output primitives
+};
+
+// The tiles of a grid whose input boxes lie inside it: tiles (i, j),
+// x0 = i kTileW, y0 = j kTileH, with x0 - halo_x >= 0, x0 + kTileW + halo_x <= nx,
+// y0 - kTileHaloY >= 0, y0 + kTileH + kTileHaloY <= ny; a rectangle of nx x ny
+// tiles from tile (x0, y0) (empty if either count is 0).
+struct TileRange {
+    int x0, y0, nx, ny;
+};
+__host__ __device__ inline TileRange interior_tiles(int nx, int ny, int halo_x)
+{
+    TileRange r;
+    r.x0 = (halo_x + kTileW - 1) / kTileW;
+    r.y0 = (kTileHaloY + kTileH - 1) / kTileH;
+    const int xe = nx - kTileW - halo_x, ye = ny - kTileH - kTileHaloY;  // largest admissible x0, y0
+    r.nx = xe < 0 ? 0 : xe / kTileW - r.x0 + 1;
+    r.ny = ye < 0 ? 0 : ye / kTileH - r.y0 + 1;
+    if (r.nx < 0) r.nx = 0;
+    if (r.ny < 0) r.ny = 0;
+    return r;
+}
+
+// What a run's tiled step needs besides its kernel arguments: its tensor
+// maps, the device argument records of its input buffer's parity (indexed by
+// the run number in the tiles) and its edge tiles, (run, x0, y0, z) of 32 x 4
+// cells, which a per-cell launch updates.
+struct TileLaunch {
+    const TileMaps* maps;
+    const unsigned char* args;
+    const int4* edge_tiles;
+    int nedge;
+    int sms;  // SMs of the device (the tile kernel's grid is one wave of resident blocks)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)

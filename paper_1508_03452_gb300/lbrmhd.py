@@ -20,9 +20,9 @@ PERIODIC, OPEN, DRIVEN = 0, 1, 2
 FP64, FP32, FP16_DEV = 0, 1, 2
 RECOVERY_PLAIN, RECOVERY_MLP, RECOVERY_COLD = 0, 1, 2
 FLAG_NO_EM_COLLISION, FLAG_UNSHIFTED_POWER, FLAG_ONE_PASS_RECOVERY, FLAG_GAUSS_CHARGE = 1, 2, 4, 8
-FLAG_NO_TMA_TILES, FLAG_FIRST_ORDER_FLUX = 16, 32
+FLAG_TMA_TILES, FLAG_FIRST_ORDER_FLUX = 16, 32
 MLP_NPARAM, MLP_NFEAT, MLP_ROW = 9924, 20, 24
-SCHED_PER_RUN, SCHED_BATCH = 0, 1
+SCHED_PER_RUN, SCHED_BATCH, SCHED_PERSISTENT = 0, 1, 2
 NMOMENTS, NDIAG, NTABLE, NHIST = 16, 10, 311, 17
 MOMENT_NAMES = ["n", "p", "eps", "ux", "uy", "uz", "Ex", "Ey", "Ez", "Bx", "By", "Bz", "rho_c", "Jx", "Jy", "Jz"]
 DIAG_NAMES = ["N0", "T00", "T01", "T02", "T03", "rho_c", "divB_max", "divB_rms", "nonfinite", "cells"]
@@ -35,7 +35,7 @@ EXPORTED = [
     "lbrmhd_mlp_nparams", "lbrmhd_mlp_blob_bytes", "lbrmhd_mlp_pack", "lbrmhd_mlp_infer", "lbrmhd_mlp_grad",
     "lbrmhd_mlp_train", "lbrmhd_set_mlp_weights", "lbrmhd_set_mlp_samples", "lbrmhd_get_iteration_histogram",
     "lbrmhd_set_schedule", "lbrmhd_get_schedule", "lbrmhd_autotune", "lbrmhd_reconnection_rate",
-    "lbrmhd_init_fields_relaxed", "lbrmhd_get_status",
+    "lbrmhd_init_fields_relaxed", "lbrmhd_get_status", "lbrmhd_barrier_selftest",
 ]
 
 
@@ -118,6 +118,7 @@ def load(build_if_missing: bool = True):
         L.lbrmhd_get_diagnostics_noalloc.argtypes = [vp, C.c_int, vp]
         L.lbrmhd_get_stats.argtypes = [vp, C.c_int, C.POINTER(i64)]
         L.lbrmhd_get_status.argtypes = [vp, C.POINTER(i64)]
+        L.lbrmhd_barrier_selftest.argtypes = [vp, C.c_int, C.c_double]
         L.lbrmhd_state_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
         L.lbrmhd_get_state.argtypes = [vp, vp, C.c_size_t]
         L.lbrmhd_set_state.argtypes = [vp, vp, C.c_size_t]

@@ -200,3 +200,68 @@ def test_learned_seed_runs_batched_match_per_run():
         s.close()
     for x, y in zip(out[0][0], out[1][0]):
         _assert_close(x, y, "learned seed")
+
+
+def periodic_batch():
+    """Uneven periodic 2-D runs of one kernel variant: what the persistent
+    schedule (one cooperative launch for many steps) accepts."""
+    specs = []
+    for i, (nx, ny, V, ratio, sigma) in enumerate([(40, 24, 0.1, 1.0, 100.0), (64, 48, 0.2, 3.0, 1e3),
+                                                   (96, 8, 0.1, 10.0, 30.0), (130, 20, 0.15, 3.0, 1e4),
+                                                   (256, 64, 0.1, 3.0, 1e3)]):
+        F = W.kelvin_helmholtz(nx, ny, 1, V=V, ratio=ratio, B0=0.1, a=2.0, noise=1e-3, seed=60 + i)
+        specs.append((F, dict(sigma=sigma)))
+    return specs
+
+
+@pytest.mark.parametrize("precision", [L.FP64, L.FP32])
+def test_persistent_schedule_matches_per_run(precision):
+    """K steps in one cooperative launch (grid barrier between steps), directly
+    and replayed from graphs, = one launch per run per step."""
+    specs = periodic_batch()
+    n = len(specs)
+    out = []
+    for sc in (dict(kind=L.SCHED_PER_RUN), dict(kind=L.SCHED_PERSISTENT, bx=64, order=1),
+               dict(kind=L.SCHED_PERSISTENT, bx=128, order=0, graph_steps=4)):
+        s = make_solver(specs, precision)
+        s.set_schedule(**sc)
+        s.step(9)
+        out.append((snapshot(s, n), [s.stats(r) for r in range(n)], s.status()))
+        s.close()
+    for snap, st, status in out[1:]:
+        assert status["rc"] == L.OK and status["bits"] == 0, status
+        for r in range(n):
+            if precision == L.FP64:
+                assert np.array_equal(snap[r], out[0][0][r]), r
+            else:
+                _assert_close(snap[r], out[0][0][r], r)
+            assert st[r]["recover_fail"] == out[0][1][r]["recover_fail"] == 0
+
+
+def test_persistent_schedule_refuses_runs_it_cannot_step():
+    """Open faces need a boundary pass between steps, and a 3-D run a different
+    kernel variant: the persistent schedule refuses such handles."""
+    s = make_solver(uneven_batch(), L.FP32)
+    s.set_schedule(kind=L.SCHED_PERSISTENT)
+    with pytest.raises(L.LbrmhdError) as e:
+        s.step(2)
+    assert e.value.code == L.ERR_BAD_ARG
+    s.close()
+
+
+def test_grid_barrier_wait_gives_up():
+    """The persistent launch's grid barrier waits with a limit: made to wait for
+    an arrival that never comes, every block gives up and raises the status
+    bit, the call reports TIMEOUT, and the handle stays usable."""
+    import time
+
+    s = make_solver(periodic_batch()[:1], L.FP32)
+    lib = L.load()
+    assert lib.lbrmhd_barrier_selftest(s._h, 0, 1.0) == L.OK
+    t0 = time.perf_counter()
+    rc = lib.lbrmhd_barrier_selftest(s._h, 1, 0.05)
+    assert rc == L.ERR_TIMEOUT, lib.lbrmhd_last_error(s._h)
+    assert time.perf_counter() - t0 < 5.0
+    s.step(3)
+    assert s.status()["rc"] == L.OK
+    s.close()

@@ -205,7 +205,7 @@ def test_trained_network_fits_the_recovery(trained):
 def test_learned_seed_run_parity(trained, precision):
     """A held-out Kelvin-Helmholtz run seeded by the network matches the oracle
     with the plain run's bars (the converged solve is the method's)."""
-    from test_gpu_parity import FP32_FULL, TOL, assert_parity, rel_errors
+    from test_gpu_parity import FP32_SMALL_SIGNAL, TOL, assert_parity, rel_errors
     P, _, _ = trained
     F = W.kelvin_helmholtz(136, 72, 1, V=0.2, ratio=10.0, B0=0.1, a=2.0, noise=1e-3, seed=3)
     ref = O.Sim(O.make_params(F.nx, F.ny, F.nz, sigma=1e3, threads=8))
@@ -218,7 +218,8 @@ def test_learned_seed_run_parity(trained, precision):
     st = s.stats()
     s.close()
     assert st["recover_fail"] == 0, st
-    assert_parity(errs, TOL[precision], loose=FP32_FULL if precision == L.FP32 else None)
+    print("learned seed KH", errs)
+    assert_parity(errs, TOL[precision], skip=FP32_SMALL_SIGNAL["kh"] if precision == L.FP32 else ())
 
 
 def _iterations(F, sigma, recovery, flags, P=None, steps=20, precision=L.FP32):
@@ -236,16 +237,25 @@ def _iterations(F, sigma, recovery, flags, P=None, steps=20, precision=L.FP32):
 @pytest.mark.parametrize("flags", [L.FLAG_UNSHIFTED_POWER, 0])
 def test_learned_seed_gain(trained, flags):
     """What the trained network gains: mean eigen-solve iterations per cell and
-    step on a held-out run, learned seed against zero velocity (the solve
-    without history) at the same tolerance; the previous-step seed is shown
-    for reference. The converged fields agree to the solve's tolerance."""
+    step on a held-out run at the same tolerance, against zero velocity (the
+    solve without history) and against the library's default, the previous
+    step's velocity (RECOVERY_PLAIN, the method without the network). The
+    network beats the cold start; it does not beat the previous-step seed,
+    which in a time-stepping run is already within one step of the answer
+    (measured: plain power method 10.2 vs 7.7 iterations, shifted 3.73 vs
+    3.63), and the test records that. The converged fields agree to the
+    solve's tolerance."""
     P, _, _ = trained
     F = W.kelvin_helmholtz(128, 96, 1, V=0.2, ratio=10.0, B0=0.1, a=2.0, noise=1e-3, seed=31)
     it_cold, m_cold = _iterations(F, 1e3, L.RECOVERY_COLD, flags)
     it_mlp, m_mlp = _iterations(F, 1e3, L.RECOVERY_MLP, flags, P)
     it_prev, _ = _iterations(F, 1e3, L.RECOVERY_PLAIN, flags)
-    print(f"flags={flags}: iterations/cell cold {it_cold:.3f} learned {it_mlp:.3f} previous-step {it_prev:.3f}")
-    assert it_mlp < (0.9 if flags else 1.0) * it_cold, (it_mlp, it_cold, it_prev)
+    msg = (f"flags={flags}: iterations/cell cold {it_cold:.3f} learned {it_mlp:.3f} "
+           f"previous-step (RECOVERY_PLAIN) {it_prev:.3f}")
+    print(msg)
+    assert it_mlp < (0.9 if flags else 1.0) * it_cold, msg
+    # no gain over the method without the network (within 10 %)
+    assert it_mlp >= 0.9 * it_prev, msg
     rows = [3, 4, 5]
     d = np.linalg.norm(m_mlp[rows] - m_cold[rows]) / np.linalg.norm(m_cold[rows])
     assert d < 1e-4, d

@@ -1,15 +1,28 @@
 """GPU parity: the CUDA library, called through its C ABI, against the FP64
 CPU oracle on the same seeded inputs.
 
-Bars: relative L2 per field group <= 1e-10 for the float64 build after the
-stated step counts. The float32 build meets <= 1e-5 on every group over a
-60-step horizon (u and E reach ~1e-5 after ~100 steps); over the full horizons it meets 1e-5 on n, p, eps and B, while
-the small velocity and electric-field perturbations (1e-4 of the population
-scale) drift by up to 1e-4 (a systematic float32 effect of ~4e-8 per step),
-which is the bar used for u and E there. The float16-deviation build has no
-bar (its error is reported by the benchmark) beyond a sanity bound.
-Integer-like checks (the EM permutation) are bit-exact.
+Bars: relative L2 per field group <= 1e-10 for the float64 build and <= 1e-5
+for the float32 build after the stated step counts. Float32 meets 1e-5 on every
+group of the Alfven wave (config 1, 500 steps) and on n, p, eps and B
+everywhere. Two small-signal groups miss it, and are kept as strict expected
+failures with their measured errors rather than a looser bar:
+  * the reduced current sheet (config 2, 2000 steps): u 5.8e-5, E 1.5e-5. The
+    flow there is ~2e-4 c, driven by the sheets' magnetic pressure, which the
+    fluid populations carry as deviations of ~1e-2 of their scale; float32
+    arithmetic on them adds ~3e-8 relative error to u per step (linear
+    growth: 2.3e-6 at 60 steps, 1.05e-5 at 500, 4.3e-5 at 1000). Measured:
+    neither storing the populations in float64 (the arithmetic is float32),
+    nor a float64-level recovery stopping floor, nor a 10x tighter recovery
+    tolerance, nor the Gauss-law charge changes it (all within 10 %).
+  * the Kelvin-Helmholtz layers (config 3 form, 40 steps): E 4.2e-5, which is
+    E_z = u_y B_x of the 1e-3 noise velocity u_y, resolved by float32 to
+    ~1e-4 of itself (u as a group, dominated by the 0.2c shear, is 3.4e-6; a
+    10x tighter recovery tolerance leaves E at 3.9e-5).
+The float16-deviation build has no bar (its error is reported by the
+benchmark) beyond a sanity bound. Integer-like checks (the EM permutation)
+are bit-exact.
 """
+import functools
 import numpy as np
 import pytest
 
@@ -60,15 +73,17 @@ def assert_parity(errs, tol, skip=(), loose=None):
     assert not bad, (bad, errs)
 
 
-FP32_FULL = {"u": 1e-4, "E": 1e-4}  # float32 bar at the full horizons (see module docstring)
+# float32 small-signal groups below 1e-5 only over shorter horizons (module docstring)
+FP32_SMALL_SIGNAL = {"sheet": ("u", "E"), "kh": ("E",)}
 
 
 @pytest.mark.parametrize("precision", [L.FP64, L.FP32])
 def test_alfven_config1(precision):
-    """Config 1 in full: 64 x 64 periodic Alfven wave, sigma = 1e6, 500 steps."""
+    """Config 1 in full: 64 x 64 periodic Alfven wave, sigma = 1e6, 500 steps,
+    every group within the bar (float32: u 3.9e-6, E 3.9e-6)."""
     F = W.alfven_wave(64, 64, 1)
     errs, _ = run_pair(F, 500, precision, sigma=1e6)
-    assert_parity(errs, TOL[precision], loose=FP32_FULL if precision == L.FP32 else None)
+    assert_parity(errs, TOL[precision])
 
 
 @pytest.mark.parametrize("case", ["alfven", "sheet"])
@@ -80,24 +95,43 @@ def test_fp32_all_groups_short_horizon(case):
     assert_parity(errs, 1e-5)
 
 
+@functools.lru_cache(maxsize=None)
+def _case_errors(case, precision):
+    if case == "sheet":
+        F = W.current_sheet(160, 12, 1, delta=8.0)
+        errs, _ = run_pair(F, 2000, precision, sigma=100.0)
+    else:
+        F = W.kelvin_helmholtz(136, 72, 1, V=0.2, ratio=10.0, B0=0.1, a=2.0, noise=1e-3, seed=3)
+        errs, _ = run_pair(F, 40, precision, sigma=1e3)
+    return errs
+
+
 @pytest.mark.parametrize("precision", [L.FP64, L.FP32])
 def test_current_sheet_reduced(precision):
-    """Config 2 on a reduced, ragged grid (160 x 12, several 128-wide tiles and
-    a tail), sigma = 100, 2000 steps."""
-    F = W.current_sheet(160, 12, 1, delta=8.0)
-    errs, _ = run_pair(F, 2000, precision, sigma=100.0)
-    assert_parity(errs, TOL[precision], loose=FP32_FULL if precision == L.FP32 else None)
+    """Config 2 on a reduced, ragged grid (160 x 12), sigma = 100, 2000 steps;
+    float32 u and E: test_fp32_small_signal_groups."""
+    skip = FP32_SMALL_SIGNAL["sheet"] if precision == L.FP32 else ()
+    assert_parity(_case_errors("sheet", precision), TOL[precision], skip=skip)
 
 
 @pytest.mark.parametrize("precision", [L.FP64, L.FP32])
 def test_kelvin_helmholtz_short_horizon(precision):
     """Config 3 form (shear +-V, density ratio 10, sigma = 1e3, seeded noise) on
-    a 136 x 72 grid for 40 steps: flowing magnetised plasma is linearly unstable
-    in the scheme (growth of rho_c through the convection current), so parity
-    is checked over a short horizon."""
-    F = W.kelvin_helmholtz(136, 72, 1, V=0.2, ratio=10.0, B0=0.1, a=2.0, noise=1e-3, seed=3)
-    errs, _ = run_pair(F, 40, precision, sigma=1e3)
-    assert_parity(errs, TOL[precision], loose=FP32_FULL if precision == L.FP32 else None)
+    a 136 x 72 grid (interior and edge tiles of the tile kernel) for 40 steps:
+    flowing magnetised plasma is linearly unstable in the scheme (growth of
+    rho_c through the convection current), so parity is checked over a short
+    horizon; float32 E: test_fp32_small_signal_groups."""
+    skip = FP32_SMALL_SIGNAL["kh"] if precision == L.FP32 else ()
+    assert_parity(_case_errors("kh", precision), TOL[precision], skip=skip)
+
+
+@pytest.mark.xfail(strict=True, reason="float32 floor of small-signal fields (module docstring): sheet u 5.8e-5, "
+                                       "E 1.5e-5 at 2000 steps; KH E 4.2e-5 at 40 steps")
+@pytest.mark.parametrize("case", ["sheet", "kh"])
+def test_fp32_small_signal_groups(case):
+    errs = _case_errors(case, L.FP32)
+    print(case, {k: errs[k] for k in FP32_SMALL_SIGNAL[case]})
+    assert all(errs[k] <= 1e-5 for k in FP32_SMALL_SIGNAL[case]), errs
 
 
 def test_three_dimensional_periodic_fp64():
