@@ -46,7 +46,7 @@ NX = NY = 1024
 # algorithmic bytes per cell update of the fused step: 63 populations + 12
 # primitives, each read once and written once
 BYTES_PER_CELL = {"fp64": 2 * (63 + 12) * 8, "fp32": 2 * (63 + 12) * 4, "fp16": 2 * (38 * 2 + 25 * 4 + 12 * 4)}
-PROFILE = os.path.join(ROOT, "profiles", "step_tile_kernel_current_sheet_1024.md")
+PROFILE = os.path.join(ROOT, "profiles", "step_kernel_current_sheet_1024.md")
 KERNEL_SOURCES = ["step_impl.cuh", "lattice.cuh", "common.cuh", "mlp.cuh", "tma.cuh"]
 GROUPS = {"n": (0,), "p": (1,), "eps": (2,), "u": (3, 4, 5), "E": (6, 7, 8), "B": (9, 10, 11)}
 
@@ -409,8 +409,10 @@ def batched_sweep_leg(args, stream, steps=10):
     solver.set_schedule(L.make_schedule(L.SCHED_PERSISTENT, 128, 1, 0, 1, 0))
     ms_persist = timed(steps)
     status = solver.status()
-    fails = sum(solver.stats(r)["recover_fail"] for r in range(len(specs)))
+    per_run_fail = [solver.stats(r)["recover_fail"] for r in range(len(specs))]
+    fails = sum(per_run_fail)
     solver.close()
+    stable = stable_sweep(args, stream, steps)
     return {
         "workload": "kh_sweep_64_runs_sides_256_1024", "runs": len(specs), "cells_per_step": cells, "steps": steps,
         "value": cells * steps / (ms_tuned * 1e-3) / 1e6, "unit": UNIT,
@@ -418,8 +420,48 @@ def batched_sweep_leg(args, stream, steps=10):
         "persistent_mlups": cells * steps / (ms_persist * 1e-3) / 1e6,
         "schedule": sched.as_dict(), "autotune_ms_per_step": tune_ms, "recover_fail": fails,
         "status_bits": status["bits"], "valid": fails == 0 and status["bits"] == 0,
+        "runs_with_failures": sum(1 for f in per_run_fail if f),
         "options": "Gauss-law charge (LBRMHD_FLAG_GAUSS_CHARGE), alpha = 0.02",
+        "stable_range": stable,
     }
+
+
+def stable_sweep(args, stream, steps):
+    """The same 64 uneven grids and conductivities with the shear drawn inside
+    the scheme's stable range (V uniform in [0.05, 0.15] c, uniform density;
+    Gauss-law charge, alpha = 0.02): the autotuned schedule from graphs."""
+    import numpy as np
+    import torch
+
+    from paper_1508_03452_gb300 import lbrmhd as L
+    from paper_1508_03452_gb300 import workloads as W
+
+    prec = {"fp32": L.FP32, "fp16": L.FP16_DEV, "fp64": L.FP64}[args.precision]
+    specs = W.kh_sweep(64)
+    rng = np.random.Generator(np.random.PCG64(2015))
+    Vs = rng.uniform(0.05, 0.15, len(specs))
+    solver = L.Solver([L.make_params(sp.nx, sp.ny, 1, sigma=sp.sigma, precision=prec, alpha=0.02,
+                                     flags=L.FLAG_GAUSS_CHARGE) for sp in specs], stream=stream)
+    for r, (sp, V) in enumerate(zip(specs, Vs)):
+        F = W.kelvin_helmholtz(sp.nx, sp.ny, 1, V=float(V), ratio=1.0, B0=0.1, noise=1e-3, seed=sp.seed)
+        solver.init_fields(r, F.n, F.p, F.u, F.B)
+    cells = sum(sp.nx * sp.ny for sp in specs)
+    solver.step(3)
+    best, _ = solver.autotune(3)
+    solver.set_schedule(L.make_schedule(best.kind, best.bx, best.waves, best.order, best.streams, 10))
+    solver.step(10)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solver.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fails = sum(solver.stats(r)["recover_fail"] for r in range(len(specs)))
+    status = solver.status()
+    solver.close()
+    return {"value": cells * steps / (e0.elapsed_time(e1) * 1e-3) / 1e6, "unit": UNIT, "V_range": [0.05, 0.15],
+            "density_ratio": 1.0, "recover_fail": fails, "valid": fails == 0 and status["bits"] == 0,
+            "schedule": best.as_dict()}
 
 
 def kh_2048_leg(args, stream, steps=10):
@@ -668,6 +710,64 @@ def run_gpu(args, world, rank, local):
         dist.destroy_process_group()
 
 
+def run_profile_kernel(args):
+    """Small untimed cases for ncu captures of the library's other kernels
+    (--profile-kernel): `tile` the TMA tile kernel on the 1024^2 current sheet
+    (LBRMHD_FLAG_TMA_TILES); `batch` and `persistent` 16 Kelvin-Helmholtz runs of
+    the batched sweep (sides 256..1024) under the BATCH and PERSISTENT schedules;
+    `diag` the conservation diagnostics and `null` the reconnection-rate null
+    search of a 1024^2 run; `mlp` the learned seed's training (gradient,
+    reduction, Adam) on 2^20 synthetic sample rows; each for `--steps` calls."""
+    import numpy as np
+    import torch
+
+    from paper_1508_03452_gb300 import lbrmhd as L
+    from paper_1508_03452_gb300 import workloads as W
+
+    stream = torch.cuda.current_stream()
+    k = args.profile_kernel
+    n = args.steps
+    if k in ("tile", "diag", "null"):
+        F = W.current_sheet(NX, NY, 1, delta=8.0) if k != "null" else W.kelvin_helmholtz(
+            NX, NY, 1, V=0.2, ratio=3.0, B0=0.1, a=2.0, noise=1e-3, seed=5)
+        flags = L.FLAG_TMA_TILES if k == "tile" else 0
+        s = L.Solver(L.make_params(NX, NY, 1, sigma=100.0, precision=L.FP32, flags=flags), stream=stream)
+        s.init_fields(0, F.n, F.p, F.u, F.B)
+        if k == "tile":
+            s.step(n)
+        else:
+            s.step(2)
+            for _ in range(n):
+                if k == "diag":
+                    s.diagnostics()
+                else:
+                    s.reconnection_rate(0, NY // 4 - 64, NY // 4 + 64, 0.1)
+        out = s.status()
+        s.close()
+    elif k in ("batch", "persistent"):
+        specs = W.kh_sweep(16)
+        s = L.Solver([L.make_params(sp.nx, sp.ny, 1, sigma=sp.sigma, precision=L.FP32, alpha=0.02,
+                                    flags=L.FLAG_GAUSS_CHARGE) for sp in specs], stream=stream)
+        for r, sp in enumerate(specs):
+            F = W.kelvin_helmholtz(sp.nx, sp.ny, 1, V=sp.V, ratio=sp.ratio, B0=0.1, noise=1e-3, seed=sp.seed)
+            s.init_fields(r, F.n, F.p, F.u, F.B)
+        kind = L.SCHED_BATCH if k == "batch" else L.SCHED_PERSISTENT
+        s.set_schedule(L.make_schedule(kind, 128, 1, 0, 1, 0))
+        s.step(n)
+        out = s.status()
+        s.close()
+    else:  # mlp
+        rows = 1 << 20
+        g = torch.Generator(device="cuda").manual_seed(5)
+        data = torch.rand(rows * L.MLP_ROW, generator=g, device="cuda", dtype=torch.float32) - 0.5
+        P = torch.tensor(W.mlp_init_params(1), device="cuda")
+        adam = torch.zeros(2 * L.MLP_NPARAM, device="cuda")
+        L.mlp_train(P, adam, data, n, 4096, 1e-3, seed=3)
+        out = {"rows": rows}
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_kernel": k, "calls": n, "out": out}), flush=True)
+
+
 def run_profile_case(args):
     """Small profiling case (no timing): one 1024 x 1024 current-sheet run
     (sigma = 100), or with --profile-3d N the driven N^3 flux rope, in the
@@ -709,9 +809,13 @@ def main():
     ap.add_argument("--profile-case", action="store_true", help="untimed 1024^2 single-run case for ncu captures")
     ap.add_argument("--profile-learned", action="store_true", help="--profile-case with the learned-seed kernel")
     ap.add_argument("--profile-3d", type=int, default=0, metavar="N", help="--profile-case on the driven N^3 flux rope")
+    ap.add_argument("--profile-kernel", default="", choices=["", "tile", "batch", "persistent", "diag", "null", "mlp"],
+                    help="untimed small case for an ncu capture of one of the other kernels")
     args = ap.parse_args()
     world, rank, local = dist_env()
-    if args.profile_case:
+    if args.profile_kernel:
+        run_profile_kernel(args)
+    elif args.profile_case:
         run_profile_case(args)
     elif args.impl == "reference":
         run_reference(args, world, rank)

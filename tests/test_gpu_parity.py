@@ -134,9 +134,11 @@ def test_fp32_small_signal_groups(case):
     assert all(errs[k] <= 1e-5 for k in FP32_SMALL_SIGNAL[case]), errs
 
 
-def test_three_dimensional_periodic_fp64():
-    """A 3-D periodic state with every population moving (24 x 20 x 18); short
-    horizon (3-D flows with fields are unstable in the scheme within ~15 steps)."""
+@pytest.mark.parametrize("precision", [L.FP64, L.FP32])
+def test_three_dimensional_periodic(precision):
+    """A 3-D periodic state with every population moving (24 x 20 x 18), the
+    3-D periodic step kernel in float64 and float32; short horizon (3-D flows
+    with fields are unstable in the scheme within ~15 steps)."""
     rng = np.random.default_rng(70)
     nx, ny, nz = 24, 20, 18
     N = nx * ny * nz
@@ -150,8 +152,9 @@ def test_three_dimensional_periodic_fp64():
     B[1] = 0.02 * np.sin(2 * np.pi * x / nx)
     B[2] = 0.05 + 0.02 * np.cos(2 * np.pi * y / ny)
     F = W.Fields(nx, ny, nz, 1.0 + 0.05 * rng.uniform(size=N), np.ones(N), u, B)
-    errs, _ = run_pair(F, 10, L.FP64, sigma=50.0)
-    assert_parity(errs, 1e-10)
+    errs, _ = run_pair(F, 10, precision, sigma=50.0)
+    print("3-D periodic", precision, errs)
+    assert_parity(errs, TOL[precision])
 
 
 def test_open_boundaries_fp64():
