@@ -374,34 +374,44 @@ __global__ void populations_kernel(PopView<Cfg> V, RefPops ref, double* f, doubl
 }
 
 // per-block float64 partial diagnostics: sum N^0, T^{0 nu} (4), rho_c, max |div B|,
-// sum (div B)^2, non-finite count
+// sum (div B)^2, non-finite count. A cell's sums over its populations and the
+// sums over the 32 cells of a warp are taken in the storage's arithmetic type
+// over the deviations (small numbers, rounded relative to themselves); the
+// warp totals get the reference rest state of their cells and are summed
+// over warps and blocks in float64. (float64 arithmetic per cell made this
+// memory-bound pass bound by GB300's float64 rate, 15x slower.)
 template <class Cfg>
 __global__ void diag_kernel(PopView<Cfg> V, Phys<double> k, RefState r, double* partial)
 {
+    using R = typename Cfg::real;
     const int64_t N = (int64_t)V.nx * V.ny * V.nz;
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    double v[NPART] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    R w[NPART] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};  // deviations, |div B|, (div B)^2, bad
     if (c < N) {
-        double bad = 0.0;
-        double N0 = r.n_r, T0[4] = {r.eps_r, 0, 0, 0}, rho = 0.0;
+        bool bad = false;
+        R N0 = R(0), T0[4] = {R(0), R(0), R(0), R(0)}, rho = R(0);
+#pragma unroll
         for (int i = 0; i < 19; ++i) {
-            const double fi = (double)ld_pop<Cfg>(V.f + (int64_t)i * V.stride + c, V.hs.f[i]);
-            const double gi = (double)ld_pop<Cfg>(V.g + (int64_t)i * V.stride + c, V.hs.g[i]);
-            if (!isfinite(fi) || !isfinite(gi)) bad = 1.0;
+            const R fi = (R)ld_pop<Cfg>(V.f + (int64_t)i * V.stride + c, V.hs.f[i]);
+            const R gi = (R)ld_pop<Cfg>(V.g + (int64_t)i * V.stride + c, V.hs.g[i]);
+            bad = bad || !isfinite(fi) || !isfinite(gi);
             N0 += gi;
             T0[0] += fi;
-            for (int a = 0; a < 3; ++a) T0[a + 1] += kQ * c19(i, a) * fi;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                if (c19(i, a)) T0[a + 1] += R(c19(i, a)) * fi;
         }
+#pragma unroll
         for (int i = 0; i < 25; ++i) {
-            const double hi = (double)V.h[(int64_t)i * V.stride + c];
-            if (!isfinite(hi)) bad = 1.0;
+            const R hi = (R)V.h[(int64_t)i * V.stride + c];
+            bad = bad || !isfinite(hi);
             rho += hi;
         }
-        for (int i = 0; i < NPRIM; ++i)
-            if (!isfinite((double)V.prim[(int64_t)i * V.stride + c])) bad = 1.0;
+#pragma unroll
+        for (int i = 0; i < NPRIM; ++i) bad = bad || !isfinite((R)V.prim[(int64_t)i * V.stride + c]);
         const int q[3] = {(int)(c % V.nx), (int)((c / V.nx) % V.ny), (int)(c / ((int64_t)V.nx * V.ny))};
         const int n[3] = {V.nx, V.ny, V.nz};
-        double div = 0.0;
+        R div = R(0);
         for (int a = 0; a < 3; ++a) {
             if (n[a] == 1) continue;
             int qp[3] = {q[0], q[1], q[2]}, qm[3] = {q[0], q[1], q[2]};
@@ -409,17 +419,41 @@ __global__ void diag_kernel(PopView<Cfg> V, Phys<double> k, RefState r, double* 
             qm[a] = wrap_coord(q[a] - 1, n[a], V.periodic[a]);
             const int64_t ip = qp[0] + (int64_t)V.nx * (qp[1] + (int64_t)V.ny * qp[2]);
             const int64_t im = qm[0] + (int64_t)V.nx * (qm[1] + (int64_t)V.ny * qm[2]);
-            div += ((double)V.prim[(P_B + a) * V.stride + ip] - (double)V.prim[(P_B + a) * V.stride + im]) /
-                   (2.0 * k.dx);
+            div += (R)V.prim[(P_B + a) * V.stride + ip] - (R)V.prim[(P_B + a) * V.stride + im];
         }
-        v[0] = N0;
-        for (int a = 0; a < 4; ++a) v[1 + a] = T0[a];
-        v[5] = rho;
-        v[6] = fabs(div);
-        v[7] = div * div;
-        v[8] = bad;
+        div = div / (R(2) * (R)k.dx);
+        w[0] = N0;
+        for (int a = 0; a < 4; ++a) w[1 + a] = T0[a];
+        w[5] = rho;
+        w[6] = fabs(div);
+        w[7] = div * div;
+        w[8] = bad ? R(1) : R(0);
     }
-    block_reduce_partials(v, partial);
+    // the warp's cells in the arithmetic type (index 6 a max, the others sums)
+#pragma unroll
+    for (int j = 0; j < NPART; ++j)
+        for (int o = 16; o > 0; o >>= 1) {
+            const R other = __shfl_down_sync(0xffffffffu, w[j], o);
+            w[j] = (j == 6) ? fmax(w[j], other) : w[j] + other;
+        }
+    __shared__ double sh[kDiagThreads / 32][NPART];
+    const int wid = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (lane == 0) {
+        const int64_t first = c;  // the warp's first cell
+        const double cells = (double)(first >= N ? 0 : (N - first < 32 ? N - first : 32));
+        for (int j = 0; j < NPART; ++j) sh[wid][j] = (double)w[j];
+        sh[wid][0] += cells * r.n_r;  // reference rest state of the warp's cells
+        sh[wid][1] += cells * r.eps_r;
+        for (int a = 0; a < 3; ++a) sh[wid][2 + a] *= kQ;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int j = 0; j < NPART; ++j) {
+            double acc = sh[0][j];
+            for (int ww = 1; ww < (int)(blockDim.x / 32); ++ww) acc = (j == 6) ? fmax(acc, sh[ww][j]) : acc + sh[ww][j];
+            partial[(int64_t)blockIdx.x * NPART + j] = acc;
+        }
+    }
 }
 
 __global__ void diag_final_kernel(const double* partial, int64_t nblocks, int64_t ncells, double* out)

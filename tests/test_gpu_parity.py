@@ -176,12 +176,23 @@ def test_flux_rope_open_and_driven_fp64():
     assert_parity(errs, 1e-10)
 
 
-def test_fp16_deviation_storage_is_close():
-    """float16 relative-deviation storage of f, g: no parity bar, only a sanity
-    bound on the error against the oracle (reported in full by the benchmark)."""
+# float16-deviation storage (f, g as float16 relative deviations, float32
+# arithmetic): its bar follows from the float16 resolution, 2^-11 = 4.9e-4 of
+# each stored deviation. The large fields (n, p, eps, B) carry it at ~1e-5 of
+# their size; u and E are the small signals of the populations (the flow is
+# ~1e-3 of a deviation's scale on the current sheet), resolved to ~1e-2. Not
+# error-matched with float32 (module docstring: 1e-5): the benchmark reports
+# both side by side.
+FP16_BAR = {"n": 1e-4, "p": 1e-4, "eps": 1e-4, "B": 1e-4, "u": 3e-2, "E": 3e-2}
+
+
+def test_fp16_deviation_storage_bar():
+    """The reduced current sheet (160 x 12, sigma = 100) over 400 steps within
+    the float16-deviation bar."""
     F = W.current_sheet(160, 12, 1, delta=8.0)
     errs, _ = run_pair(F, 400, L.FP16_DEV, sigma=100.0)
-    assert errs["B"] < 1e-3 and errs["n"] < 1e-4 and errs["eps"] < 1e-4, errs
+    print("fp16 sheet 400 steps", errs)
+    assert_parity(errs, 0.0, loose=FP16_BAR)
 
 
 @pytest.mark.parametrize("precision", [L.FP64, L.FP32])
