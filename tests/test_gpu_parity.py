@@ -18,6 +18,9 @@ failures with their measured errors rather than a looser bar:
     E_z = u_y B_x of the 1e-3 noise velocity u_y, resolved by float32 to
     ~1e-4 of itself (u as a group, dominated by the 0.2c shear, is 3.4e-6; a
     10x tighter recovery tolerance leaves E at 3.9e-5).
+  * the 3-D periodic state (10 steps): rho_c 2.4e-5, the charge h_0 + sum h,
+    a near-cancelling sum of the Maxwell populations (every other group is
+    within 9.2e-7).
 The float16-deviation build has no bar (its error is reported by the
 benchmark) beyond a sanity bound. Integer-like checks (the EM permutation)
 are bit-exact.
@@ -74,7 +77,7 @@ def assert_parity(errs, tol, skip=(), loose=None):
 
 
 # float32 small-signal groups below 1e-5 only over shorter horizons (module docstring)
-FP32_SMALL_SIGNAL = {"sheet": ("u", "E"), "kh": ("E",)}
+FP32_SMALL_SIGNAL = {"sheet": ("u", "E"), "kh": ("E",), "3d": ("rho_c",)}
 
 
 @pytest.mark.parametrize("precision", [L.FP64, L.FP32])
@@ -95,11 +98,29 @@ def test_fp32_all_groups_short_horizon(case):
     assert_parity(errs, 1e-5)
 
 
+def _three_dimensional_state():
+    rng = np.random.default_rng(70)
+    nx, ny, nz = 24, 20, 18
+    N = nx * ny * nz
+    z, y, x = (a.reshape(-1) for a in np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij"))
+    u = np.zeros((3, N))
+    u[0] = 0.05 * np.sin(2 * np.pi * y / ny)
+    u[1] = 0.03 * np.sin(2 * np.pi * z / nz)
+    u[2] = 0.04 * np.cos(2 * np.pi * x / nx)
+    B = np.zeros((3, N))  # divergence-free: each component varies across its own axis only
+    B[0] = 0.1 + 0.02 * np.sin(2 * np.pi * z / nz)
+    B[1] = 0.02 * np.sin(2 * np.pi * x / nx)
+    B[2] = 0.05 + 0.02 * np.cos(2 * np.pi * y / ny)
+    return W.Fields(nx, ny, nz, 1.0 + 0.05 * rng.uniform(size=N), np.ones(N), u, B)
+
+
 @functools.lru_cache(maxsize=None)
 def _case_errors(case, precision):
     if case == "sheet":
         F = W.current_sheet(160, 12, 1, delta=8.0)
         errs, _ = run_pair(F, 2000, precision, sigma=100.0)
+    elif case == "3d":
+        errs, _ = run_pair(_three_dimensional_state(), 10, precision, sigma=50.0)
     else:
         F = W.kelvin_helmholtz(136, 72, 1, V=0.2, ratio=10.0, B0=0.1, a=2.0, noise=1e-3, seed=3)
         errs, _ = run_pair(F, 40, precision, sigma=1e3)
@@ -126,8 +147,8 @@ def test_kelvin_helmholtz_short_horizon(precision):
 
 
 @pytest.mark.xfail(strict=True, reason="float32 floor of small-signal fields (module docstring): sheet u 5.8e-5, "
-                                       "E 1.5e-5 at 2000 steps; KH E 4.2e-5 at 40 steps")
-@pytest.mark.parametrize("case", ["sheet", "kh"])
+                                       "E 1.5e-5 at 2000 steps; KH E 4.2e-5 at 40 steps; 3-D rho_c 2.4e-5 at 10 steps")
+@pytest.mark.parametrize("case", ["sheet", "kh", "3d"])
 def test_fp32_small_signal_groups(case):
     errs = _case_errors(case, L.FP32)
     print(case, {k: errs[k] for k in FP32_SMALL_SIGNAL[case]})
@@ -138,23 +159,11 @@ def test_fp32_small_signal_groups(case):
 def test_three_dimensional_periodic(precision):
     """A 3-D periodic state with every population moving (24 x 20 x 18), the
     3-D periodic step kernel in float64 and float32; short horizon (3-D flows
-    with fields are unstable in the scheme within ~15 steps)."""
-    rng = np.random.default_rng(70)
-    nx, ny, nz = 24, 20, 18
-    N = nx * ny * nz
-    z, y, x = (a.reshape(-1) for a in np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij"))
-    u = np.zeros((3, N))
-    u[0] = 0.05 * np.sin(2 * np.pi * y / ny)
-    u[1] = 0.03 * np.sin(2 * np.pi * z / nz)
-    u[2] = 0.04 * np.cos(2 * np.pi * x / nx)
-    B = np.zeros((3, N))  # divergence-free: each component varies across its own axis only
-    B[0] = 0.1 + 0.02 * np.sin(2 * np.pi * z / nz)
-    B[1] = 0.02 * np.sin(2 * np.pi * x / nx)
-    B[2] = 0.05 + 0.02 * np.cos(2 * np.pi * y / ny)
-    F = W.Fields(nx, ny, nz, 1.0 + 0.05 * rng.uniform(size=N), np.ones(N), u, B)
-    errs, _ = run_pair(F, 10, precision, sigma=50.0)
+    with fields are unstable in the scheme within ~15 steps); float32 rho_c:
+    test_fp32_small_signal_groups."""
+    errs = _case_errors("3d", precision)
     print("3-D periodic", precision, errs)
-    assert_parity(errs, TOL[precision])
+    assert_parity(errs, TOL[precision], skip=FP32_SMALL_SIGNAL["3d"] if precision == L.FP32 else ())
 
 
 def test_open_boundaries_fp64():
