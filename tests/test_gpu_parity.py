@@ -317,3 +317,30 @@ def test_full_size_sampled_step_fp32():
         nb = np.linalg.norm(b)
         err = np.linalg.norm(a - b) / nb if nb > 0 else np.linalg.norm(a - b)
         assert err <= 1e-5 or np.linalg.norm(a - b) < 1e-9, (name, err)
+
+
+def test_full_size_multi_step_fp32_in_the_benchmark_launch_configuration():
+    """Config 2 at its full size (1024 x 1024) in the launch configuration the
+    benchmark times: the three runs (sigma = 10, 100, 1000) in one handle, one
+    launch per run per step on three streams, replayed from 10-step CUDA
+    graphs; 20 steps, the sigma = 100 run against the oracle over every cell,
+    every group within the float32 bar."""
+    torch = pytest.importorskip("torch")
+    nx = ny = 1024
+    F = W.current_sheet(nx, ny, 1, delta=8.0)
+    s = L.Solver([L.make_params(nx, ny, 1, sigma=sg, precision=L.FP32) for sg in (10.0, 100.0, 1000.0)],
+                 stream=torch.cuda.current_stream())
+    for r in range(3):
+        s.init_fields(r, F.n, F.p, F.u, F.B)
+    s.set_schedule(kind=L.SCHED_PER_RUN, streams=3, graph_steps=10)
+    s.step(20)
+    mg = s.moments(1)
+    st = s.status()
+    s.close()
+    assert st["rc"] == L.OK, st
+    ref = O.Sim(O.make_params(nx, ny, 1, sigma=100.0, threads=16))
+    ref.init(F.n, F.p, F.u, F.B)
+    ref.step(20)
+    errs = rel_errors(mg, ref.moments())
+    print("full size 20 steps", errs)
+    assert_parity(errs, TOL[L.FP32])
