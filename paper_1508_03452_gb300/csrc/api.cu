@@ -19,8 +19,8 @@ thread_local std::string g_create_error;
 struct RunState {
     lbrmhd_params p{};
     int64_t N = 0, stride = 0;
-    void* pops[2] = {nullptr, nullptr};  // 38 planes: f (19) then g (19)
-    void* h[2] = {nullptr, nullptr};     // 25 planes
+    void* pops[2] = {nullptr, nullptr};  // f, g: 9 group planes of 4-vectors, then the rest pairs (fg_elem)
+    void* h[2] = {nullptr, nullptr};     // h: 12 pair planes of 2-vectors, then h_24 (h_elem)
     void* prim[2] = {nullptr, nullptr};  // 12 planes
     int cur = 0;
     bool initialized = false;
@@ -172,8 +172,7 @@ template <class Cfg>
 lb::PopView<Cfg> view(const RunState& r, int buf)
 {
     lb::PopView<Cfg> v{};
-    v.f = (typename Cfg::pop*)r.pops[buf];
-    v.g = v.f + 19 * r.stride;
+    v.fg = (typename Cfg::pop*)r.pops[buf];
     v.h = (typename Cfg::hpop*)r.h[buf];
     v.prim = (typename Cfg::prim*)r.prim[buf];
     v.nx = r.p.nx;
@@ -307,17 +306,17 @@ bool tile_layout_ok(const lbrmhd_params& p, bool open_var)
     return p.nx % px == 0 && p.nx >= lb::kTileW + 2 * px && p.ny >= lb::kTileH + 2 * lb::kTileHaloY;
 }
 
-// encodes one map of `rank` dims over `base` (x, y, then planes of `plane`
-// bytes, then groups of `group` bytes); false if the driver rejects it
-bool encode_map(CUtensorMap* m, CUtensorMapDataType dt, int elem, void* base, int rank, const RunState& r,
-                int planes, int groups, const cuuint32_t* box)
+// encodes one map of `rank` dims over `base`: rows of `vec` x nx elements
+// (vec values per cell), ny rows, then `planes` planes of `vec` x stride
+// elements; false if the driver rejects it
+bool encode_map(CUtensorMap* m, CUtensorMapDataType dt, int elem, void* base, int rank, const RunState& r, int vec,
+                int planes, const cuuint32_t* box)
 {
     const EncodeTiledFn enc = encode_tiled();
     if (!enc) return false;
-    const cuuint64_t dims[4] = {(cuuint64_t)r.p.nx, (cuuint64_t)r.p.ny, (cuuint64_t)planes, (cuuint64_t)groups};
-    const cuuint64_t strides[3] = {(cuuint64_t)r.p.nx * elem, (cuuint64_t)r.stride * elem,
-                                   (cuuint64_t)r.stride * elem * planes};
-    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const cuuint64_t dims[3] = {(cuuint64_t)vec * r.p.nx, (cuuint64_t)r.p.ny, (cuuint64_t)planes};
+    const cuuint64_t strides[2] = {(cuuint64_t)vec * r.p.nx * elem, (cuuint64_t)vec * r.stride * elem};
+    const cuuint32_t estr[3] = {1, 1, 1};
     return enc(m, dt, (cuuint32_t)rank, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -333,22 +332,25 @@ void make_tile_maps(RunState& r, int run_index)
     const CUtensorMapDataType pdt = pb == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     const CUtensorMapDataType fdt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     const cuuint32_t bh = lb::kTileH + 2 * lb::kTileHaloY;
-    const cuuint32_t box_fg[4] = {(cuuint32_t)(lb::kTileW + 2 * px), bh, 2, 2};
-    const cuuint32_t box_h[3] = {(cuuint32_t)(lb::kTileW + 2 * pxh), bh, 4};
+    const cuuint32_t bwf = lb::kTileW + 2 * px, bwh = lb::kTileW + 2 * pxh;
+    const cuuint32_t box_fg[3] = {4 * bwf, bh, 1};
+    const cuuint32_t box_r[2] = {2 * bwf, bh};
+    const cuuint32_t box_h[3] = {2 * bwh, bh, 2};
+    const cuuint32_t box_h24[2] = {bwh, bh};
     const cuuint32_t box_p[3] = {lb::kTileW, lb::kTileH, (cuuint32_t)lb::NPRIM};
-    const cuuint32_t box_fo[3] = {lb::kTileW, lb::kTileH, 38};
-    const cuuint32_t box_ho[3] = {lb::kTileW, lb::kTileH, 25};
     std::vector<lb::TileMaps> maps(2);
     bool ok = true;
     for (int in = 0; in < 2 && ok; ++in) {
         const int out = 1 - in;
         lb::TileMaps& m = maps[in];
-        ok = ok && encode_map(&m.fg_in, pdt, pb, r.pops[in], 4, r, 19, 2, box_fg);
-        ok = ok && encode_map(&m.h_in, fdt, 4, r.h[in], 3, r, 25, 1, box_h);
-        ok = ok && encode_map(&m.p_in, fdt, 4, r.prim[in], 3, r, lb::NPRIM, 1, box_p);
-        ok = ok && encode_map(&m.fg_out, pdt, pb, r.pops[out], 3, r, 38, 1, box_fo);
-        ok = ok && encode_map(&m.h_out, fdt, 4, r.h[out], 3, r, 25, 1, box_ho);
-        ok = ok && encode_map(&m.p_out, fdt, 4, r.prim[out], 3, r, lb::NPRIM, 1, box_p);
+        char* fg = (char*)r.pops[in];
+        char* hh = (char*)r.h[in];
+        ok = ok && encode_map(&m.fg_in, pdt, pb, fg, 3, r, 4, lb::kFGroups, box_fg);
+        ok = ok && encode_map(&m.r_in, pdt, pb, fg + lb::fg_elem(0, 0, 0, r.stride) * pb, 2, r, 2, 1, box_r);
+        ok = ok && encode_map(&m.h_in, fdt, 4, hh, 3, r, 2, 12, box_h);
+        ok = ok && encode_map(&m.h24_in, fdt, 4, hh + lb::h_elem(24, 0, r.stride) * 4, 2, r, 1, 1, box_h24);
+        ok = ok && encode_map(&m.p_in, fdt, 4, r.prim[in], 3, r, 1, lb::NPRIM, box_p);
+        ok = ok && encode_map(&m.p_out, fdt, 4, r.prim[out], 3, r, 1, lb::NPRIM, box_p);
     }
     if (!ok) return;
     // the 32 x 4 tiles outside the rectangle of interior tiles, as (run, x0, y0, 0)
@@ -380,12 +382,10 @@ lb::StepArgs<Cfg> make_args(lbrmhd_handle h, const RunState& r, int in)
     using R = typename Cfg::real;
     lb::StepArgs<Cfg> A{};
     const int out = 1 - in;
-    A.fin = (const typename Cfg::pop*)r.pops[in];
-    A.gin = A.fin + 19 * r.stride;
+    A.fgin = (const typename Cfg::pop*)r.pops[in];
     A.hin = (const typename Cfg::hpop*)r.h[in];
     A.pin = (const typename Cfg::prim*)r.prim[in];
-    A.fout = (typename Cfg::pop*)r.pops[out];
-    A.gout = A.fout + 19 * r.stride;
+    A.fgout = (typename Cfg::pop*)r.pops[out];
     A.hout = (typename Cfg::hpop*)r.h[out];
     A.pout = (typename Cfg::prim*)r.prim[out];
     A.nx = r.p.nx;
@@ -1073,6 +1073,25 @@ int relax_run(lbrmhd_handle h, RunState& r, int max_iters, double tol, int* iter
     return LBRMHD_OK;
 }
 
+// The populations of a run's buffer as contiguous element ranges over its N
+// cells (the padding of each plane left out): fluid, the nine group planes (4
+// values per cell) and the rest pair; Maxwell, the twelve pairs and h_24.
+struct Segment {
+    int64_t first, count;
+};
+std::vector<Segment> state_segments(const RunState& r, bool fluid)
+{
+    std::vector<Segment> s;
+    if (fluid) {
+        for (int G = 0; G < lb::kFGroups; ++G) s.push_back({lb::fg_elem(2 * G + 1, 0, 0, r.stride), 4 * r.N});
+        s.push_back({lb::fg_elem(0, 0, 0, r.stride), 2 * r.N});
+    } else {
+        for (int m = 0; m < 12; ++m) s.push_back({lb::h_elem(2 * m, 0, r.stride), 2 * r.N});
+        s.push_back({lb::h_elem(24, 0, r.stride), r.N});
+    }
+    return s;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1483,12 +1502,16 @@ int lbrmhd_get_state(lbrmhd_handle h, void* host_buf, size_t bytes)
         if (rc) return rc;
         std::memcpy(o, tot, kStatsBytes);
         o += kStatsBytes;
-        for (int pl = 0; pl < 38; ++pl, o += r.N * pb)
-            LB_CK(cudaMemcpyAsync(o, (char*)r.pops[r.cur] + pl * r.stride * pb, r.N * pb, cudaMemcpyDeviceToHost,
+        for (const Segment& sg : state_segments(r, true)) {
+            LB_CK(cudaMemcpyAsync(o, (char*)r.pops[r.cur] + sg.first * pb, sg.count * pb, cudaMemcpyDeviceToHost,
                                   h->stream));
-        for (int pl = 0; pl < 25; ++pl, o += r.N * hb)
-            LB_CK(cudaMemcpyAsync(o, (char*)r.h[r.cur] + pl * r.stride * hb, r.N * hb, cudaMemcpyDeviceToHost,
+            o += sg.count * pb;
+        }
+        for (const Segment& sg : state_segments(r, false)) {
+            LB_CK(cudaMemcpyAsync(o, (char*)r.h[r.cur] + sg.first * hb, sg.count * hb, cudaMemcpyDeviceToHost,
                                   h->stream));
+            o += sg.count * hb;
+        }
         for (int pl = 0; pl < lb::NPRIM; ++pl, o += r.N * hb)
             LB_CK(cudaMemcpyAsync(o, (char*)r.prim[r.cur] + pl * r.stride * hb, r.N * hb, cudaMemcpyDeviceToHost,
                                   h->stream));
@@ -1519,12 +1542,16 @@ int lbrmhd_set_state(lbrmhd_handle h, const void* host_buf, size_t bytes)
         const int rc = write_stats(h, r, tot);
         if (rc) return rc;
         o += kStatsBytes;
-        for (int pl = 0; pl < 38; ++pl, o += r.N * pb)
-            LB_CK(cudaMemcpyAsync((char*)r.pops[r.cur] + pl * r.stride * pb, o, r.N * pb, cudaMemcpyHostToDevice,
+        for (const Segment& sg : state_segments(r, true)) {
+            LB_CK(cudaMemcpyAsync((char*)r.pops[r.cur] + sg.first * pb, o, sg.count * pb, cudaMemcpyHostToDevice,
                                   h->stream));
-        for (int pl = 0; pl < 25; ++pl, o += r.N * hb)
-            LB_CK(cudaMemcpyAsync((char*)r.h[r.cur] + pl * r.stride * hb, o, r.N * hb, cudaMemcpyHostToDevice,
+            o += sg.count * pb;
+        }
+        for (const Segment& sg : state_segments(r, false)) {
+            LB_CK(cudaMemcpyAsync((char*)r.h[r.cur] + sg.first * hb, o, sg.count * hb, cudaMemcpyHostToDevice,
                                   h->stream));
+            o += sg.count * hb;
+        }
         for (int pl = 0; pl < lb::NPRIM; ++pl, o += r.N * hb)
             LB_CK(cudaMemcpyAsync((char*)r.prim[r.cur] + pl * r.stride * hb, o, r.N * hb, cudaMemcpyHostToDevice,
                                   h->stream));

@@ -45,8 +45,8 @@ template <int I, class Cfg, class R>
 struct EqStore {
     static __device__ __forceinline__ void run(const PopView<Cfg>& V, int64_t c, const EqCell<R>& q)
     {
-        st_pop<Cfg>(V.f + (int64_t)I * V.stride + c, (typename Cfg::real)feq_dev<I>(q), V.hs.finv[I]);
-        st_pop<Cfg>(V.g + (int64_t)I * V.stride + c, (typename Cfg::real)geq_dev<I>(q), V.hs.ginv[I]);
+        st_pop<Cfg>(V.fg + fg_elem(I, 0, c, V.stride), (typename Cfg::real)feq_dev<I>(q), V.hs.finv[I]);
+        st_pop<Cfg>(V.fg + fg_elem(I, 1, c, V.stride), (typename Cfg::real)geq_dev<I>(q), V.hs.ginv[I]);
         EqStore<I + 1, Cfg, R>::run(V, c, q);
     }
 };
@@ -60,7 +60,7 @@ struct HeqStore {
     static __device__ __forceinline__ void run(const PopView<Cfg>& V, int64_t c, const R* E, const R* B, const R* J,
                                                const Phys<R>& k)
     {
-        V.h[(int64_t)K * V.stride + c] = (typename Cfg::hpop)heq13<K>(E, B, J, k);
+        V.h[h_elem(K, c, V.stride)] = (typename Cfg::hpop)heq13<K>(E, B, J, k);
         HeqStore<K + 1, Cfg, R>::run(V, c, E, B, J, k);
     }
 };
@@ -83,7 +83,7 @@ __device__ __forceinline__ void set_equilibrium(const PopView<Cfg>& V, int64_t c
     const R dE[3] = {s.E[0] - k.Er[0], s.E[1] - k.Er[1], s.E[2] - k.Er[2]};
     const R dB[3] = {s.B[0] - k.Br[0], s.B[1] - k.Br[1], s.B[2] - k.Br[2]};
     HeqStore<0, Cfg, R>::run(V, c, dE, dB, J, k);
-    V.h[24 * V.stride + c] = (typename Cfg::hpop)s.rho;
+    V.h[h_elem(24, c, V.stride)] = (typename Cfg::hpop)s.rho;
 }
 
 // ---------------------------------------------------------------------------
@@ -207,7 +207,7 @@ struct FixF {
                                                const EqCell<R>& qn, const R* fv)
     {
         const R d = k_aw<I>(qo) * (feq_dev<I>(qn) - feq_dev<I>(qo));
-        st_pop<Cfg>(V.f + (int64_t)I * V.stride + c, fv[I] + d, V.hs.finv[I]);
+        st_pop<Cfg>(V.fg + fg_elem(I, 0, c, V.stride), fv[I] + d, V.hs.finv[I]);
         FixF<I + 1, Cfg, R>::run(V, c, qo, qn, fv);
     }
 };
@@ -263,13 +263,13 @@ __global__ void bfix_kernel(PopView<Cfg> V, Phys<typename Cfg::real> k, int a, i
     load_prim<Cfg>(V.prim, V.stride, cb, so);
     R fv[19], hv[8];
 #pragma unroll
-    for (int i = 0; i < 19; ++i) fv[i] = ld_pop<Cfg>(V.f + (int64_t)i * V.stride + cb, V.hs.f[i]);
+    for (int i = 0; i < 19; ++i) fv[i] = ld_pop<Cfg>(V.fg + fg_elem(i, 0, cb, V.stride), V.hs.f[i]);
     int hp = 0;  // the plane whose normal is axis a
 #pragma unroll
     for (int p = 0; p < 3; ++p)
         if (plane_normal(p) == a) hp = p;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) hv[j] = (R)V.h[(int64_t)(8 * hp + j) * V.stride + cb];
+    for (int j = 0; j < 8; ++j) hv[j] = (R)V.h[h_elem(8 * hp + j, cb, V.stride)];
     const R dB = Bn_new - so.B[a];
     Prim<R> sn = so;
     sn.B[a] = Bn_new;
@@ -278,7 +278,7 @@ __global__ void bfix_kernel(PopView<Cfg> V, Phys<typename Cfg::real> k, int a, i
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const R bn = R(((j % 2) == 0 ? -1 : 1) * plane_orient(hp));
-        V.h[(int64_t)(8 * hp + j) * V.stride + cb] = (typename Cfg::hpop)(hv[j] + dB * bn / R(8));
+        V.h[h_elem(8 * hp + j, cb, V.stride)] = (typename Cfg::hpop)(hv[j] + dB * bn / R(8));
     }
     EqCell<R> qo, qn;
     eq_cell(so, k, qo);
@@ -366,11 +366,11 @@ __global__ void populations_kernel(PopView<Cfg> V, RefPops ref, double* f, doubl
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (c >= N) return;
     for (int i = 0; i < 19; ++i) {
-        if (f) f[i * N + c] = ref.f[i] + (double)ld_pop<Cfg>(V.f + (int64_t)i * V.stride + c, V.hs.f[i]);
-        if (g) g[i * N + c] = ref.g[i] + (double)ld_pop<Cfg>(V.g + (int64_t)i * V.stride + c, V.hs.g[i]);
+        if (f) f[i * N + c] = ref.f[i] + (double)ld_pop<Cfg>(V.fg + fg_elem(i, 0, c, V.stride), V.hs.f[i]);
+        if (g) g[i * N + c] = ref.g[i] + (double)ld_pop<Cfg>(V.fg + fg_elem(i, 1, c, V.stride), V.hs.g[i]);
     }
     if (h)
-        for (int i = 0; i < 25; ++i) h[i * N + c] = ref.h[i] + (double)V.h[(int64_t)i * V.stride + c];
+        for (int i = 0; i < 25; ++i) h[i * N + c] = ref.h[i] + (double)V.h[h_elem(i, c, V.stride)];
 }
 
 // per-block float64 partial diagnostics: sum N^0, T^{0 nu} (4), rho_c, max |div B|,
@@ -390,20 +390,33 @@ __global__ void diag_kernel(PopView<Cfg> V, Phys<double> k, RefState r, double* 
     if (c < N) {
         bool bad = false;
         R N0 = R(0), T0[4] = {R(0), R(0), R(0), R(0)}, rho = R(0);
-#pragma unroll
-        for (int i = 0; i < 19; ++i) {
-            const R fi = (R)ld_pop<Cfg>(V.f + (int64_t)i * V.stride + c, V.hs.f[i]);
-            const R gi = (R)ld_pop<Cfg>(V.g + (int64_t)i * V.stride + c, V.hs.g[i]);
+        auto add = [&](int i, R fi, R gi) {
             bad = bad || !isfinite(fi) || !isfinite(gi);
             N0 += gi;
             T0[0] += fi;
 #pragma unroll
             for (int a = 0; a < 3; ++a)
                 if (c19(i, a)) T0[a + 1] += R(c19(i, a)) * fi;
+        };
+        {
+            const V2<R> v = ld_fgpair<Cfg>(V.fg + fg_elem(0, 0, c, V.stride));
+            add(0, Cfg::kHalf ? v.x * V.hs.f[0] : v.x, Cfg::kHalf ? v.y * V.hs.g[0] : v.y);
         }
 #pragma unroll
-        for (int i = 0; i < 25; ++i) {
-            const R hi = (R)V.h[(int64_t)i * V.stride + c];
+        for (int i = 1; i < 19; i += 2) {
+            const V4<R> v = ld_quad<Cfg>(V.fg + fg_elem(i, 0, c, V.stride));
+            add(i, Cfg::kHalf ? v.x * V.hs.f[i] : v.x, Cfg::kHalf ? v.y * V.hs.g[i] : v.y);
+            add(i + 1, Cfg::kHalf ? v.z * V.hs.f[i + 1] : v.z, Cfg::kHalf ? v.w * V.hs.g[i + 1] : v.w);
+        }
+#pragma unroll
+        for (int m = 0; m < 12; ++m) {
+            const V2<R> v = ld_hpair<Cfg>(V.h + h_elem(2 * m, c, V.stride));
+            bad = bad || !isfinite(v.x) || !isfinite(v.y);
+            rho += v.x;
+            rho += v.y;
+        }
+        {
+            const R hi = (R)V.h[h_elem(24, c, V.stride)];
             bad = bad || !isfinite(hi);
             rho += hi;
         }

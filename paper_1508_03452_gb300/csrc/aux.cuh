@@ -9,9 +9,8 @@ namespace lb {
 // one buffer set (current state) of one run
 template <class Cfg>
 struct PopView {
-    typename Cfg::pop* f;
-    typename Cfg::pop* g;
-    typename Cfg::hpop* h;
+    typename Cfg::pop* fg;  // f and g in the group order of fg_elem
+    typename Cfg::hpop* h;  // h in the pair order of h_elem
     typename Cfg::prim* prim;
     int nx, ny, nz;
     int64_t stride;

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstring>
+
 #include "lattice.cuh"
 
 namespace lb {
@@ -38,6 +40,26 @@ struct CfgF16 {  // float16 relative deviations for f and g
 // primitive planes
 enum { P_N = 0, P_EPS = 1, P_U = 2, P_E = 5, P_B = 8, P_RHO = 11, NPRIM = 12 };
 
+// Storage order of the populations of one buffer (every plane holds `stride`
+// cells). Fluid: the opposite D3Q19 directions i = 2G-1 and 2G (G = 1..9)
+// stream over the same cells, and so do f and g of one direction, so group G
+// keeps {f_{2G-1}, g_{2G-1}, f_{2G}, g_{2G}} of a cell together (4-vector G-1
+// of the cell: one vector load per stencil point serves four populations); the
+// rest pair {f_0, g_0} follows the nine group planes as 2-vectors. Maxwell: the
+// D3Q13 populations 2m and 2m+1 (m = 0..11) hop the same way and form 2-vector
+// m; the rest population h_24 follows as a plane of its own.
+constexpr int kFGroups = 9;
+__host__ __device__ constexpr int64_t fg_elem(int i, int which, int64_t c, int64_t stride)
+{
+    return i == 0 ? 4 * kFGroups * stride + 2 * c + which
+                  : 4 * (((i - 1) >> 1) * stride + c) + 2 * ((i - 1) & 1) + which;
+}
+// element of Maxwell population k (0..24) of cell c
+__host__ __device__ constexpr int64_t h_elem(int k, int64_t c, int64_t stride)
+{
+    return k < 24 ? 2 * ((k >> 1) * stride + c) + (k & 1) : 24 * stride + c;
+}
+
 // per-run recovery counters: [0] failures [1] iteration sum [2] iteration max,
 // then kHistBins bins: cells that converged in 1, 2, ..., kHistBins - 1
 // iterations, and in kHistBins or more
@@ -69,12 +91,10 @@ struct StepArgs {
     using hpop = typename Cfg::hpop;
     using prim = typename Cfg::prim;
     using real = typename Cfg::real;
-    const pop* __restrict__ fin;
-    const pop* __restrict__ gin;
-    const hpop* __restrict__ hin;
+    const pop* __restrict__ fgin;  // f and g in the group order of fg_elem
+    const hpop* __restrict__ hin;  // h in the pair order of h_elem
     const prim* __restrict__ pin;
-    pop* __restrict__ fout;
-    pop* __restrict__ gout;
+    pop* __restrict__ fgout;
     hpop* __restrict__ hout;
     prim* __restrict__ pout;
     int nx, ny, nz;
@@ -130,6 +150,140 @@ __device__ __forceinline__ void st_pop(typename Cfg::pop* p, typename Cfg::real 
         *p = __float2half_rn(v * inv_scale);
     else
         *p = v;
+}
+
+// vector loads / stores of a fluid group (4 values at p, p 4-element aligned)
+// and of a 2-vector (the rest pair, an h pair), in stored units
+template <class R>
+struct V4 {
+    R x, y, z, w;
+};
+template <class R>
+struct V2 {
+    R x, y;
+};
+
+__device__ __forceinline__ float2 half2_bits_to_float2(unsigned u)
+{
+    __half2 h;
+    static_assert(sizeof(h) == sizeof(u), "half2 size");
+    memcpy(&h, &u, sizeof(u));
+    return __half22float2(h);
+}
+__device__ __forceinline__ unsigned float2_to_half2_bits(float a, float b)
+{
+    const __half2 h = __floats2half2_rn(a, b);
+    unsigned u;
+    memcpy(&u, &h, sizeof(u));
+    return u;
+}
+
+template <class Cfg>
+__device__ __forceinline__ V4<typename Cfg::real> ld_quad(const typename Cfg::pop* p)
+{
+    if constexpr (Cfg::kHalf) {
+        const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+        const float2 a = half2_bits_to_float2(u.x), b = half2_bits_to_float2(u.y);
+        return {a.x, a.y, b.x, b.y};
+    } else if constexpr (sizeof(typename Cfg::pop) == 8) {
+        const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+        const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+        return {a.x, a.y, b.x, b.y};
+    } else {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+        return {a.x, a.y, a.z, a.w};
+    }
+}
+
+// inv: the float16 scales of the four values (unused for float32 / float64)
+template <class Cfg>
+__device__ __forceinline__ void st_quad(typename Cfg::pop* p, const V4<typename Cfg::real>& v, const V4<float>& inv)
+{
+    if constexpr (Cfg::kHalf) {
+        *reinterpret_cast<uint2*>(p) =
+            make_uint2(float2_to_half2_bits(v.x * inv.x, v.y * inv.y), float2_to_half2_bits(v.z * inv.z, v.w * inv.w));
+    } else if constexpr (sizeof(typename Cfg::pop) == 8) {
+        reinterpret_cast<double2*>(p)[0] = make_double2(v.x, v.y);
+        reinterpret_cast<double2*>(p)[1] = make_double2(v.z, v.w);
+    } else {
+        *reinterpret_cast<float4*>(p) = make_float4(v.x, v.y, v.z, v.w);
+    }
+}
+
+template <class Cfg>
+__device__ __forceinline__ V2<typename Cfg::real> ld_fgpair(const typename Cfg::pop* p)
+{
+    if constexpr (Cfg::kHalf) {
+        const float2 a = half2_bits_to_float2(__ldg(reinterpret_cast<const unsigned*>(p)));
+        return {a.x, a.y};
+    } else if constexpr (sizeof(typename Cfg::pop) == 8) {
+        const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+        return {a.x, a.y};
+    } else {
+        const float2 a = __ldg(reinterpret_cast<const float2*>(p));
+        return {a.x, a.y};
+    }
+}
+
+template <class Cfg>
+__device__ __forceinline__ void st_fgpair(typename Cfg::pop* p, typename Cfg::real f, typename Cfg::real g,
+                                          float inv_f, float inv_g)
+{
+    if constexpr (Cfg::kHalf)
+        *reinterpret_cast<unsigned*>(p) = float2_to_half2_bits(f * inv_f, g * inv_g);
+    else if constexpr (sizeof(typename Cfg::pop) == 8)
+        *reinterpret_cast<double2*>(p) = make_double2(f, g);
+    else
+        *reinterpret_cast<float2*>(p) = make_float2(f, g);
+}
+
+// the same from shared memory (a tile's staged copy)
+template <class Cfg>
+__device__ __forceinline__ V4<typename Cfg::real> ld_quad_sh(const typename Cfg::pop* p)
+{
+    if constexpr (Cfg::kHalf) {
+        const uint2 u = *reinterpret_cast<const uint2*>(p);
+        const float2 a = half2_bits_to_float2(u.x), b = half2_bits_to_float2(u.y);
+        return {a.x, a.y, b.x, b.y};
+    } else {
+        static_assert(sizeof(typename Cfg::pop) == 4, "shared-memory tiles hold float32 or float16");
+        const float4 a = *reinterpret_cast<const float4*>(p);
+        return {a.x, a.y, a.z, a.w};
+    }
+}
+template <class Cfg>
+__device__ __forceinline__ V2<typename Cfg::real> ld_pair_sh(const typename Cfg::pop* p)
+{
+    if constexpr (Cfg::kHalf) {
+        const float2 a = half2_bits_to_float2(*reinterpret_cast<const unsigned*>(p));
+        return {a.x, a.y};
+    } else {
+        const float2 a = *reinterpret_cast<const float2*>(p);
+        return {a.x, a.y};
+    }
+}
+
+// a Maxwell pair (2m, 2m+1) at p
+template <class Cfg>
+__device__ __forceinline__ V2<typename Cfg::real> ld_hpair(const typename Cfg::hpop* p)
+{
+    using R = typename Cfg::real;
+    if constexpr (sizeof(typename Cfg::hpop) == 8) {
+        const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+        return {(R)a.x, (R)a.y};
+    } else {
+        const float2 a = __ldg(reinterpret_cast<const float2*>(p));
+        return {(R)a.x, (R)a.y};
+    }
+}
+
+template <class Cfg>
+__device__ __forceinline__ void st_hpair(typename Cfg::hpop* p, typename Cfg::real a, typename Cfg::real b)
+{
+    if constexpr (sizeof(typename Cfg::hpop) == 8)
+        *reinterpret_cast<double2*>(p) = make_double2(a, b);
+    else
+        *reinterpret_cast<float2*>(p) = make_float2((float)a, (float)b);
 }
 
 // wrapped (periodic) or clamped (open / driven) coordinate

@@ -72,100 +72,177 @@ __device__ __forceinline__ Off make_off(int x, int y, int z, int nx, int ny, int
     return o;
 }
 
-// One streamed fluid population (pre-collision value at t + dt); p points at
-// this cell in the population's plane. The update is linear and the limiter
-// positively homogeneous (minmod(s a, s b) = s minmod(a, b), s > 0), so
-// float16 values are streamed in their stored units and scaled once.
-template <int I, bool IS3D, bool VISC, class Cfg>
-__device__ __forceinline__ typename Cfg::real stream_pop(const typename Cfg::pop* __restrict__ p, const Off& o,
-                                                         const Phys<typename Cfg::real>& k, float scale)
+// Moments of the streamed f_I, g_I (deviations): T^{mu nu} with p = (1, q chat)
+// and N^mu.
+template <int I, class R>
+__device__ __forceinline__ void acc_fg(R f, R g, R (&Tm)[10], R& Nm, R (&Na)[3])
+{
+    constexpr int cx = c19(I, 0), cy = c19(I, 1), cz = c19(I, 2);
+    Tm[0] += f;
+    if (cx) Tm[1] += R(cx) * f;
+    if (cy) Tm[2] += R(cy) * f;
+    if (cz) Tm[3] += R(cz) * f;
+    if (cx) Tm[4] += f;  // xx (chat^2 = 1)
+    if (cy) Tm[5] += f;  // yy
+    if (cz) Tm[6] += f;  // zz
+    if (cx * cy) Tm[7] += R(cx * cy) * f;
+    if (cx * cz) Tm[8] += R(cx * cz) * f;
+    if (cy * cz) Tm[9] += R(cy * cz) * f;
+    Nm += g;
+    if (cx) Na[0] += R(cx) * g;
+    if (cy) Na[1] += R(cy) * g;
+    if (cz) Na[2] += R(cz) * g;
+}
+
+// The four streamed populations of fluid group G (pre-collision values at
+// t + dt of f_I, g_I, f_J, g_J for the opposite directions I = 2G-1, J = 2G);
+// ld(a, d) gives the group's 4-vector of the cell d cells away along axis a
+// (d = 0: this cell). Along an axis where I moves by s = +-1 the values at
+// -2..+2 serve both directions (I's upwind side is J's downwind side); along
+// an axis where neither moves only the +-1 values enter (the bulk viscosity
+// of f). The update is linear and the limiter positively homogeneous
+// (minmod(s a, s b) = s minmod(a, b), s > 0), so float16 values are streamed
+// in their stored units and scaled once.
+template <int G, bool IS3D, class Cfg, class Ld>
+__device__ __forceinline__ V4<typename Cfg::real> stream_group(const Ld& ld, const Phys<typename Cfg::real>& k,
+                                                               const HalfScale& hs)
 {
     using R = typename Cfg::real;
+    constexpr int I = 2 * G - 1, J = 2 * G;
     constexpr int s[3] = {c19(I, 0), c19(I, 1), c19(I, 2)};
-    const R v0 = ld_pop<Cfg>(p, 1.0f);
-    R flux = R(0), lap = R(0);
+    const V4<R> v0 = ld(0, 0);
+    R fl[4] = {R(0), R(0), R(0), R(0)}, lap[2] = {R(0), R(0)};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (a == 2 && !IS3D) continue;
-        const int* oa = a == 0 ? o.x : (a == 1 ? o.y : o.z);
-        const int sa = s[a];
-        if (sa != 0) {
-            const R um2 = ld_pop<Cfg>(p + oa[2 - 2 * sa], 1.0f);
-            const R um1 = ld_pop<Cfg>(p + oa[2 - sa], 1.0f);
-            const R up1 = ld_pop<Cfg>(p + oa[2 + sa], 1.0f);
-            flux += flux_diff(um2, um1, v0, up1, k.kappa);
-            if (VISC) lap += (um1 + up1) - R(2) * v0;
-        } else if (VISC) {
-            lap += (ld_pop<Cfg>(p + oa[1], 1.0f) + ld_pop<Cfg>(p + oa[3], 1.0f)) - R(2) * v0;
+        if (s[a] != 0) {
+            const V4<R> m2 = ld(a, -2), m1 = ld(a, -1), p1 = ld(a, 1), p2 = ld(a, 2);
+            const V4<R>& i2 = s[a] > 0 ? m2 : p2;  // I's second upwind cell (-2s)
+            const V4<R>& i1 = s[a] > 0 ? m1 : p1;  // I's upwind cell (-s) = J's downwind cell
+            const V4<R>& ip = s[a] > 0 ? p1 : m1;  // I's downwind cell (+s) = J's upwind cell
+            const V4<R>& j2 = s[a] > 0 ? p2 : m2;  // J's second upwind cell (+2s)
+            fl[0] += flux_diff(i2.x, i1.x, v0.x, ip.x, k.kappa);
+            fl[1] += flux_diff(i2.y, i1.y, v0.y, ip.y, k.kappa);
+            fl[2] += flux_diff(j2.z, ip.z, v0.z, i1.z, k.kappa);
+            fl[3] += flux_diff(j2.w, ip.w, v0.w, i1.w, k.kappa);
+            lap[0] += (i1.x + ip.x) - R(2) * v0.x;
+            lap[1] += (ip.z + i1.z) - R(2) * v0.z;
+        } else {
+            const V4<R> m1 = ld(a, -1), p1 = ld(a, 1);
+            lap[0] += (m1.x + p1.x) - R(2) * v0.x;
+            lap[1] += (m1.z + p1.z) - R(2) * v0.z;
         }
     }
-    R out = v0 - k.C * flux;
-    if (VISC && I != 0) out += k.kvisc * lap;
-    if constexpr (Cfg::kHalf) out *= scale;
+    V4<R> out;
+    out.x = v0.x - k.C * fl[0];
+    out.x += k.kvisc * lap[0];
+    out.y = v0.y - k.C * fl[1];
+    out.z = v0.z - k.C * fl[2];
+    out.z += k.kvisc * lap[1];
+    out.w = v0.w - k.C * fl[3];
+    if constexpr (Cfg::kHalf) {
+        out.x *= hs.f[I];
+        out.y *= hs.g[I];
+        out.z *= hs.f[J];
+        out.w *= hs.g[J];
+    }
     return out;
 }
 
-// Streams f and g (population I onwards) into the shared-memory buffer `sp`
-// (slot I for f, 19 + I for g) and accumulates their moments.
-template <int I, bool IS3D, class Cfg>
+// the streamed rest pair (f_0, g_0): it does not move and takes no bulk viscosity
+template <class Cfg>
+__device__ __forceinline__ V2<typename Cfg::real> rest_pair(V2<typename Cfg::real> v, const HalfScale& hs)
+{
+    if constexpr (Cfg::kHalf) {
+        v.x *= hs.f[0];
+        v.y *= hs.g[0];
+    }
+    return v;
+}
+
+// slots and moments of the streamed populations of group G (G = 0: the rest pair in v.x, v.y)
+template <int G, class Cfg>
+__device__ __forceinline__ void store_group(const V4<typename Cfg::real>& v, typename Cfg::real* sp, int nth,
+                                            typename Cfg::real (&Tm)[10], typename Cfg::real& Nm,
+                                            typename Cfg::real (&Na)[3])
+{
+    if constexpr (G == 0) {
+        sp[0] = v.x;
+        sp[19 * nth] = v.y;
+        acc_fg<0>(v.x, v.y, Tm, Nm, Na);
+    } else {
+        constexpr int I = 2 * G - 1, J = 2 * G;
+        sp[I * nth] = v.x;
+        sp[(19 + I) * nth] = v.y;
+        acc_fg<I>(v.x, v.y, Tm, Nm, Na);
+        sp[J * nth] = v.z;
+        sp[(19 + J) * nth] = v.w;
+        acc_fg<J>(v.z, v.w, Tm, Nm, Na);
+    }
+}
+
+// Streams f and g group by group (G onwards; G = 0 is the rest pair) into the
+// shared-memory buffer `sp` (slot i for f_i, 19 + i for g_i) and accumulates
+// their moments in the order of the populations.
+template <int G, bool IS3D, class Cfg>
 struct StreamAll {
     using R = typename Cfg::real;
     static __device__ __forceinline__ void run(const StepArgs<Cfg>& A, const Off& o, int64_t c, R* sp, int nth,
                                                R (&Tm)[10], R& Nm, R (&Na)[3])
     {
-        const R f = stream_pop<I, IS3D, true, Cfg>(A.fin + (int64_t)I * A.stride + c, o, A.k, A.hs.f[I]);
-        const R g = stream_pop<I, IS3D, false, Cfg>(A.gin + (int64_t)I * A.stride + c, o, A.k, A.hs.g[I]);
-        sp[I * nth] = f;
-        sp[(19 + I) * nth] = g;
-        constexpr int cx = c19(I, 0), cy = c19(I, 1), cz = c19(I, 2);
-        // T^{mu nu} of the deviations: p = (1, q chat)
-        Tm[0] += f;
-        if (cx) Tm[1] += R(cx) * f;
-        if (cy) Tm[2] += R(cy) * f;
-        if (cz) Tm[3] += R(cz) * f;
-        if (cx) Tm[4] += f;  // xx (chat^2 = 1)
-        if (cy) Tm[5] += f;  // yy
-        if (cz) Tm[6] += f;  // zz
-        if (cx * cy) Tm[7] += R(cx * cy) * f;
-        if (cx * cz) Tm[8] += R(cx * cz) * f;
-        if (cy * cz) Tm[9] += R(cy * cz) * f;
-        Nm += g;
-        if (cx) Na[0] += R(cx) * g;
-        if (cy) Na[1] += R(cy) * g;
-        if (cz) Na[2] += R(cz) * g;
-        StreamAll<I + 1, IS3D, Cfg>::run(A, o, c, sp, nth, Tm, Nm, Na);
+        if constexpr (G == 0) {
+            const V2<R> v = rest_pair<Cfg>(ld_fgpair<Cfg>(A.fgin + fg_elem(0, 0, c, A.stride)), A.hs);
+            store_group<0, Cfg>(V4<R>{v.x, v.y, R(0), R(0)}, sp, nth, Tm, Nm, Na);
+        } else {
+            const typename Cfg::pop* p = A.fgin + fg_elem(2 * G - 1, 0, c, A.stride);
+            auto ld = [&](int a, int d) {
+                const int* oa = a == 0 ? o.x : (a == 1 ? o.y : o.z);
+                return ld_quad<Cfg>(d == 0 ? p : p + 4 * oa[d + 2]);
+            };
+            store_group<G, Cfg>(stream_group<G, IS3D, Cfg>(ld, A.k, A.hs), sp, nth, Tm, Nm, Na);
+        }
+        StreamAll<G + 1, IS3D, Cfg>::run(A, o, c, sp, nth, Tm, Nm, Na);
     }
 };
 template <bool IS3D, class Cfg>
-struct StreamAll<19, IS3D, Cfg> {
+struct StreamAll<kFGroups + 1, IS3D, Cfg> {
     using R = typename Cfg::real;
     static __device__ __forceinline__ void run(const StepArgs<Cfg>&, const Off&, int64_t, R*, int, R (&)[10], R&,
                                                R (&)[3]) {}
 };
 
 // Exact D3Q13 pull h_k(x) = h_c,k(x - hop_k) into slot 38 + k, accumulating
-// E' - Er (before the sqrt(2) c / 2 factor), the plane-normal B - Br sums and rho_c.
-template <int K, bool IS3D, class Cfg>
+// E' - Er (before the sqrt(2) c / 2 factor), the plane-normal B - Br sums and
+// rho_c; the pair k = 2m, 2m + 1 hops the same way and arrives in one load.
+template <int K, class R>
+__device__ __forceinline__ void acc_h(R hv, R* sp, int nth, R (&dEp)[3], R (&bn)[3], R& rho)
+{
+    constexpr int p = K / 8, i = (K % 8) / 2, j = K % 2, ie = (i + 3) % 4;
+    sp[(38 + K) * nth] = hv;
+    rho += hv;
+    constexpr int se = j == 0 ? 1 : -1;  // e_{i1} = -e_{i0}
+    dEp[plane_a1(p)] += R(se * hop_s1(ie)) * hv;
+    dEp[plane_a2(p)] += R(se * hop_s2(ie)) * hv;
+    bn[plane_normal(p)] += R(-se * plane_orient(p)) * hv;  // b_{i0} = -o_p, b_{i1} = +o_p
+}
+
+template <int M, bool IS3D, class Cfg>
 struct PullH {
     using R = typename Cfg::real;
     static __device__ __forceinline__ void run(const StepArgs<Cfg>& A, const Off& o, int64_t c, R* sp, int nth,
                                                R (&dEp)[3], R (&bn)[3], R& rho)
     {
-        constexpr int p = K / 8, i = (K % 8) / 2, j = K % 2, ie = (i + 3) % 4;
+        constexpr int K = 2 * M;
         int off = o.x[2 - hop13(K, 0)] + o.y[2 - hop13(K, 1)];
         if (IS3D) off += o.z[2 - hop13(K, 2)];
-        const R hv = (R)A.hin[(int64_t)K * A.stride + c + off];
-        sp[(38 + K) * nth] = hv;
-        rho += hv;
-        constexpr int se = j == 0 ? 1 : -1;  // e_{i1} = -e_{i0}
-        dEp[plane_a1(p)] += R(se * hop_s1(ie)) * hv;
-        dEp[plane_a2(p)] += R(se * hop_s2(ie)) * hv;
-        bn[plane_normal(p)] += R(-se * plane_orient(p)) * hv;  // b_{i0} = -o_p, b_{i1} = +o_p
-        PullH<K + 1, IS3D, Cfg>::run(A, o, c, sp, nth, dEp, bn, rho);
+        const V2<R> hv = ld_hpair<Cfg>(A.hin + h_elem(K, c + off, A.stride));
+        acc_h<K>(hv.x, sp, nth, dEp, bn, rho);
+        acc_h<K + 1>(hv.y, sp, nth, dEp, bn, rho);
+        PullH<M + 1, IS3D, Cfg>::run(A, o, c, sp, nth, dEp, bn, rho);
     }
 };
 template <bool IS3D, class Cfg>
-struct PullH<24, IS3D, Cfg> {
+struct PullH<12, IS3D, Cfg> {
     using R = typename Cfg::real;
     static __device__ __forceinline__ void run(const StepArgs<Cfg>&, const Off&, int64_t, R*, int, R (&)[3], R (&)[3],
                                                R&) {}
@@ -197,69 +274,78 @@ __device__ __forceinline__ float2 eq_pair(const EqCell<float>& q)
     return __fmul2_rn(make_float2((float)w19(I), (float)wg19(I)), v);
 }
 
-// TILE: the post-collision values go to the block's shared-memory output
-// tile `ofg` (f then g, one row of nth cells per population) instead of
-// global memory
-template <int I, class Cfg, bool TILE>
+// post-collision (f_I, g_I) of one cell from the streamed values in the slots
+template <int I, class Cfg>
+__device__ __forceinline__ void collide_fg(const StepArgs<Cfg>& A, const typename Cfg::real* sp, int nth,
+                                           const EqCell<typename Cfg::real>& q, typename Cfg::real& fo,
+                                           typename Cfg::real& go)
+{
+    using R = typename Cfg::real;
+    const R fd = sp[I * nth], gd = sp[(19 + I) * nth];
+    const R K = k_aw<I>(q);
+    if constexpr (sizeof(R) == 4) {
+        // f and g of one direction relax in lock-step: the float32 pair
+        // instructions do both (fd - K (fd - feq), gd - (dt/tau)(gd - geq))
+        const float2 eq = eq_pair<I>(q);
+        const float2 d = make_float2(fd, gd);
+        const float2 t = __fadd2_rn(d, make_float2(-eq.x, -eq.y));
+        const float2 o = __ffma2_rn(make_float2(-K, -A.k.inv_tau), t, d);
+        fo = o.x;
+        go = o.y;
+    } else {
+        fo = fd - K * (fd - feq_dev<I>(q));
+        go = gd - A.k.inv_tau * (gd - geq_dev<I>(q));
+    }
+}
+
+// Collision of f and g and the stores, group by group (G onwards) into cell c
+// of the output buffer.
+template <int G, class Cfg>
 struct CollideFG {
     using R = typename Cfg::real;
     static __device__ __forceinline__ void run(const StepArgs<Cfg>& A, int64_t c, const R* sp, int nth,
-                                               const EqCell<R>& q, typename Cfg::pop* ofg)
+                                               const EqCell<R>& q)
     {
-        const R fd = sp[I * nth], gd = sp[(19 + I) * nth];
-        const R K = k_aw<I>(q);
-        R fo, go;
-        if constexpr (sizeof(R) == 4) {
-            // f and g of one direction relax in lock-step: the float32 pair
-            // instructions do both (fd - K (fd - feq), gd - (dt/tau)(gd - geq))
-            const float2 eq = eq_pair<I>(q);
-            const float2 d = make_float2(fd, gd);
-            const float2 t = __fadd2_rn(d, make_float2(-eq.x, -eq.y));
-            const float2 o = __ffma2_rn(make_float2(-K, -A.k.inv_tau), t, d);
-            fo = o.x;
-            go = o.y;
+        if constexpr (G == 0) {
+            R fo, go;
+            collide_fg<0, Cfg>(A, sp, nth, q, fo, go);
+            st_fgpair<Cfg>(A.fgout + fg_elem(0, 0, c, A.stride), fo, go, A.hs.finv[0], A.hs.ginv[0]);
         } else {
-            fo = fd - K * (fd - feq_dev<I>(q));
-            go = gd - A.k.inv_tau * (gd - geq_dev<I>(q));
+            constexpr int I = 2 * G - 1, J = 2 * G;
+            V4<R> v;
+            collide_fg<I, Cfg>(A, sp, nth, q, v.x, v.y);
+            collide_fg<J, Cfg>(A, sp, nth, q, v.z, v.w);
+            const V4<float> inv = {A.hs.finv[I], A.hs.ginv[I], A.hs.finv[J], A.hs.ginv[J]};
+            st_quad<Cfg>(A.fgout + fg_elem(I, 0, c, A.stride), v, inv);
         }
-        if constexpr (TILE) {
-            st_pop<Cfg>(ofg + I * nth, fo, A.hs.finv[I]);
-            st_pop<Cfg>(ofg + (19 + I) * nth, go, A.hs.ginv[I]);
-        } else {
-            st_pop<Cfg>(A.fout + (int64_t)I * A.stride + c, fo, A.hs.finv[I]);
-            st_pop<Cfg>(A.gout + (int64_t)I * A.stride + c, go, A.hs.ginv[I]);
-        }
-        CollideFG<I + 1, Cfg, TILE>::run(A, c, sp, nth, q, ofg);
+        CollideFG<G + 1, Cfg>::run(A, c, sp, nth, q);
     }
 };
-template <class Cfg, bool TILE>
-struct CollideFG<19, Cfg, TILE> {
+template <class Cfg>
+struct CollideFG<kFGroups + 1, Cfg> {
     using R = typename Cfg::real;
-    static __device__ __forceinline__ void run(const StepArgs<Cfg>&, int64_t, const R*, int, const EqCell<R>&,
-                                               typename Cfg::pop*) {}
+    static __device__ __forceinline__ void run(const StepArgs<Cfg>&, int64_t, const R*, int, const EqCell<R>&) {}
 };
 
-// TILE: the post-collision h replaces the streamed value in its slot (the
-// slots then form the block's h output tile)
-template <int K, class Cfg, bool TILE>
+// Collision of the Maxwell pair (2M, 2M + 1) into cell c of the output buffer.
+template <int M, class Cfg>
 struct CollideH {
     using R = typename Cfg::real;
-    static __device__ __forceinline__ void run(const StepArgs<Cfg>& A, int64_t c, R* sp, int nth, const R* E,
+    static __device__ __forceinline__ void run(const StepArgs<Cfg>& A, int64_t c, const R* sp, int nth, const R* E,
                                                const R* B, const R* J, bool em_coll)
     {
-        const R hv = sp[(38 + K) * nth];
-        const R v = em_coll ? R(2) * heq13<K>(E, B, J, A.k) - hv : hv;
-        if constexpr (TILE)
-            sp[(38 + K) * nth] = v;
-        else
-            A.hout[(int64_t)K * A.stride + c] = (typename Cfg::hpop)v;
-        CollideH<K + 1, Cfg, TILE>::run(A, c, sp, nth, E, B, J, em_coll);
+        constexpr int K = 2 * M;
+        const R h0 = sp[(38 + K) * nth], h1 = sp[(39 + K) * nth];
+        const R v0 = em_coll ? R(2) * heq13<K>(E, B, J, A.k) - h0 : h0;
+        const R v1 = em_coll ? R(2) * heq13<K + 1>(E, B, J, A.k) - h1 : h1;
+        st_hpair<Cfg>(A.hout + h_elem(K, c, A.stride), v0, v1);
+        CollideH<M + 1, Cfg>::run(A, c, sp, nth, E, B, J, em_coll);
     }
 };
-template <class Cfg, bool TILE>
-struct CollideH<24, Cfg, TILE> {
+template <class Cfg>
+struct CollideH<12, Cfg> {
     using R = typename Cfg::real;
-    static __device__ __forceinline__ void run(const StepArgs<Cfg>&, int64_t, R*, int, const R*, const R*,
+    static __device__ __forceinline__ void run(const StepArgs<Cfg>&, int64_t, const R*, int, const R*, const R*,
                                                const R*, bool) {}
 };
 
@@ -381,22 +467,24 @@ __device__ __forceinline__ void warp_max_into(double v, double* dst)
 #define LB_RING_STAGES 4
 #endif
 constexpr int kRingStages = LB_RING_STAGES;  // copies in flight per block
-constexpr int kFgStages = 10;                     // directions (0,1), (2,3), ..., (18, -)
-constexpr int kHStages = 7;                       // h planes 0-3, 4-7, ..., 24
+constexpr int kFgStages = 1 + kFGroups;          // the rest pairs, then fluid groups 1..9
+constexpr int kHStages = 7;                       // h pairs (0, 1), (2, 3), ..., (10, 11), then h_24
 constexpr int kTileStages = kFgStages + kHStages;  // 17
 
 template <class Cfg>
 struct TileGeo {
     using pop = typename Cfg::pop;
-    static constexpr int PX = tile_halo_x((int)sizeof(pop));  // f, g column halo: one 16-byte unit
+    static constexpr int PX = tile_halo_x((int)sizeof(pop));  // f, g column halo (every box starts 16-byte aligned)
     static constexpr int PXH = tile_halo_x(4);                // h column halo (float)
-    static constexpr int BWF = kTileW + 2 * PX;       // f, g box width
-    static constexpr int BWH = kTileW + 2 * PXH;      // h box width
+    static constexpr int BWF = kTileW + 2 * PX;       // f, g box width in cells
+    static constexpr int BWH = kTileW + 2 * PXH;      // h box width in cells
     static constexpr int BH = kTileH + 2 * kTileHaloY;  // box height
-    static constexpr int FG_PLANE = BWF * BH;         // elements per f or g plane in a stage
-    static constexpr int H_PLANE = BWH * BH;
-    static constexpr unsigned FG_STAGE_BYTES = 4u * FG_PLANE * sizeof(pop);
-    static constexpr unsigned H_STAGE_BYTES = 4u * H_PLANE * sizeof(float);
+    static constexpr int FG_CELLS = BWF * BH;         // cells of an f, g box
+    static constexpr int H_PLANE = BWH * BH;          // cells of an h box
+    static constexpr unsigned FG_STAGE_BYTES = 4u * FG_CELLS * sizeof(pop);  // one group
+    static constexpr unsigned R_STAGE_BYTES = 2u * FG_CELLS * sizeof(pop);   // the rest pairs
+    static constexpr unsigned H_STAGE_BYTES = 4u * H_PLANE * sizeof(float);  // two h pairs
+    static constexpr unsigned H24_STAGE_BYTES = 1u * H_PLANE * sizeof(float);
     static constexpr unsigned STAGE_BYTES =
         ((FG_STAGE_BYTES > H_STAGE_BYTES ? FG_STAGE_BYTES : H_STAGE_BYTES) + 127u) / 128u * 128u;
     static constexpr unsigned PRIM_BYTES = (unsigned)NPRIM * kTileThreads * sizeof(float);
@@ -407,7 +495,6 @@ template <class Cfg>
 struct TileCtx {
     unsigned char* ring;  // kRingStages x STAGE_BYTES
     float* pbuf;          // [NPRIM][kTileThreads]: input primitives, then the output ones
-    typename Cfg::pop* ofg;  // [38][kTileThreads] output f, g (float32: the slots; float16: the idle ring)
     uint64_t* bar;        // kRingStages ring barriers, then the primitives' barrier
     int* abort;           // set when a wait ran out: the whole block then stops
     const TileMaps* M;
@@ -418,130 +505,34 @@ struct TileCtx {
     uint32_t ppar;        // phase parity of this tile's primitive copy
 };
 
-// issue the copy of stage j of the tile at (x0, y0), ring index g (one thread)
+// issue the copy of stage j of the tile at (x0, y0), ring index g (one thread);
+// the x coordinates count elements of the maps' rows (4 or 2 per cell for the
+// groups and pairs)
 template <class Cfg>
 __device__ __forceinline__ void tile_issue(const TileCtx<Cfg>& t, int g, int x0, int y0, int j)
 {
     using G = TileGeo<Cfg>;
     const int s = g % kRingStages;
     unsigned char* dst = t.ring + (size_t)s * G::STAGE_BYTES;
-    if (j < kFgStages) {
+    if (j == 0) {
+        mbar_arrive_expect_tx(&t.bar[s], G::R_STAGE_BYTES);
+        tma_load_2d(dst, &t.M->r_in, 2 * (x0 - G::PX), y0 - kTileHaloY, &t.bar[s]);
+    } else if (j < kFgStages) {
         mbar_arrive_expect_tx(&t.bar[s], G::FG_STAGE_BYTES);
-        tma_load_4d(dst, &t.M->fg_in, x0 - G::PX, y0 - 2, 2 * j, 0, &t.bar[s]);
-    } else {
+        tma_load_3d(dst, &t.M->fg_in, 4 * (x0 - G::PX), y0 - kTileHaloY, j - 1, &t.bar[s]);
+    } else if (j < kTileStages - 1) {
         mbar_arrive_expect_tx(&t.bar[s], G::H_STAGE_BYTES);
-        tma_load_3d(dst, &t.M->h_in, x0 - G::PXH, y0 - 2, 4 * (j - kFgStages), &t.bar[s]);
+        tma_load_3d(dst, &t.M->h_in, 2 * (x0 - G::PXH), y0 - kTileHaloY, 2 * (j - kFgStages), &t.bar[s]);
+    } else {
+        mbar_arrive_expect_tx(&t.bar[s], G::H24_STAGE_BYTES);
+        tma_load_2d(dst, &t.M->h24_in, x0 - G::PXH, y0 - kTileHaloY, &t.bar[s]);
     }
 }
 
-// One streamed fluid population from its shared-memory tile plane; p points
-// at this cell, neighbours at compile-time offsets (dx + BWF dy). The same
-// operations in the same order as stream_pop (2-D).
-template <int I, bool VISC, class Cfg>
-__device__ __forceinline__ typename Cfg::real stream_tile(const typename Cfg::pop* p, const Phys<typename Cfg::real>& k,
-                                                          float scale)
-{
-    using R = typename Cfg::real;
-    constexpr int BW = TileGeo<Cfg>::BWF;
-    auto ld = [](const typename Cfg::pop* q) -> R {
-        if constexpr (Cfg::kHalf)
-            return __half2float(*q) * 1.0f;
-        else
-            return *q;
-    };
-    constexpr int s[2] = {c19(I, 0), c19(I, 1)};
-    const R v0 = ld(p);
-    R flux = R(0), lap = R(0);
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-        const int st = a == 0 ? 1 : BW;
-        const int sa = s[a];
-        if (sa != 0) {
-            const R um2 = ld(p - 2 * sa * st);
-            const R um1 = ld(p - sa * st);
-            const R up1 = ld(p + sa * st);
-            flux += flux_diff(um2, um1, v0, up1, k.kappa);
-            if (VISC) lap += (um1 + up1) - R(2) * v0;
-        } else if (VISC) {
-            lap += (ld(p - st) + ld(p + st)) - R(2) * v0;
-        }
-    }
-    R out = v0 - k.C * flux;
-    if (VISC && I != 0) out += k.kvisc * lap;
-    if constexpr (Cfg::kHalf) out *= scale;
-    return out;
-}
-
-// moments of one streamed (f, g) pair of direction I, as in StreamAll
-template <int I, class R>
-__device__ __forceinline__ void fg_moments(R f, R g, R (&Tm)[10], R& Nm, R (&Na)[3])
-{
-    constexpr int cx = c19(I, 0), cy = c19(I, 1), cz = c19(I, 2);
-    Tm[0] += f;
-    if (cx) Tm[1] += R(cx) * f;
-    if (cy) Tm[2] += R(cy) * f;
-    if (cz) Tm[3] += R(cz) * f;
-    if (cx) Tm[4] += f;
-    if (cy) Tm[5] += f;
-    if (cz) Tm[6] += f;
-    if (cx * cy) Tm[7] += R(cx * cy) * f;
-    if (cx * cz) Tm[8] += R(cx * cz) * f;
-    if (cy * cz) Tm[9] += R(cy * cz) * f;
-    Nm += g;
-    if (cx) Na[0] += R(cx) * g;
-    if (cy) Na[1] += R(cy) * g;
-    if (cz) Na[2] += R(cz) * g;
-}
-
-// moments of one pulled h of moving population K, as in PullH
-template <int K, class R>
-__device__ __forceinline__ void h_moments(R hv, R (&dEp)[3], R (&bn)[3], R& rho)
-{
-    constexpr int p = K / 8, i = (K % 8) / 2, j = K % 2, ie = (i + 3) % 4;
-    rho += hv;
-    constexpr int se = j == 0 ? 1 : -1;
-    dEp[plane_a1(p)] += R(se * hop_s1(ie)) * hv;
-    dEp[plane_a2(p)] += R(se * hop_s2(ie)) * hv;
-    bn[plane_normal(p)] += R(-se * plane_orient(p)) * hv;
-}
-
-template <int I, class Cfg>
-__device__ __forceinline__ void tile_fg_dir(const typename Cfg::pop* b, int center, int d, const StepArgs<Cfg>& A,
-                                            typename Cfg::real* sp, int nth, typename Cfg::real (&Tm)[10],
-                                            typename Cfg::real& Nm, typename Cfg::real (&Na)[3])
-{
-    using R = typename Cfg::real;
-    using G = TileGeo<Cfg>;
-    if constexpr (I < 19) {
-        const R f = stream_tile<I, true, Cfg>(b + d * G::FG_PLANE + center, A.k, A.hs.f[I]);
-        const R g = stream_tile<I, false, Cfg>(b + (2 + d) * G::FG_PLANE + center, A.k, A.hs.g[I]);
-        sp[I * nth] = f;
-        sp[(19 + I) * nth] = g;
-        fg_moments<I>(f, g, Tm, Nm, Na);
-    }
-}
-
-template <int K, class Cfg>
-__device__ __forceinline__ void tile_h_plane(const float* b, int center, int d, typename Cfg::real* sp, int nth,
-                                             typename Cfg::real (&dEp)[3], typename Cfg::real (&bn)[3],
-                                             typename Cfg::real& rho)
-{
-    using R = typename Cfg::real;
-    using G = TileGeo<Cfg>;
-    if constexpr (K < 24) {
-        const R hv = (R)b[d * G::H_PLANE + center - hop13(K, 1) * G::BWH - hop13(K, 0)];
-        sp[(38 + K) * nth] = hv;
-        h_moments<K>(hv, dEp, bn, rho);
-    } else if constexpr (K == 24) {
-        const R hv = (R)b[d * G::H_PLANE + center];
-        sp[62 * nth] = hv;
-        rho += hv;
-    }
-}
-
-// Stage J of the ring: wait for its copy, stream its planes, release the
-// buffer and refill it with stage J + kRingStages. Returns false (for every
-// thread of the block) if a copy did not arrive in time.
+// Stage J of the ring: wait for its copy, stream its populations (the same
+// operations in the same order as the per-cell path), release the buffer and
+// refill it with stage J + kRingStages. Returns false (for every thread of the
+// block) if a copy did not arrive in time.
 template <int J, class Cfg>
 struct TileStages {
     using R = typename Cfg::real;
@@ -549,6 +540,7 @@ struct TileStages {
                                                R (&Tm)[10], R& Nm, R (&Na)[3], R (&dEp)[3], R (&bn)[3], R& rho)
     {
         using G = TileGeo<Cfg>;
+        using pop = typename Cfg::pop;
         const int g = t.gbase + J;
         const int s = g % kRingStages;
         const unsigned char* buf = t.ring + (size_t)s * G::STAGE_BYTES;
@@ -558,18 +550,40 @@ struct TileStages {
         if (!arrived) *reinterpret_cast<volatile int*>(t.abort) = 1;
         if (arrived) {
             if constexpr (J < kFgStages) {
-                const auto* b = reinterpret_cast<const typename Cfg::pop*>(buf);
-                const int center = (ty + 2) * G::BWF + tx + G::PX;
-                tile_fg_dir<2 * J, Cfg>(b, center, 0, A, sp, nth, Tm, Nm, Na);
-                tile_fg_dir<2 * J + 1, Cfg>(b, center, 1, A, sp, nth, Tm, Nm, Na);
+                const pop* b = reinterpret_cast<const pop*>(buf);
+                const int cell = (ty + kTileHaloY) * G::BWF + tx + G::PX;
+                if constexpr (J == 0) {
+                    const V2<R> v = rest_pair<Cfg>(ld_pair_sh<Cfg>(b + 2 * cell), A.hs);
+                    store_group<0, Cfg>(V4<R>{v.x, v.y, R(0), R(0)}, sp, nth, Tm, Nm, Na);
+                } else {
+                    auto ld = [&](int a, int d) { return ld_quad_sh<Cfg>(b + 4 * (cell + d * (a == 0 ? 1 : G::BWF))); };
+                    store_group<J, Cfg>(stream_group<J, false, Cfg>(ld, A.k, A.hs), sp, nth, Tm, Nm, Na);
+                }
             } else {
                 const float* b = reinterpret_cast<const float*>(buf);
-                const int center = (ty + 2) * G::BWH + tx + G::PXH;
-                constexpr int K0 = 4 * (J - kFgStages);
-                tile_h_plane<K0, Cfg>(b, center, 0, sp, nth, dEp, bn, rho);
-                tile_h_plane<K0 + 1, Cfg>(b, center, 1, sp, nth, dEp, bn, rho);
-                tile_h_plane<K0 + 2, Cfg>(b, center, 2, sp, nth, dEp, bn, rho);
-                tile_h_plane<K0 + 3, Cfg>(b, center, 3, sp, nth, dEp, bn, rho);
+                const int cell = (ty + kTileHaloY) * G::BWH + tx + G::PXH;
+                if constexpr (J < kTileStages - 1) {
+                    constexpr int M0 = 2 * (J - kFgStages);  // pairs M0, M0 + 1
+#pragma unroll
+                    for (int d = 0; d < 2; ++d) {
+                        // the pair 2m, 2m + 1 (m = M0 + d) hops the same way
+                        constexpr int K0 = 2 * M0;
+                        const int K = K0 + 2 * d;
+                        const int src = d * G::H_PLANE + cell - hop13(K, 1) * G::BWH - hop13(K, 0);
+                        const float2 hv = *reinterpret_cast<const float2*>(b + 2 * src);
+                        if (d == 0) {
+                            acc_h<K0>((R)hv.x, sp, nth, dEp, bn, rho);
+                            acc_h<K0 + 1>((R)hv.y, sp, nth, dEp, bn, rho);
+                        } else {
+                            acc_h<K0 + 2>((R)hv.x, sp, nth, dEp, bn, rho);
+                            acc_h<K0 + 3>((R)hv.y, sp, nth, dEp, bn, rho);
+                        }
+                    }
+                } else {
+                    const R hv = (R)b[cell];
+                    sp[62 * nth] = hv;
+                    rho += hv;
+                }
             }
         }
         __syncthreads();  // every thread is done with buffer s (and has seen any abort)
@@ -658,7 +672,7 @@ __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, 
     } else {
         StreamAll<0, IS3D, Cfg>::run(A, o, c, sp, nth, Tm, Nm, Na);
         PullH<0, IS3D, Cfg>::run(A, o, c, sp, nth, dEp, bn, rho);
-        const R h24 = (R)A.hin[24 * A.stride + c];
+        const R h24 = (R)A.hin[h_elem(24, c, A.stride)];
         sp[62 * nth] = h24;
         rho += h24;
     }
@@ -927,16 +941,13 @@ __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, 
     EqCell<R> q;
     eq_cell(nw, n_dev, eps_dev, dE, dB, k, q);
     if (kOpenCode && relax_eq) SetEqFG<0, Cfg>::run(sp, nth, q);
-    CollideFG<0, Cfg, TILE>::run(A, c + dco, sp, nth, q, TILE ? tc->ofg + tid : nullptr);
+    CollideFG<0, Cfg>::run(A, c + dco, sp, nth, q);
     const bool em_coll = (A.flags & FLAG_NO_EM_COLLISION) == 0;
     // h_c - h_ref = 2 h^eq(E - Er, B - Br, J) - (h - h_ref)  (Eq. Maxwell-eq is linear)
     const int64_t co = c + dco;
-    CollideH<0, Cfg, TILE>::run(A, co, sp, nth, dE, dB, J, em_coll);
+    CollideH<0, Cfg>::run(A, co, sp, nth, dE, dB, J, em_coll);
     const R h24o = em_coll ? R(2) * nw.rho - sp[62 * nth] : sp[62 * nth];
-    if constexpr (TILE)
-        sp[62 * nth] = h24o;
-    else
-        A.hout[24 * A.stride + co] = (typename Cfg::hpop)h24o;
+    A.hout[h_elem(24, co, A.stride)] = (typename Cfg::hpop)h24o;
     auto stp = [&](int P, R v) {
         if constexpr (TILE)
             tc->pbuf[P * nth + tid] = (float)v;
@@ -1007,7 +1018,7 @@ template <class Cfg>
 __host__ __device__ constexpr size_t tile_smem_bytes(int seed)
 {
     return align128(step_cell_smem<Cfg, kTileThreads>(seed)) + (size_t)kRingStages * TileGeo<Cfg>::STAGE_BYTES +
-           TileGeo<Cfg>::PRIM_BYTES + (Cfg::kHalf ? align128(38u * kTileThreads * sizeof(typename Cfg::pop)) : 0) + 128;
+           TileGeo<Cfg>::PRIM_BYTES + 128;
 }
 
 // resident tile blocks per SM targeted: as many threads per SM as the per-cell kernel
@@ -1036,14 +1047,6 @@ __global__ void __launch_bounds__(kTileThreads, TileMinBlocks<Cfg, SEED>::value)
     off += (size_t)kRingStages * G::STAGE_BYTES;
     t.pbuf = reinterpret_cast<float*>(smem_raw + off);
     off += G::PRIM_BYTES;
-    // the output f, g tile: float32 overwrites the streamed values in their
-    // slots; float16 uses its own area after the primitives
-    if constexpr (Cfg::kHalf) {
-        t.ofg = reinterpret_cast<typename Cfg::pop*>(smem_raw + off);
-        off += align128(38u * kTileThreads * sizeof(typename Cfg::pop));
-    } else {
-        t.ofg = reinterpret_cast<typename Cfg::pop*>(smem_raw);
-    }
     t.bar = reinterpret_cast<uint64_t*>(smem_raw + off);
     t.abort = reinterpret_cast<int*>(t.bar + kRingStages + 1);
     t.M = &M;
@@ -1084,8 +1087,6 @@ __global__ void __launch_bounds__(kTileThreads, TileMinBlocks<Cfg, SEED>::value)
         fence_proxy_async_smem();  // the output tiles written by every thread, before the copies read them
         __syncthreads();
         if (tid == 0) {
-            tma_store_3d(&M.fg_out, t.ofg, t.x0, t.y0, 0);
-            tma_store_3d(&M.h_out, reinterpret_cast<const float*>(smem_raw) + 38 * kTileThreads, t.x0, t.y0, 0);
             tma_store_3d(&M.p_out, t.pbuf, t.x0, t.y0, 0);
             tma_store_commit();
         }

@@ -27,15 +27,18 @@ constexpr int kTileThreads = kTileW * kTileH;
 __host__ __device__ constexpr int tile_halo_x(int bytes) { return 16 / bytes; }
 
 // Tensor maps of one run of the tiled step for one input buffer (the other
-// buffer is the output). Boxes: fg_in (kTileW + 2 halo, kTileH + 4, 2, 2),
-// h_in (kTileW + 8, kTileH + 4, 4), p_in (kTileW, kTileH, 12); the outputs
-// (kTileW, kTileH, 38 | 25 | 12).
+// buffer is the output, written by the cells' own vector stores and, for the
+// primitives, by p_out). The population maps follow the group / pair storage
+// order: a row of the fluid groups is the 4 nx values (4 per cell) of one
+// group; boxes fg_in (4 (kTileW + 2 halo), kTileH + 4, 1 group), r_in (the
+// rest pairs: 2 (kTileW + 2 halo), kTileH + 4), h_in (2 (kTileW + 8), kTileH + 4,
+// 2 pairs), h24_in (kTileW + 8, kTileH + 4), p_in and p_out (kTileW, kTileH, 12).
 struct TileMaps {  // (aligned as CUtensorMap)
-    CUtensorMap fg_in;   // (x, y, direction 0..18, f | g) of the input f, g planes
-    CUtensorMap h_in;    // (x, y, k 0..24) input h
+    CUtensorMap fg_in;   // (4 x, y, group 0..8) input fluid groups
+    CUtensorMap r_in;    // (2 x, y) input rest pairs {f_0, g_0}
+    CUtensorMap h_in;    // (2 x, y, pair 0..11) input h pairs
+    CUtensorMap h24_in;  // (x, y) input h_24
     CUtensorMap p_in;    // (x, y, primitive 0..11) input primitives
-    CUtensorMap fg_out;  // (x, y, plane 0..37) output f then g
-    CUtensorMap h_out;   // (x, y, k) output h
     CUtensorMap p_out;   // (x, y, primitive) output primitives
 };
 
@@ -124,6 +127,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 }
 
 // 3-D / 4-D tile loads into shared memory, completing on *bar (byte count)
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, uint64_t* bar)
 {
     asm volatile(
