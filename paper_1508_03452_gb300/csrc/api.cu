@@ -21,7 +21,7 @@ struct RunState {
     int64_t N = 0, stride = 0;
     void* pops[2] = {nullptr, nullptr};  // f, g: 9 group planes of 4-vectors, then the rest pairs (fg_elem)
     void* h[2] = {nullptr, nullptr};     // h: 12 pair planes of 2-vectors, then h_24 (h_elem)
-    void* prim[2] = {nullptr, nullptr};  // 12 planes
+    void* prim[2] = {nullptr, nullptr};  // 3 planes of primitive 4-vectors (prim_elem)
     int cur = 0;
     bool initialized = false;
     lb::RefState ref{1.0, 4.0, 1.0};
@@ -337,7 +337,7 @@ void make_tile_maps(RunState& r, int run_index)
     const cuuint32_t box_r[2] = {2 * bwf, bh};
     const cuuint32_t box_h[3] = {2 * bwh, bh, 2};
     const cuuint32_t box_h24[2] = {bwh, bh};
-    const cuuint32_t box_p[3] = {lb::kTileW, lb::kTileH, (cuuint32_t)lb::NPRIM};
+    const cuuint32_t box_p[3] = {4 * lb::kTileW, lb::kTileH, (cuuint32_t)lb::kPrimVecs};
     std::vector<lb::TileMaps> maps(2);
     bool ok = true;
     for (int in = 0; in < 2 && ok; ++in) {
@@ -349,8 +349,8 @@ void make_tile_maps(RunState& r, int run_index)
         ok = ok && encode_map(&m.r_in, pdt, pb, fg + lb::fg_elem(0, 0, 0, r.stride) * pb, 2, r, 2, 1, box_r);
         ok = ok && encode_map(&m.h_in, fdt, 4, hh, 3, r, 2, 12, box_h);
         ok = ok && encode_map(&m.h24_in, fdt, 4, hh + lb::h_elem(24, 0, r.stride) * 4, 2, r, 1, 1, box_h24);
-        ok = ok && encode_map(&m.p_in, fdt, 4, r.prim[in], 3, r, 1, lb::NPRIM, box_p);
-        ok = ok && encode_map(&m.p_out, fdt, 4, r.prim[out], 3, r, 1, lb::NPRIM, box_p);
+        ok = ok && encode_map(&m.p_in, fdt, 4, r.prim[in], 3, r, 4, lb::kPrimVecs, box_p);
+        ok = ok && encode_map(&m.p_out, fdt, 4, r.prim[out], 3, r, 4, lb::kPrimVecs, box_p);
     }
     if (!ok) return;
     // the 32 x 4 tiles outside the rectangle of interior tiles, as (run, x0, y0, 0)
@@ -747,9 +747,7 @@ int init_run(lbrmhd_handle h, RunState& r, const lb::InitInputs& in)
     LB_CK(cudaMemsetAsync(r.d_stats, 0, kStatsAlloc, h->stream));
     LB_CK(cudaStreamSynchronize(h->stream));
     if (bad) return fail(h, LBRMHD_ERR_BAD_ARG, "initial state has |u| >= c or n <= 0");
-    const size_t qb = sizeof(typename Cfg::prim);
-    LB_CK(cudaMemcpyAsync(r.d_ez0, (const char*)r.prim[r.cur] + (size_t)(lb::P_E + 2) * r.stride * qb, r.N * qb,
-                          cudaMemcpyDeviceToDevice, h->stream));
+    LB_CK(lb::launch_prim_component<Cfg>(view<Cfg>(r, r.cur), lb::P_E + 2, (typename Cfg::prim*)r.d_ez0, h->stream));
     if (capped(r)) LB_CK(lb::launch_umax_state<Cfg>(view<Cfg>(r, r.cur), r.d_umax, h->stream));
     r.initialized = true;
     runs_changed(h);
@@ -1060,10 +1058,8 @@ int relax_run(lbrmhd_handle h, RunState& r, int max_iters, double tol, int* iter
         r.cur = start;
     }
     // a fresh start: counters, step count, E^z_0, the cut-off's maximum
-    const size_t qb = sizeof(typename Cfg::prim);
     LB_CK(cudaMemsetAsync(r.d_stats, 0, kStatsAlloc, h->stream));
-    LB_CK(cudaMemcpyAsync(r.d_ez0, (const char*)r.prim[r.cur] + (size_t)(lb::P_E + 2) * r.stride * qb, r.N * qb,
-                          cudaMemcpyDeviceToDevice, h->stream));
+    LB_CK(lb::launch_prim_component<Cfg>(view<Cfg>(r, r.cur), lb::P_E + 2, (typename Cfg::prim*)r.d_ez0, h->stream));
     if (capped(r)) LB_CK(lb::launch_umax_state<Cfg>(view<Cfg>(r, r.cur), r.d_umax, h->stream));
     LB_CK(cudaStreamSynchronize(h->stream));
     r.steps = 0;
@@ -1512,9 +1508,9 @@ int lbrmhd_get_state(lbrmhd_handle h, void* host_buf, size_t bytes)
                                   h->stream));
             o += sg.count * hb;
         }
-        for (int pl = 0; pl < lb::NPRIM; ++pl, o += r.N * hb)
-            LB_CK(cudaMemcpyAsync(o, (char*)r.prim[r.cur] + pl * r.stride * hb, r.N * hb, cudaMemcpyDeviceToHost,
-                                  h->stream));
+        for (int q = 0; q < lb::kPrimVecs; ++q, o += 4 * r.N * hb)
+            LB_CK(cudaMemcpyAsync(o, (char*)r.prim[r.cur] + lb::prim_elem(4 * q, 0, r.stride) * hb, 4 * r.N * hb,
+                                  cudaMemcpyDeviceToHost, h->stream));
         LB_CK(cudaMemcpyAsync(o, r.d_ez0, r.N * hb, cudaMemcpyDeviceToHost, h->stream));
         o += r.N * hb;
     }
@@ -1552,9 +1548,9 @@ int lbrmhd_set_state(lbrmhd_handle h, const void* host_buf, size_t bytes)
                                   h->stream));
             o += sg.count * hb;
         }
-        for (int pl = 0; pl < lb::NPRIM; ++pl, o += r.N * hb)
-            LB_CK(cudaMemcpyAsync((char*)r.prim[r.cur] + pl * r.stride * hb, o, r.N * hb, cudaMemcpyHostToDevice,
-                                  h->stream));
+        for (int q = 0; q < lb::kPrimVecs; ++q, o += 4 * r.N * hb)
+            LB_CK(cudaMemcpyAsync((char*)r.prim[r.cur] + lb::prim_elem(4 * q, 0, r.stride) * hb, o, 4 * r.N * hb,
+                                  cudaMemcpyHostToDevice, h->stream));
         LB_CK(cudaMemcpyAsync(r.d_ez0, o, r.N * hb, cudaMemcpyHostToDevice, h->stream));
         o += r.N * hb;
         const int rc2 = refresh_umax(h, r);

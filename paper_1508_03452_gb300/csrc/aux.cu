@@ -17,28 +17,28 @@ __device__ __forceinline__ void load_prim(const typename Cfg::prim* P, int64_t s
                                           Prim<typename Cfg::real>& s)
 {
     using R = typename Cfg::real;
-    s.n = (R)P[P_N * stride + c];
-    s.eps = (R)P[P_EPS * stride + c];
+    s.n = (R)P[prim_elem(P_N, c, stride)];
+    s.eps = (R)P[prim_elem(P_EPS, c, stride)];
     for (int a = 0; a < 3; ++a) {
-        s.u[a] = (R)P[(P_U + a) * stride + c];
-        s.E[a] = (R)P[(P_E + a) * stride + c];
-        s.B[a] = (R)P[(P_B + a) * stride + c];
+        s.u[a] = (R)P[prim_elem(P_U + a, c, stride)];
+        s.E[a] = (R)P[prim_elem(P_E + a, c, stride)];
+        s.B[a] = (R)P[prim_elem(P_B + a, c, stride)];
     }
-    s.rho = (R)P[P_RHO * stride + c];
+    s.rho = (R)P[prim_elem(P_RHO, c, stride)];
 }
 
 template <class Cfg, class R>
 __device__ __forceinline__ void store_prim(typename Cfg::prim* P, int64_t stride, int64_t c, const Prim<R>& s)
 {
     using T = typename Cfg::prim;
-    P[P_N * stride + c] = (T)s.n;
-    P[P_EPS * stride + c] = (T)s.eps;
+    P[prim_elem(P_N, c, stride)] = (T)s.n;
+    P[prim_elem(P_EPS, c, stride)] = (T)s.eps;
     for (int a = 0; a < 3; ++a) {
-        P[(P_U + a) * stride + c] = (T)s.u[a];
-        P[(P_E + a) * stride + c] = (T)s.E[a];
-        P[(P_B + a) * stride + c] = (T)s.B[a];
+        P[prim_elem(P_U + a, c, stride)] = (T)s.u[a];
+        P[prim_elem(P_E + a, c, stride)] = (T)s.E[a];
+        P[prim_elem(P_B + a, c, stride)] = (T)s.B[a];
     }
-    P[P_RHO * stride + c] = (T)s.rho;
+    P[prim_elem(P_RHO, c, stride)] = (T)s.rho;
 }
 
 template <int I, class Cfg, class R>
@@ -249,7 +249,7 @@ __global__ void bfix_kernel(PopView<Cfg> V, Phys<typename Cfg::real> k, int a, i
         int rp[3] = {r1[0], r1[1], r1[2]}, rm[3] = {r1[0], r1[1], r1[2]};
         rp[ax] = wrap_coord(r1[ax] + 1, n[ax], V.periodic[ax]);
         rm[ax] = wrap_coord(r1[ax] - 1, n[ax], V.periodic[ax]);
-        tang += ((R)V.prim[(P_B + ax) * V.stride + idx(rp)] - (R)V.prim[(P_B + ax) * V.stride + idx(rm)]) /
+        tang += ((R)V.prim[prim_elem(P_B + ax, idx(rp), V.stride)] - (R)V.prim[prim_elem(P_B + ax, idx(rm), V.stride)]) /
                 (R(2) * k.dx);
     }
     int r2[3] = {q[0], q[1], q[2]};
@@ -257,7 +257,7 @@ __global__ void bfix_kernel(PopView<Cfg> V, Phys<typename Cfg::real> k, int a, i
     int rb[3] = {q[0], q[1], q[2]};
     rb[a] = b;
     const int64_t cb = idx(rb);
-    const R Bfar = (R)V.prim[(P_B + a) * V.stride + idx(r2)];
+    const R Bfar = (R)V.prim[prim_elem(P_B + a, idx(r2), V.stride)];
     const R Bn_new = Bfar + R(sgn) * R(2) * k.dx * tang;
     Prim<R> so;
     load_prim<Cfg>(V.prim, V.stride, cb, so);
@@ -273,7 +273,7 @@ __global__ void bfix_kernel(PopView<Cfg> V, Phys<typename Cfg::real> k, int a, i
     const R dB = Bn_new - so.B[a];
     Prim<R> sn = so;
     sn.B[a] = Bn_new;
-    V.prim[(P_B + a) * V.stride + cb] = (typename Cfg::prim)Bn_new;
+    V.prim[prim_elem(P_B + a, cb, V.stride)] = (typename Cfg::prim)Bn_new;
     // h: populations of the plane whose normal is axis a, b = -/+ o_p n_hat
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -329,6 +329,16 @@ __global__ void drive_kernel(PopView<Cfg> V, Phys<typename Cfg::real> k, int lay
 // ---------------------------------------------------------------------------
 // outputs
 // ---------------------------------------------------------------------------
+// component P of every cell's primitives into out (N values)
+template <class Cfg>
+__global__ void prim_component_kernel(PopView<Cfg> V, int P, typename Cfg::prim* out)
+{
+    const int64_t N = (int64_t)V.nx * V.ny * V.nz;
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c < N) out[c] = V.prim[prim_elem(P, c, V.stride)];
+}
+
+
 template <class Cfg>
 __global__ void moments_kernel(PopView<Cfg> V, Phys<double> k, double* out)
 {
@@ -336,14 +346,18 @@ __global__ void moments_kernel(PopView<Cfg> V, Phys<double> k, double* out)
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (c >= N) return;
     Prim<double> s;
-    s.n = (double)V.prim[P_N * V.stride + c];
-    s.eps = (double)V.prim[P_EPS * V.stride + c];
-    for (int a = 0; a < 3; ++a) {
-        s.u[a] = (double)V.prim[(P_U + a) * V.stride + c];
-        s.E[a] = (double)V.prim[(P_E + a) * V.stride + c];
-        s.B[a] = (double)V.prim[(P_B + a) * V.stride + c];
+    {
+        typename Cfg::real pv[NPRIM];
+        ld_prims<Cfg>(V.prim + prim_elem(0, c, V.stride), V.stride, pv);
+        s.n = (double)pv[P_N];
+        s.eps = (double)pv[P_EPS];
+        for (int a = 0; a < 3; ++a) {
+            s.u[a] = (double)pv[P_U + a];
+            s.E[a] = (double)pv[P_E + a];
+            s.B[a] = (double)pv[P_B + a];
+        }
+        s.rho = (double)pv[P_RHO];
     }
-    s.rho = (double)V.prim[P_RHO * V.stride + c];
     double J[3];
     ohm_current(s.E, s.u, s.B, s.rho, k, J);
     out[0 * N + c] = s.n;
@@ -421,7 +435,11 @@ __global__ void diag_kernel(PopView<Cfg> V, Phys<double> k, RefState r, double* 
             rho += hi;
         }
 #pragma unroll
-        for (int i = 0; i < NPRIM; ++i) bad = bad || !isfinite((R)V.prim[(int64_t)i * V.stride + c]);
+        {
+            R pv[NPRIM];
+            ld_prims<Cfg>(V.prim + prim_elem(0, c, V.stride), V.stride, pv);
+            for (int i = 0; i < NPRIM; ++i) bad = bad || !isfinite(pv[i]);
+        }
         const int q[3] = {(int)(c % V.nx), (int)((c / V.nx) % V.ny), (int)(c / ((int64_t)V.nx * V.ny))};
         const int n[3] = {V.nx, V.ny, V.nz};
         R div = R(0);
@@ -432,7 +450,7 @@ __global__ void diag_kernel(PopView<Cfg> V, Phys<double> k, RefState r, double* 
             qm[a] = wrap_coord(q[a] - 1, n[a], V.periodic[a]);
             const int64_t ip = qp[0] + (int64_t)V.nx * (qp[1] + (int64_t)V.ny * qp[2]);
             const int64_t im = qm[0] + (int64_t)V.nx * (qm[1] + (int64_t)V.ny * qm[2]);
-            div += (R)V.prim[(P_B + a) * V.stride + ip] - (R)V.prim[(P_B + a) * V.stride + im];
+            div += (R)V.prim[prim_elem(P_B + a, ip, V.stride)] - (R)V.prim[prim_elem(P_B + a, im, V.stride)];
         }
         div = div / (R(2) * (R)k.dx);
         w[0] = N0;
@@ -531,7 +549,7 @@ __global__ void null_partial_kernel(PopView<Cfg> V, int y_lo, int y_hi, double* 
     long long i = LLONG_MAX;
     if (t < nb) {
         const long long c = (long long)y_lo * V.nx + t;
-        const double bx = (double)V.prim[P_B * V.stride + c], by = (double)V.prim[(P_B + 1) * V.stride + c];
+        const double bx = (double)V.prim[prim_elem(P_B, c, V.stride)], by = (double)V.prim[prim_elem(P_B + 1, c, V.stride)];
         const double b2 = __dadd_rn(__dmul_rn(bx, bx), __dmul_rn(by, by));  // no FMA: rounds as written
         if (b2 == b2) {  // NaN never wins
             v = b2;
@@ -557,7 +575,7 @@ __global__ void null_final_kernel(const double* part_v, const long long* part_i,
     if (threadIdx.x == 0) {
         const int64_t N = (int64_t)V.nx * V.ny;
         if (i >= 0 && i < N) {
-            const double ez = (double)V.prim[(P_E + 2) * V.stride + i];
+            const double ez = (double)V.prim[prim_elem(P_E + 2, i, V.stride)];
             out[0] = (ez - (double)ez0[i]) / B0;
             out[1] = (double)(i % V.nx);
             out[2] = (double)(i / V.nx);
@@ -630,6 +648,14 @@ cudaError_t launch_moments(const PopView<Cfg>& V, const Phys<double>& k, double*
 }
 
 template <class Cfg>
+cudaError_t launch_prim_component(const PopView<Cfg>& V, int P, typename Cfg::prim* out, cudaStream_t s)
+{
+    const int64_t N = (int64_t)V.nx * V.ny * V.nz;
+    prim_component_kernel<Cfg><<<blocks_for(N, 256), 256, 0, s>>>(V, P, out);
+    return cudaGetLastError();
+}
+
+template <class Cfg>
 cudaError_t launch_populations(const PopView<Cfg>& V, const RefPops& ref, double* f, double* g, double* h,
                                cudaStream_t s)
 {
@@ -673,7 +699,7 @@ __global__ void umax_state_kernel(PopView<Cfg> V, double* out)
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
         double u2 = 0.0;
         for (int a = 0; a < 3; ++a) {
-            const double u = (double)V.prim[(P_U + a) * V.stride + c];
+            const double u = (double)V.prim[prim_elem(P_U + a, c, V.stride)];
             u2 += u * u;
         }
         m = fmax(m, u2);
@@ -698,7 +724,7 @@ __global__ void relax_history_kernel(PopView<Cfg> V, double* e)
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (c >= N) return;
     for (int a = 0; a < 3; ++a) {
-        const double E = (double)V.prim[(P_E + a) * V.stride + c];
+        const double E = (double)V.prim[prim_elem(P_E + a, c, V.stride)];
         e[a * N + c] = E;
         e[(3 + a) * N + c] = E;
     }
@@ -735,6 +761,7 @@ cudaError_t launch_relax_history(const PopView<Cfg>& V, double* e, cudaStream_t 
     template cudaError_t launch_boundaries<CFG>(const PopView<CFG>&, const Phys<CFG::real>&, const int*, int,      \
                                                 const double*, cudaStream_t);                                      \
     template cudaError_t launch_moments<CFG>(const PopView<CFG>&, const Phys<double>&, double*, cudaStream_t);     \
+    template cudaError_t launch_prim_component<CFG>(const PopView<CFG>&, int, CFG::prim*, cudaStream_t);           \
     template cudaError_t launch_populations<CFG>(const PopView<CFG>&, const RefPops&, double*, double*, double*,  \
                                                  cudaStream_t);                                                    \
     template cudaError_t launch_diag<CFG>(const PopView<CFG>&, const Phys<double>&, const RefState&, double*,      \

@@ -105,6 +105,9 @@ cudaError_t launch_boundaries(const PopView<Cfg>& V, const Phys<typename Cfg::re
 cudaError_t launch_drive_profile(int nx, int ny, double u0, double* uv, cudaStream_t s);
 template <class Cfg>
 cudaError_t launch_moments(const PopView<Cfg>& V, const Phys<double>& k, double* out, cudaStream_t s);
+// primitive component P (a P_ index) of every cell into out (N values of the primitive type)
+template <class Cfg>
+cudaError_t launch_prim_component(const PopView<Cfg>& V, int P, typename Cfg::prim* out, cudaStream_t s);
 // max |u|^2 of a state into out[0], out[1] = 0 (body-force cut-off)
 template <class Cfg>
 cudaError_t launch_umax_state(const PopView<Cfg>& V, double* out, cudaStream_t s);

@@ -37,8 +37,15 @@ struct CfgF16 {  // float16 relative deviations for f and g
     static constexpr bool kHalf = true;
 };
 
-// primitive planes
+// primitive fields, stored as three 4-vectors per cell: {n, eps, u_x, u_y},
+// {u_z, E_x, E_y, E_z}, {B_x, B_y, B_z, rho_c} (vector P / 4 of the cell,
+// component P % 4; three planes of `stride` 4-vectors)
 enum { P_N = 0, P_EPS = 1, P_U = 2, P_E = 5, P_B = 8, P_RHO = 11, NPRIM = 12 };
+constexpr int kPrimVecs = NPRIM / 4;
+__host__ __device__ constexpr int64_t prim_elem(int P, int64_t c, int64_t stride)
+{
+    return 4 * ((P >> 2) * stride + c) + (P & 3);
+}
 
 // Storage order of the populations of one buffer (every plane holds `stride`
 // cells). Fluid: the opposite D3Q19 directions i = 2G-1 and 2G (G = 1..9)
@@ -260,6 +267,42 @@ __device__ __forceinline__ V2<typename Cfg::real> ld_pair_sh(const typename Cfg:
     } else {
         const float2 a = *reinterpret_cast<const float2*>(p);
         return {a.x, a.y};
+    }
+}
+
+// the three primitive 4-vectors of a cell (p at its first element of plane 0)
+// as 12 values in the order of the P_ indices; the planes are 4 stride apart
+template <class Cfg>
+__device__ __forceinline__ void ld_prims(const typename Cfg::prim* p, int64_t stride, typename Cfg::real (&v)[NPRIM])
+{
+    using R = typename Cfg::real;
+#pragma unroll
+    for (int q = 0; q < kPrimVecs; ++q) {
+        const typename Cfg::prim* pq = p + 4 * q * stride;
+        if constexpr (sizeof(typename Cfg::prim) == 8) {
+            const double2 a = __ldg(reinterpret_cast<const double2*>(pq));
+            const double2 b = __ldg(reinterpret_cast<const double2*>(pq) + 1);
+            v[4 * q] = (R)a.x, v[4 * q + 1] = (R)a.y, v[4 * q + 2] = (R)b.x, v[4 * q + 3] = (R)b.y;
+        } else {
+            const float4 a = __ldg(reinterpret_cast<const float4*>(pq));
+            v[4 * q] = (R)a.x, v[4 * q + 1] = (R)a.y, v[4 * q + 2] = (R)a.z, v[4 * q + 3] = (R)a.w;
+        }
+    }
+}
+
+template <class Cfg>
+__device__ __forceinline__ void st_prims(typename Cfg::prim* p, int64_t stride, const typename Cfg::real (&v)[NPRIM])
+{
+#pragma unroll
+    for (int q = 0; q < kPrimVecs; ++q) {
+        typename Cfg::prim* pq = p + 4 * q * stride;
+        if constexpr (sizeof(typename Cfg::prim) == 8) {
+            reinterpret_cast<double2*>(pq)[0] = make_double2(v[4 * q], v[4 * q + 1]);
+            reinterpret_cast<double2*>(pq)[1] = make_double2(v[4 * q + 2], v[4 * q + 3]);
+        } else {
+            *reinterpret_cast<float4*>(pq) =
+                make_float4((float)v[4 * q], (float)v[4 * q + 1], (float)v[4 * q + 2], (float)v[4 * q + 3]);
+        }
     }
 }
 

@@ -494,7 +494,7 @@ struct TileGeo {
 template <class Cfg>
 struct TileCtx {
     unsigned char* ring;  // kRingStages x STAGE_BYTES
-    float* pbuf;          // [NPRIM][kTileThreads]: input primitives, then the output ones
+    float* pbuf;          // [3][kTileThreads][4]: input primitive 4-vectors, then the output ones
     uint64_t* bar;        // kRingStages ring barriers, then the primitives' barrier
     int* abort;           // set when a wait ran out: the whole block then stops
     const TileMaps* M;
@@ -679,20 +679,32 @@ __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, 
     // previous primitives (the tile path's box has arrived with the last stage)
     auto ldp = [&](int P) -> R {
         if constexpr (TILE)
-            return (R)tc->pbuf[P * nth + tid];
+            return (R)tc->pbuf[4 * ((P >> 2) * nth + tid) + (P & 3)];
         else
-            return (R)A.pin[P * A.stride + c];
+            return (R)A.pin[prim_elem(P, c, A.stride)];
     };
 
     // previous primitives used by the recovery
     Prim<R> old;
-    old.n = ldp(P_N);
-    old.eps = ldp(P_EPS);
+    {
+        R pv[NPRIM];
+        if constexpr (TILE) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        old.u[a] = ldp(P_U + a);
-        old.E[a] = ldp(P_E + a);
-        old.B[a] = ldp(P_B + a);
+            for (int q = 0; q < kPrimVecs; ++q) {
+                const float4 a = reinterpret_cast<const float4*>(tc->pbuf)[q * nth + tid];
+                pv[4 * q] = (R)a.x, pv[4 * q + 1] = (R)a.y, pv[4 * q + 2] = (R)a.z, pv[4 * q + 3] = (R)a.w;
+            }
+        } else {
+            ld_prims<Cfg>(A.pin + prim_elem(0, c, A.stride), A.stride, pv);
+        }
+        old.n = pv[P_N];
+        old.eps = pv[P_EPS];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            old.u[a] = pv[P_U + a];
+            old.E[a] = pv[P_E + a];
+            old.B[a] = pv[P_B + a];
+        }
     }
     old.rho = R(0);
     if constexpr (kOpenCode) {
@@ -780,11 +792,14 @@ __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, 
     R rho_j = rho;
     if (!TILE && (A.flags & FLAG_GAUSS_CHARGE)) {
         R div = R(0);
-        if (A.nx > 1) div += (R)A.pin[P_E * A.stride + c + o.x[3]] - (R)A.pin[P_E * A.stride + c + o.x[1]];
+        if (A.nx > 1)
+            div += (R)A.pin[prim_elem(P_E, c + o.x[3], A.stride)] - (R)A.pin[prim_elem(P_E, c + o.x[1], A.stride)];
         if (A.ny > 1)
-            div += (R)A.pin[(P_E + 1) * A.stride + c + o.y[3]] - (R)A.pin[(P_E + 1) * A.stride + c + o.y[1]];
+            div += (R)A.pin[prim_elem(P_E + 1, c + o.y[3], A.stride)] -
+                   (R)A.pin[prim_elem(P_E + 1, c + o.y[1], A.stride)];
         if (IS3D && A.nz > 1)
-            div += (R)A.pin[(P_E + 2) * A.stride + c + o.z[3]] - (R)A.pin[(P_E + 2) * A.stride + c + o.z[1]];
+            div += (R)A.pin[prim_elem(P_E + 2, c + o.z[3], A.stride)] -
+                   (R)A.pin[prim_elem(P_E + 2, c + o.z[1], A.stride)];
         rho_j = k.eps0 * div / (R(2) * k.dx);
     }
     const bool one_pass = (A.flags & FLAG_ONE_PASS_RECOVERY) != 0;
@@ -948,21 +963,26 @@ __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, 
     CollideH<0, Cfg>::run(A, co, sp, nth, dE, dB, J, em_coll);
     const R h24o = em_coll ? R(2) * nw.rho - sp[62 * nth] : sp[62 * nth];
     A.hout[h_elem(24, co, A.stride)] = (typename Cfg::hpop)h24o;
-    auto stp = [&](int P, R v) {
-        if constexpr (TILE)
-            tc->pbuf[P * nth + tid] = (float)v;
-        else
-            A.pout[P * A.stride + co] = (typename Cfg::prim)v;
-    };
-    stp(P_N, nw.n);
-    stp(P_EPS, nw.eps);
+    {
+        R pv[NPRIM];
+        pv[P_N] = nw.n;
+        pv[P_EPS] = nw.eps;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        stp(P_U + a, nw.u[a]);
-        stp(P_E + a, nw.E[a]);
-        stp(P_B + a, nw.B[a]);
+        for (int a = 0; a < 3; ++a) {
+            pv[P_U + a] = nw.u[a];
+            pv[P_E + a] = nw.E[a];
+            pv[P_B + a] = nw.B[a];
+        }
+        pv[P_RHO] = nw.rho;
+        if constexpr (TILE) {
+#pragma unroll
+            for (int q = 0; q < kPrimVecs; ++q)
+                reinterpret_cast<float4*>(tc->pbuf)[q * nth + tid] =
+                    make_float4((float)pv[4 * q], (float)pv[4 * q + 1], (float)pv[4 * q + 2], (float)pv[4 * q + 3]);
+        } else {
+            st_prims<Cfg>(A.pout + prim_elem(0, co, A.stride), A.stride, pv);
+        }
     }
-    stp(P_RHO, nw.rho);
 
     // recovery counters, aggregated per warp
     const unsigned mask = __activemask();
@@ -1073,7 +1093,7 @@ __global__ void __launch_bounds__(kTileThreads, TileMinBlocks<Cfg, SEED>::value)
             // (issued as the previous tile's last stages were consumed)
             if (k > 0) tma_store_wait_read();
             mbar_arrive_expect_tx(&t.bar[kRingStages], G::PRIM_BYTES);
-            tma_load_3d(t.pbuf, &M.p_in, t.x0, t.y0, 0, &t.bar[kRingStages]);
+            tma_load_3d(t.pbuf, &M.p_in, 4 * t.x0, t.y0, 0, &t.bar[kRingStages]);
             if (k == 0)
                 for (int j = 0; j < kRingStages; ++j) tile_issue<Cfg>(t, j, t.x0, t.y0, j);
         }
@@ -1087,7 +1107,7 @@ __global__ void __launch_bounds__(kTileThreads, TileMinBlocks<Cfg, SEED>::value)
         fence_proxy_async_smem();  // the output tiles written by every thread, before the copies read them
         __syncthreads();
         if (tid == 0) {
-            tma_store_3d(&M.p_out, t.pbuf, t.x0, t.y0, 0);
+            tma_store_3d(&M.p_out, t.pbuf, 4 * t.x0, t.y0, 0);
             tma_store_commit();
         }
     }

@@ -32,14 +32,15 @@ __host__ __device__ constexpr int tile_halo_x(int bytes) { return 16 / bytes; }
 // order: a row of the fluid groups is the 4 nx values (4 per cell) of one
 // group; boxes fg_in (4 (kTileW + 2 halo), kTileH + 4, 1 group), r_in (the
 // rest pairs: 2 (kTileW + 2 halo), kTileH + 4), h_in (2 (kTileW + 8), kTileH + 4,
-// 2 pairs), h24_in (kTileW + 8, kTileH + 4), p_in and p_out (kTileW, kTileH, 12).
+// 2 pairs), h24_in (kTileW + 8, kTileH + 4), p_in and p_out (4 kTileW, kTileH, 3: the
+// primitives' three 4-vectors).
 struct TileMaps {  // (aligned as CUtensorMap)
     CUtensorMap fg_in;   // (4 x, y, group 0..8) input fluid groups
     CUtensorMap r_in;    // (2 x, y) input rest pairs {f_0, g_0}
     CUtensorMap h_in;    // (2 x, y, pair 0..11) input h pairs
     CUtensorMap h24_in;  // (x, y) input h_24
-    CUtensorMap p_in;    // (x, y, primitive 0..11) input primitives
-    CUtensorMap p_out;   // (x, y, primitive) output primitives
+    CUtensorMap p_in;    // (4 x, y, vector 0..2) input primitives
+    CUtensorMap p_out;   // (4 x, y, vector) output primitives
 };
 
 // The tiles of a grid whose input boxes lie inside it: tiles (i, j),
