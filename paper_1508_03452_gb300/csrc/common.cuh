@@ -21,6 +21,7 @@ struct CfgF64 {
     using hpop = double;
     using prim = double;
     static constexpr bool kHalf = false;
+    static constexpr bool kVecSlots = true;  // shared-memory slot order of the step kernel
 };
 struct CfgF32 {
     using real = float;
@@ -28,6 +29,7 @@ struct CfgF32 {
     using hpop = float;
     using prim = float;
     static constexpr bool kHalf = false;
+    static constexpr bool kVecSlots = true;  // shared-memory slot order of the step kernel
 };
 struct CfgF16 {  // float16 relative deviations for f and g
     using real = float;
@@ -35,6 +37,7 @@ struct CfgF16 {  // float16 relative deviations for f and g
     using hpop = float;
     using prim = float;
     static constexpr bool kHalf = true;
+    static constexpr bool kVecSlots = false;  // shared-memory slot order of the step kernel
 };
 
 // primitive fields, stored as three 4-vectors per cell: {n, eps, u_x, u_y},

@@ -160,65 +160,181 @@ __device__ __forceinline__ V2<typename Cfg::real> rest_pair(V2<typename Cfg::rea
     return v;
 }
 
+// Shared-memory slots of one thread's streamed (pre-collision) populations.
+// Vector order (VEC; t: the thread's index in its block of nth threads): fluid
+// group G (1..9) as a 4-vector at element 4 ((G - 1) nth + t), the rest pair
+// {f_0, g_0} at 36 nth + 2 t, Maxwell pair m (0..11) at 38 nth + 2 (m nth + t),
+// h_24 at 62 nth + t, so that a group or pair is one vector access. Row order
+// (!VEC): one row of nth values per population, f_i in row i, g_i in 19 + i,
+// h_k in 38 + k (float16 storage runs faster with it: fewer registers live
+// around the vector accesses).
+template <class R, bool VEC>
+struct Slots {
+    R* b;
+    int nth, t;
+    __device__ __forceinline__ R* f(int i) const
+    {
+        if constexpr (VEC)
+            return i == 0 ? b + 36 * nth + 2 * t : b + 4 * (((i - 1) >> 1) * nth + t) + 2 * ((i - 1) & 1);
+        else
+            return b + i * nth + t;
+    }
+    __device__ __forceinline__ R* g(int i) const
+    {
+        if constexpr (VEC)
+            return f(i) + 1;
+        else
+            return b + (19 + i) * nth + t;
+    }
+    __device__ __forceinline__ R* h(int k) const
+    {
+        if constexpr (VEC)
+            return k < 24 ? b + 38 * nth + 2 * ((k >> 1) * nth + t) + (k & 1) : b + 62 * nth + t;
+        else
+            return b + (38 + k) * nth + t;
+    }
+};
+
+// the slots of a storage configuration
+template <class Cfg>
+using CfgSlots = Slots<typename Cfg::real, Cfg::kVecSlots>;
+
+template <class R>
+__device__ __forceinline__ void st_v4(R* p, const V4<R>& v)
+{
+    if constexpr (sizeof(R) == 8) {
+        reinterpret_cast<double2*>(p)[0] = make_double2(v.x, v.y);
+        reinterpret_cast<double2*>(p)[1] = make_double2(v.z, v.w);
+    } else {
+        *reinterpret_cast<float4*>(p) = make_float4(v.x, v.y, v.z, v.w);
+    }
+}
+template <class R>
+__device__ __forceinline__ V4<R> ld_v4(const R* p)
+{
+    if constexpr (sizeof(R) == 8) {
+        const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+        return {a.x, a.y, b.x, b.y};
+    } else {
+        const float4 a = *reinterpret_cast<const float4*>(p);
+        return {a.x, a.y, a.z, a.w};
+    }
+}
+template <class R>
+__device__ __forceinline__ void st_v2(R* p, R x, R y)
+{
+    if constexpr (sizeof(R) == 8)
+        *reinterpret_cast<double2*>(p) = make_double2(x, y);
+    else
+        *reinterpret_cast<float2*>(p) = make_float2(x, y);
+}
+template <class R>
+__device__ __forceinline__ V2<R> ld_v2(const R* p)
+{
+    if constexpr (sizeof(R) == 8) {
+        const double2 a = *reinterpret_cast<const double2*>(p);
+        return {a.x, a.y};
+    } else {
+        const float2 a = *reinterpret_cast<const float2*>(p);
+        return {a.x, a.y};
+    }
+}
+
+// group G (f_I, g_I, f_J, g_J), the rest pair and Maxwell pair m in the slots
+template <class R, bool VEC>
+__device__ __forceinline__ void put_group(const Slots<R, VEC>& S, int G, const V4<R>& v)
+{
+    if constexpr (VEC) {
+        st_v4(S.f(2 * G - 1), v);
+    } else {
+        *S.f(2 * G - 1) = v.x;
+        *S.g(2 * G - 1) = v.y;
+        *S.f(2 * G) = v.z;
+        *S.g(2 * G) = v.w;
+    }
+}
+template <class R, bool VEC>
+__device__ __forceinline__ V4<R> get_group(const Slots<R, VEC>& S, int G)
+{
+    if constexpr (VEC)
+        return ld_v4(S.f(2 * G - 1));
+    else
+        return {*S.f(2 * G - 1), *S.g(2 * G - 1), *S.f(2 * G), *S.g(2 * G)};
+}
+template <class R, bool VEC>
+__device__ __forceinline__ void put_pair(R* a, R* b, R x, R y)
+{
+    if constexpr (VEC) {
+        st_v2(a, x, y);
+    } else {
+        *a = x;
+        *b = y;
+    }
+}
+template <class R, bool VEC>
+__device__ __forceinline__ V2<R> get_pair(const R* a, const R* b)
+{
+    if constexpr (VEC)
+        return ld_v2(a);
+    else
+        return {*a, *b};
+}
+
 // slots and moments of the streamed populations of group G (G = 0: the rest pair in v.x, v.y)
 template <int G, class Cfg>
-__device__ __forceinline__ void store_group(const V4<typename Cfg::real>& v, typename Cfg::real* sp, int nth,
+__device__ __forceinline__ void store_group(const V4<typename Cfg::real>& v, const CfgSlots<Cfg>& S,
                                             typename Cfg::real (&Tm)[10], typename Cfg::real& Nm,
                                             typename Cfg::real (&Na)[3])
 {
     if constexpr (G == 0) {
-        sp[0] = v.x;
-        sp[19 * nth] = v.y;
+        put_pair<typename Cfg::real, Cfg::kVecSlots>(S.f(0), S.g(0), v.x, v.y);
         acc_fg<0>(v.x, v.y, Tm, Nm, Na);
     } else {
         constexpr int I = 2 * G - 1, J = 2 * G;
-        sp[I * nth] = v.x;
-        sp[(19 + I) * nth] = v.y;
+        put_group(S, G, v);
         acc_fg<I>(v.x, v.y, Tm, Nm, Na);
-        sp[J * nth] = v.z;
-        sp[(19 + J) * nth] = v.w;
         acc_fg<J>(v.z, v.w, Tm, Nm, Na);
     }
 }
 
 // Streams f and g group by group (G onwards; G = 0 is the rest pair) into the
-// shared-memory buffer `sp` (slot i for f_i, 19 + i for g_i) and accumulates
-// their moments in the order of the populations.
+// shared-memory slots and accumulates their moments in the order of the
+// populations.
 template <int G, bool IS3D, class Cfg>
 struct StreamAll {
     using R = typename Cfg::real;
-    static __device__ __forceinline__ void run(const StepArgs<Cfg>& A, const Off& o, int64_t c, R* sp, int nth,
+    static __device__ __forceinline__ void run(const StepArgs<Cfg>& A, const Off& o, int64_t c, const CfgSlots<Cfg>& S,
                                                R (&Tm)[10], R& Nm, R (&Na)[3])
     {
         if constexpr (G == 0) {
             const V2<R> v = rest_pair<Cfg>(ld_fgpair<Cfg>(A.fgin + fg_elem(0, 0, c, A.stride)), A.hs);
-            store_group<0, Cfg>(V4<R>{v.x, v.y, R(0), R(0)}, sp, nth, Tm, Nm, Na);
+            store_group<0, Cfg>(V4<R>{v.x, v.y, R(0), R(0)}, S, Tm, Nm, Na);
         } else {
             const typename Cfg::pop* p = A.fgin + fg_elem(2 * G - 1, 0, c, A.stride);
             auto ld = [&](int a, int d) {
                 const int* oa = a == 0 ? o.x : (a == 1 ? o.y : o.z);
                 return ld_quad<Cfg>(d == 0 ? p : p + 4 * oa[d + 2]);
             };
-            store_group<G, Cfg>(stream_group<G, IS3D, Cfg>(ld, A.k, A.hs), sp, nth, Tm, Nm, Na);
+            store_group<G, Cfg>(stream_group<G, IS3D, Cfg>(ld, A.k, A.hs), S, Tm, Nm, Na);
         }
-        StreamAll<G + 1, IS3D, Cfg>::run(A, o, c, sp, nth, Tm, Nm, Na);
+        StreamAll<G + 1, IS3D, Cfg>::run(A, o, c, S, Tm, Nm, Na);
     }
 };
 template <bool IS3D, class Cfg>
 struct StreamAll<kFGroups + 1, IS3D, Cfg> {
     using R = typename Cfg::real;
-    static __device__ __forceinline__ void run(const StepArgs<Cfg>&, const Off&, int64_t, R*, int, R (&)[10], R&,
-                                               R (&)[3]) {}
+    static __device__ __forceinline__ void run(const StepArgs<Cfg>&, const Off&, int64_t, const CfgSlots<Cfg>&,
+                                               R (&)[10],
+                                               R&, R (&)[3]) {}
 };
 
 // Exact D3Q13 pull h_k(x) = h_c,k(x - hop_k) into slot 38 + k, accumulating
 // E' - Er (before the sqrt(2) c / 2 factor), the plane-normal B - Br sums and
 // rho_c; the pair k = 2m, 2m + 1 hops the same way and arrives in one load.
 template <int K, class R>
-__device__ __forceinline__ void acc_h(R hv, R* sp, int nth, R (&dEp)[3], R (&bn)[3], R& rho)
+__device__ __forceinline__ void acc_h(R hv, R (&dEp)[3], R (&bn)[3], R& rho)
 {
     constexpr int p = K / 8, i = (K % 8) / 2, j = K % 2, ie = (i + 3) % 4;
-    sp[(38 + K) * nth] = hv;
     rho += hv;
     constexpr int se = j == 0 ? 1 : -1;  // e_{i1} = -e_{i0}
     dEp[plane_a1(p)] += R(se * hop_s1(ie)) * hv;
@@ -229,23 +345,25 @@ __device__ __forceinline__ void acc_h(R hv, R* sp, int nth, R (&dEp)[3], R (&bn)
 template <int M, bool IS3D, class Cfg>
 struct PullH {
     using R = typename Cfg::real;
-    static __device__ __forceinline__ void run(const StepArgs<Cfg>& A, const Off& o, int64_t c, R* sp, int nth,
+    static __device__ __forceinline__ void run(const StepArgs<Cfg>& A, const Off& o, int64_t c, const CfgSlots<Cfg>& S,
                                                R (&dEp)[3], R (&bn)[3], R& rho)
     {
         constexpr int K = 2 * M;
         int off = o.x[2 - hop13(K, 0)] + o.y[2 - hop13(K, 1)];
         if (IS3D) off += o.z[2 - hop13(K, 2)];
         const V2<R> hv = ld_hpair<Cfg>(A.hin + h_elem(K, c + off, A.stride));
-        acc_h<K>(hv.x, sp, nth, dEp, bn, rho);
-        acc_h<K + 1>(hv.y, sp, nth, dEp, bn, rho);
-        PullH<M + 1, IS3D, Cfg>::run(A, o, c, sp, nth, dEp, bn, rho);
+        put_pair<R, Cfg::kVecSlots>(S.h(K), S.h(K + 1), hv.x, hv.y);
+        acc_h<K>(hv.x, dEp, bn, rho);
+        acc_h<K + 1>(hv.y, dEp, bn, rho);
+        PullH<M + 1, IS3D, Cfg>::run(A, o, c, S, dEp, bn, rho);
     }
 };
 template <bool IS3D, class Cfg>
 struct PullH<12, IS3D, Cfg> {
     using R = typename Cfg::real;
-    static __device__ __forceinline__ void run(const StepArgs<Cfg>&, const Off&, int64_t, R*, int, R (&)[3], R (&)[3],
-                                               R&) {}
+    static __device__ __forceinline__ void run(const StepArgs<Cfg>&, const Off&, int64_t, const CfgSlots<Cfg>&,
+                                               R (&)[3],
+                                               R (&)[3], R&) {}
 };
 
 // (f_i^eq, g_i^eq) deviations of population I as one float32 pair: the
@@ -274,14 +392,13 @@ __device__ __forceinline__ float2 eq_pair(const EqCell<float>& q)
     return __fmul2_rn(make_float2((float)w19(I), (float)wg19(I)), v);
 }
 
-// post-collision (f_I, g_I) of one cell from the streamed values in the slots
+// post-collision (f_I, g_I) of one cell from the streamed values (fd, gd)
 template <int I, class Cfg>
-__device__ __forceinline__ void collide_fg(const StepArgs<Cfg>& A, const typename Cfg::real* sp, int nth,
+__device__ __forceinline__ void collide_fg(const StepArgs<Cfg>& A, typename Cfg::real fd, typename Cfg::real gd,
                                            const EqCell<typename Cfg::real>& q, typename Cfg::real& fo,
                                            typename Cfg::real& go)
 {
     using R = typename Cfg::real;
-    const R fd = sp[I * nth], gd = sp[(19 + I) * nth];
     const R K = k_aw<I>(q);
     if constexpr (sizeof(R) == 4) {
         // f and g of one direction relax in lock-step: the float32 pair
@@ -303,58 +420,66 @@ __device__ __forceinline__ void collide_fg(const StepArgs<Cfg>& A, const typenam
 template <int G, class Cfg>
 struct CollideFG {
     using R = typename Cfg::real;
-    static __device__ __forceinline__ void run(const StepArgs<Cfg>& A, int64_t c, const R* sp, int nth,
+    static __device__ __forceinline__ void run(const StepArgs<Cfg>& A, int64_t c, const CfgSlots<Cfg>& S,
                                                const EqCell<R>& q)
     {
         if constexpr (G == 0) {
             R fo, go;
-            collide_fg<0, Cfg>(A, sp, nth, q, fo, go);
+            const V2<R> d = get_pair<R, Cfg::kVecSlots>(S.f(0), S.g(0));
+            collide_fg<0, Cfg>(A, d.x, d.y, q, fo, go);
             st_fgpair<Cfg>(A.fgout + fg_elem(0, 0, c, A.stride), fo, go, A.hs.finv[0], A.hs.ginv[0]);
         } else {
             constexpr int I = 2 * G - 1, J = 2 * G;
             V4<R> v;
-            collide_fg<I, Cfg>(A, sp, nth, q, v.x, v.y);
-            collide_fg<J, Cfg>(A, sp, nth, q, v.z, v.w);
+            const V4<R> d = get_group(S, G);
+            collide_fg<I, Cfg>(A, d.x, d.y, q, v.x, v.y);
+            collide_fg<J, Cfg>(A, d.z, d.w, q, v.z, v.w);
             const V4<float> inv = {A.hs.finv[I], A.hs.ginv[I], A.hs.finv[J], A.hs.ginv[J]};
             st_quad<Cfg>(A.fgout + fg_elem(I, 0, c, A.stride), v, inv);
         }
-        CollideFG<G + 1, Cfg>::run(A, c, sp, nth, q);
+        CollideFG<G + 1, Cfg>::run(A, c, S, q);
     }
 };
 template <class Cfg>
 struct CollideFG<kFGroups + 1, Cfg> {
     using R = typename Cfg::real;
-    static __device__ __forceinline__ void run(const StepArgs<Cfg>&, int64_t, const R*, int, const EqCell<R>&) {}
+    static __device__ __forceinline__ void run(const StepArgs<Cfg>&, int64_t, const CfgSlots<Cfg>&, const EqCell<R>&) {}
 };
 
 // Collision of the Maxwell pair (2M, 2M + 1) into cell c of the output buffer.
 template <int M, class Cfg>
 struct CollideH {
     using R = typename Cfg::real;
-    static __device__ __forceinline__ void run(const StepArgs<Cfg>& A, int64_t c, const R* sp, int nth, const R* E,
+    static __device__ __forceinline__ void run(const StepArgs<Cfg>& A, int64_t c, const CfgSlots<Cfg>& S, const R* E,
                                                const R* B, const R* J, bool em_coll)
     {
         constexpr int K = 2 * M;
-        const R h0 = sp[(38 + K) * nth], h1 = sp[(39 + K) * nth];
+        const V2<R> hs = get_pair<R, Cfg::kVecSlots>(S.h(K), S.h(K + 1));
+        const R h0 = hs.x, h1 = hs.y;
         const R v0 = em_coll ? R(2) * heq13<K>(E, B, J, A.k) - h0 : h0;
         const R v1 = em_coll ? R(2) * heq13<K + 1>(E, B, J, A.k) - h1 : h1;
         st_hpair<Cfg>(A.hout + h_elem(K, c, A.stride), v0, v1);
-        CollideH<M + 1, Cfg>::run(A, c, sp, nth, E, B, J, em_coll);
+        CollideH<M + 1, Cfg>::run(A, c, S, E, B, J, em_coll);
     }
 };
 template <class Cfg>
 struct CollideH<12, Cfg> {
     using R = typename Cfg::real;
-    static __device__ __forceinline__ void run(const StepArgs<Cfg>&, int64_t, const R*, int, const R*, const R*,
+    static __device__ __forceinline__ void run(const StepArgs<Cfg>&, int64_t, const CfgSlots<Cfg>&, const R*, const R*,
                                                const R*, bool) {}
 };
 
 constexpr int kStepSlots = 63;  // 19 f + 19 g + 25 h pre-collision values per cell in shared memory
 #ifndef LB_STEP_MIN_BLOCKS
-// resident 128-thread blocks per SM targeted for float32 arithmetic: 4 (128
-// registers, no spills) is 3 % faster than 5 (96 registers) since the
-// self-consistent recovery loop holds more values live
-#define LB_STEP_MIN_BLOCKS 4
+// resident 128-thread blocks per SM targeted for 2-D runs in float32 storage:
+// 5 (at most 102 registers) is 2.4 % faster than 4 with the vector loads,
+// stores and slots, which hold fewer values live
+#define LB_STEP_MIN_BLOCKS 5
+#endif
+#ifndef LB_STEP_MIN_BLOCKS_3D
+// 3-D runs in float32 storage: 4 (128 registers); at 5 the longer stencil
+// spills and the 256^3 flux rope runs 14 % slower
+#define LB_STEP_MIN_BLOCKS_3D 4
 #endif
 #ifndef LB_STEP_BX
 #define LB_STEP_BX 128  // block width along x (the block is LB_STEP_BX x 128 / LB_STEP_BX)
@@ -366,11 +491,12 @@ constexpr int kStepSlots = 63;  // 19 f + 19 g + 25 h pre-collision values per c
 #define LB_STEP_MIN_BLOCKS_MLP 3  // the learned-seed variant: 3 blocks (168 registers) beat 4 by 18 %
 #endif
 // float64: 2 blocks
-template <class Cfg, int SEED>
+template <class Cfg, int SEED, bool IS3D = false>
 struct StepMinBlocks {
     static constexpr int value = sizeof(typename Cfg::real) == 8 ? 2
                                  : SEED == SEED_MLP             ? LB_STEP_MIN_BLOCKS_MLP
                                  : Cfg::kHalf                   ? LB_STEP_MIN_BLOCKS_F16
+                                 : IS3D                         ? LB_STEP_MIN_BLOCKS_3D
                                                                 : LB_STEP_MIN_BLOCKS;
 };
 
@@ -381,20 +507,20 @@ struct StepMinBlocks {
 template <int I, class Cfg>
 struct AddForce {
     using R = typename Cfg::real;
-    static __device__ __forceinline__ void run(R* sp, int nth, const R (&F)[3], R s, R w)
+    static __device__ __forceinline__ void run(const CfgSlots<Cfg>& S, const R (&F)[3], R s, R w)
     {
         constexpr int cx = c19(I, 0), cy = c19(I, 1), cz = c19(I, 2);
         if constexpr (cx == 0 && cy == 0 && cz == 0)
-            sp[I * nth] += w;
+            *S.f(I) += w;
         else
-            sp[I * nth] += s * (R(cx) * F[0] + R(cy) * F[1] + R(cz) * F[2]);
-        AddForce<I + 1, Cfg>::run(sp, nth, F, s, w);
+            *S.f(I) += s * (R(cx) * F[0] + R(cy) * F[1] + R(cz) * F[2]);
+        AddForce<I + 1, Cfg>::run(S, F, s, w);
     }
 };
 template <class Cfg>
 struct AddForce<19, Cfg> {
     using R = typename Cfg::real;
-    static __device__ __forceinline__ void run(R*, int, const R (&)[3], R, R) {}
+    static __device__ __forceinline__ void run(const CfgSlots<Cfg>&, const R (&)[3], R, R) {}
 };
 
 // Relaxed initialisation (reading R27): f and g of the cell at the
@@ -402,17 +528,17 @@ struct AddForce<19, Cfg> {
 template <int I, class Cfg>
 struct SetEqFG {
     using R = typename Cfg::real;
-    static __device__ __forceinline__ void run(R* sp, int nth, const EqCell<R>& q)
+    static __device__ __forceinline__ void run(const CfgSlots<Cfg>& S, const EqCell<R>& q)
     {
-        sp[I * nth] = feq_dev<I>(q);
-        sp[(19 + I) * nth] = geq_dev<I>(q);
-        SetEqFG<I + 1, Cfg>::run(sp, nth, q);
+        *S.f(I) = feq_dev<I>(q);
+        *S.g(I) = geq_dev<I>(q);
+        SetEqFG<I + 1, Cfg>::run(S, q);
     }
 };
 template <class Cfg>
 struct SetEqFG<19, Cfg> {
     using R = typename Cfg::real;
-    static __device__ __forceinline__ void run(R*, int, const EqCell<R>&) {}
+    static __device__ __forceinline__ void run(const CfgSlots<Cfg>&, const EqCell<R>&) {}
 };
 
 // Relaxed initialisation: move the B carried by the streamed h by dB through
@@ -421,17 +547,17 @@ struct SetEqFG<19, Cfg> {
 template <int K, class Cfg>
 struct ShiftHB {
     using R = typename Cfg::real;
-    static __device__ __forceinline__ void run(R* sp, int nth, const R (&dB)[3])
+    static __device__ __forceinline__ void run(const CfgSlots<Cfg>& S, const R (&dB)[3])
     {
         constexpr int p = K / 8, j = K % 2, se = j == 0 ? 1 : -1;
-        sp[(38 + K) * nth] += R(-se * plane_orient(p)) * R(0.125) * dB[plane_normal(p)];
-        ShiftHB<K + 1, Cfg>::run(sp, nth, dB);
+        *S.h(K) += R(-se * plane_orient(p)) * R(0.125) * dB[plane_normal(p)];
+        ShiftHB<K + 1, Cfg>::run(S, dB);
     }
 };
 template <class Cfg>
 struct ShiftHB<24, Cfg> {
     using R = typename Cfg::real;
-    static __device__ __forceinline__ void run(R*, int, const R (&)[3]) {}
+    static __device__ __forceinline__ void run(const CfgSlots<Cfg>&, const R (&)[3]) {}
 };
 
 // warp-wide maximum of a non-negative float64, folded into *dst (atomicMax on
@@ -536,8 +662,9 @@ __device__ __forceinline__ void tile_issue(const TileCtx<Cfg>& t, int g, int x0,
 template <int J, class Cfg>
 struct TileStages {
     using R = typename Cfg::real;
-    static __device__ __forceinline__ bool run(const TileCtx<Cfg>& t, const StepArgs<Cfg>& A, int tid, R* sp, int nth,
-                                               R (&Tm)[10], R& Nm, R (&Na)[3], R (&dEp)[3], R (&bn)[3], R& rho)
+    static __device__ __forceinline__ bool run(const TileCtx<Cfg>& t, const StepArgs<Cfg>& A, int tid,
+                                               const CfgSlots<Cfg>& S, R (&Tm)[10], R& Nm, R (&Na)[3], R (&dEp)[3],
+                                               R (&bn)[3], R& rho)
     {
         using G = TileGeo<Cfg>;
         using pop = typename Cfg::pop;
@@ -554,10 +681,10 @@ struct TileStages {
                 const int cell = (ty + kTileHaloY) * G::BWF + tx + G::PX;
                 if constexpr (J == 0) {
                     const V2<R> v = rest_pair<Cfg>(ld_pair_sh<Cfg>(b + 2 * cell), A.hs);
-                    store_group<0, Cfg>(V4<R>{v.x, v.y, R(0), R(0)}, sp, nth, Tm, Nm, Na);
+                    store_group<0, Cfg>(V4<R>{v.x, v.y, R(0), R(0)}, S, Tm, Nm, Na);
                 } else {
                     auto ld = [&](int a, int d) { return ld_quad_sh<Cfg>(b + 4 * (cell + d * (a == 0 ? 1 : G::BWF))); };
-                    store_group<J, Cfg>(stream_group<J, false, Cfg>(ld, A.k, A.hs), sp, nth, Tm, Nm, Na);
+                    store_group<J, Cfg>(stream_group<J, false, Cfg>(ld, A.k, A.hs), S, Tm, Nm, Na);
                 }
             } else {
                 const float* b = reinterpret_cast<const float*>(buf);
@@ -571,17 +698,18 @@ struct TileStages {
                         const int K = K0 + 2 * d;
                         const int src = d * G::H_PLANE + cell - hop13(K, 1) * G::BWH - hop13(K, 0);
                         const float2 hv = *reinterpret_cast<const float2*>(b + 2 * src);
+                        put_pair<R, Cfg::kVecSlots>(S.h(K), S.h(K + 1), (R)hv.x, (R)hv.y);
                         if (d == 0) {
-                            acc_h<K0>((R)hv.x, sp, nth, dEp, bn, rho);
-                            acc_h<K0 + 1>((R)hv.y, sp, nth, dEp, bn, rho);
+                            acc_h<K0>((R)hv.x, dEp, bn, rho);
+                            acc_h<K0 + 1>((R)hv.y, dEp, bn, rho);
                         } else {
-                            acc_h<K0 + 2>((R)hv.x, sp, nth, dEp, bn, rho);
-                            acc_h<K0 + 3>((R)hv.y, sp, nth, dEp, bn, rho);
+                            acc_h<K0 + 2>((R)hv.x, dEp, bn, rho);
+                            acc_h<K0 + 3>((R)hv.y, dEp, bn, rho);
                         }
                     }
                 } else {
                     const R hv = (R)b[cell];
-                    sp[62 * nth] = hv;
+                    *S.h(24) = hv;
                     rho += hv;
                 }
             }
@@ -605,14 +733,14 @@ struct TileStages {
             else if (t.has_next)
                 tile_issue<Cfg>(t, g + kRingStages, t.nx0, t.ny0, jn - kTileStages);
         }
-        return TileStages<J + 1, Cfg>::run(t, A, tid, sp, nth, Tm, Nm, Na, dEp, bn, rho);
+        return TileStages<J + 1, Cfg>::run(t, A, tid, S, Tm, Nm, Na, dEp, bn, rho);
     }
 };
 template <class Cfg>
 struct TileStages<kTileStages, Cfg> {
     using R = typename Cfg::real;
-    static __device__ __forceinline__ bool run(const TileCtx<Cfg>&, const StepArgs<Cfg>&, int, R*, int, R (&)[10], R&,
-                                               R (&)[3], R (&)[3], R (&)[3], R&)
+    static __device__ __forceinline__ bool run(const TileCtx<Cfg>&, const StepArgs<Cfg>&, int, const CfgSlots<Cfg>&,
+                                               R (&)[10], R&, R (&)[3], R (&)[3], R (&)[3], R&)
     {
         return true;
     }
@@ -632,7 +760,7 @@ __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, 
 {
     constexpr int nth = NTH;  // threads of the block: a compile-time stride of the shared-memory slots
     using R = typename Cfg::real;
-    R* sp = reinterpret_cast<R*>(smem_raw) + tid;
+    const CfgSlots<Cfg> S{reinterpret_cast<R*>(smem_raw), nth, tid};
     const bool active = x < A.nx && y < A.ny;
     if constexpr (SEED != SEED_MLP) {
         if (!active) return;  // no block-wide barrier follows
@@ -668,12 +796,12 @@ __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, 
     R Nm = R(0), Na[3] = {R(0), R(0), R(0)};
     R dEp[3] = {R(0), R(0), R(0)}, bn[3] = {R(0), R(0), R(0)}, rho = R(0);
     if constexpr (TILE) {
-        if (!TileStages<0, Cfg>::run(*tc, A, tid, sp, nth, Tm, Nm, Na, dEp, bn, rho)) return;
+        if (!TileStages<0, Cfg>::run(*tc, A, tid, S, Tm, Nm, Na, dEp, bn, rho)) return;
     } else {
-        StreamAll<0, IS3D, Cfg>::run(A, o, c, sp, nth, Tm, Nm, Na);
-        PullH<0, IS3D, Cfg>::run(A, o, c, sp, nth, dEp, bn, rho);
+        StreamAll<0, IS3D, Cfg>::run(A, o, c, S, Tm, Nm, Na);
+        PullH<0, IS3D, Cfg>::run(A, o, c, S, dEp, bn, rho);
         const R h24 = (R)A.hin[h_elem(24, c, A.stride)];
-        sp[62 * nth] = h24;
+        *S.h(24) = h24;
         rho += h24;
     }
     // previous primitives (the tile path's box has arrived with the last stage)
@@ -712,7 +840,7 @@ __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, 
             const double* fd = A.fdrive + 2 * (xs + (int64_t)A.nx * ys);
             const R F[3] = {(R)fd[0], (R)fd[1], R(0)};
             const R w = (F[0] * old.u[0] + F[1] * old.u[1]) * A.force_dt;
-            AddForce<0, Cfg>::run(sp, nth, F, A.force_cdt, w);
+            AddForce<0, Cfg>::run(S, F, A.force_cdt, w);
             Tm[0] += w;
 #pragma unroll
             for (int a = 0; a < 3; ++a) Tm[a + 1] += R(10) * A.force_cdt * F[a];
@@ -942,7 +1070,7 @@ __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, 
                     nw.B[a] = (R)B0;
                     dB[a] = (R)(B0 - (double)k.Br[a]);
                 }
-                ShiftHB<0, Cfg>::run(sp, nth, dBs);
+                ShiftHB<0, Cfg>::run(S, dBs);
                 ohm_current(nw.E, nw.u, nw.B, nw.rho, k, J);
                 relax_eq = true;
             }
@@ -955,13 +1083,13 @@ __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, 
     for (int a = 0; a < 3; ++a) dE[a] = nw.E[a] - k.Er[a];
     EqCell<R> q;
     eq_cell(nw, n_dev, eps_dev, dE, dB, k, q);
-    if (kOpenCode && relax_eq) SetEqFG<0, Cfg>::run(sp, nth, q);
-    CollideFG<0, Cfg>::run(A, c + dco, sp, nth, q);
+    if (kOpenCode && relax_eq) SetEqFG<0, Cfg>::run(S, q);
+    CollideFG<0, Cfg>::run(A, c + dco, S, q);
     const bool em_coll = (A.flags & FLAG_NO_EM_COLLISION) == 0;
     // h_c - h_ref = 2 h^eq(E - Er, B - Br, J) - (h - h_ref)  (Eq. Maxwell-eq is linear)
     const int64_t co = c + dco;
-    CollideH<0, Cfg>::run(A, co, sp, nth, dE, dB, J, em_coll);
-    const R h24o = em_coll ? R(2) * nw.rho - sp[62 * nth] : sp[62 * nth];
+    CollideH<0, Cfg>::run(A, co, S, dE, dB, J, em_coll);
+    const R h24o = em_coll ? R(2) * nw.rho - *S.h(24) : *S.h(24);
     A.hout[h_elem(24, co, A.stride)] = (typename Cfg::hpop)h24o;
     {
         R pv[NPRIM];
@@ -1009,7 +1137,8 @@ __device__ __forceinline__ void step_cell(const StepArgs<Cfg>& A, int x, int y, 
 
 // one run: a 2-D grid of blocks over (x, y) and z
 template <class Cfg, bool IS3D, int SEED, bool OPEN>
-__global__ void __launch_bounds__(kStepThreads, StepMinBlocks<Cfg, SEED>::value) step_kernel(const StepArgs<Cfg> A)
+__global__ void __launch_bounds__(kStepThreads, StepMinBlocks<Cfg, SEED, IS3D>::value)
+    step_kernel(const StepArgs<Cfg> A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     step_cell<Cfg, IS3D, SEED, OPEN>(A, blockIdx.x * blockDim.x + threadIdx.x,
@@ -1129,7 +1258,7 @@ __host__ __device__ constexpr size_t batch_args_bytes()
 // the arguments of a tile's run from device memory into shared memory when
 // the run changes from its previous tile.
 template <class Cfg, bool IS3D, int SEED, bool OPEN>
-__global__ void __launch_bounds__(kStepThreads, StepMinBlocks<Cfg, SEED>::value)
+__global__ void __launch_bounds__(kStepThreads, StepMinBlocks<Cfg, SEED, IS3D>::value)
     step_batch_kernel(const unsigned char* __restrict__ args, const int4* __restrict__ tiles, int ntiles, int bx)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1191,7 +1320,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* counter, unsigned int
 }
 
 template <class Cfg, bool IS3D, int SEED, bool OPEN>
-__global__ void __launch_bounds__(kStepThreads, StepMinBlocks<Cfg, SEED>::value)
+__global__ void __launch_bounds__(kStepThreads, StepMinBlocks<Cfg, SEED, IS3D>::value)
     step_persistent_kernel(const unsigned char* __restrict__ args, size_t parity_bytes, int in0,
                            const int4* __restrict__ tiles, int ntiles, int bx, int nsteps, unsigned int* counter,
                            int* status, unsigned long long wait_ns)
