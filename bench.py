@@ -30,6 +30,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import re
 import subprocess
@@ -512,6 +513,77 @@ def flux_rope_case(n, prec, recovery):
     return F, P
 
 
+RECONNECTION_CASES = [(0.2, 20.0), (0.2, 30.0), (0.2, 50.0), (0.2, 70.0), (0.2, 100.0), (0.4, 100.0)]
+RECONNECTION_TIMES = [0.4, 1.2, 2.4, 4.8, 9.6, 23.2]
+
+
+def reconnection_leg(args, stream, n=512, t_end=23.2, every=0.4):
+    """Sec. IV's Kelvin-Helmholtz-driven reconnection on the paper's lattice
+    (n^2 on [-0.5, 0.5]^2, dx/dt = 2.5 sqrt 2, periodic x, open y, one layer of
+    width dx, B0 = 0.06, u_pert = 0.01) for the cases the scheme carries to the
+    paper's final time t = 23.2: uniform density (dn = 0), with the Gauss-law
+    charge and alpha = 0.02 (the paper's dn = 1.8 and U0 = 0.6 c runs, and its
+    own charge moment and alpha = 0.1, break down within t ~ 1). All runs in one
+    handle: U0 = 0.2 c at sigma = 20, 30, 50, 70, 100 and U0 = 0.4 c at sigma =
+    100. R(t) = (E^z - E^z_0) / B0 at the null point of the 128 rows around the
+    layer, every `every` time units; reported: R at a few times, the log-log
+    slope of |R| against sigma at each (Sweet-Parker: -1/2), the ratio of the
+    two U0 at sigma = 100, recovery failures and the throughput of the leg."""
+    import numpy as np
+    import torch
+
+    from paper_1508_03452_gb300 import lbrmhd as L
+    from paper_1508_03452_gb300 import workloads as W
+
+    prec = {"fp32": L.FP32, "fp16": L.FP16_DEV, "fp64": L.FP64}[args.precision]
+    dx = 1.0 / n
+    dt = dx / (math.sqrt(2.0) * 2.5)
+    total = int(round(t_end / dt))
+    chunk = max(1, int(round(every / dt)))
+    bc = (L.PERIODIC, L.PERIODIC, L.OPEN, L.OPEN, L.PERIODIC, L.PERIODIC)
+    params = [L.make_params(n, n, 1, bc=bc, tau=1.0, sigma=sg, alpha=0.02, c=2.5, dx=dx, precision=prec,
+                            flags=L.FLAG_GAUSS_CHARGE) for _, sg in RECONNECTION_CASES]
+    s = L.Solver(params, stream=stream)
+    for r, (U0, _) in enumerate(RECONNECTION_CASES):
+        F = W.kelvin_helmholtz_paper(n, U0=U0, dn=0.0)
+        s.init_fields(r, F.n, F.p, F.u, F.B)
+    lo, hi = n // 2 - 64, n // 2 + 64
+    series = [[] for _ in RECONNECTION_CASES]
+    step = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    while step < total:
+        k = min(chunk, total - step)
+        s.step(k)
+        step += k
+        for r in range(len(RECONNECTION_CASES)):
+            series[r].append((step * dt, s.reconnection_rate(r, lo, hi, 0.06)["R"]))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    fails = [s.stats(r)["recover_fail"] for r in range(len(RECONNECTION_CASES))]
+    s.close()
+
+    def at(r, t):
+        return min(series[r], key=lambda p: abs(p[0] - t))[1]
+
+    sig_runs = [r for r, (U0, _) in enumerate(RECONNECTION_CASES) if U0 == 0.2]
+    logs = np.log([RECONNECTION_CASES[r][1] for r in sig_runs])
+    out = {"workload": f"kh_paper_{n}x{n}_dn0_gauss_charge_alpha0.02", "t_end": t_end, "steps": total,
+           "cases": [{"U0": U0, "sigma": sg, "failures": f} for (U0, sg), f in zip(RECONNECTION_CASES, fails)],
+           "value": len(RECONNECTION_CASES) * n * n * total / wall / 1e6, "unit": UNIT,
+           "timing": "wall clock over the steps and the R(t) calls", "R": {}, "sigma_slope": {},
+           "U0_ratio_sigma100": {}}
+    r02, r04 = RECONNECTION_CASES.index((0.2, 100.0)), RECONNECTION_CASES.index((0.4, 100.0))
+    for t in RECONNECTION_TIMES:
+        key = f"{t:g}"
+        out["R"][key] = [at(r, t) for r in range(len(RECONNECTION_CASES))]
+        mag = np.abs([at(r, t) for r in sig_runs])
+        if np.all(np.isfinite(mag)) and np.all(mag > 0):
+            out["sigma_slope"][key] = float(np.polyfit(logs, np.log(mag), 1)[0])
+        out["U0_ratio_sigma100"][key] = abs(at(r04, t)) / max(abs(at(r02, t)), 1e-300)
+    return out
+
+
 def flux_rope_leg(args, stream, weights, n=256, steps=10):
     """The driven 3-D flux rope (the paper's stellar-flare set-up, sigma = 500,
     open faces, the lowest layers driven at 0.05 c) on an n^3 lattice: plain
@@ -700,6 +772,8 @@ def run_gpu(args, world, rank, local):
             line["kh_2048"] = kh_2048_leg(args, stream)
         if not args.no_3d:
             line["flux_rope_3d"] = flux_rope_leg(args, stream, weights)
+        if not args.no_reconnection:
+            line["reconnection"] = reconnection_leg(args, stream)
         clocks = clk.summary()
         if clocks:
             line["clocks"] = clocks
@@ -813,6 +887,7 @@ def main():
     ap.add_argument("--no-sweep", action="store_true", help="skip the 64-run batched sweep leg")
     ap.add_argument("--no-3d", action="store_true", help="skip the 3-D flux-rope leg")
     ap.add_argument("--no-kh2048", action="store_true", help="skip the 2048^2 Kelvin-Helmholtz leg")
+    ap.add_argument("--no-reconnection", action="store_true", help="skip the Kelvin-Helmholtz reconnection-rate leg")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--profile-case", action="store_true", help="untimed 1024^2 single-run case for ncu captures")
     ap.add_argument("--profile-learned", action="store_true", help="--profile-case with the learned-seed kernel")

@@ -45,3 +45,76 @@ def test_paper_kh_readings_fp64():
 def test_paper_kh_gauss_charge_first_order_flux_fp64():
     errs = _pair(64, 200, L.FLAG_GAUSS_CHARGE | L.FLAG_FIRST_ORDER_FLUX, O.GAUSS_CHARGE | O.FIRST_ORDER, 0.02)
     assert max(errs.values()) <= 1e-10, errs
+
+
+def test_reconnection_rate_scales_as_sweet_parker_while_the_initial_sheet_diffuses():
+    """R(t) = (E^z - E^z_0) / B0 at the null point (Sec. IV) on the paper's
+    lattice (512^2, c = 2.5, periodic x, open y, one layer of width dx,
+    B0 = 0.06, U0 = 0.2 c) for sigma = 20, 50, 100 in one handle, with the
+    options that carry these runs to the paper's times (uniform density,
+    Gauss-law charge, alpha = 0.02). While the initial sheet diffuses (t <~ 1)
+    the rate falls with the conductivity as sigma^-1/2, the Sweet-Parker side
+    of the paper's fit (measured slope -0.47 at t = 0.4, -0.44 at t = 1.2). At
+    the paper's t = 23.2 the low-sigma sheets have diffused across the box and
+    the slope turns positive, so the paper's R(23.2) fit is not reproduced;
+    this test holds the part that is."""
+    import math
+    n = 512
+    dx = 1.0 / n
+    dt = dx / (math.sqrt(2.0) * 2.5)
+    sigmas = (20.0, 50.0, 100.0)
+    bc = (L.PERIODIC, L.PERIODIC, L.OPEN, L.OPEN, L.PERIODIC, L.PERIODIC)
+    s = L.Solver([L.make_params(n, n, 1, bc=bc, tau=1.0, sigma=sg, alpha=0.02, c=2.5, dx=dx,
+                                flags=L.FLAG_GAUSS_CHARGE) for sg in sigmas])
+    F = W.kelvin_helmholtz_paper(n, U0=0.2, dn=0.0)
+    for r in range(len(sigmas)):
+        s.init_fields(r, F.n, F.p, F.u, F.B)
+    slopes, done = {}, 0
+    for t in (0.4, 1.2):
+        k = int(round(t / dt)) - done
+        s.step(k)
+        done += k
+        R = [s.reconnection_rate(r, n // 2 - 64, n // 2 + 64, 0.06)["R"] for r in range(len(sigmas))]
+        assert all(np.isfinite(R)) and all(abs(v) > 0 for v in R), R
+        slopes[t] = float(np.polyfit(np.log(sigmas), np.log(np.abs(R)), 1)[0])
+    fails = [s.stats(r)["recover_fail"] for r in range(len(sigmas))]
+    s.close()
+    print("slope of log |R| against log sigma:", slopes, "failures:", fails)
+    assert fails == [0, 0, 0], fails
+    for t, a in slopes.items():
+        assert -0.6 <= a <= -0.35, (t, a)
+
+
+def test_kelvin_helmholtz_mode_grows_faster_with_the_shear():
+    """The instability that is to drive the reconnection (Sec. IV) does develop
+    on the paper's lattice with these options: the k = 2 pi Fourier amplitude of
+    u_y along the layer grows after the initial transient, faster for the
+    larger shear (measured amplitudes at t = 1, 2, 4: 0.0015, 0.0034, 0.0136 at
+    U0 = 0.2 c; 0.0026, 0.0112, 0.099 at U0 = 0.4 c; saturation near t = 8)."""
+    import math
+    n = 512
+    dx = 1.0 / n
+    dt = dx / (math.sqrt(2.0) * 2.5)
+    bc = (L.PERIODIC, L.PERIODIC, L.OPEN, L.OPEN, L.PERIODIC, L.PERIODIC)
+    x = -0.5 + (np.arange(n) + 0.5) * dx
+    amps = {}
+    for U0 in (0.2, 0.4):
+        s = L.Solver(L.make_params(n, n, 1, bc=bc, tau=1.0, sigma=100.0, alpha=0.02, c=2.5, dx=dx,
+                                   flags=L.FLAG_GAUSS_CHARGE))
+        F = W.kelvin_helmholtz_paper(n, U0=U0, dn=0.0)
+        s.init_fields(0, F.n, F.p, F.u, F.B)
+        done, a = 0, []
+        for t in (1.0, 2.0, 4.0):
+            k = int(round(t / dt)) - done
+            s.step(k)
+            done += k
+            uy = s.moments()[4].reshape(n, n)[n // 2 - 20:n // 2 + 20]
+            a.append(float(np.abs((uy * np.exp(-2j * math.pi * x)[None, :]).mean(axis=1)).max() * 2))
+        assert s.stats()["recover_fail"] == 0
+        s.close()
+        amps[U0] = a
+    print("k = 2 pi amplitude of u_y at t = 1, 2, 4:", amps)
+    for U0, (a1, a2, a4) in amps.items():
+        assert a4 > 3.0 * a2 > 3.0 * a1, (U0, amps[U0])
+    growth = {U0: math.log(a[2] / a[0]) / 3.0 for U0, a in amps.items()}
+    assert growth[0.4] > 1.3 * growth[0.2], growth
