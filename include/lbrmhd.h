@@ -89,11 +89,12 @@ extern "C" {
 #define LBRMHD_FLAG_TMA_TILES 16 /* 2-D periodic runs stored in float32 / float16 step by the TMA tile
                                     kernel: persistent blocks stream 32 x 8-cell tiles whose populations and
                                     halo arrive by tensor-map copies through a ring of shared-memory buffers,
-                                    stencil reads from shared memory, outputs by tensor-map stores, plus a
-                                    per-cell launch over the edge tiles. The same update as the default
-                                    per-cell kernel (to float rounding); measured slower on GB300 (the
-                                    block-wide waits per ring stage cost more than the loads they replace), so
-                                    it is an option, not the default. Ignored with LBRMHD_FLAG_GAUSS_CHARGE. */
+                                    stencil reads from shared memory, populations out by the cells' vector
+                                    stores and primitives by a tensor-map store, plus a per-cell launch over
+                                    the edge tiles. The same update as the default per-cell kernel (to float
+                                    rounding); not faster on GB300 (the block-wide waits per ring stage cost
+                                    as much as the vector loads they replace), so it is an option, not the
+                                    default. Ignored with LBRMHD_FLAG_GAUSS_CHARGE. */
 #define LBRMHD_FLAG_FIRST_ORDER_FLUX 32 /* a study option, not the paper's scheme: the fluid face fluxes without
                                            the minmod-limited correction (Sec. III streaming, reading of h_i^a),
                                            i.e. plain first-order upwind, as the limiter gives at a discontinuity */

@@ -328,7 +328,7 @@ struct StreamAll<kFGroups + 1, IS3D, Cfg> {
                                                R&, R (&)[3]) {}
 };
 
-// Exact D3Q13 pull h_k(x) = h_c,k(x - hop_k) into slot 38 + k, accumulating
+// Exact D3Q13 pull h_k(x) = h_c,k(x - hop_k) into its slot, accumulating
 // E' - Er (before the sqrt(2) c / 2 factor), the plane-normal B - Br sums and
 // rho_c; the pair k = 2m, 2m + 1 hops the same way and arrives in one load.
 template <int K, class R>
@@ -1217,9 +1217,9 @@ __global__ void __launch_bounds__(kTileThreads, TileMinBlocks<Cfg, SEED>::value)
         t.gbase = kTileStages * k;
         t.ppar = (uint32_t)(k & 1);
         if (tid == 0) {
-            // the previous tile's output copies have read the slots and the
-            // primitive tile; this tile's first stages are already in flight
-            // (issued as the previous tile's last stages were consumed)
+            // the previous tile's primitive copy-out has read the primitive
+            // tile; this tile's first stages are already in flight (issued as
+            // the previous tile's last stages were consumed)
             if (k > 0) tma_store_wait_read();
             mbar_arrive_expect_tx(&t.bar[kRingStages], G::PRIM_BYTES);
             tma_load_3d(t.pbuf, &M.p_in, 4 * t.x0, t.y0, 0, &t.bar[kRingStages]);
@@ -1233,7 +1233,7 @@ __global__ void __launch_bounds__(kTileThreads, TileMinBlocks<Cfg, SEED>::value)
             if (tid == 0) atomicOr(A.status, STATUS_TMA_TIMEOUT);
             return;
         }
-        fence_proxy_async_smem();  // the output tiles written by every thread, before the copies read them
+        fence_proxy_async_smem();  // the primitive tile written by every thread, before the copy reads it
         __syncthreads();
         if (tid == 0) {
             tma_store_3d(&M.p_out, t.pbuf, 4 * t.x0, t.y0, 0);
