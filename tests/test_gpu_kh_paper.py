@@ -118,3 +118,48 @@ def test_kelvin_helmholtz_mode_grows_faster_with_the_shear():
         assert a4 > 3.0 * a2 > 3.0 * a1, (U0, amps[U0])
     growth = {U0: math.log(a[2] / a[0]) / 3.0 for U0, a in amps.items()}
     assert growth[0.4] > 1.3 * growth[0.2], growth
+
+
+def test_kelvin_helmholtz_growth_matches_the_oracle():
+    """A chaotic run is compared by its statistics beyond the step-by-step
+    horizon: the seeded k = 2 pi mode of u_y grows the same way on the GPU
+    (float64 and float32 builds) as on the oracle, over 905 steps (t = 2) of
+    the paper's set-up at 128^2 (U0 = 0.4 c, uniform density, Gauss-law charge,
+    alpha = 0.02; oracle amplitudes 0.00375 at t = 1, 0.00818 at t = 2)."""
+    import math
+    n = 128
+    dx = 1.0 / n
+    dt = dx / (math.sqrt(2.0) * 2.5)
+    x = -0.5 + (np.arange(n) + 0.5) * dx
+    F = W.kelvin_helmholtz_paper(n, U0=0.4, dn=0.0)
+
+    def amp(m):
+        uy = m[4].reshape(n, n)[n // 2 - 10:n // 2 + 10]
+        return float(np.abs((uy * np.exp(-2j * math.pi * x)[None, :]).mean(axis=1)).max() * 2)
+
+    ref = O.Sim(O.make_params(n, n, 1, bc=(O.PERIODIC, O.PERIODIC, O.OPEN, O.OPEN, O.PERIODIC, O.PERIODIC),
+                              sigma=100.0, alpha=0.02, c=2.5, dx=dx, flags=O.GAUSS_CHARGE, threads=16))
+    ref.init(F.n, F.p, F.u, F.B)
+    runs = {p: L.Solver(L.make_params(n, n, 1, bc=(L.PERIODIC, L.PERIODIC, L.OPEN, L.OPEN, L.PERIODIC, L.PERIODIC),
+                                      sigma=100.0, alpha=0.02, c=2.5, dx=dx, flags=L.FLAG_GAUSS_CHARGE, precision=p))
+            for p in (L.FP64, L.FP32)}
+    for s in runs.values():
+        s.init_fields(0, F.n, F.p, F.u, F.B)
+    done, a = 0, {"oracle": [], L.FP64: [], L.FP32: []}
+    for t in (1.0, 2.0):
+        k = int(round(t / dt)) - done
+        ref.step(k)
+        a["oracle"].append(amp(ref.moments()))
+        for p, s in runs.items():
+            s.step(k)
+            a[p].append(amp(s.moments()))
+        done += k
+    fails = [s.stats()["recover_fail"] for s in runs.values()] + [ref.stats()["recover_fail"]]
+    for s in runs.values():
+        s.close()
+    print("k = 2 pi amplitude of u_y at t = 1, 2:", a)
+    assert fails == [0, 0, 0], fails
+    assert a["oracle"][1] > 1.8 * a["oracle"][0], a
+    for p, tol in ((L.FP64, 1e-6), (L.FP32, 1e-3)):
+        for g, r in zip(a[p], a["oracle"]):
+            assert abs(g - r) <= tol * r, (p, a)
