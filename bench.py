@@ -221,17 +221,46 @@ def _oracle_strip_mlups(seconds: float, threads: int):
     return NX * ny * steps / el / 1e6, steps, el
 
 
+def _oracle_config_mlups(threads: int):
+    """The oracle on the other workloads, bounded: config 1 in full (the 64^2
+    Alfven wave, sigma = 1e6, 500 steps), config 3 on a 2048 x 16 periodic strip
+    of the 2048^2 Kelvin-Helmholtz layers (20 steps), config 5 on a 32^3 flux rope
+    (open faces, driven bottom; 10 steps)."""
+    import oracle as O
+    from paper_1508_03452_gb300 import workloads as W
+
+    out = {}
+    cases = [
+        ("config1_alfven_64x64_full", W.alfven_wave(64, 64, 1), dict(sigma=1e6), 500),
+        ("config3_kh_2048x16_strip",
+         W.kelvin_helmholtz(2048, 16, 1, V=0.3, ratio=10.0, B0=0.1, a=2.0, noise=1e-3, seed=3), dict(sigma=1e3), 20),
+        ("config5_flux_rope_32^3", W.flux_rope(32, 32, 32),
+         dict(sigma=500.0, bc=(O.OPEN,) * 4 + (O.DRIVEN, O.OPEN), drive_u0=0.05, drive_layers=W.drive_layers_for(32)),
+         10),
+    ]
+    for name, F, kw, steps in cases:
+        s = O.Sim(O.make_params(F.nx, F.ny, F.nz, threads=threads, **kw))
+        s.init(F.n, F.p, F.u, F.B)
+        t0 = time.perf_counter()
+        s.step(steps)
+        el = time.perf_counter() - t0
+        out[name] = {"value": F.nx * F.ny * F.nz * steps / el / 1e6, "unit": UNIT, "steps": steps, "seconds": el}
+    return out
+
+
 def cpu_baseline_sample(seconds: float = 12.0, threads: int | None = None):
     """The oracle as it stands on the host cores: the sigma = 100 current sheet,
     full 1024-wide rows, a strip of 32 rows (periodic), stepped for ~`seconds`
-    on all cores, and for a quarter of that on one thread."""
+    on all cores, and for a quarter of that on one thread; bounded samples of
+    the other workloads beside it."""
     threads = threads or os.cpu_count() or 1
     v, steps, el = _oracle_strip_mlups(seconds, threads)
     v1, steps1, el1 = _oracle_strip_mlups(seconds / 4, 1)
     return {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"current sheet sigma=100, {NX}x32 periodic strip of the 1024x1024 workload, {steps} steps, "
                       f"{el:.1f} s, FP64 C oracle with OpenMP",
-            "single_thread": {"value": v1, "unit": UNIT, "steps": steps1, "seconds": el1}}
+            "single_thread": {"value": v1, "unit": UNIT, "steps": steps1, "seconds": el1},
+            "other_workloads": _oracle_config_mlups(threads)}
 
 
 def run_reference(args, world, rank):
