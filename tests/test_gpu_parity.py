@@ -253,9 +253,12 @@ def test_diagnostics_match_oracle_totals():
     assert abs(d[5] - h.sum()) < 1e-11
 
 
-def test_checkpoint_resume_bit_exact():
+@pytest.mark.parametrize("precision", [L.FP32, L.FP16_DEV, L.FP64])
+def test_checkpoint_resume_bit_exact(precision):
+    """Checkpoint / restore of the raw state (the population groups and pairs
+    and the primitive vectors of every storage format) continues bit for bit."""
     F = W.kelvin_helmholtz(48, 40, 1, V=0.3, ratio=3.0, B0=0.1, a=2.0, noise=1e-2, seed=13)
-    P = L.make_params(F.nx, F.ny, 1, sigma=100.0, precision=L.FP32)
+    P = L.make_params(F.nx, F.ny, 1, sigma=100.0, precision=precision)
     a = L.Solver(P)
     a.init_fields(0, F.n, F.p, F.u, F.B)
     a.step(20)
