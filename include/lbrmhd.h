@@ -94,7 +94,8 @@ extern "C" {
                                     the edge tiles. The same update as the default per-cell kernel (to float
                                     rounding); not faster on GB300 (the block-wide waits per ring stage cost
                                     as much as the vector loads they replace), so it is an option, not the
-                                    default. Ignored with LBRMHD_FLAG_GAUSS_CHARGE. */
+                                    default. Ignored with LBRMHD_FLAG_GAUSS_CHARGE and under the BATCH
+                                    and PERSISTENT schedules. */
 #define LBRMHD_FLAG_FIRST_ORDER_FLUX 32 /* a study option, not the paper's scheme: the fluid face fluxes without
                                            the minmod-limited correction (Sec. III streaming, reading of h_i^a),
                                            i.e. plain first-order upwind, as the limiter gives at a discontinuity */
@@ -136,10 +137,12 @@ typedef struct lbrmhd_state_s* lbrmhd_handle;
 
 /* Creates n_runs independent runs (params[0..n_runs-1]; grids may differ) and
  * allocates their device state: per run two copies (read / write) of the 19 +
- * 19 + 25 populations and 12 primitive fields per cell. Errors: BAD_ARG for
- * any invalid parameter (grid < 1, c, dx or tau <= 0, sigma < 0, gamma_ad <=
- * 1, DRIVEN on a face other than -z, precision mixed across runs), OOM, CUDA
- * (no usable GPU). On failure *out is NULL. */
+ * 19 + 25 populations and 12 primitive fields per cell (element offsets in 64
+ * bits; a run may hold up to 2^29 cells, the range of the step kernel's 32-bit
+ * stencil offsets). Errors: BAD_ARG for any invalid parameter (grid < 1 or
+ * above 2^29 cells, c, dx or tau <= 0, sigma < 0, gamma_ad <= 1, DRIVEN on a
+ * face other than -z, precision mixed across runs), OOM, CUDA (no usable
+ * GPU). On failure *out is NULL. */
 int lbrmhd_create(const lbrmhd_params* params, int n_runs, lbrmhd_handle* out);
 
 /* Frees all device memory of the handle. A NULL handle is ignored. */
@@ -326,11 +329,16 @@ typedef struct lbrmhd_schedule {
 } lbrmhd_schedule;
 
 /* Sets the schedule. Default (never set): PER_RUN, 1 stream, no graph.
- * Errors: BAD_ARG. */
+ * The per-run launch covers grids with ny <= 65535 and nz <= 65535 (CUDA's
+ * limit on a launch grid's y and z extents); a PER_RUN schedule of a handle
+ * holding a taller run steps every run through the tile list instead (BATCH,
+ * bx 128, waves 1, order 0, the graph_steps set), and lbrmhd_get_schedule
+ * returns the schedule in effect. Errors: BAD_ARG. */
 int lbrmhd_set_schedule(lbrmhd_handle h, const lbrmhd_schedule* sched);
 int lbrmhd_get_schedule(lbrmhd_handle h, lbrmhd_schedule* sched);
 
-/* Autotuner: times PER_RUN on 1, 4 and up to 16 streams, every BATCH
+/* Autotuner: times PER_RUN on 1, 4 and up to 16 streams (when the per-run
+ * launch covers every run), every BATCH
  * combination of bx {128, 64, 32}, waves {0, 1}, order {0, 1}, and (where the
  * runs admit it) PERSISTENT with bx {128, 64, 32}, order {0, 1}, one step per
  * launch, on the handle's current state with `trials` dry

@@ -418,7 +418,28 @@ lb::StepArgs<Cfg> make_args(lbrmhd_handle h, const RunState& r, int in)
     return A;
 }
 
-lbrmhd_schedule effective_schedule(lbrmhd_handle h) { return h->sched; }
+// whether the per-run launch covers run r: its grid is (nx / bx) x (ny x bx / 128)
+// x nz blocks with bx <= 128, and a grid's y and z extents are limited to 65535
+bool per_run_launchable(const RunState& r) { return r.p.ny <= 65535 && r.p.nz <= 65535; }
+
+// the schedule the steps run with: the one set, except that a PER_RUN schedule
+// of a handle with a run the per-run launch cannot cover walks the tile list
+// (BATCH, 128-wide tiles, one wave of resident blocks) for every run
+lbrmhd_schedule effective_schedule(lbrmhd_handle h)
+{
+    lbrmhd_schedule s = h->sched;
+    if (s.kind != LBRMHD_SCHED_PER_RUN) return s;
+    for (const auto& r : h->runs)
+        if (!per_run_launchable(r)) {
+            s.kind = LBRMHD_SCHED_BATCH;
+            s.bx = 128;
+            s.waves = 1;
+            s.order = 0;
+            s.streams = 1;
+            break;
+        }
+    return s;
+}
 
 // tile list of the batched schedule, grouped by kernel variant (2-D / 3-D,
 // recovery seed); within a group tiles follow the runs in order (order 0) or
@@ -799,7 +820,9 @@ int init_common(lbrmhd_handle h, int run, const double* n, const double* p, cons
 std::string check_params(const lbrmhd_params& p)
 {
     if (p.nx < 1 || p.ny < 1 || p.nz < 1) return "grid sizes must be >= 1";
-    if ((int64_t)p.nx * p.ny * p.nz > ((int64_t)1 << 34)) return "grid too large";
+    // the step kernel forms its stencil offsets (up to the periodic wrap, ~N
+    // cells) in 32 bits and scales them by the 4-wide population groups
+    if ((int64_t)p.nx * p.ny * p.nz > ((int64_t)1 << 29)) return "grid too large (more than 2^29 cells)";
     if (!(p.c > 0) || !(p.dx > 0) || !(p.tau > 0)) return "c, dx and tau must be > 0";
     if (!(p.sigma >= 0)) return "sigma must be >= 0";
     if (!(p.gamma_ad > 1)) return "gamma_ad must be > 1";
@@ -940,9 +963,13 @@ int autotune(lbrmhd_handle h, int trials, lbrmhd_schedule* best_out, double* bes
     if (!(cache && *cache && cache_lookup(cache, sig, &best, &best_ms))) {
         std::vector<lbrmhd_schedule> cand;
         const int nr = (int)h->runs.size();
-        cand.push_back({LBRMHD_SCHED_PER_RUN, 128, 0, 0, 1, 0});
-        if (nr > 1) cand.push_back({LBRMHD_SCHED_PER_RUN, 128, 0, 0, std::min(nr, 4), 0});
-        if (nr > 4) cand.push_back({LBRMHD_SCHED_PER_RUN, 128, 0, 0, std::min(nr, 16), 0});
+        bool per_run = true;
+        for (const auto& r : h->runs) per_run = per_run && per_run_launchable(r);
+        if (per_run) {
+            cand.push_back({LBRMHD_SCHED_PER_RUN, 128, 0, 0, 1, 0});
+            if (nr > 1) cand.push_back({LBRMHD_SCHED_PER_RUN, 128, 0, 0, std::min(nr, 4), 0});
+            if (nr > 4) cand.push_back({LBRMHD_SCHED_PER_RUN, 128, 0, 0, std::min(nr, 16), 0});
+        }
         for (int bx : {128, 64, 32})
             for (int waves : {0, 1})
                 for (int order : {0, 1})
@@ -1418,12 +1445,13 @@ int lbrmhd_get_status(lbrmhd_handle h, int64_t* out3)
     LB_CK(cudaMemcpyAsync(&status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     LB_CK(cudaStreamSynchronize(h->stream));
     int64_t fails = 0, tiled = 0;
+    const bool per_run = effective_schedule(h).kind == LBRMHD_SCHED_PER_RUN;  // the tile kernel's only schedule
     for (const auto& r : h->runs) {
         unsigned long long s[lb::kNumStats];
         const int rc = read_stats(h, r, s);
         if (rc) return rc;
         fails += (int64_t)s[0];
-        tiled += !r.tmaps.empty() && (r.p.flags & LBRMHD_FLAG_TMA_TILES) != 0 &&
+        tiled += per_run && !r.tmaps.empty() && (r.p.flags & LBRMHD_FLAG_TMA_TILES) != 0 &&
                          (r.p.flags & LBRMHD_FLAG_GAUSS_CHARGE) == 0
                      ? 1
                      : 0;

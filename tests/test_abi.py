@@ -73,6 +73,11 @@ def test_bad_parameters_are_rejected():
     with pytest.raises(L.LbrmhdError) as e:
         L.Solver(L.make_params(8, 4, 4, bc=(L.OPEN, L.PERIODIC, 0, 0, 0, 0)))
     assert e.value.code == L.ERR_BAD_ARG
+    # above 2^29 cells the step kernel's 32-bit stencil offsets (x4 per group vector) would overflow
+    with pytest.raises(L.LbrmhdError) as e:
+        L.Solver(L.make_params(32768, 16385, 1))
+    assert e.value.code == L.ERR_BAD_ARG
+    assert "2^29" in str(e.value)
     # the photospheric body force: needs forced layers, replaces the DRIVEN
     # face, finite values; unknown flags are refused
     for kw in (dict(drive_f0=0.05, drive_layers=0), dict(drive_f0=0.05, drive_layers=2,
@@ -94,6 +99,9 @@ def test_valid_options_pass_validation():
         with pytest.raises(L.LbrmhdError) as e:
             L.Solver(L.make_params(8, 8, 8, **kw))
         assert e.value.code == L.ERR_CUDA, kw
+    with pytest.raises(L.LbrmhdError) as e:  # the largest grid (2^29 cells)
+        L.Solver(L.make_params(32768, 16384, 1))
+    assert e.value.code == L.ERR_CUDA
     lib = L.load()
     assert lib.lbrmhd_init_fields_relaxed(None, 0, None, None, None, None, 10, 1e-6, None, None) == L.ERR_BAD_ARG
 
