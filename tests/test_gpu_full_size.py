@@ -1,0 +1,108 @@
+"""Parity at the full sizes of the Kelvin-Helmholtz and flux-rope workloads, in
+the launch configuration the benchmark times them in (one run per handle, the
+default per-run schedule):
+
+* Kelvin-Helmholtz shear layers on the full 2048 x 2048 lattice (V = 0.3 c,
+  density ratio 10, B0 = 0.1, sigma = 1e3, seeded noise 1e-3): the 13 steps the
+  benchmark runs (3 warm-up + 10 timed), every cell against the FP64 oracle.
+  FP64 within 1e-10 on every group; FP32 within 1e-5 on every group but E,
+  the small-signal group of the KH layers (E_z = u_y B_x of the 1e-3 noise),
+  whose error is printed (2.6e-5 against the FP64 GPU build in the benchmark).
+* the driven 3-D flux rope on the full 256^3 lattice (sigma = 500, open faces,
+  the lowest layers driven at 0.05 c), float32: three GPU steps, then one step
+  of 400 sampled interior cells checked against the oracle's update of the same
+  (GPU) state, every group within 1e-5.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1508_03452_gb300 import lbrmhd as L
+from paper_1508_03452_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+KH_N, KH_STEPS = 2048, 13
+
+
+def _kh_fields():
+    return W.kelvin_helmholtz(KH_N, KH_N, 1, V=0.3, ratio=10.0, B0=0.1, a=2.0, noise=1e-3, seed=3)
+
+
+@functools.lru_cache(maxsize=1)
+def _kh_oracle_moments():
+    F = _kh_fields()
+    ref = O.Sim(O.make_params(KH_N, KH_N, 1, sigma=1e3, threads=16))
+    ref.init(F.n, F.p, F.u, F.B)
+    ref.step(KH_STEPS)
+    return ref.moments()
+
+
+@pytest.mark.parametrize("precision", [L.FP64, L.FP32])
+def test_full_size_kelvin_helmholtz_2048(precision):
+    from test_gpu_parity import assert_parity, rel_errors
+
+    F = _kh_fields()
+    s = L.Solver(L.make_params(KH_N, KH_N, 1, sigma=1e3, precision=precision))
+    try:
+        s.init_fields(0, F.n, F.p, F.u, F.B)
+        s.step(KH_STEPS)
+        st = s.status()
+        mg = s.moments()
+    finally:
+        s.close()
+    assert st["rc"] == L.OK and st["recover_fail"] == 0, st
+    errs = rel_errors(mg, _kh_oracle_moments())
+    print("KH 2048^2", "FP64" if precision == L.FP64 else "FP32", errs)
+    if precision == L.FP64:
+        assert_parity(errs, 1e-10)
+    else:
+        assert_parity(errs, 1e-5, skip=("E",))
+
+
+def test_full_size_flux_rope_256_sampled_step_fp32():
+    from test_gpu_parity import assert_parity
+
+    n, sigma, u0 = 256, 500.0, 0.05
+    layers = W.drive_layers_for(n)
+    F = W.flux_rope(n, n, n)
+    bc = (L.OPEN,) * 4 + (L.DRIVEN, L.OPEN)
+    s = L.Solver(L.make_params(n, n, n, bc=bc, sigma=sigma, drive_u0=u0, drive_layers=layers, precision=L.FP32))
+    try:
+        s.init_fields(0, F.n, F.p, F.u, F.B)
+        s.step(3)
+        fc, gc, hc = s.populations()
+        m = s.moments()
+        prim = np.zeros((O.NPRIM, F.N))
+        prim[O.N_] = m[0]
+        prim[O.EPS_] = m[2]
+        prim[O.U_:O.U_ + 3] = m[3:6]
+        prim[O.E_:O.E_ + 3] = m[6:9]
+        prim[O.B_:O.B_ + 3] = m[9:12]
+        prim[O.RHOC_] = m[12]
+        prim[O.J_:O.J_ + 3] = m[13:16]
+        del m
+        # interior cells: two cells from every open face, above the driven layers
+        rng = np.random.default_rng(71)
+        x, y = rng.integers(2, n - 2, 400), rng.integers(2, n - 2, 400)
+        z = rng.integers(layers + 2, n - 2, 400)
+        cells = np.unique(x + n * (y + n * z))
+        obc = (O.OPEN,) * 4 + (O.DRIVEN, O.OPEN)
+        ref = O.Sim(O.make_params(n, n, n, bc=obc, sigma=sigma, drive_u0=u0, drive_layers=layers, threads=16))
+        _, _, _, pr = ref.update_cells_from(fc, gc, hc, prim, cells)
+        del fc, gc, hc, prim, ref
+        s.step(1)
+        st = s.status()
+        m1 = s.moments()[:, cells]
+    finally:
+        s.close()
+    assert st["rc"] == L.OK and st["recover_fail"] == 0, st
+    errs = {}
+    for name, rows, orows in (("n", [0], [O.N_]), ("eps", [2], [O.EPS_]), ("u", [3, 4, 5], [2, 3, 4]),
+                              ("E", [6, 7, 8], [5, 6, 7]), ("B", [9, 10, 11], [8, 9, 10])):
+        a, b = m1[rows], pr[:, orows].T
+        errs[name] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    print("flux rope 256^3 sampled step", errs)
+    assert_parity(errs, 1e-5)
