@@ -1,15 +1,21 @@
-"""Parity at the full sizes of the Kelvin-Helmholtz and flux-rope workloads, in
-the launch configuration the benchmark times them in (one run per handle, the
-default per-run schedule):
+"""Parity at the full sizes of the Kelvin-Helmholtz, batched-sweep and
+flux-rope workloads, in launch configurations the benchmark times them in:
 
 * Kelvin-Helmholtz shear layers on the full 2048 x 2048 lattice (V = 0.3 c,
-  density ratio 10, B0 = 0.1, sigma = 1e3, seeded noise 1e-3): the 13 steps the
+  density ratio 10, B0 = 0.1, sigma = 1e3, seeded noise 1e-3), one run per
+  handle on the default per-run schedule: the 13 steps the
   benchmark runs (3 warm-up + 10 timed), every cell against the FP64 oracle.
   FP64 within 1e-10 on every group; FP32 within 1e-5 on every group but E,
   the small-signal group of the KH layers (E_z = u_y B_x of the 1e-3 noise),
   whose error is printed (2.6e-5 against the FP64 GPU build in the benchmark).
+* the batched sweep in full: 64 Kelvin-Helmholtz runs of uneven grids (sides
+  256..1024, sigma, V and density ratio drawn as the workload draws them) in
+  one handle with the Gauss-law charge and alpha = 0.02, stepped 3 times per
+  run and 10 times in one persistent launch; every run free of recovery
+  failures, and eight of them (every eighth) against the oracle over every
+  cell: FP32 within 1e-5 on every group but the KH small-signal E.
 * the driven 3-D flux rope on the full 256^3 lattice (sigma = 500, open faces,
-  the lowest layers driven at 0.05 c), float32: three GPU steps, then one step
+  the lowest layers driven at 0.05 c), float32, one run per handle: three GPU steps, then one step
   of 400 sampled interior cells checked against the oracle's update of the same
   (GPU) state, every group within 1e-5.
 """
@@ -106,3 +112,35 @@ def test_full_size_flux_rope_256_sampled_step_fp32():
         errs[name] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
     print("flux rope 256^3 sampled step", errs)
     assert_parity(errs, 1e-5)
+
+
+def test_full_size_batched_sweep_fp32_persistent():
+    from test_gpu_parity import assert_parity, rel_errors
+
+    specs = W.kh_sweep(64)
+    s = L.Solver([L.make_params(sp.nx, sp.ny, 1, sigma=sp.sigma, precision=L.FP32, alpha=0.02,
+                                flags=L.FLAG_GAUSS_CHARGE) for sp in specs])
+    fields = lambda sp: W.kelvin_helmholtz(sp.nx, sp.ny, 1, V=sp.V, ratio=sp.ratio, B0=0.1, noise=1e-3, seed=sp.seed)
+    checked = list(range(0, len(specs), 8))
+    try:
+        for r, sp in enumerate(specs):
+            F = fields(sp)
+            s.init_fields(r, F.n, F.p, F.u, F.B)
+        s.step(3)
+        s.set_schedule(L.make_schedule(L.SCHED_PERSISTENT, 128, 1, 0, 1, 0))
+        s.step(10)
+        st = s.status()
+        fails = [s.stats(r)["recover_fail"] for r in range(len(specs))]
+        mg = {r: s.moments(r) for r in checked}
+    finally:
+        s.close()
+    assert st["rc"] == L.OK and sum(fails) == 0, (st, fails)
+    for r in checked:
+        sp = specs[r]
+        F = fields(sp)
+        ref = O.Sim(O.make_params(sp.nx, sp.ny, 1, sigma=sp.sigma, alpha=0.02, flags=O.GAUSS_CHARGE, threads=16))
+        ref.init(F.n, F.p, F.u, F.B)
+        ref.step(13)
+        errs = rel_errors(mg[r], ref.moments())
+        print("sweep run", r, sp, errs)
+        assert_parity(errs, 1e-5, skip=("E",))
