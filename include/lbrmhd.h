@@ -283,8 +283,10 @@ int lbrmhd_get_status(lbrmhd_handle h, int64_t* out3);
 int lbrmhd_get_iteration_histogram(lbrmhd_handle h, int run, int64_t* out);
 
 /* Checkpoint / resume: the raw device state of every run (populations and
- * primitives in their storage format, plus step counters). Resuming from a
- * checkpoint is bit-exact. `bytes` must be lbrmhd_state_bytes(). */
+ * primitives in their storage format, plus step counters) after a tag naming
+ * the storage layout and precision. Resuming from a checkpoint is bit-exact.
+ * `bytes` must be lbrmhd_state_bytes(); lbrmhd_set_state refuses (BAD_ARG) a
+ * blob whose tag differs (another layout or precision). */
 int lbrmhd_state_bytes(lbrmhd_handle h, size_t* bytes);
 int lbrmhd_get_state(lbrmhd_handle h, void* host_buf, size_t bytes);
 int lbrmhd_set_state(lbrmhd_handle h, const void* host_buf, size_t bytes);

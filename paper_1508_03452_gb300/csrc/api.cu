@@ -1494,13 +1494,19 @@ int lbrmhd_get_iteration_histogram(lbrmhd_handle h, int run, int64_t* out)
     return LBRMHD_OK;
 }
 
-// checkpoint blob: per run [int64 steps][NMEANS double reference means][uint64 stats x kNumStats]
-// [pops 38 N][h 25 N][prim 12 N][initial E^z N] (storage format)
+// checkpoint blob: [uint64 layout tag] then per run [int64 steps][NMEANS double
+// reference means][uint64 stats x kNumStats][pops 38 N][h 25 N][prim 12 N]
+// [initial E^z N] (storage format). The tag names the storage layout (fluid
+// groups as 4-vectors, Maxwell pairs as 2-vectors, primitive 4-vectors) and the
+// precision; a blob of another layout is refused.
+constexpr uint64_t kStateLayoutTag = 0x4c42524d48440200ull;  // "LBRMHD", layout 2, low byte = precision
+uint64_t state_tag(int precision) { return kStateLayoutTag | (uint64_t)(precision & 0xff); }
+
 int lbrmhd_state_bytes(lbrmhd_handle h, size_t* bytes)
 {
     if (!h || !bytes) return LBRMHD_ERR_BAD_ARG;
     const size_t pb = pop_bytes(h->precision), hb = hp_bytes(h->precision);
-    size_t total = 0;
+    size_t total = 8;
     for (auto& r : h->runs)
         total += 8 + 8 * lb::NMEANS + kStatsBytes + (size_t)r.N * (38 * pb + 25 * hb + (lb::NPRIM + 1) * hb);
     *bytes = total;
@@ -1515,6 +1521,9 @@ int lbrmhd_get_state(lbrmhd_handle h, void* host_buf, size_t bytes)
     LB_CK(cudaSetDevice(h->device));
     const size_t pb = pop_bytes(h->precision), hb = hp_bytes(h->precision);
     char* o = (char*)host_buf;
+    const uint64_t tag = state_tag(h->precision);
+    std::memcpy(o, &tag, 8);
+    o += 8;
     for (auto& r : h->runs) {
         if (!r.initialized) return fail(h, LBRMHD_ERR_STATE, "run not initialised");
         std::memcpy(o, &r.steps, 8);
@@ -1554,6 +1563,11 @@ int lbrmhd_set_state(lbrmhd_handle h, const void* host_buf, size_t bytes)
     LB_CK(cudaSetDevice(h->device));
     const size_t pb = pop_bytes(h->precision), hb = hp_bytes(h->precision);
     const char* o = (const char*)host_buf;
+    uint64_t tag = 0;
+    std::memcpy(&tag, o, 8);
+    if (tag != state_tag(h->precision))
+        return fail(h, LBRMHD_ERR_BAD_ARG, "checkpoint of another storage layout or precision");
+    o += 8;
     for (auto& r : h->runs) {
         std::memcpy(&r.steps, o, 8);
         o += 8;

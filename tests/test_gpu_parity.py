@@ -261,7 +261,8 @@ def test_diagnostics_match_oracle_totals():
 @pytest.mark.parametrize("precision", [L.FP32, L.FP16_DEV, L.FP64])
 def test_checkpoint_resume_bit_exact(precision):
     """Checkpoint / restore of the raw state (the population groups and pairs
-    and the primitive vectors of every storage format) continues bit for bit."""
+    and the primitive vectors of every storage format) continues bit for bit;
+    a blob whose layout tag differs is refused."""
     F = W.kelvin_helmholtz(48, 40, 1, V=0.3, ratio=3.0, B0=0.1, a=2.0, noise=1e-2, seed=13)
     P = L.make_params(F.nx, F.ny, 1, sigma=100.0, precision=precision)
     a = L.Solver(P)
@@ -272,6 +273,11 @@ def test_checkpoint_resume_bit_exact(precision):
     b.step(9)
     blob = b.get_state()
     c = L.Solver(P)
+    bad = bytearray(blob)
+    bad[1] ^= 0x01  # the layout tag in front of the state
+    with pytest.raises(L.LbrmhdError) as e:
+        c.set_state(bytes(bad))
+    assert e.value.code == L.ERR_BAD_ARG
     c.set_state(blob)
     c.step(11)
     assert np.array_equal(a.moments(), c.moments())
