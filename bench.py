@@ -86,12 +86,16 @@ def code_only(src: str) -> str:
 
 
 def kernel_sha() -> str:
-    """Identity of the step kernel's code (comments excluded), which the
-    committed ncu summary records beside the counters it took."""
+    """Identity of the step kernel's code (comments excluded) and of the nvcc
+    flags it is compiled with (include paths excluded), which the committed
+    ncu summary records beside the counters it took."""
+    from paper_1508_03452_gb300 import build as B
+
     h = hashlib.sha256()
     for name in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_1508_03452_gb300", "csrc", name)) as f:
             h.update(code_only(f.read()).encode())
+    h.update(" ".join(B.ARCH + [f for f in B.NVCC_FLAGS if not f.startswith("-I")]).encode())
     return h.hexdigest()[:16]
 
 
